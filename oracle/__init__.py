@@ -1,0 +1,293 @@
+"""FP64 CPU oracle of the w-stacking imaging path (ctypes wrapper).
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA library
+never imports it and shares no code, header or table with it.
+
+The C source ``rick_oracle.c`` states which passage of arXiv 2601.19714 each
+function follows (Eq. 1 direct inversion, Eq. 2 w-stacking, Eq. 3 gridding)
+and the readings R1-R7 it fixes where the paper is silent.  This wrapper only
+marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rick_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+
+GAUSS, KAISER_BESSEL, LEARNED = 0, 1, 2
+_KINDS = {"gauss": GAUSS, "kb": KAISER_BESSEL, "kaiser_bessel": KAISER_BESSEL, "learned": LEARNED}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, no FMA contraction) if needed."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("N", C.c_int32), ("Nw", C.c_int32), ("S", C.c_int32), ("kernel", C.c_int32),
+                ("kernel_param", C.c_double), ("fov", C.c_double), ("w_min", C.c_double),
+                ("w_max", C.c_double), ("mlp", C.POINTER(C.c_double)),
+                ("mlp_hidden", C.c_int32), ("mlp_lattice", C.c_int32)]
+
+
+@dataclass
+class Config:
+    """Imaging parameters in the paper's notation (Sec. 2): mesh side N,
+    number of w-planes Nw, kernel support S, field of view, w range."""
+    N: int
+    Nw: int
+    S: int
+    kernel: str
+    kernel_param: float
+    fov: float
+    w_min: float
+    w_max: float
+    mlp: np.ndarray | None = None
+    mlp_hidden: int = 64
+    mlp_lattice: int = 0
+    _keep: list = field(default_factory=list, repr=False)
+
+    def c(self) -> _Cfg:
+        cfg = _Cfg(self.N, self.Nw, self.S, _KINDS[self.kernel], self.kernel_param, self.fov,
+                   self.w_min, self.w_max, None, self.mlp_hidden, self.mlp_lattice)
+        if self.mlp is not None:
+            arr = np.ascontiguousarray(self.mlp, dtype=np.float64)
+            self._keep = [arr]
+            cfg.mlp = arr.ctypes.data_as(C.POINTER(C.c_double))
+        return cfg
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+def _declare(L):
+    d, i32, i64, p = C.c_double, C.c_int32, C.c_long, C.c_void_p
+    cfgp = C.POINTER(_Cfg)
+    L.oracle_bessel_i0.restype = d
+    L.oracle_bessel_i0.argtypes = [d]
+    L.oracle_kernel_value.restype = d
+    L.oracle_kernel_value.argtypes = [C.c_int, d, C.c_int, d]
+    L.oracle_gauss_legendre.argtypes = [C.c_int, p, p]
+    L.oracle_taper.argtypes = [C.c_int, d, C.c_int, C.c_int, p]
+    L.oracle_ifft2.restype = C.c_int
+    L.oracle_ifft2.argtypes = [C.c_int, p]
+    L.oracle_gelu.restype = d
+    L.oracle_gelu.argtypes = [d]
+    L.oracle_gelu_grad.restype = d
+    L.oracle_gelu_grad.argtypes = [d]
+    L.oracle_mlp_param_count.restype = C.c_size_t
+    L.oracle_mlp_param_count.argtypes = [C.c_int]
+    L.oracle_mlp_forward.argtypes = [p, C.c_int, p, p, p, p]
+    L.oracle_mlp_backward.argtypes = [p, C.c_int, p, p, p]
+    L.oracle_plane_w.restype = d
+    L.oracle_plane_w.argtypes = [cfgp, C.c_int]
+    vis_args = [cfgp, p, p, C.c_int, p, p, p, i64]
+    L.oracle_place.argtypes = [cfgp, p, p, C.c_int, p, p, i64, p, p, p, p, p, p]
+    L.oracle_grid_plane.restype = i64
+    L.oracle_grid_plane.argtypes = vis_args + [C.c_int, C.c_int, p]
+    L.oracle_channel_stats.argtypes = [cfgp, p, p, C.c_int, p, p, i64, C.c_int, p, p, p]
+    L.oracle_image.restype = C.c_int
+    L.oracle_image.argtypes = vis_args + [C.c_int, p, p]
+    L.oracle_image_at.restype = C.c_int
+    L.oracle_image_at.argtypes = vis_args + [C.c_int, C.c_int, i64, p, p, p]
+    L.oracle_dft_at.restype = C.c_int
+    L.oracle_dft_at.argtypes = vis_args + [C.c_int, i64, p, p, p]
+    del i32
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class _Vis:
+    """Contiguous copies of one set of visibilities in the oracle's layout."""
+
+    def __init__(self, uvw, chan_scale, vis, weight, flag):
+        self.uvw = np.ascontiguousarray(uvw, dtype=np.float64).reshape(-1, 3)
+        self.scale = np.ascontiguousarray(chan_scale, dtype=np.float64).reshape(-1)
+        self.C = self.scale.shape[0]
+        self.nrow = self.uvw.shape[0]
+        v = np.ascontiguousarray(vis, dtype=np.complex64).reshape(self.nrow, self.C)
+        self.vis = v.view(np.float32)
+        self.weight = np.ascontiguousarray(weight, dtype=np.float32).reshape(self.nrow, self.C)
+        self.flag = (None if flag is None else
+                     np.ascontiguousarray(flag, dtype=np.uint8).reshape(self.nrow, self.C))
+
+    def args(self):
+        return [_ptr(self.uvw), _ptr(self.scale), self.C, _ptr(self.vis), _ptr(self.weight),
+                _ptr(self.flag), self.nrow]
+
+
+# --------------------------------------------------------------------- #
+# kernel functions, quadrature, FFT                                       #
+# --------------------------------------------------------------------- #
+
+def bessel_i0(x: float) -> float:
+    return lib().oracle_bessel_i0(float(x))
+
+
+def kernel_value(kind: str, param: float, S: int, s: float) -> float:
+    return lib().oracle_kernel_value(_KINDS[kind], float(param), int(S), float(s))
+
+
+def gauss_legendre(n: int):
+    x = np.zeros(n)
+    w = np.zeros(n)
+    lib().oracle_gauss_legendre(n, _ptr(x), _ptr(w))
+    return x, w
+
+
+def taper(kind: str, param: float, S: int, N: int) -> np.ndarray:
+    out = np.zeros(N)
+    lib().oracle_taper(_KINDS[kind], float(param), int(S), int(N), _ptr(out))
+    return out
+
+
+def ifft2(a: np.ndarray) -> np.ndarray:
+    """Unnormalised inverse 2-D DFT (exponent +) of a square power-of-two array."""
+    out = np.ascontiguousarray(a, dtype=np.complex128).copy()
+    if lib().oracle_ifft2(out.shape[0], _ptr(out)) != 0:
+        raise ValueError("oracle_ifft2: N must be a power of two")
+    return out
+
+
+def gelu(x: float) -> float:
+    return lib().oracle_gelu(float(x))
+
+
+def gelu_grad(x: float) -> float:
+    return lib().oracle_gelu_grad(float(x))
+
+
+def mlp_param_count(H: int) -> int:
+    return int(lib().oracle_mlp_param_count(H))
+
+
+def mlp_forward(params: np.ndarray, H: int, inp) -> np.ndarray:
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inp, dtype=np.float64)
+    out = np.zeros(16)
+    lib().oracle_mlp_forward(_ptr(prm), H, _ptr(x), _ptr(out), None, None)
+    return out
+
+
+def mlp_backward(params: np.ndarray, H: int, inp, gout) -> np.ndarray:
+    prm = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(inp, dtype=np.float64)
+    g = np.ascontiguousarray(gout, dtype=np.float64)
+    grad = np.zeros_like(prm)
+    lib().oracle_mlp_backward(_ptr(prm), H, _ptr(x), _ptr(g), _ptr(grad))
+    return grad
+
+
+# --------------------------------------------------------------------- #
+# the imaging path                                                        #
+# --------------------------------------------------------------------- #
+
+def plane_w(cfg: Config, k: int) -> float:
+    c = cfg.c()
+    return lib().oracle_plane_w(C.byref(c), k)
+
+
+def place(cfg: Config, uvw, chan_scale, weight, flag=None):
+    """Per-visibility placement: status, plane k, footprint start (i0, j0),
+    fractional offsets (fx, fy); arrays shaped [nrow, C]."""
+    v = _Vis(uvw, chan_scale, np.zeros((len(uvw), len(np.atleast_1d(chan_scale))), np.complex64),
+             weight, flag)
+    shape = (v.nrow, v.C)
+    st, k, i0, j0 = (np.zeros(shape, np.int32) for _ in range(4))
+    fx, fy = np.zeros(shape), np.zeros(shape)
+    c = cfg.c()
+    lib().oracle_place(C.byref(c), _ptr(v.uvw), _ptr(v.scale), v.C, _ptr(v.weight), _ptr(v.flag),
+                       v.nrow, _ptr(st), _ptr(k), _ptr(i0), _ptr(j0), _ptr(fx), _ptr(fy))
+    return dict(status=st, k=k, i0=i0, j0=j0, fx=fx, fy=fy)
+
+
+def channel_stats(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0):
+    v = _Vis(uvw, chan_scale, np.zeros((len(uvw), len(np.atleast_1d(chan_scale))), np.complex64),
+             weight, flag)
+    ws = C.c_double()
+    ng, nd = C.c_long(), C.c_long()
+    c = cfg.c()
+    lib().oracle_channel_stats(C.byref(c), _ptr(v.uvw), _ptr(v.scale), v.C, _ptr(v.weight),
+                               _ptr(v.flag), v.nrow, channel, C.byref(ws), C.byref(ng),
+                               C.byref(nd))
+    return ws.value, ng.value, nd.value
+
+
+def grid_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, plane=0):
+    """Gridded plane ``plane`` of channel ``channel`` (Eq. 3), complex128 [N, N]."""
+    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    out = np.zeros((cfg.N, cfg.N), np.complex128)
+    c = cfg.c()
+    n = lib().oracle_grid_plane(C.byref(c), *v.args(), channel, plane, _ptr(out))
+    if n < 0:
+        raise ValueError("oracle_grid_plane: invalid configuration")
+    return out
+
+
+def image(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0):
+    """Complex w-stacking dirty image of one channel (O1), complex128 [N, N]
+    indexed [q, p] (m row, l column), and the channel's sum of weights."""
+    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    out = np.zeros((cfg.N, cfg.N), np.complex128)
+    ws = C.c_double()
+    c = cfg.c()
+    rc = lib().oracle_image(C.byref(c), *v.args(), channel, _ptr(out), C.byref(ws))
+    if rc != 0:
+        raise ValueError(f"oracle_image failed ({rc})")
+    return out, ws.value
+
+
+def image_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=(), q=(),
+             plane=-1):
+    """O1 at pixels (p, q) evaluated visibility by visibility (no FFT).  With
+    ``plane >= 0``: the transformed plane F_plane[q, p] before the phase screen."""
+    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    pp = np.ascontiguousarray(p, dtype=np.int32)
+    qq = np.ascontiguousarray(q, dtype=np.int32)
+    out = np.zeros(pp.shape[0], np.complex128)
+    c = cfg.c()
+    rc = lib().oracle_image_at(C.byref(c), *v.args(), channel, plane, pp.shape[0], _ptr(pp),
+                               _ptr(qq), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_image_at failed ({rc})")
+    return out
+
+
+def dft_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=(), q=()):
+    """O2: direct Fourier inversion of Eq. 1 at pixels (p, q), complex."""
+    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    pp = np.ascontiguousarray(p, dtype=np.int32)
+    qq = np.ascontiguousarray(q, dtype=np.int32)
+    out = np.zeros(pp.shape[0], np.complex128)
+    c = cfg.c()
+    rc = lib().oracle_dft_at(C.byref(c), *v.args(), channel, pp.shape[0], _ptr(pp), _ptr(qq),
+                             _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_dft_at failed ({rc})")
+    return out
