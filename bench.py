@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the w-stacking hot path on GB300.
+
+One step = the whole path over one batch: rick_bin + rick_grid_binned
+(placement, binning and gridding of every visibility of every channel onto
+its w-plane), rick_fft_wplanes (every plane), rick_phase_correct_reduce
+(phase screen + sum over planes into the dirty images).  Inputs are resident
+in HBM when the timed region starts; `e2e` repeats the measurement through
+rick_dirty_image_host, with the host->device copy of the inputs and the
+device->host copy of the images inside the timed region.
+
+Workload (default): the MeerKAT-shaped configuration -- 64 antennas, 2016
+baselines x 1000 steps x 16 channels (856-1712 MHz) = 32.3 M visibilities,
+5 % flagged, 200 point sources, 4096^2 grid, 32 w-planes, Kaiser-Bessel S = 8,
+FoV 1.5 deg.  Synthetic, seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("gridded visibilities/sec and achieved HBM GB/s at 1 GB300; "
+          "image error vs FP64 oracle")
+UNIT = "vis/s"
+
+
+# --------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def make_workload(seed: int, device: str):
+    from visgen.workloads import meerkat
+    img, obs = meerkat(seed, device=device)
+    return img, obs
+
+
+def plan_config(img, nchan):
+    from paper_2601_19714_gb300 import rick
+    return rick.Config(N=img.N, n_wplanes=img.Nw, support=img.S, n_channels=nchan,
+                       fov_rad=img.fov, w_min=img.w_min, w_max=img.w_max, kernel="kb",
+                       kernel_param=img.kernel_param)
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample
+# --------------------------------------------------------------------------
+
+def oracle_sample(img, obs, n_planes: int, reps: int = 1):
+    """Time oracle.image() on the visibilities of channel 0 that fall on
+    n_planes middle w-planes (so that it grids, transforms and phase-corrects
+    exactly that many planes).  Returns (vis/s, n_vis, seconds, description)."""
+    import oracle
+    cfg = oracle.Config(img.N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov, img.w_min,
+                        img.w_max)
+    vis = obs.vis.cpu().numpy() if hasattr(obs.vis, "cpu") else obs.vis
+    one = np.ones(1)
+    uvw0 = obs.uvw * obs.chan_scale[0]
+    pl = oracle.place(cfg, uvw0, one, obs.weight[:, :1], None if obs.flag is None else obs.flag[:, :1])
+    k0 = img.Nw // 2 - n_planes // 2
+    sel = (pl["status"][:, 0] == 1) & (pl["k"][:, 0] >= k0) & (pl["k"][:, 0] < k0 + n_planes)
+    u, v, w = uvw0[sel], np.ascontiguousarray(vis[sel, :1]), np.ascontiguousarray(obs.weight[sel, :1])
+    secs = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        oracle.image(cfg, u, one, v, w)
+        secs.append(time.perf_counter() - t)
+    n = int(sel.sum())
+    s = min(secs)
+    desc = (f"channel 0, the {n} visibilities on w-planes {k0}..{k0 + n_planes - 1} of "
+            f"{img.Nw} (oracle grids, FFTs and phase-corrects those {n_planes} planes of "
+            f"{img.N}^2), FP64, 1 thread")
+    return n / s, n, s, desc
+
+
+def image_error_probe(img, obs, image_ch0: np.ndarray, n_pix: int = 8):
+    """Oracle O1 (per-visibility form) at probe pixels of channel 0 vs the
+    GPU image: max|delta|/peak over the probes."""
+    import oracle
+    cfg = oracle.Config(img.N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov, img.w_min,
+                        img.w_max)
+    N = img.N
+    dl = img.fov / N
+    src = obs.sources
+    order = np.argsort(-src[:, 2])[: n_pix - 1]
+    p = np.clip(np.rint(src[order, 0] / dl + N // 2), 0, N - 1).astype(np.int32)
+    q = np.clip(np.rint(src[order, 1] / dl + N // 2), 0, N - 1).astype(np.int32)
+    p = np.append(p, N // 2).astype(np.int32)
+    q = np.append(q, N // 2).astype(np.int32)
+    vis = obs.vis.cpu().numpy() if hasattr(obs.vis, "cpu") else obs.vis
+    ref = oracle.image_at(cfg, obs.uvw, obs.chan_scale, vis, obs.weight, obs.flag, channel=0,
+                          p=p, q=q).real
+    got = image_ch0[q, p]
+    return float(np.abs(got - ref).max() / np.abs(ref).max()), int(len(p))
+
+
+# --------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------
+
+def run_reference(args):
+    """The oracle as it stands, timed on this host: each step images a
+    bounded sample (one w-plane's visibilities of channel 0)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    img, obs = make_workload(args.seed, "cuda" if torch.cuda.is_available() else "cpu")
+    obs.vis = obs.vis.cpu().numpy()
+    for _ in range(args.warmup):
+        oracle_sample(img, obs, 1)
+    rates, nv, secs = [], 0, 0.0
+    desc = ""
+    for _ in range(args.steps):
+        r, nv, s, desc = oracle_sample(img, obs, 1)
+        rates.append(r)
+        secs += s
+    value = statistics.median(rates)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "meerkat_4096sq_32w_16ch_kb8", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_19714_gb300 import rick
+    from paper_2601_19714_gb300 import _build
+    _build.build()
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    img, obs = make_workload(args.seed + rank, "cuda")
+    C = obs.nchan
+    N, Nw = img.N, img.Nw
+    dev = dict(uvw=torch.from_numpy(obs.uvw).cuda(), chan_scale=torch.from_numpy(obs.chan_scale).cuda(),
+               vis=obs.vis, weight=torch.from_numpy(obs.weight).cuda(),
+               flag=torch.from_numpy(obs.flag).cuda())
+    nrow = obs.nrow
+    plan = rick.Plan(plan_config(img, C))
+    plan.reserve(nrow)
+    grids = torch.empty((C, Nw, N, N), dtype=torch.complex64, device="cuda")
+    image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    wsum = torch.empty(C, dtype=torch.float64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    ev = {k: [] for k in ("t0", "t1", "t2", "t3", "t4")}
+
+    def step(record=False):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        image.zero_()
+        if e: e[0].record(stream)
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], nrow,
+                 wsum, counts)
+        if e: e[1].record(stream)
+        plan.grid_binned(0, C, 0, Nw, grids)
+        if e: e[2].record(stream)
+        plan.fft_wplanes(grids, C * Nw)
+        if e: e[3].record(stream)
+        plan.phase_correct_reduce(grids, 0, C, 0, Nw, wsum, image)
+        if e: e[4].record(stream)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_grid, n_drop = counts.cpu().tolist()
+
+    launches0 = plan.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_events = []
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(args.steps):
+            stage_events.append(step(record=True))
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = plan.launch_count() - launches0
+    ms = start.elapsed_time(stop) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    stage_ms = {"bin": [], "grid": [], "fft": [], "phase": []}
+    for e in stage_events:
+        stage_ms["bin"].append(e[0].elapsed_time(e[1]))
+        stage_ms["grid"].append(e[1].elapsed_time(e[2]))
+        stage_ms["fft"].append(e[2].elapsed_time(e[3]))
+        stage_ms["phase"].append(e[3].elapsed_time(e[4]))
+    st = {k: statistics.median(v) for k, v in stage_ms.items()}
+
+    hbm, peak_kind = peaks()
+    NN = N * N
+    cells = C * Nw * NN
+    b_grid = 8.0 * cells + 16.0 * n_grid                  # write every cell once + read each record
+    b_fft = 2 * 8.0 * cells                               # one read + one write per plane (minimum)
+    b_phase = 8.0 * cells + 8.0 * C * NN                  # read planes + image read/write
+    b_bin = (24.0 * nrow + C * nrow * (8 + 4 + 1)         # inputs
+             + C * nrow * (4 + 4 + 16) * 2 + 16.0 * n_grid)  # key/rank/stage write+read, records
+    gbs = {k: b / (st[k] * 1e-3) / 1e9 for k, b in
+           (("bin", b_bin), ("grid", b_grid), ("fft", b_fft), ("phase", b_phase))}
+    dominant = max(st, key=st.get)
+    dom_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase}[dominant]
+
+    # ---- end to end through the host entry point -------------------------------
+    del grids
+    torch.cuda.empty_cache()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_uvw, h_sc = pin(obs.uvw), pin(obs.chan_scale)
+    h_vis = obs.vis.cpu().pin_memory()
+    h_w, h_f = pin(obs.weight), pin(obs.flag)
+    h_img = torch.empty((C, N, N), dtype=torch.float32).pin_memory()
+    h_ws = torch.empty(C, dtype=torch.float64).pin_memory()
+    h_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
+    eplan = rick.Plan(plan_config(img, C))
+
+    def e2e_step():
+        eplan.dirty_image_host(h_uvw, h_sc, h_vis, h_w, h_f, h_img, h_ws, h_cnt)
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        e2e_step()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    te = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_ms = float(te.item())
+    h2d = (h_uvw.numel() * 8 + h_sc.numel() * 8 + h_vis.numel() * 8 + h_w.numel() * 4 +
+           h_f.numel())
+    d2h = h_img.numel() * 4 + h_ws.numel() * 8 + 16
+    img_ch0 = image[0].cpu().numpy()
+    del eplan
+
+    if rank == 0:
+        units = n_grid * world
+        line = {
+            "metric": METRIC, "value": units / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "meerkat_4096sq_32w_16ch_kb8", "antennas": 64,
+                       "baselines": 2016, "time_steps": 1000, "channels": C,
+                       "visibilities": int(nrow * C), "gridded": int(n_grid),
+                       "dropped": int(n_drop), "N": N, "w_planes": Nw, "support": img.S,
+                       "kernel": "kaiser_bessel", "index_phase": "fp64", "fov_deg": round(math.degrees(img.fov), 4),
+                       "tile": plan.cfg.tile or 64,
+                       "l2": "inputs larger than L2 (grids 68.7 GB, not flushed)",
+                       "parallelism": f"replicas x{world} (seed per rank)"},
+            "stages_ms": st,
+            "stage_gbs": gbs,
+            "gridder_vis_per_s": n_grid / (st["grid"] * 1e-3),
+            "bin_plus_grid_vis_per_s": n_grid / ((st["bin"] + st["grid"]) * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": dominant,
+                         "achieved": dom_bytes / (st[dominant] * 1e-3) / 1e9,
+                         "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": dom_bytes / (st[dominant] * 1e-3) / 1e9 / hbm,
+                         "traffic": None},
+            "roofline_grid": {"bound": "hbm", "achieved": gbs["grid"], "peak": hbm,
+                              "unit": "GB/s", "frac": gbs["grid"] / hbm},
+            "roofline_phase": {"bound": "hbm", "achieved": gbs["phase"], "peak": hbm,
+                               "unit": "GB/s", "frac": gbs["phase"] / hbm},
+            "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            r, nv, s, desc = oracle_sample(img, obs, 2)
+            line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": desc, "seconds": s}
+            err, npix = image_error_probe(img, obs, img_ch0)
+            line["image_error"] = {"max_rel_vs_fp64_oracle": err, "probe_pixels": npix,
+                                   "channel": 0, "how": "oracle O1 per-visibility form"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * rick.h -- C ABI of librick, a single-GPU (sm_103a) w-stacking imager.
+ *
+ * The library computes the hot path of the w-stacking method of
+ * arXiv 2601.19714 ("Accelerating radio astronomy imaging with RICK"):
+ *   1. rick_grid:  convolutional gridding of visibilities onto the closest
+ *                  of Nw w-planes (Sec. 2, Eq. 3; the binning of visibilities
+ *                  into tiles is the GPU form of the bucket sort of Sec. 3.2,
+ *                  with tile halos in the role of the ghost regions of Eq. 5);
+ *   2. rick_fft_wplanes: a 2-D inverse FFT of every w-plane (Sec. 2, Sec. 3.4);
+ *   3. rick_phase_correct_reduce: the w phase screen exp(+2 pi i w_k (n-1))
+ *                  applied to each transformed plane and the sum over planes
+ *                  (Eq. 2), normalised by the sum of weights (natural
+ *                  weighting, Sec. 4.1.1) and by the gridding taper.
+ *
+ * Conventions shared by every call (the readings of the paper they fix are
+ * listed in the repository's design notes):
+ *   - u, v, w are in wavelengths at a reference frequency, stored [nrow][3]
+ *     (FP64).  Channel c scales them by chan_scale[c] = nu_c / nu_ref.
+ *   - Visibilities are complex64 interleaved (re, im), [nrow][C][2] floats;
+ *     weights float32 [nrow][C]; flags uint8 [nrow][C] (non-zero = flagged)
+ *     or NULL.  A visibility is skipped if flagged or if its weight is zero
+ *     or not finite, and dropped (counted) if its support leaves the grid.
+ *   - Grid cell i holds u = (i - N/2)/fov; a visibility at x = u fov + N/2
+ *     covers the S cells x - S/2 < i <= x + S/2.  Plane k covers
+ *     w in [w_min + k dw, w_min + (k+1) dw), dw = (w_max - w_min)/Nw, with
+ *     k = floor((w - w_min) * (Nw/(w_max - w_min))) clamped to [0, Nw-1];
+ *     its phase screen uses w_k = w_min + (k + 1/2) dw.
+ *   - Grids are complex64 [planes][N][N] (row = v cell, column = u cell),
+ *     stored with the checkerboard sign (-1)^(i+j) that centres the FFT.
+ *   - Images are float32 [C][N][N] (row q = m, column p = l), pixel p at
+ *     l = (p - N/2) fov/N.  Images ACCUMULATE (+=) so that plane groups can
+ *     be streamed; the caller zeroes them once.
+ *   - Unless a call says otherwise, array pointers are DEVICE pointers owned
+ *     by the caller; the plan owns only its tables and scratch.  Calls are
+ *     asynchronous and ordered on the given stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).
+ *   - Every call returns a rick_status; RICK_OK = 0.  No C++ exception
+ *     crosses the ABI.  rick_last_error() gives a message for the calling
+ *     thread.  Errors found by a kernel (there are none by design; the
+ *     status word exists for internal consistency checks) are reported by
+ *     rick_plan_sync_status().
+ *   - A plan may be used from one host thread at a time.
+ */
+#ifndef RICK_H
+#define RICK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RICK_OK = 0,
+    RICK_ERR_INVALID_ARG = 1, /* a size, pointer or configuration value is invalid */
+    RICK_ERR_OOM = 2,         /* device or host allocation failed */
+    RICK_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    RICK_ERR_CUFFT = 4,       /* cuFFT plan creation or execution failed */
+    RICK_ERR_TIMEOUT = 5,     /* reserved: a bounded device-side wait expired */
+    RICK_ERR_UNSUPPORTED = 6, /* valid, but outside what this build supports */
+    RICK_ERR_INTERNAL = 7,    /* a device-side consistency check failed */
+    RICK_ERR_CAPACITY = 8     /* more visibilities than the plan's reservation */
+} rick_status;
+
+typedef enum {
+    RICK_KERNEL_GAUSS = 0,          /* exp(-s^2/(2 sigma^2)), kernel_param = sigma in cells */
+    RICK_KERNEL_KAISER_BESSEL = 1,  /* I0(beta sqrt(1-(2s/S)^2))/I0(beta), kernel_param = beta */
+    RICK_KERNEL_TABLE = 2           /* learned support-4 taps from rick_set_kernel_table;
+                                       kernel_param = beta of the support-4 Kaiser-Bessel
+                                       whose taper divides the image */
+} rick_kernel_kind;
+
+typedef enum {
+    RICK_PREC_FP32_FP64IDX = 0, /* FP64 uvw->cell index and phase; FP32 accumulation (default) */
+    RICK_PREC_ALL_FP32 = 1      /* index and phase in FP32 as well (precision study) */
+} rick_precision;
+
+typedef struct rick_config {
+    int32_t N;            /* grid side = image side: power of two, 64..65536 */
+    int32_t n_wplanes;    /* Nw >= 1 */
+    int32_t support;      /* S: 1..16 (4 for RICK_KERNEL_TABLE), S <= tile */
+    int32_t n_channels;   /* C >= 1 */
+    double fov_rad;       /* field of view, direction cosines, 0 < fov < 1 */
+    double w_min, w_max;  /* w range of the planes, wavelengths; w_max > w_min if Nw > 1 */
+    double kernel_param;  /* see rick_kernel_kind */
+    int32_t kernel_kind;  /* rick_kernel_kind */
+    int32_t precision;    /* rick_precision */
+    int32_t tile;         /* gridder tile side T: 32, 64 or 128 (0 = 64); T <= N */
+    int32_t grid_threads; /* gridder CTA size: 128, 256 or 512 (0 = 256) */
+    int32_t fft_batch;    /* planes per cuFFT execution (0 = up to 4 GiB of planes) */
+    int32_t reserved;     /* must be 0 */
+    int64_t grid_budget_bytes; /* rick_dirty_image: device bytes for plane groups (0 = all) */
+} rick_config;
+
+typedef struct rick_plan rick_plan;
+
+/* ---- plan ------------------------------------------------------------ */
+
+/* Validate cfg, build the kernel and taper tables (FP64 on the host) and the
+ * cuFFT plans.  The current CUDA device is the plan's device.  On failure
+ * *out is NULL and nothing is leaked. */
+rick_status rick_plan_create(const rick_config* cfg, rick_plan** out);
+
+/* Release the plan and everything it owns.  NULL is accepted. */
+rick_status rick_plan_destroy(rick_plan* plan);
+
+/* Pre-allocate binning scratch for up to max_rows rows (all channels), so
+ * that later calls with nrow <= max_rows allocate nothing; required before a
+ * sequence of calls is captured into a CUDA graph.  Without it, rick_bin
+ * grows the scratch on demand (synchronously). */
+rick_status rick_plan_reserve(rick_plan* plan, int64_t max_rows);
+
+/* The taper C(p), p = 0..N-1, that rick_phase_correct_reduce divides by:
+ * C(p) = integral_{-S/2}^{S/2} g(s) cos(2 pi s (p - N/2)/N) ds.  Host out. */
+rick_status rick_plan_taper(const rick_plan* plan, double* taper_host);
+
+/* Learned kernel: taps[Nw][L+1][L+1][16] (device, float32, copied into the
+ * plan) on an (L+1)x(L+1) lattice of fractional offsets (dx, dy) in [0,1]^2
+ * per w-plane; tap t = 4b + a weighs footprint cell (i0 + a, j0 + b).  The
+ * gridder interpolates bilinearly between lattice points.  Only for plans
+ * with kernel_kind = RICK_KERNEL_TABLE; 1 <= L <= 256. */
+rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t lattice, void* stream);
+
+/* ---- the hot path ---------------------------------------------------- */
+
+/* Place and bin: for every visibility compute, in FP64 (FP32 under
+ * RICK_PREC_ALL_FP32), its footprint start, fractional offset and w-plane,
+ * then counting-sort the visibilities by (channel, plane, tile, halo class)
+ * into plan scratch.  weight_sum[C] (device, out) receives the sum of the
+ * weights of the gridded visibilities of each channel; counts[2] (device,
+ * out, nullable) receives (gridded, dropped).  nrow * C < 2^32 - 1. */
+rick_status rick_bin(rick_plan* plan, const double* uvw, const double* chan_scale,
+                     const float* vis, const float* weight, const uint8_t* flag, int64_t nrow,
+                     double* weight_sum, int64_t* counts, void* stream);
+
+/* Grid the binned visibilities of channels [chan_begin, chan_end) onto
+ * planes [plane_begin, plane_end) (Eq. 3).  grids is
+ * [chan_end-chan_begin][plane_end-plane_begin][N][N] complex64; every cell
+ * of it is written (cells no visibility touches are written as zero), so it
+ * need not be cleared.  Requires a preceding rick_bin on the same plan. */
+rick_status rick_grid_binned(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
+                             int32_t plane_begin, int32_t plane_end, float* grids, void* stream);
+
+/* rick_bin followed by rick_grid_binned for all channels and planes
+ * [plane_begin, plane_end). */
+rick_status rick_grid(rick_plan* plan, const double* uvw, const double* chan_scale,
+                      const float* vis, const float* weight, const uint8_t* flag, int64_t nrow,
+                      int32_t plane_begin, int32_t plane_end, float* grids, double* weight_sum,
+                      int64_t* counts, void* stream);
+
+/* In place, unnormalised 2-D inverse FFT (exponent +) of n_planes
+ * consecutive N x N complex64 planes (cuFFT, batched). */
+rick_status rick_fft_wplanes(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
+
+/* Phase screen and reduction over planes (Eq. 2): for channels
+ * [chan_begin, chan_end) and transformed planes [plane_begin, plane_end)
+ * (grids laid out as for rick_grid_binned),
+ *   image[c][q][p] += (-1)^(p+q) n / (weight_sum[c] C(p) C(q))
+ *                     * Re sum_k F_k[q][p] exp(+2 pi i w_k (n - 1)),
+ * n = sqrt(1 - l^2 - m^2).  The phase is formed in FP64 per pixel (fixed
+ * point per plane).  weight_sum is indexed by absolute channel.
+ * image_real is [chan_end-chan_begin][N][N]; image_complex (nullable) the
+ * same shape complex64 and receives the value before Re. */
+rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
+                                      int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                      const double* weight_sum, float* image_real,
+                                      float* image_complex, void* stream);
+
+/* The whole path on device buffers: bin, then for each group of channels and
+ * planes that fits grid_budget_bytes grid, transform and reduce into
+ * image_real[C][N][N] (+=) using plan-owned grid memory.  weight_sum[C] and
+ * counts[2] as for rick_bin (both nullable). */
+rick_status rick_dirty_image(rick_plan* plan, const double* uvw, const double* chan_scale,
+                             const float* vis, const float* weight, const uint8_t* flag,
+                             int64_t nrow, float* image_real, float* image_complex,
+                             double* weight_sum, int64_t* counts, void* stream);
+
+/* As rick_dirty_image, but every pointer is a HOST pointer: the inputs are
+ * copied to plan-owned device memory, the image (overwritten, not
+ * accumulated) and weight_sum/counts (nullable) are copied back, and the
+ * call returns when they are in host memory.  Page-locked host buffers give
+ * the fastest copies. */
+rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const double* chan_scale,
+                                  const float* vis, const float* weight, const uint8_t* flag,
+                                  int64_t nrow, float* image_real, double* weight_sum,
+                                  int64_t* counts, void* stream);
+
+/* ---- introspection --------------------------------------------------- */
+
+/* Synchronise the plan's last stream and report device-side errors. */
+rick_status rick_plan_sync_status(rick_plan* plan);
+
+/* Number of this library's kernels the plan has launched so far. */
+int64_t rick_plan_launch_count(const rick_plan* plan);
+
+/* Copy the binning result of the last rick_bin to host memory, for tests:
+ * offsets[n_keys + 1] (uint32, start of every (channel, plane, tile, class)
+ * bin) and records[n_records][4] (uint32: W*V re and im as float bits, then
+ * the packed x and y: first footprint cell relative to the tile in the top 8
+ * bits, fractional offset * 2^24 in the low 24).  Pass NULL to query the
+ * sizes only.  Synchronous. */
+rick_status rick_plan_bins(rick_plan* plan, int64_t* n_keys, int64_t* n_records,
+                           uint32_t* offsets, uint32_t* records);
+
+const char* rick_status_string(rick_status status);
+const char* rick_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RICK_H */

@@ -1,0 +1,766 @@
+// rick_api.cu -- the C ABI of librick: plans, validation, scratch, cuFFT,
+// and the host-side sequencing of the w-stacking path.
+//
+// Everything here is host code; the kernels live in rick_bin.cu (placement
+// and binning), rick_grid.cu (gridding, Eq. 3) and rick_phase.cu (phase
+// screen and reduction, Eq. 2).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rick_internal.cuh"
+
+using namespace rick;
+
+namespace {
+
+thread_local char g_err[1024] = "";
+
+void set_err(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+#define RK_CUDA(expr)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_err("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__,    \
+                    __LINE__);                                                            \
+            return e_ == cudaErrorMemoryAllocation ? RICK_ERR_OOM : RICK_ERR_CUDA;        \
+        }                                                                                 \
+    } while (0)
+
+#define RK_TRY(expr)                          \
+    do {                                      \
+        rick_status s_ = (expr);              \
+        if (s_ != RICK_OK) return s_;         \
+    } while (0)
+
+#define RK_ARG(cond, msg)                     \
+    do {                                      \
+        if (!(cond)) {                        \
+            set_err("invalid argument: %s", msg); \
+            return RICK_ERR_INVALID_ARG;      \
+        }                                     \
+    } while (0)
+
+// ---- FP64 host math for the tables (independent of any other code) -------
+
+double bessel_i0(double x) {
+    // I0(x) = sum_k (x^2/4)^k / (k!)^2
+    const double y = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 400 && term > 1e-17 * sum; ++k) {
+        term *= y / ((double)k * k);
+        sum += term;
+    }
+    return sum;
+}
+
+double kernel_fn(int kind, double param, int S, double s) {
+    if (std::fabs(s) > 0.5 * S) return 0.0;
+    if (kind == RICK_KERNEL_GAUSS) return std::exp(-0.5 * s * s / (param * param));
+    const double t = 2.0 * s / S;
+    return bessel_i0(param * std::sqrt(std::fmax(0.0, 1.0 - t * t))) / bessel_i0(param);
+}
+
+// n-point Gauss-Legendre rule on [-1, 1] (Newton iteration on P_n).
+void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = std::cos(pi * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double pm = 1.0, pc = z;
+            for (int k = 2; k <= n; ++k) {
+                const double pn = ((2 * k - 1) * z * pc - (k - 1) * pm) / k;
+                pm = pc;
+                pc = pn;
+            }
+            dp = n * (z * pc - pm) / (z * z - 1.0);
+            const double dz = pc / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// C(p) = int_{-S/2}^{S/2} g(s) cos(2 pi s (p - N/2)/N) ds: the continuous
+// Fourier transform of the kernel at pixel p, by composite Gauss-Legendre
+// quadrature (24 nodes per cell of the support).  C is even about N/2.
+void make_taper(int kind, double param, int S, int N, std::vector<double>& C) {
+    std::vector<double> gx, gw;
+    legendre_rule(24, gx, gw);
+    std::vector<double> s, wg;
+    for (int seg = 0; seg < S; ++seg) {
+        const double a = -0.5 * S + seg;
+        for (size_t i = 0; i < gx.size(); ++i) {
+            const double si = a + 0.5 + 0.5 * gx[i];
+            s.push_back(si);
+            wg.push_back(0.5 * gw[i] * kernel_fn(kind, param, S, si));
+        }
+    }
+    const double two_pi = 6.283185307179586476925;
+    std::vector<double> val(N / 2 + 1);
+    for (int d = 0; d <= N / 2; ++d) {
+        double acc = 0.0;
+        for (size_t i = 0; i < s.size(); ++i) acc += wg[i] * std::cos(two_pi * s[i] * d / N);
+        val[d] = acc;
+    }
+    C.assign(N, 0.0);
+    for (int p = 0; p < N; ++p) C[p] = val[p >= N / 2 ? p - N / 2 : N / 2 - p];
+}
+
+}  // namespace
+
+struct rick_plan {
+    rick_config cfg;
+    int device = 0, num_sms = 0;
+    int T = 64, NT = 0, threads = 256;
+    uint64_t nkeys = 0;
+    double w_scale = 0.0, dw = 0.0;
+    std::vector<double> taper;
+    float* d_inv_taper = nullptr;
+    float* d_table = nullptr;
+    int lattice = 0;
+    // binning scratch
+    int64_t cap_vis = 0;
+    uint32_t* d_key = nullptr;
+    uint32_t* d_rank = nullptr;
+    VisRecord* d_stage = nullptr;
+    VisRecord* d_records = nullptr;
+    uint32_t* d_hist = nullptr;
+    uint32_t* d_offsets = nullptr;
+    uint32_t* d_partials = nullptr;
+    uint32_t* d_counter = nullptr;
+    unsigned long long* d_counts = nullptr;
+    int* d_status = nullptr;
+    double* d_wsum = nullptr;
+    bool binned = false;
+    // cuFFT: batch B and single-plane plans
+    cufftHandle fft_b = 0, fft_1 = 0;
+    bool have_b = false, have_1 = false;
+    int fft_B = 1;
+    // plan-owned grid and staging for rick_dirty_image(_host)
+    float2* d_grid = nullptr;
+    size_t grid_cap = 0;
+    unsigned char* d_in = nullptr;
+    size_t in_cap = 0;
+    float* d_img = nullptr;
+    size_t img_cap = 0;
+    int64_t launches = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+void release(rick_plan* P) {
+    dfree(P->d_inv_taper);
+    dfree(P->d_table);
+    dfree(P->d_key);
+    dfree(P->d_rank);
+    dfree(P->d_stage);
+    dfree(P->d_records);
+    dfree(P->d_hist);
+    dfree(P->d_offsets);
+    dfree(P->d_partials);
+    dfree(P->d_counter);
+    dfree(P->d_counts);
+    dfree(P->d_status);
+    dfree(P->d_wsum);
+    dfree(P->d_grid);
+    dfree(P->d_in);
+    dfree(P->d_img);
+    if (P->have_b) cufftDestroy(P->fft_b);
+    if (P->have_1) cufftDestroy(P->fft_1);
+    P->have_b = P->have_1 = false;
+}
+
+rick_status validate(const rick_config* c) {
+    RK_ARG(c != nullptr, "cfg is NULL");
+    RK_ARG(c->N >= 64 && c->N <= 65536 && (c->N & (c->N - 1)) == 0,
+           "N must be a power of two in [64, 65536]");
+    const int T = c->tile ? c->tile : 64;
+    RK_ARG(T == 32 || T == 64 || T == 128, "tile must be 32, 64 or 128");
+    RK_ARG(T <= c->N, "tile must not exceed N");
+    RK_ARG(c->n_wplanes >= 1, "n_wplanes must be >= 1");
+    RK_ARG(c->n_channels >= 1, "n_channels must be >= 1");
+    RK_ARG(c->support >= 1 && c->support <= 16 && c->support <= T, "support must be in [1, min(16, tile)]");
+    RK_ARG(c->fov_rad > 0.0 && c->fov_rad < 1.0, "fov_rad must be in (0, 1)");
+    RK_ARG(std::isfinite(c->w_min) && std::isfinite(c->w_max), "w range must be finite");
+    RK_ARG(c->n_wplanes == 1 || c->w_max > c->w_min, "w_max must exceed w_min when n_wplanes > 1");
+    RK_ARG(c->kernel_kind == RICK_KERNEL_GAUSS || c->kernel_kind == RICK_KERNEL_KAISER_BESSEL ||
+               c->kernel_kind == RICK_KERNEL_TABLE,
+           "unknown kernel_kind");
+    RK_ARG(c->kernel_param > 0.0 && std::isfinite(c->kernel_param), "kernel_param must be > 0");
+    RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE || c->support == 4, "table kernels have support 4");
+    RK_ARG(c->precision == RICK_PREC_FP32_FP64IDX || c->precision == RICK_PREC_ALL_FP32,
+           "unknown precision");
+    const int th = c->grid_threads ? c->grid_threads : 256;
+    RK_ARG(th == 128 || th == 256 || th == 512, "grid_threads must be 128, 256 or 512");
+    RK_ARG(c->fft_batch >= 0, "fft_batch must be >= 0");
+    RK_ARG(c->reserved == 0, "reserved must be 0");
+    RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
+    const uint64_t NT = (uint64_t)(c->N / T);
+    const uint64_t nkeys = (uint64_t)c->n_channels * c->n_wplanes * NT * NT * 4ull;
+    if (nkeys >= 0xFFFFFFFFull) {
+        set_err("channels x planes x tiles exceeds the 32-bit bin space; use a larger tile or "
+                "fewer channels per plan");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    return RICK_OK;
+}
+
+rick_status ensure_vis_capacity(rick_plan* P, int64_t nvis) {
+    if (nvis <= P->cap_vis) return RICK_OK;
+    dfree(P->d_key);
+    dfree(P->d_rank);
+    dfree(P->d_stage);
+    dfree(P->d_records);
+    P->cap_vis = 0;
+    const size_t n = (size_t)nvis;
+    RK_CUDA(cudaMalloc(&P->d_key, n * sizeof(uint32_t)));
+    RK_CUDA(cudaMalloc(&P->d_rank, n * sizeof(uint32_t)));
+    RK_CUDA(cudaMalloc(&P->d_stage, n * sizeof(VisRecord)));
+    RK_CUDA(cudaMalloc(&P->d_records, n * sizeof(VisRecord)));
+    P->cap_vis = nvis;
+    return RICK_OK;
+}
+
+rick_status make_fft_plan(cufftHandle* h, bool* have, int N, int batch) {
+    if (cufftCreate(h) != CUFFT_SUCCESS) {
+        set_err("cufftCreate failed");
+        return RICK_ERR_CUFFT;
+    }
+    *have = true;
+    long long n[2] = {N, N};
+    size_t work = 0;
+    const long long dist = (long long)N * N;
+    cufftResult r = cufftMakePlanMany64(*h, 2, n, nullptr, 1, dist, nullptr, 1, dist, CUFFT_C2C,
+                                        batch, &work);
+    if (r != CUFFT_SUCCESS) {
+        set_err("cufftMakePlanMany64(N=%d, batch=%d) failed: %d", N, batch, (int)r);
+        return r == CUFFT_ALLOC_FAILED ? RICK_ERR_OOM : RICK_ERR_CUFFT;
+    }
+    return RICK_OK;
+}
+
+rick_status plan_init(rick_plan* P, const rick_config* cfg) {
+    P->cfg = *cfg;
+    rick_config& c = P->cfg;
+    P->T = c.tile ? c.tile : 64;
+    c.tile = P->T;
+    P->threads = c.grid_threads ? c.grid_threads : 256;
+    c.grid_threads = P->threads;
+    P->NT = c.N / P->T;
+    P->nkeys = (uint64_t)c.n_channels * c.n_wplanes * (uint64_t)P->NT * P->NT * 4ull;
+    if (c.n_wplanes > 1) {
+        P->w_scale = (double)c.n_wplanes / (c.w_max - c.w_min);
+        P->dw = (c.w_max - c.w_min) / c.n_wplanes;
+    }
+    RK_CUDA(cudaGetDevice(&P->device));
+    RK_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+
+    const int taper_kind = c.kernel_kind == RICK_KERNEL_TABLE ? RICK_KERNEL_KAISER_BESSEL : c.kernel_kind;
+    make_taper(taper_kind, c.kernel_param, c.support, c.N, P->taper);
+    std::vector<float> inv(c.N);
+    for (int p = 0; p < c.N; ++p) inv[p] = (float)(1.0 / P->taper[p]);
+    RK_CUDA(cudaMalloc(&P->d_inv_taper, sizeof(float) * c.N));
+    RK_CUDA(cudaMemcpy(P->d_inv_taper, inv.data(), sizeof(float) * c.N, cudaMemcpyHostToDevice));
+
+    RK_CUDA(cudaMalloc(&P->d_hist, sizeof(uint32_t) * P->nkeys));
+    RK_CUDA(cudaMalloc(&P->d_offsets, sizeof(uint32_t) * (P->nkeys + 1)));
+    RK_CUDA(cudaMalloc(&P->d_partials, sizeof(uint32_t) * scan_partials_needed(P->nkeys)));
+    RK_CUDA(cudaMalloc(&P->d_counter, sizeof(uint32_t)));
+    RK_CUDA(cudaMalloc(&P->d_counts, 2 * sizeof(unsigned long long)));
+    RK_CUDA(cudaMalloc(&P->d_status, sizeof(int)));
+    RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
+    RK_CUDA(cudaMalloc(&P->d_wsum, sizeof(double) * c.n_channels));
+
+    const size_t plane_bytes = (size_t)c.N * c.N * sizeof(float2);
+    int B = c.fft_batch;
+    if (B <= 0) {
+        const size_t cap = (size_t)4 << 30;
+        B = (int)(cap / plane_bytes);
+        const long long total = (long long)c.n_wplanes * c.n_channels;
+        if (B > total) B = (int)total;
+        if (B < 1) B = 1;
+    }
+    P->fft_B = B;
+    c.fft_batch = B;
+    RK_TRY(make_fft_plan(&P->fft_1, &P->have_1, c.N, 1));
+    if (B > 1) RK_TRY(make_fft_plan(&P->fft_b, &P->have_b, c.N, B));
+    return RICK_OK;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+rick_status check_launch(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        set_err("%s: %s", what, cudaGetErrorString(e));
+        return RICK_ERR_CUDA;
+    }
+    return RICK_OK;
+}
+
+rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
+                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
+                     int64_t* counts, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(nrow >= 0, "nrow must be >= 0");
+    RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
+    const int64_t nvis = nrow * (int64_t)c.n_channels;
+    RK_ARG(nrow == 0 || nvis / nrow == c.n_channels, "nrow * C overflows");
+    if (nvis >= (int64_t)0xFFFFFFFFLL) {
+        set_err("nrow * C = %lld exceeds 2^32 - 2 visibilities per plan call", (long long)nvis);
+        return RICK_ERR_UNSUPPORTED;
+    }
+    if (nrow > 0) {
+        RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
+    }
+    RK_TRY(ensure_vis_capacity(P, nvis));
+    P->last_stream = st;
+    int launches = 0;
+    RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
+    RK_CUDA(cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st));
+    RK_CUDA(cudaMemsetAsync(P->d_counts, 0, 2 * sizeof(unsigned long long), st));
+    PlaceParams pp;
+    pp.N = c.N;
+    pp.S = c.support;
+    pp.Nw = c.n_wplanes;
+    pp.C = c.n_channels;
+    pp.T = P->T;
+    pp.NT = P->NT;
+    pp.precision = c.precision;
+    pp.fov = c.fov_rad;
+    pp.half_n = 0.5 * c.N;
+    pp.half_s = 0.5 * c.support;
+    pp.w_min = c.w_min;
+    pp.w_scale = P->w_scale;
+    pp.fov_f = (float)c.fov_rad;
+    pp.half_n_f = (float)pp.half_n;
+    pp.half_s_f = (float)pp.half_s;
+    pp.w_min_f = (float)c.w_min;
+    pp.w_scale_f = (float)P->w_scale;
+    rick_status s = check_launch(
+        launch_place(pp, uvw, chan_scale, reinterpret_cast<const float2*>(vis), weight, flag, nvis,
+                     P->d_hist, P->d_key, P->d_rank, P->d_stage, weight_sum, P->d_counts,
+                     P->num_sms, st, &launches),
+        "placement kernel");
+    if (s == RICK_OK)
+        s = check_launch(launch_scan(P->d_hist, P->d_offsets, P->d_partials, P->nkeys, st, &launches),
+                         "scan kernels");
+    if (s == RICK_OK)
+        s = check_launch(launch_scatter(P->d_key, P->d_rank, P->d_stage, P->d_offsets,
+                                        P->d_records, nvis, P->num_sms, st, &launches),
+                         "scatter kernel");
+    P->launches += launches;
+    RK_TRY(s);
+    if (counts)
+        RK_CUDA(cudaMemcpyAsync(counts, P->d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    P->binned = true;
+    return RICK_OK;
+}
+
+rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(P->binned, "rick_bin must precede gridding");
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= c.n_wplanes, "plane range");
+    RK_ARG(grids != nullptr, "grids is NULL");
+    RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
+    if (c.kernel_kind == RICK_KERNEL_TABLE && !P->d_table) {
+        set_err("table kernel: call rick_set_kernel_table first");
+        return RICK_ERR_INVALID_ARG;
+    }
+    const uint64_t items = (uint64_t)(c1 - c0) * (k1 - k0) * (uint64_t)P->NT * P->NT;
+    RK_ARG(items < 0xFFFFFFFFull, "too many tiles in one call");
+    GridParams G;
+    G.N = c.N;
+    G.S = c.support;
+    G.T = P->T;
+    G.NT = P->NT;
+    G.Nw = c.n_wplanes;
+    G.c0 = c0;
+    G.nc = c1 - c0;
+    G.k0 = k0;
+    G.nk = k1 - k0;
+    G.n_items = (uint32_t)items;
+    G.kind = c.kernel_kind;
+    G.kb_beta = (float)c.kernel_param;
+    G.kb_inv_i0beta = (float)(1.0 / bessel_i0(c.kernel_param));
+    G.two_over_s = 2.0f / (float)c.support;
+    G.gauss_inv_2sigma2 = (float)(0.5 / (c.kernel_param * c.kernel_param));
+    G.table = P->d_table;
+    G.lattice = P->lattice;
+    P->last_stream = st;
+    RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
+    int launches = 0;
+    rick_status s = check_launch(launch_grid(G, P->d_offsets, P->d_records,
+                                             reinterpret_cast<float2*>(grids), P->d_counter,
+                                             P->threads, P->num_sms, st, &launches),
+                                 "gridding kernel");
+    P->launches += launches;
+    return s;
+}
+
+rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st) {
+    RK_ARG(n_planes >= 0, "n_planes must be >= 0");
+    RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
+    const size_t NN = (size_t)P->cfg.N * P->cfg.N;
+    cufftComplex* g = reinterpret_cast<cufftComplex*>(grids);
+    int64_t done = 0;
+    P->last_stream = st;
+    if (P->have_b) {
+        if (cufftSetStream(P->fft_b, st) != CUFFT_SUCCESS) {
+            set_err("cufftSetStream failed");
+            return RICK_ERR_CUFFT;
+        }
+        for (; done + P->fft_B <= n_planes; done += P->fft_B) {
+            cufftComplex* d = g + (size_t)done * NN;
+            const cufftResult r = cufftExecC2C(P->fft_b, d, d, CUFFT_INVERSE);
+            if (r != CUFFT_SUCCESS) {
+                set_err("cufftExecC2C (batch) failed: %d", (int)r);
+                return RICK_ERR_CUFFT;
+            }
+        }
+    }
+    if (done < n_planes) {
+        if (cufftSetStream(P->fft_1, st) != CUFFT_SUCCESS) {
+            set_err("cufftSetStream failed");
+            return RICK_ERR_CUFFT;
+        }
+        for (; done < n_planes; ++done) {
+            cufftComplex* d = g + (size_t)done * NN;
+            const cufftResult r = cufftExecC2C(P->fft_1, d, d, CUFFT_INVERSE);
+            if (r != CUFFT_SUCCESS) {
+                set_err("cufftExecC2C failed: %d", (int)r);
+                return RICK_ERR_CUFFT;
+            }
+        }
+    }
+    return RICK_OK;
+}
+
+rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0, int k1,
+                       const double* weight_sum, float* image_real, float* image_complex,
+                       cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= c.n_wplanes, "plane range");
+    RK_ARG(grids && weight_sum && image_real, "grids, weight_sum and image_real are required");
+    RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image_real & 7u) == 0 &&
+               ((uintptr_t)image_complex & 15u) == 0,
+           "grids/image_complex must be 16-byte and image_real 8-byte aligned");
+    PhaseParams pp;
+    pp.N = c.N;
+    pp.nc = c1 - c0;
+    pp.nk = k1 - k0;
+    pp.dl = c.fov_rad / c.N;
+    pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
+    pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
+    pp.precision = c.precision;
+    P->last_stream = st;
+    int launches = 0;
+    rick_status s = check_launch(
+        launch_phase_reduce(pp, reinterpret_cast<const float2*>(grids), weight_sum + c0,
+                            P->d_inv_taper, image_real, reinterpret_cast<float2*>(image_complex),
+                            st, &launches),
+        "phase kernel");
+    P->launches += launches;
+    return s;
+}
+
+// Plane groups for the plan-owned grid: all channels x all planes if they fit
+// the budget, else whole channels, else planes of one channel.
+void plan_groups(const rick_plan* P, int* gc, int* gk) {
+    const rick_config& c = P->cfg;
+    const size_t plane = (size_t)c.N * c.N * sizeof(float2);
+    const size_t budget = c.grid_budget_bytes > 0 ? (size_t)c.grid_budget_bytes : (size_t)-1;
+    const size_t per_chan = plane * c.n_wplanes;
+    if (budget / per_chan >= (size_t)c.n_channels) {
+        *gc = c.n_channels;
+        *gk = c.n_wplanes;
+    } else if (budget >= per_chan) {
+        *gc = (int)(budget / per_chan);
+        *gk = c.n_wplanes;
+    } else {
+        *gc = 1;
+        size_t k = budget / plane;
+        *gk = k < 1 ? 1 : (int)k;
+    }
+}
+
+rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan_scale,
+                             const float* vis, const float* weight, const uint8_t* flag,
+                             int64_t nrow, float* image_real, float* image_complex,
+                             double* weight_sum, int64_t* counts, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(image_real != nullptr, "image_real is NULL");
+    double* ws = weight_sum ? weight_sum : P->d_wsum;
+    RK_TRY(bin_impl(P, uvw, chan_scale, vis, weight, flag, nrow, ws, counts, st));
+    int gc, gk;
+    plan_groups(P, &gc, &gk);
+    const size_t NN = (size_t)c.N * c.N;
+    const size_t need = (size_t)gc * gk * NN * sizeof(float2);
+    if (need > P->grid_cap) {
+        dfree(P->d_grid);
+        P->grid_cap = 0;
+        RK_CUDA(cudaMalloc(&P->d_grid, need));
+        P->grid_cap = need;
+    }
+    float* g = reinterpret_cast<float*>(P->d_grid);
+    for (int c0 = 0; c0 < c.n_channels; c0 += gc) {
+        const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
+        for (int k0 = 0; k0 < c.n_wplanes; k0 += gk) {
+            const int k1 = k0 + gk < c.n_wplanes ? k0 + gk : c.n_wplanes;
+            RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st));
+            RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st));
+            RK_TRY(phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
+                              image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st));
+        }
+    }
+    return RICK_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+rick_status rick_plan_create(const rick_config* cfg, rick_plan** out) {
+    if (!out) {
+        set_err("invalid argument: out is NULL");
+        return RICK_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    RK_TRY(validate(cfg));
+    rick_plan* P = new (std::nothrow) rick_plan();
+    if (!P) {
+        set_err("host allocation failed");
+        return RICK_ERR_OOM;
+    }
+    rick_status s = plan_init(P, cfg);
+    if (s != RICK_OK) {
+        release(P);
+        delete P;
+        return s;
+    }
+    *out = P;
+    return RICK_OK;
+}
+
+rick_status rick_plan_destroy(rick_plan* plan) {
+    if (!plan) return RICK_OK;
+    release(plan);
+    delete plan;
+    return RICK_OK;
+}
+
+rick_status rick_plan_reserve(rick_plan* plan, int64_t max_rows) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    RK_ARG(max_rows >= 0, "max_rows must be >= 0");
+    const int64_t nvis = max_rows * (int64_t)plan->cfg.n_channels;
+    RK_ARG(max_rows == 0 || nvis / max_rows == plan->cfg.n_channels, "overflow");
+    if (nvis >= (int64_t)0xFFFFFFFFLL) {
+        set_err("reservation exceeds 2^32 - 2 visibilities");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    return ensure_vis_capacity(plan, nvis);
+}
+
+rick_status rick_plan_taper(const rick_plan* plan, double* taper_host) {
+    RK_ARG(plan && taper_host, "plan and taper_host are required");
+    std::memcpy(taper_host, plan->taper.data(), sizeof(double) * plan->cfg.N);
+    return RICK_OK;
+}
+
+rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t lattice, void* stream) {
+    RK_ARG(plan && taps, "plan and taps are required");
+    RK_ARG(plan->cfg.kernel_kind == RICK_KERNEL_TABLE, "plan does not use a table kernel");
+    RK_ARG(lattice >= 1 && lattice <= 256, "lattice must be in [1, 256]");
+    const size_t n = (size_t)plan->cfg.n_wplanes * (lattice + 1) * (lattice + 1) * 16;
+    if (lattice != plan->lattice) {
+        dfree(plan->d_table);
+        plan->lattice = 0;
+        RK_CUDA(cudaMalloc(&plan->d_table, n * sizeof(float)));
+        plan->lattice = lattice;
+    }
+    RK_CUDA(cudaMemcpyAsync(plan->d_table, taps, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                            as_stream(stream)));
+    return RICK_OK;
+}
+
+rick_status rick_bin(rick_plan* plan, const double* uvw, const double* chan_scale, const float* vis,
+                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
+                     int64_t* counts, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return bin_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts,
+                    as_stream(stream));
+}
+
+rick_status rick_grid_binned(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
+                             int32_t plane_begin, int32_t plane_end, float* grids, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return grid_impl(plan, chan_begin, chan_end, plane_begin, plane_end, grids, as_stream(stream));
+}
+
+rick_status rick_grid(rick_plan* plan, const double* uvw, const double* chan_scale, const float* vis,
+                      const float* weight, const uint8_t* flag, int64_t nrow, int32_t plane_begin,
+                      int32_t plane_end, float* grids, double* weight_sum, int64_t* counts,
+                      void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    RK_TRY(bin_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts,
+                    as_stream(stream)));
+    return grid_impl(plan, 0, plan->cfg.n_channels, plane_begin, plane_end, grids,
+                     as_stream(stream));
+}
+
+rick_status rick_fft_wplanes(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return fft_impl(plan, grids, n_planes, as_stream(stream));
+}
+
+rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
+                                      int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                      const double* weight_sum, float* image_real,
+                                      float* image_complex, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return phase_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, weight_sum,
+                      image_real, image_complex, as_stream(stream));
+}
+
+rick_status rick_dirty_image(rick_plan* plan, const double* uvw, const double* chan_scale,
+                             const float* vis, const float* weight, const uint8_t* flag,
+                             int64_t nrow, float* image_real, float* image_complex,
+                             double* weight_sum, int64_t* counts, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return dirty_image_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, image_real,
+                            image_complex, weight_sum, counts, as_stream(stream));
+}
+
+rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const double* chan_scale,
+                                  const float* vis, const float* weight, const uint8_t* flag,
+                                  int64_t nrow, float* image_real, double* weight_sum,
+                                  int64_t* counts, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    RK_ARG(nrow >= 0 && image_real != nullptr, "nrow >= 0 and image_real are required");
+    const rick_config& c = plan->cfg;
+    const size_t C = (size_t)c.n_channels, R = (size_t)nrow;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t b_uvw = up(R * 3 * sizeof(double)), b_sc = up(C * sizeof(double));
+    const size_t b_vis = up(R * C * 2 * sizeof(float)), b_w = up(R * C * sizeof(float));
+    const size_t b_f = flag ? up(R * C) : 0, b_ws = up(C * sizeof(double)), b_cnt = 256;
+    const size_t need = b_uvw + b_sc + b_vis + b_w + b_f + b_ws + b_cnt;
+    if (need > plan->in_cap) {
+        dfree(plan->d_in);
+        plan->in_cap = 0;
+        RK_CUDA(cudaMalloc(&plan->d_in, need));
+        plan->in_cap = need;
+    }
+    const size_t NN = (size_t)c.N * c.N, img_bytes = C * NN * sizeof(float);
+    if (img_bytes > plan->img_cap) {
+        dfree(plan->d_img);
+        plan->img_cap = 0;
+        RK_CUDA(cudaMalloc(&plan->d_img, img_bytes));
+        plan->img_cap = img_bytes;
+    }
+    unsigned char* b = plan->d_in;
+    double* d_uvw = reinterpret_cast<double*>(b);
+    double* d_sc = reinterpret_cast<double*>(b + b_uvw);
+    float* d_vis = reinterpret_cast<float*>(b + b_uvw + b_sc);
+    float* d_w = reinterpret_cast<float*>(b + b_uvw + b_sc + b_vis);
+    uint8_t* d_f = flag ? b + b_uvw + b_sc + b_vis + b_w : nullptr;
+    double* d_ws = reinterpret_cast<double*>(b + b_uvw + b_sc + b_vis + b_w + b_f);
+    int64_t* d_cnt = reinterpret_cast<int64_t*>(b + b_uvw + b_sc + b_vis + b_w + b_f + b_ws);
+    cudaStream_t st = as_stream(stream);
+    if (R) {
+        RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
+        RK_CUDA(cudaMemcpyAsync(d_uvw, uvw, R * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        RK_CUDA(cudaMemcpyAsync(d_vis, vis, R * C * 2 * sizeof(float), cudaMemcpyHostToDevice, st));
+        RK_CUDA(cudaMemcpyAsync(d_w, weight, R * C * sizeof(float), cudaMemcpyHostToDevice, st));
+        if (flag) RK_CUDA(cudaMemcpyAsync(d_f, flag, R * C, cudaMemcpyHostToDevice, st));
+    }
+    if (chan_scale)
+        RK_CUDA(cudaMemcpyAsync(d_sc, chan_scale, C * sizeof(double), cudaMemcpyHostToDevice, st));
+    RK_CUDA(cudaMemsetAsync(plan->d_img, 0, img_bytes, st));
+    RK_TRY(dirty_image_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, plan->d_img, nullptr, d_ws,
+                            d_cnt, st));
+    RK_CUDA(cudaMemcpyAsync(image_real, plan->d_img, img_bytes, cudaMemcpyDeviceToHost, st));
+    if (weight_sum)
+        RK_CUDA(cudaMemcpyAsync(weight_sum, d_ws, C * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (counts)
+        RK_CUDA(cudaMemcpyAsync(counts, d_cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RK_CUDA(cudaStreamSynchronize(st));
+    return RICK_OK;
+}
+
+rick_status rick_plan_sync_status(rick_plan* plan) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    RK_CUDA(cudaStreamSynchronize(plan->last_stream));
+    int st = 0;
+    RK_CUDA(cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) {
+        set_err("device-side check failed (code %d)", st);
+        return RICK_ERR_INTERNAL;
+    }
+    return RICK_OK;
+}
+
+int64_t rick_plan_launch_count(const rick_plan* plan) { return plan ? plan->launches : -1; }
+
+rick_status rick_plan_bins(rick_plan* plan, int64_t* n_keys, int64_t* n_records, uint32_t* offsets,
+                           uint32_t* records) {
+    RK_ARG(plan && n_keys && n_records, "plan, n_keys and n_records are required");
+    RK_ARG(plan->binned, "nothing binned yet");
+    RK_CUDA(cudaStreamSynchronize(plan->last_stream));
+    uint32_t total = 0;
+    RK_CUDA(cudaMemcpy(&total, plan->d_offsets + plan->nkeys, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    *n_keys = (int64_t)plan->nkeys;
+    *n_records = total;
+    if (offsets)
+        RK_CUDA(cudaMemcpy(offsets, plan->d_offsets, sizeof(uint32_t) * (plan->nkeys + 1),
+                           cudaMemcpyDeviceToHost));
+    if (records && total)
+        RK_CUDA(cudaMemcpy(records, plan->d_records, sizeof(VisRecord) * total, cudaMemcpyDeviceToHost));
+    return RICK_OK;
+}
+
+const char* rick_status_string(rick_status s) {
+    switch (s) {
+        case RICK_OK: return "RICK_OK";
+        case RICK_ERR_INVALID_ARG: return "RICK_ERR_INVALID_ARG";
+        case RICK_ERR_OOM: return "RICK_ERR_OOM";
+        case RICK_ERR_CUDA: return "RICK_ERR_CUDA";
+        case RICK_ERR_CUFFT: return "RICK_ERR_CUFFT";
+        case RICK_ERR_TIMEOUT: return "RICK_ERR_TIMEOUT";
+        case RICK_ERR_UNSUPPORTED: return "RICK_ERR_UNSUPPORTED";
+        case RICK_ERR_INTERNAL: return "RICK_ERR_INTERNAL";
+        case RICK_ERR_CAPACITY: return "RICK_ERR_CAPACITY";
+    }
+    return "unknown rick_status";
+}
+
+const char* rick_last_error(void) { return g_err; }
+
+}  // extern "C"

@@ -1,0 +1,369 @@
+// rick_bin.cu -- placement and binning of visibilities (the "a0" step).
+//
+// The paper's bucket sort assigns visibilities to v-slabs and widens each
+// slab by a ghost region of half the kernel (Sec. 3.2, Eq. 5).  On one GPU the
+// same idea becomes a counting sort of the visibilities into square tiles of
+// every (channel, w-plane): each visibility is stored once, in the tile that
+// holds the first cell of its footprint, together with a halo class saying
+// whether the footprint spills into the tile to the right and/or below.  The
+// gridder of a tile then reads its own bins plus the spilling classes of its
+// left, upper and upper-left neighbours.
+//
+// Kernels:
+//   k_place    per visibility: FP64 cell position, plane, tile, class; rank in
+//              its bin from a warp-aggregated atomicAdd on the histogram
+//              (__match_any_sync groups lanes with the same key); partial sums
+//              of the weights per channel.
+//   k_scan_*   exclusive scan of the histogram -> bin offsets.
+//   k_scatter  record -> offsets[key] + rank.
+#include "rick_internal.cuh"
+
+namespace rick {
+
+namespace {
+
+constexpr int kPlaceThreads = 256;
+
+struct Placed {
+    uint32_t key;
+    VisRecord rec;
+    int status;  // 1 gridded, 0 skipped, -1 dropped
+};
+
+// FP64 placement.  The operations and their order are fixed (no contraction)
+// so that the footprint start and plane index are the IEEE results of
+//   u = uvw * s;  x = u * fov + N/2;  sx = x - S/2;  i0 = floor(sx) + 1
+//   k = floor((w - w_min) * (Nw / (w_max - w_min)))   (clamped)
+__device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, double v0, double w0,
+                                             double sc, int c, float W, float2 V) {
+    Placed out;
+    out.key = kInvalidKey;
+    out.status = 0;
+    const double u = __dmul_rn(u0, sc), v = __dmul_rn(v0, sc), w = __dmul_rn(w0, sc);
+    const double x = __dadd_rn(__dmul_rn(u, P.fov), P.half_n);
+    const double y = __dadd_rn(__dmul_rn(v, P.fov), P.half_n);
+    if (!isfinite(x) || !isfinite(y) || !isfinite(w)) {
+        out.status = -1;
+        return out;
+    }
+    const double sx = __dsub_rn(x, P.half_s), sy = __dsub_rn(y, P.half_s);
+    const double flx = floor(sx), fly = floor(sy);
+    if (flx < -1.0 || fly < -1.0 || flx + P.S > P.N - 1 || fly + P.S > P.N - 1) {
+        out.status = -1;
+        return out;
+    }
+    const int i0 = (int)flx + 1, j0 = (int)fly + 1;
+    const double fx = __dsub_rn(sx, flx), fy = __dsub_rn(sy, fly);
+    int k = 0;
+    if (P.Nw > 1) {
+        double kf = floor(__dmul_rn(__dsub_rn(w, P.w_min), P.w_scale));
+        kf = fmin(fmax(kf, 0.0), (double)(P.Nw - 1));
+        k = (int)kf;
+    }
+    uint32_t fqx = __double2uint_rn(fx * 16777216.0), fqy = __double2uint_rn(fy * 16777216.0);
+    fqx = min(fqx, kFracMask);
+    fqy = min(fqy, kFracMask);
+    const int tx = i0 / P.T, ty = j0 / P.T;
+    const int il = i0 - tx * P.T, jl = j0 - ty * P.T;
+    const int cls = halo_class(il + P.S - 1 >= P.T, jl + P.S - 1 >= P.T);
+    const uint64_t key =
+        ((((uint64_t)c * P.Nw + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
+    out.key = (uint32_t)key;
+    out.rec.wv_re = W * V.x;
+    out.rec.wv_im = W * V.y;
+    out.rec.px = ((uint32_t)il << kFracBits) | fqx;
+    out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
+    out.status = 1;
+    return out;
+}
+
+// All-FP32 placement (precision study): same steps in single precision.
+__device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, double v0, double w0,
+                                             double sc, int c, float W, float2 V) {
+    Placed out;
+    out.key = kInvalidKey;
+    out.status = 0;
+    const float s = (float)sc;
+    const float u = (float)u0 * s, v = (float)v0 * s, w = (float)w0 * s;
+    const float x = u * P.fov_f + P.half_n_f, y = v * P.fov_f + P.half_n_f;
+    if (!isfinite(x) || !isfinite(y) || !isfinite(w)) {
+        out.status = -1;
+        return out;
+    }
+    const float sx = x - P.half_s_f, sy = y - P.half_s_f;
+    const float flx = floorf(sx), fly = floorf(sy);
+    if (flx < -1.0f || fly < -1.0f || flx + P.S > P.N - 1 || fly + P.S > P.N - 1) {
+        out.status = -1;
+        return out;
+    }
+    const int i0 = (int)flx + 1, j0 = (int)fly + 1;
+    const float fx = sx - flx, fy = sy - fly;
+    int k = 0;
+    if (P.Nw > 1) {
+        float kf = floorf((w - P.w_min_f) * P.w_scale_f);
+        kf = fminf(fmaxf(kf, 0.0f), (float)(P.Nw - 1));
+        k = (int)kf;
+    }
+    uint32_t fqx = __float2uint_rn(fx * 16777216.0f), fqy = __float2uint_rn(fy * 16777216.0f);
+    fqx = min(fqx, kFracMask);
+    fqy = min(fqy, kFracMask);
+    const int tx = i0 / P.T, ty = j0 / P.T;
+    const int il = i0 - tx * P.T, jl = j0 - ty * P.T;
+    const int cls = halo_class(il + P.S - 1 >= P.T, jl + P.S - 1 >= P.T);
+    const uint64_t key =
+        ((((uint64_t)c * P.Nw + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
+    out.key = (uint32_t)key;
+    out.rec.wv_re = W * V.x;
+    out.rec.wv_im = W * V.y;
+    out.rec.px = ((uint32_t)il << kFracBits) | fqx;
+    out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
+    out.status = 1;
+    return out;
+}
+
+// One thread per visibility (grid-stride).  The launch makes the stride a
+// multiple of C, so every thread sees one channel only and can keep a private
+// FP64 partial sum of that channel's weights.
+template <int PREC>
+__global__ void __launch_bounds__(kPlaceThreads)
+k_place(PlaceParams P, const double* __restrict__ uvw, const double* __restrict__ chan_scale,
+        const float2* __restrict__ vis, const float* __restrict__ weight,
+        const uint8_t* __restrict__ flag, int64_t nvis, uint32_t* __restrict__ hist,
+        uint32_t* __restrict__ key_out, uint32_t* __restrict__ rank_out,
+        VisRecord* __restrict__ stage, double* __restrict__ weight_sum,
+        unsigned long long* __restrict__ counts) {
+    __shared__ double s_wsum[kPlaceThreads];
+    __shared__ unsigned long long s_cnt[2];
+    const int lane = threadIdx.x & 31;
+    const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int c = (int)(tid0 % P.C);
+    const double sc = chan_scale[c];
+    s_wsum[threadIdx.x] = 0.0;
+    if (threadIdx.x < 2) s_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+
+    double my_wsum = 0.0;
+    uint32_t n_grid = 0, n_drop = 0;
+    for (int64_t base = tid0 - lane; base < nvis; base += stride) {
+        const int64_t idx = base + lane;
+        Placed pl;
+        pl.key = kInvalidKey;
+        pl.status = 0;
+        if (idx < nvis) {
+            const bool flagged = flag != nullptr && flag[idx] != 0;
+            const float W = weight[idx];
+            if (!flagged && W != 0.0f && isfinite(W)) {
+                const int64_t r = idx / P.C;
+                const double u0 = uvw[3 * r], v0 = uvw[3 * r + 1], w0 = uvw[3 * r + 2];
+                const float2 V = vis[idx];
+                pl = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc, c, W, V)
+                                                : place_fp64(P, u0, v0, w0, sc, c, W, V);
+                if (pl.status == 1) {
+                    my_wsum += (double)W;
+                    ++n_grid;
+                } else if (pl.status == -1) {
+                    ++n_drop;
+                }
+            }
+        }
+        // rank within the bin: one atomic per distinct key in the warp
+        const unsigned peers = __match_any_sync(0xffffffffu, pl.key);
+        const int leader = __ffs(peers) - 1;
+        uint32_t first = 0;
+        if (lane == leader && pl.key != kInvalidKey) first = atomicAdd(&hist[pl.key], __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (idx < nvis) {
+            key_out[idx] = pl.key;
+            if (pl.key != kInvalidKey) {
+                rank_out[idx] = first + __popc(peers & ((1u << lane) - 1u));
+                stage[idx] = pl.rec;
+            }
+        }
+    }
+
+    // per-channel weight sums: block reduction in shared memory, then global
+    if (P.C <= kPlaceThreads) {
+        if (my_wsum != 0.0) atomicAdd(&s_wsum[c], my_wsum);
+    } else if (my_wsum != 0.0) {
+        atomicAdd(&weight_sum[c], my_wsum);
+    }
+    const unsigned g = __reduce_add_sync(0xffffffffu, n_grid);
+    const unsigned d = __reduce_add_sync(0xffffffffu, n_drop);
+    if (lane == 0) {
+        if (g) atomicAdd(&s_cnt[0], (unsigned long long)g);
+        if (d) atomicAdd(&s_cnt[1], (unsigned long long)d);
+    }
+    __syncthreads();
+    if (P.C <= kPlaceThreads && threadIdx.x < P.C && s_wsum[threadIdx.x] != 0.0)
+        atomicAdd(&weight_sum[threadIdx.x], s_wsum[threadIdx.x]);
+    if (threadIdx.x < 2 && s_cnt[threadIdx.x]) atomicAdd(&counts[threadIdx.x], s_cnt[threadIdx.x]);
+}
+
+// ---- exclusive scan (three kernels) ---------------------------------------
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t s_warp[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    if (warp == 0) {
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t warp_excl = warp ? s_warp[warp - 1] : 0u;
+    *total = s_warp[nw - 1];
+    const uint32_t r = warp_excl + x - v;
+    __syncthreads();  // s_warp reusable
+    return r;
+}
+
+__device__ __forceinline__ void load_items(const uint32_t* in, uint64_t n, uint64_t first,
+                                           uint32_t v[kScanItems]) {
+    if (first + kScanItems <= n) {
+        const uint4* p = reinterpret_cast<const uint4*>(in + first);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const uint4 t = p[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q) v[q] = first + q < n ? in[first + q] : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const uint32_t* __restrict__ in, uint64_t n, uint32_t* __restrict__ partials) {
+    const uint64_t first = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    load_items(in, n, first, v);
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s += v[q];
+    uint32_t total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block totals in place.
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t* partials, uint64_t nb) {
+    uint32_t carry = 0;
+    for (uint64_t base = 0; base < nb; base += blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        const uint32_t v = i < nb ? partials[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan(v, &total);
+        if (i < nb) partials[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, uint64_t n,
+             const uint32_t* __restrict__ partials) {
+    const uint64_t first = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    load_items(in, n, first, v);
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) s += v[q];
+    uint32_t total;
+    uint32_t run = partials[blockIdx.x] + block_exclusive_scan(s, &total);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        const uint64_t i = first + q;
+        if (i < n) out[i] = run;
+        run += v[q];
+        if (i + 1 == n) out[n] = run;  // offsets[n] = total number of records
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+          const VisRecord* __restrict__ stage, const uint32_t* __restrict__ offsets,
+          VisRecord* __restrict__ records, int64_t nvis) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvis; i += stride) {
+        const uint32_t k = key[i];
+        if (k != kInvalidKey) records[offsets[k] + rank[i]] = stage[i];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* chan_scale,
+                         const float2* vis, const float* weight, const uint8_t* flag,
+                         int64_t nvis, uint32_t* hist, uint32_t* key, uint32_t* rank,
+                         VisRecord* stage, double* weight_sum, unsigned long long* counts,
+                         int num_sms, cudaStream_t stream, int* launches) {
+    if (nvis <= 0) return cudaSuccess;
+    // grid: a multiple of C blocks (so that the stride is a multiple of C),
+    // about 8 blocks per SM, never more than the work needs
+    const int64_t per_block = kPlaceThreads;
+    int64_t want = (nvis + per_block - 1) / per_block;
+    int64_t target = (int64_t)num_sms * 8;
+    if (want < target) target = want;
+    int64_t mult = (target + P.C - 1) / P.C;
+    if (mult < 1) mult = 1;
+    const int64_t blocks = mult * P.C;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (P.precision == RICK_PREC_ALL_FP32)
+        k_place<RICK_PREC_ALL_FP32><<<(unsigned)blocks, kPlaceThreads, 0, stream>>>(
+            P, uvw, chan_scale, vis, weight, flag, nvis, hist, key, rank, stage, weight_sum,
+            counts);
+    else
+        k_place<RICK_PREC_FP32_FP64IDX><<<(unsigned)blocks, kPlaceThreads, 0, stream>>>(
+            P, uvw, chan_scale, vis, weight, flag, nvis, hist, key, rank, stage, weight_sum,
+            counts);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partials, uint64_t n,
+                        cudaStream_t stream, int* launches) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t nb = (n + kScanChunk - 1) / kScanChunk;
+    if (nb > 0x7fffffffULL) return cudaErrorInvalidConfiguration;
+    k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, stream>>>(in, n, partials);
+    k_scan_partials<<<1, 1024, 0, stream>>>(partials, nb);
+    k_scan_apply<<<(unsigned)nb, kScanThreads, 0, stream>>>(in, out, n, partials);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+uint64_t scan_partials_needed(uint64_t n) { return (n + kScanChunk - 1) / kScanChunk + 1; }
+
+cudaError_t launch_scatter(const uint32_t* key, const uint32_t* rank, const VisRecord* stage,
+                           const uint32_t* offsets, VisRecord* records, int64_t nvis,
+                           int num_sms, cudaStream_t stream, int* launches) {
+    if (nvis <= 0) return cudaSuccess;
+    int64_t blocks = (nvis + 255) / 256;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    k_scatter<<<(unsigned)blocks, 256, 0, stream>>>(key, rank, stage, offsets, records, nvis);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+}  // namespace rick

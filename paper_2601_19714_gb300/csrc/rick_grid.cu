@@ -1,0 +1,268 @@
+// rick_grid.cu -- convolutional gridding onto w-planes (Eq. 3), the "a1" step.
+//
+// Design (one GB300, HBM-bound): the unit of work is one T x T tile of one
+// (channel, w-plane).  A persistent CTA takes tiles from a global counter
+// (in chunks), accumulates every visibility that touches the tile into a
+// shared-memory subgrid (separate re/im planes with a padded pitch so that
+// the S x S footprint of one visibility, spread over the 32 lanes of a warp,
+// hits 32 distinct banks), then writes the whole tile to HBM once with
+// coalesced 16-byte streaming stores, applying the checkerboard sign.  Tiles
+// that no visibility touches are written as zeros without touching shared
+// memory.  So every grid cell is written exactly once: the zero fill is fused
+// into the gridder and no global atomics are needed, because a tile is owned
+// by exactly one CTA (the halo of neighbouring tiles is read, not written --
+// the binning stores each visibility once with its halo class).
+//
+// Kernel taps: separable g(i - x) g(j - y) (Gaussian, Kaiser-Bessel), or the
+// learned non-separable 4x4 taps interpolated from a per-plane table.  Each
+// lane evaluates the 2S (or 16) taps of one record into a warp-private
+// staging area; then the warp walks the 32 records, lanes spread over the
+// footprint cells, and adds into shared memory (red.shared.add.f32).
+#include "rick_internal.cuh"
+
+namespace rick {
+
+namespace {
+
+constexpr uint32_t kItemsPerGrab = 8;
+
+__device__ __forceinline__ float tap_value(const GridParams& G, float s) {
+    if (G.kind == RICK_KERNEL_GAUSS) return expf(-s * s * G.gauss_inv_2sigma2);
+    const float t = s * G.two_over_s;
+    const float a = fmaxf(1.0f - t * t, 0.0f);
+    return cyl_bessel_i0f(G.kb_beta * sqrtf(a)) * G.kb_inv_i0beta;
+}
+
+// Learned taps: bilinear interpolation of the plane's (L+1)^2 x 16 table.
+__device__ __forceinline__ void table_taps(const GridParams& G, int k, float fx, float fy,
+                                           float* out /* 16, stride 1 */) {
+    const int L = G.lattice;
+    const float X = fx * L, Y = fy * L;
+    const int ix = min((int)X, L - 1), iy = min((int)Y, L - 1);
+    const float ax = X - ix, ay = Y - iy;
+    const size_t row = (size_t)(L + 1);
+    const float4* t00 = reinterpret_cast<const float4*>(G.table + (((size_t)k * row + iy) * row + ix) * 16);
+    const float4* t10 = t00 + 4;
+    const float4* t01 = t00 + row * 4;
+    const float4* t11 = t01 + 4;
+    const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay,
+                w11 = ax * ay;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 a = __ldg(t00 + q), b = __ldg(t10 + q), c = __ldg(t01 + q), d = __ldg(t11 + q);
+        out[4 * q + 0] = w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x;
+        out[4 * q + 1] = w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y;
+        out[4 * q + 2] = w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z;
+        out[4 * q + 3] = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
+    }
+}
+
+// Accumulate records [rb, re) whose coordinates are relative to a tile at
+// offset (dx, dy) from this one (0 or -T per axis).
+template <int KIND, int SS>
+__device__ __forceinline__ void accumulate_range(const GridParams& G, const VisRecord* __restrict__ records,
+                                                 uint32_t rb, uint32_t re, int dx, int dy, int k,
+                                                 float* s_re, float* s_im, int pitch,
+                                                 float* wstage, int stg) {
+    const int S = SS > 0 ? SS : G.S;
+    const int T = G.T;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    constexpr float kInvFrac = 1.0f / 16777216.0f;
+    for (uint32_t base = rb + 32u * warp; base < re; base += 32u * nwarps) {
+        const uint32_t idx = base + lane;
+        VisRecord rec = {0.f, 0.f, 0u, 0u};
+        if (idx < re) rec = records[idx];
+        const int i0 = (int)(rec.px >> kFracBits) + dx;
+        const int j0 = (int)(rec.py >> kFracBits) + dy;
+        const float fx = (float)(rec.px & kFracMask) * kInvFrac;
+        const float fy = (float)(rec.py & kFracMask) * kInvFrac;
+        float* my = wstage + lane * stg;
+        if (KIND == RICK_KERNEL_TABLE) {
+            table_taps(G, k, fx, fy, my);
+        } else {
+            const float off = 1.0f - 0.5f * (float)S;  // s_a = a + 1 - S/2 - f
+#pragma unroll
+            for (int a = 0; a < (SS > 0 ? SS : 16); ++a) {
+                if (SS == 0 && a >= S) break;
+                my[a] = tap_value(G, (float)a + off - fx);
+                my[S + a] = tap_value(G, (float)a + off - fy);
+            }
+        }
+        __syncwarp();
+        const int n = (int)min(32u, re - base);
+        constexpr int kTaps = SS * SS;
+        if (SS > 0 && kTaps <= 16) {
+            // two records per pass: lanes 0-15 take record r, lanes 16-31 record r+1
+            const int t = lane & 15;
+            const int a = t % (SS > 0 ? SS : 1), b = t / (SS > 0 ? SS : 1);
+            for (int r0 = 0; r0 < n; r0 += 2) {
+                const int r = r0 + (lane >> 4);
+                const int rs = r < n ? r : r0;
+                const float wr = __shfl_sync(0xffffffffu, rec.wv_re, rs);
+                const float wi = __shfl_sync(0xffffffffu, rec.wv_im, rs);
+                const int ri = __shfl_sync(0xffffffffu, i0, rs) + a;
+                const int rj = __shfl_sync(0xffffffffu, j0, rs) + b;
+                if (r < n && t < kTaps && (unsigned)ri < (unsigned)T && (unsigned)rj < (unsigned)T) {
+                    const float* st = wstage + r * stg;
+                    const float g = KIND == RICK_KERNEL_TABLE ? st[t] : st[a] * st[S + b];
+                    atomicAdd(&s_re[rj * pitch + ri], wr * g);
+                    atomicAdd(&s_im[rj * pitch + ri], wi * g);
+                }
+            }
+        } else {
+            const int taps = S * S;
+            for (int r = 0; r < n; ++r) {
+                const float wr = __shfl_sync(0xffffffffu, rec.wv_re, r);
+                const float wi = __shfl_sync(0xffffffffu, rec.wv_im, r);
+                const int ri0 = __shfl_sync(0xffffffffu, i0, r);
+                const int rj0 = __shfl_sync(0xffffffffu, j0, r);
+                const float* st = wstage + r * stg;
+                for (int t = lane; t < taps; t += 32) {
+                    const int a = t % S, b = t / S;
+                    const int i = ri0 + a, j = rj0 + b;
+                    if ((unsigned)i < (unsigned)T && (unsigned)j < (unsigned)T) {
+                        const float g = st[a] * st[S + b];
+                        atomicAdd(&s_re[j * pitch + i], wr * g);
+                        atomicAdd(&s_im[j * pitch + i], wi * g);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int KIND, int SS>
+__global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
+                       const VisRecord* __restrict__ records, float2* __restrict__ grids,
+                       uint32_t* __restrict__ work_counter) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ uint32_t s_first;
+    const int T = G.T, pitch = T + 8, N = G.N, NT = G.NT;
+    float* s_re = smem;
+    float* s_im = smem + T * pitch;
+    const int stg = KIND == RICK_KERNEL_TABLE ? 17 : 2 * (SS > 0 ? SS : G.S) + 1;
+    float* wstage = smem + 2 * T * pitch + (threadIdx.x >> 5) * 32 * stg;
+    const uint32_t tiles = (uint32_t)NT * NT;
+    const int half = T / 2;
+
+    for (;;) {
+        if (threadIdx.x == 0) s_first = atomicAdd(work_counter, kItemsPerGrab);
+        __syncthreads();
+        const uint32_t first = s_first;
+        __syncthreads();
+        if (first >= G.n_items) break;
+        const uint32_t last = min(first + kItemsPerGrab, G.n_items);
+        for (uint32_t item = first; item < last; ++item) {
+            const uint32_t plane = item / tiles, tile = item - plane * tiles;
+            const int kk = (int)(plane % G.nk), cc = (int)(plane / G.nk);
+            const int c = G.c0 + cc, k = G.k0 + kk;
+            const int ty = (int)(tile / NT), tx = (int)(tile - (uint32_t)ty * NT);
+            const uint64_t key = ((((uint64_t)c * G.Nw + k) * NT + ty) * NT + tx) * 4u;
+            // own bins (all classes), left (classes 2-3), up (1-2), up-left (2)
+            const uint32_t o0 = __ldg(offsets + key), o4 = __ldg(offsets + key + 4);
+            uint32_t l2 = 0, l4 = 0, u1 = 0, u3 = 0, d2 = 0, d3 = 0;
+            if (tx > 0) {
+                l2 = __ldg(offsets + key - 2);
+                l4 = __ldg(offsets + key);
+            }
+            if (ty > 0) {
+                const uint64_t ku = key - 4ull * NT;
+                u1 = __ldg(offsets + ku + 1);
+                u3 = __ldg(offsets + ku + 3);
+                if (tx > 0) {
+                    d2 = __ldg(offsets + ku - 2);
+                    d3 = __ldg(offsets + ku - 1);
+                }
+            }
+            const uint32_t total = (o4 - o0) + (l4 - l2) + (u3 - u1) + (d3 - d2);
+            float2* out = grids + ((uint64_t)plane * N + (uint64_t)ty * T) * N + (uint64_t)tx * T;
+            if (total == 0) {
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int e = threadIdx.x; e < T * half; e += blockDim.x) {
+                    const int j = e / half, i = (e - j * half) * 2;
+                    __stcs(reinterpret_cast<float4*>(out + (size_t)j * N + i), z);
+                }
+                continue;
+            }
+            {
+                float4* s4 = reinterpret_cast<float4*>(smem);
+                const int n4 = (2 * T * pitch) / 4;
+                const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int e = threadIdx.x; e < n4; e += blockDim.x) s4[e] = z;
+            }
+            __syncthreads();
+            accumulate_range<KIND, SS>(G, records, o0, o4, 0, 0, k, s_re, s_im, pitch, wstage, stg);
+            if (l4 > l2)
+                accumulate_range<KIND, SS>(G, records, l2, l4, -T, 0, k, s_re, s_im, pitch, wstage, stg);
+            if (u3 > u1)
+                accumulate_range<KIND, SS>(G, records, u1, u3, 0, -T, k, s_re, s_im, pitch, wstage, stg);
+            if (d3 > d2)
+                accumulate_range<KIND, SS>(G, records, d2, d3, -T, -T, k, s_re, s_im, pitch, wstage, stg);
+            __syncthreads();
+            for (int e = threadIdx.x; e < T * half; e += blockDim.x) {
+                const int j = e / half, i = (e - j * half) * 2;
+                const float2 re = *reinterpret_cast<const float2*>(s_re + j * pitch + i);
+                const float2 im = *reinterpret_cast<const float2*>(s_im + j * pitch + i);
+                const float sg = (j & 1) ? -1.f : 1.f;  // (-1)^(i+j), i even, T even
+                __stcs(reinterpret_cast<float4*>(out + (size_t)j * N + i),
+                       make_float4(sg * re.x, sg * im.x, -sg * re.y, -sg * im.y));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <int KIND, int SS>
+cudaError_t launch_one(const GridParams& G, const uint32_t* offsets, const VisRecord* records,
+                       float2* grids, uint32_t* counter, int threads, int num_sms,
+                       cudaStream_t stream) {
+    const int stg = KIND == RICK_KERNEL_TABLE ? 17 : 2 * (SS > 0 ? SS : G.S) + 1;
+    const size_t smem =
+        sizeof(float) * ((size_t)2 * G.T * (G.T + 8) + (size_t)(threads / 32) * 32 * stg);
+    auto fn = k_grid<KIND, SS>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    uint64_t blocks = (uint64_t)per_sm * num_sms;
+    const uint64_t need = (G.n_items + kItemsPerGrab - 1) / kItemsPerGrab;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    fn<<<(unsigned)blocks, threads, smem, stream>>>(G, offsets, records, grids, counter);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_grid(const GridParams& G, const uint32_t* offsets, const VisRecord* records,
+                        float2* grids, uint32_t* work_counter, int threads, int num_sms,
+                        cudaStream_t stream, int* launches) {
+    if (G.n_items == 0) return cudaSuccess;
+    cudaError_t e;
+    if (G.kind == RICK_KERNEL_TABLE) {
+        e = launch_one<RICK_KERNEL_TABLE, 4>(G, offsets, records, grids, work_counter, threads,
+                                             num_sms, stream);
+    } else if (G.kind == RICK_KERNEL_GAUSS) {
+        switch (G.S) {
+            case 4: e = launch_one<RICK_KERNEL_GAUSS, 4>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            case 7: e = launch_one<RICK_KERNEL_GAUSS, 7>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            case 8: e = launch_one<RICK_KERNEL_GAUSS, 8>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            default: e = launch_one<RICK_KERNEL_GAUSS, 0>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+        }
+    } else {
+        switch (G.S) {
+            case 4: e = launch_one<RICK_KERNEL_KAISER_BESSEL, 4>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            case 7: e = launch_one<RICK_KERNEL_KAISER_BESSEL, 7>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            case 8: e = launch_one<RICK_KERNEL_KAISER_BESSEL, 8>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+            default: e = launch_one<RICK_KERNEL_KAISER_BESSEL, 0>(G, offsets, records, grids, work_counter, threads, num_sms, stream); break;
+        }
+    }
+    if (e == cudaSuccess) ++*launches;
+    return e;
+}
+
+}  // namespace rick

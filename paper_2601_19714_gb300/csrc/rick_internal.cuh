@@ -1,0 +1,93 @@
+// rick_internal.cuh -- types shared by the translation units of librick.
+//
+// Data layout in HBM (all device memory):
+//   inputs   uvw[nrow][3] f64, chan_scale[C] f64, vis[nrow][C] complex64,
+//            weight[nrow][C] f32, flag[nrow][C] u8
+//   binning  key[nvis] u32, rank[nvis] u32, stage[nvis] VisRecord (unsorted),
+//            hist[nkeys] u32, offsets[nkeys+1] u32, records[nvis] VisRecord
+//            (sorted by key = (((c*Nw + k)*NT + ty)*NT + tx)*4 + halo class)
+//   grids    [channels][planes][N][N] complex64, checkerboard-signed
+//   images   [channels][N][N] f32
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include "rick.h"
+
+namespace rick {
+
+// One binned visibility: W*V (FP32) and, per axis, the first footprint cell
+// relative to the anchor tile (top 8 bits) and the fractional offset
+// f = (x - S/2) - floor(x - S/2) in units of 2^-24 (low 24 bits).
+struct __align__(16) VisRecord {
+    float wv_re, wv_im;
+    uint32_t px, py;
+};
+
+constexpr uint32_t kInvalidKey = 0xFFFFFFFFu;
+constexpr int kFracBits = 24;
+constexpr uint32_t kFracMask = (1u << kFracBits) - 1u;
+
+// Halo classes of a visibility relative to its anchor tile, ordered so that
+// each neighbour reads one contiguous class range:
+//   0 interior, 1 spills down only, 2 spills right and down, 3 spills right only.
+// The tile to the right reads classes [2,4), the tile below [1,3), the
+// diagonal tile [2,3).
+__host__ __device__ inline int halo_class(bool right, bool down) {
+    return right ? (down ? 2 : 3) : (down ? 1 : 0);
+}
+
+struct PlaceParams {
+    int N, S, Nw, C, T, NT;
+    int precision;
+    double fov, half_n, half_s, w_min, w_scale;  // w_scale = Nw/(w_max - w_min), 0 if Nw == 1
+    float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
+};
+
+struct GridParams {
+    int N, S, T, NT, Nw;
+    int c0, nc, k0, nk;
+    uint32_t n_items;     // nc * nk * NT * NT tiles
+    int kind;             // rick_kernel_kind
+    float kb_beta, kb_inv_i0beta, two_over_s;  // Kaiser-Bessel
+    float gauss_inv_2sigma2;                   // Gaussian
+    const float* table;   // RICK_KERNEL_TABLE: [Nw][L+1][L+1][16]
+    int lattice;
+};
+
+struct PhaseParams {
+    int N, nc, nk;
+    double dl;            // fov / N
+    double w_first;       // w of plane plane_begin (plane centre)
+    double dw;            // plane spacing (0 if Nw == 1)
+    int precision;
+};
+
+// --- launchers (one per kernel family), all asynchronous on `stream` -------
+
+cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* chan_scale,
+                         const float2* vis, const float* weight, const uint8_t* flag,
+                         int64_t nvis, uint32_t* hist, uint32_t* key, uint32_t* rank,
+                         VisRecord* stage, double* weight_sum, unsigned long long* counts,
+                         int num_sms, cudaStream_t stream, int* launches);
+
+cudaError_t launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partials, uint64_t n,
+                        cudaStream_t stream, int* launches);
+
+cudaError_t launch_scatter(const uint32_t* key, const uint32_t* rank, const VisRecord* stage,
+                           const uint32_t* offsets, VisRecord* records, int64_t nvis,
+                           int num_sms, cudaStream_t stream, int* launches);
+
+cudaError_t launch_grid(const GridParams& G, const uint32_t* offsets, const VisRecord* records,
+                        float2* grids, uint32_t* work_counter, int threads, int num_sms,
+                        cudaStream_t stream, int* launches);
+
+cudaError_t launch_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
+                                const float* taper, float* image_real, float2* image_complex,
+                                cudaStream_t stream, int* launches);
+
+uint64_t scan_partials_needed(uint64_t n);
+
+}  // namespace rick

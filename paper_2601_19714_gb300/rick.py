@@ -1,0 +1,289 @@
+"""Thin ctypes binding of librick (include/rick.h).
+
+Argument marshalling only: every step of the imaging path runs in the
+library's CUDA kernels (and cuFFT).  There is no fallback: if librick.so is
+missing or cannot be loaded, importing the binding raises.
+
+Torch tensors are accepted wherever the C ABI takes a device pointer; their
+dtype, contiguity and device are checked here, and ``data_ptr()`` plus the
+current CUDA stream are passed through.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "librick.so")
+
+RICK_OK = 0
+STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_ERR_CUDA",
+          4: "RICK_ERR_CUFFT", 5: "RICK_ERR_TIMEOUT", 6: "RICK_ERR_UNSUPPORTED",
+          7: "RICK_ERR_INTERNAL", 8: "RICK_ERR_CAPACITY"}
+KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
+PRECISIONS = {"fp64idx": 0, "fp32": 1}
+
+EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
+           "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
+           "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_dirty_image",
+           "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
+           "rick_plan_bins", "rick_status_string", "rick_last_error"]
+
+
+class RickError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class rick_config(C.Structure):
+    _fields_ = [("N", C.c_int32), ("n_wplanes", C.c_int32), ("support", C.c_int32),
+                ("n_channels", C.c_int32), ("fov_rad", C.c_double), ("w_min", C.c_double),
+                ("w_max", C.c_double), ("kernel_param", C.c_double), ("kernel_kind", C.c_int32),
+                ("precision", C.c_int32), ("tile", C.c_int32), ("grid_threads", C.c_int32),
+                ("fft_batch", C.c_int32), ("reserved", C.c_int32),
+                ("grid_budget_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librick.so (built by ``paper_2601_19714_gb300._build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"librick.so not built ({path}); run __graft_entry__.build()")
+    L = C.CDLL(path)
+    p, i32, i64, st = C.c_void_p, C.c_int32, C.c_int64, C.c_int
+    sig = {
+        "rick_plan_create": [C.POINTER(rick_config), C.POINTER(p)],
+        "rick_plan_destroy": [p],
+        "rick_plan_reserve": [p, i64],
+        "rick_plan_taper": [p, p],
+        "rick_set_kernel_table": [p, p, i32, p],
+        "rick_bin": [p, p, p, p, p, p, i64, p, p, p],
+        "rick_grid_binned": [p, i32, i32, i32, i32, p, p],
+        "rick_grid": [p, p, p, p, p, p, i64, i32, i32, p, p, p, p],
+        "rick_fft_wplanes": [p, p, i64, p],
+        "rick_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
+        "rick_dirty_image": [p, p, p, p, p, p, i64, p, p, p, p, p],
+        "rick_dirty_image_host": [p, p, p, p, p, p, i64, p, p, p, p],
+        "rick_plan_sync_status": [p],
+        "rick_plan_bins": [p, C.POINTER(i64), C.POINTER(i64), p, p],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.rick_plan_launch_count.argtypes = [p]
+    L.rick_plan_launch_count.restype = i64
+    L.rick_status_string.argtypes = [st]
+    L.rick_status_string.restype = C.c_char_p
+    L.rick_last_error.argtypes = []
+    L.rick_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != RICK_OK:
+        msg = load().rick_last_error().decode(errors="replace")
+        raise RickError(status, where, msg)
+
+
+def _ptr(t, dtype=None, name="tensor", align=1):
+    """Device pointer of a contiguous CUDA tensor (or None / an int)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if dtype is not None and t.dtype not in dtype:
+        raise TypeError(f"{name}: dtype {t.dtype} not in {dtype}")
+    ptr = t.data_ptr()
+    if ptr % align:
+        raise ValueError(f"{name}: must be {align}-byte aligned")
+    return ptr
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dt():
+    import torch
+    return dict(f64=(torch.float64,), f32=(torch.float32,), c64=(torch.complex64, torch.float32),
+                u8=(torch.uint8, torch.bool), i64=(torch.int64,))
+
+
+@dataclass
+class Config:
+    """Imaging parameters in the paper's notation (Sec. 2) plus launch knobs."""
+    N: int
+    n_wplanes: int
+    support: int
+    n_channels: int
+    fov_rad: float
+    w_min: float
+    w_max: float
+    kernel: str = "kb"
+    kernel_param: float = 12.0
+    precision: str = "fp64idx"
+    tile: int = 0
+    grid_threads: int = 0
+    fft_batch: int = 0
+    grid_budget_bytes: int = 0
+
+    def c(self) -> rick_config:
+        return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
+                           self.w_min, self.w_max, self.kernel_param, KERNELS[self.kernel],
+                           PRECISIONS[self.precision], self.tile, self.grid_threads,
+                           self.fft_batch, 0, self.grid_budget_bytes)
+
+
+class Plan:
+    """A librick plan (owns tables, cuFFT plans and binning scratch)."""
+
+    def __init__(self, cfg: Config):
+        L = load()
+        self.cfg = cfg
+        self._c = cfg.c()
+        h = C.c_void_p()
+        _check(L.rick_plan_create(C.byref(self._c), C.byref(h)), "rick_plan_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rick_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---- plan utilities ---------------------------------------------------
+    def reserve(self, max_rows: int):
+        _check(load().rick_plan_reserve(self.handle, int(max_rows)), "rick_plan_reserve")
+
+    def taper(self):
+        import numpy as np
+        out = np.zeros(self.cfg.N, np.float64)
+        _check(load().rick_plan_taper(self.handle, out.ctypes.data), "rick_plan_taper")
+        return out
+
+    def set_kernel_table(self, taps, lattice: int, stream=None):
+        d = _dt()
+        _check(load().rick_set_kernel_table(self.handle, _ptr(taps, d["f32"], "taps", 16),
+                                            int(lattice), _stream(stream)),
+               "rick_set_kernel_table")
+
+    def launch_count(self) -> int:
+        return int(load().rick_plan_launch_count(self.handle))
+
+    def sync_status(self):
+        _check(load().rick_plan_sync_status(self.handle), "rick_plan_sync_status")
+
+    def bins(self):
+        import numpy as np
+        L = load()
+        nk, nr = C.c_int64(), C.c_int64()
+        _check(L.rick_plan_bins(self.handle, C.byref(nk), C.byref(nr), None, None), "rick_plan_bins")
+        off = np.zeros(nk.value + 1, np.uint32)
+        rec = np.zeros((max(nr.value, 1), 4), np.uint32)
+        _check(L.rick_plan_bins(self.handle, C.byref(nk), C.byref(nr), off.ctypes.data,
+                                rec.ctypes.data), "rick_plan_bins")
+        return off, rec[:nr.value]
+
+    # ---- the hot path -------------------------------------------------------
+    def _vis_args(self, uvw, chan_scale, vis, weight, flag):
+        d = _dt()
+        return [_ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+                _ptr(vis, d["c64"], "vis", 8), _ptr(weight, d["f32"], "weight", 4),
+                _ptr(flag, d["u8"], "flag")]
+
+    def bin(self, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts=None, stream=None):
+        d = _dt()
+        _check(load().rick_bin(self.handle, *self._vis_args(uvw, chan_scale, vis, weight, flag),
+                               int(nrow), _ptr(weight_sum, d["f64"], "weight_sum", 8),
+                               _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_bin")
+
+    def grid_binned(self, chan_begin, chan_end, plane_begin, plane_end, grids, stream=None):
+        d = _dt()
+        _check(load().rick_grid_binned(self.handle, chan_begin, chan_end, plane_begin, plane_end,
+                                       _ptr(grids, d["c64"], "grids", 16), _stream(stream)),
+               "rick_grid_binned")
+
+    def grid(self, uvw, chan_scale, vis, weight, flag, nrow, plane_begin, plane_end, grids,
+             weight_sum, counts=None, stream=None):
+        d = _dt()
+        _check(load().rick_grid(self.handle, *self._vis_args(uvw, chan_scale, vis, weight, flag),
+                                int(nrow), plane_begin, plane_end,
+                                _ptr(grids, d["c64"], "grids", 16),
+                                _ptr(weight_sum, d["f64"], "weight_sum", 8),
+                                _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_grid")
+
+    def fft_wplanes(self, grids, n_planes, stream=None):
+        d = _dt()
+        _check(load().rick_fft_wplanes(self.handle, _ptr(grids, d["c64"], "grids", 16),
+                                       int(n_planes), _stream(stream)), "rick_fft_wplanes")
+
+    def phase_correct_reduce(self, grids, chan_begin, chan_end, plane_begin, plane_end,
+                             weight_sum, image_real, image_complex=None, stream=None):
+        d = _dt()
+        _check(load().rick_phase_correct_reduce(
+            self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
+            plane_end, _ptr(weight_sum, d["f64"], "weight_sum", 8),
+            _ptr(image_real, d["f32"], "image_real", 8),
+            _ptr(image_complex, d["c64"], "image_complex", 16), _stream(stream)),
+            "rick_phase_correct_reduce")
+
+    def dirty_image(self, uvw, chan_scale, vis, weight, flag, nrow, image_real,
+                    image_complex=None, weight_sum=None, counts=None, stream=None):
+        d = _dt()
+        _check(load().rick_dirty_image(
+            self.handle, *self._vis_args(uvw, chan_scale, vis, weight, flag), int(nrow),
+            _ptr(image_real, d["f32"], "image_real", 8),
+            _ptr(image_complex, d["c64"], "image_complex", 16),
+            _ptr(weight_sum, d["f64"], "weight_sum", 8), _ptr(counts, d["i64"], "counts", 8),
+            _stream(stream)), "rick_dirty_image")
+
+    def dirty_image_host(self, uvw, chan_scale, vis, weight, flag, image_real, weight_sum=None,
+                         counts=None, stream=None):
+        """Host buffers in and out (numpy arrays or CPU tensors, contiguous)."""
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                if a.is_cuda or not a.is_contiguous():
+                    raise ValueError("host path takes contiguous CPU tensors")
+                return a.data_ptr()
+            if not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("host path takes C-contiguous arrays")
+            return a.ctypes.data
+        nrow = uvw.shape[0]
+        _check(load().rick_dirty_image_host(self.handle, hp(uvw), hp(chan_scale), hp(vis),
+                                            hp(weight), hp(flag), int(nrow), hp(image_real),
+                                            hp(weight_sum), hp(counts), _stream(stream)),
+               "rick_dirty_image_host")

@@ -1,0 +1,286 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: index work (plane, footprint start, fractional offset, bin) is
+bit-exact; floating-point images match the oracle within max|delta|/peak
+<= 1e-5 (the tolerance the workload definition states for FP32 accumulation
+with FP64 index/phase); the all-FP32 variant is reported, with only a loose
+sanity bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import visgen
+from tests.gpu_util import (host_vis, oracle_config, plan_config, rel_err, run_path, to_device)
+from visgen.workloads import meerkat, tiny_wstack
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_19714_gb300 import rick
+    rick.load()
+    return rick
+
+
+def _oracle_images(orc, img, obs, channels, **kw):
+    cfg = oracle_config(orc, img, **kw)
+    vis = host_vis(obs)
+    out = []
+    for c in channels:
+        I, _ = orc.image(cfg, obs.uvw, obs.chan_scale, vis, obs.weight, obs.flag, channel=c)
+        out.append(I)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# index work: bit-exact
+# ----------------------------------------------------------------------------
+
+def _expected_records(orc, img, obs, T):
+    cfg = oracle_config(orc, img)
+    pl = orc.place(cfg, obs.uvw, obs.chan_scale, obs.weight, obs.flag)
+    st = pl["status"]
+    C = obs.chan_scale.shape[0]
+    NT = img.N // T
+    r, c = np.nonzero(st == 1)
+    k, i0, j0 = pl["k"][r, c], pl["i0"][r, c], pl["j0"][r, c]
+    fqx = np.minimum(np.rint(pl["fx"][r, c] * 2.0 ** 24), 2 ** 24 - 1).astype(np.int64)
+    fqy = np.minimum(np.rint(pl["fy"][r, c] * 2.0 ** 24), 2 ** 24 - 1).astype(np.int64)
+    tx, ty = i0 // T, j0 // T
+    il, jl = i0 - tx * T, j0 - ty * T
+    right, down = il + img.S - 1 >= T, jl + img.S - 1 >= T
+    cls = np.where(right, np.where(down, 2, 3), np.where(down, 1, 0))
+    key = ((((c.astype(np.int64) * img.Nw + k) * NT + ty) * NT + tx) * 4 + cls)
+    vis = host_vis(obs)
+    wv = (obs.weight[r, c].astype(np.float32) * vis[r, c].astype(np.complex64)).astype(np.complex64)
+    px = (il.astype(np.int64) << 24) | fqx
+    py = (jl.astype(np.int64) << 24) | fqy
+    return key, px, py, wv, (st == 1).sum(), (st == -1).sum()
+
+
+@pytest.mark.parametrize("T", [32, 64])
+def test_binning_is_bit_exact(rk, orc, T):
+    import torch
+    img, obs = tiny_wstack(11, nvis=7001, N=256)
+    # a few flagged, zero-weight and off-grid visibilities
+    obs.weight[5::97] = 0.0
+    obs.flag = np.zeros_like(obs.weight, dtype=np.uint8)
+    obs.flag[7::53] = 1
+    obs.uvw[3::211, 0] *= 1.8
+    plan = rk.Plan(plan_config(img, 1, tile=T))
+    dev = to_device(obs)
+    wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+    plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], dev["nrow"],
+             wsum, counts)
+    off, rec = plan.bins()
+    key_e, px_e, py_e, wv_e, ng, nd = _expected_records(orc, img, obs, T)
+    assert counts.cpu().tolist() == [ng, nd] and nd > 0
+    # GPU records with their keys
+    key_g = np.repeat(np.arange(len(off) - 1), np.diff(off.astype(np.int64)))
+    assert len(key_g) == len(key_e) == ng
+    o_g = np.lexsort((rec[:, 3], rec[:, 2], key_g))
+    o_e = np.lexsort((py_e, px_e, key_e))
+    np.testing.assert_array_equal(key_g[o_g], key_e[o_e])
+    np.testing.assert_array_equal(rec[o_g, 2].astype(np.int64), px_e[o_e])
+    np.testing.assert_array_equal(rec[o_g, 3].astype(np.int64), py_e[o_e])
+    wv_g = rec[o_g, :2].copy().view(np.float32)
+    np.testing.assert_array_equal(wv_g[:, 0], wv_e[o_e].real)
+    np.testing.assert_array_equal(wv_g[:, 1], wv_e[o_e].imag)
+    ws_e = float(obs.weight[(obs.flag == 0) & (obs.weight != 0)].sum())  # before drops
+    cfg = oracle_config(orc, img)
+    ws_o, _, _ = orc.channel_stats(cfg, obs.uvw, obs.chan_scale, obs.weight, obs.flag)
+    assert wsum.item() == pytest.approx(ws_o, rel=1e-12) and ws_o < ws_e
+
+
+# ----------------------------------------------------------------------------
+# stage by stage against the oracle
+# ----------------------------------------------------------------------------
+
+def test_grid_and_fft_planes_match_oracle(rk, orc):
+    import torch
+    img, obs = tiny_wstack(12, nvis=20_000, N=256)
+    plan = rk.Plan(plan_config(img, 1))
+    dev = to_device(obs)
+    Nw, N = img.Nw, img.N
+    grids = torch.empty((1, Nw, N, N), dtype=torch.complex64, device="cuda")
+    wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+    plan.grid(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], None, dev["nrow"], 0, Nw,
+              grids, wsum)
+    g = grids.cpu().numpy()[0]
+    cfg = oracle_config(orc, img)
+    for k in range(Nw):
+        G = orc.grid_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k)
+        assert rel_err(g[k], G) < 1e-6, k
+    plan.fft_wplanes(grids, Nw)
+    f = grids.cpu().numpy()[0]
+    for k in (0, 3, 7):
+        F = orc.ifft2(orc.grid_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k))
+        assert rel_err(f[k], F) < 1e-5, k
+
+
+def test_tiny_wstack_dirty_image(rk, orc):
+    """The tiny workload at its stated size: 20k visibilities, 256^2, 8 planes,
+    Gaussian S = 7: max|delta|/peak <= 1e-5 for the real and complex image."""
+    img, obs = tiny_wstack(0)
+    plan = rk.Plan(plan_config(img, 1))
+    I_g, C_g, ws, counts = run_path(plan, to_device(obs), 1, img.N, img.Nw, complex_out=True)
+    (I_o,) = _oracle_images(orc, img, obs, [0])
+    assert counts.tolist() == [20_000, 0]
+    assert ws[0] == 20_000.0
+    assert rel_err(I_g[0], I_o.real) <= TOL
+    assert rel_err(C_g[0], I_o) <= TOL
+    assert np.unravel_index(np.argmax(I_g[0]), I_g[0].shape) == \
+        np.unravel_index(np.argmax(I_o.real), I_o.shape)
+
+
+@pytest.mark.parametrize("T,threads", [(32, 128), (64, 256), (128, 512)])
+def test_tile_and_cta_shapes_agree(rk, orc, T, threads):
+    img, obs = tiny_wstack(13, nvis=9000, N=256, Nw=5)
+    plan = rk.Plan(plan_config(img, 1, tile=T, grid_threads=threads, fft_batch=2))
+    I_g, _, _, _ = run_path(plan, to_device(obs), 1, img.N, img.Nw)
+    (I_o,) = _oracle_images(orc, img, obs, [0])
+    assert rel_err(I_g[0], I_o.real) <= TOL
+
+
+def test_multichannel_kaiser_bessel_ragged(rk, orc):
+    """A small MeerKAT-shaped set: 5 channels (one fully flagged), KB S = 8,
+    random weights, 5 % flags, planes not a multiple of the FFT batch, row
+    count not a multiple of any block size."""
+    img, obs = meerkat(3, n_ant=12, n_steps=97, nchan=5, N=512, Nw=7, n_src=20, fov_deg=1.5)
+    obs.flag[:, 2] = 1
+    plan = rk.Plan(plan_config(img, 5, fft_batch=3))
+    I_g, _, ws, counts = run_path(plan, to_device(obs), 5, img.N, img.Nw)
+    assert ws[2] == 0.0 and np.all(I_g[2] == 0.0)
+    refs = _oracle_images(orc, img, obs, [0, 1, 3, 4])
+    for c, I_o in zip([0, 1, 3, 4], refs):
+        assert rel_err(I_g[c], I_o.real) <= TOL, c
+
+
+def test_plane_group_streaming_matches_single_pass(rk, orc):
+    import torch
+    img, obs = meerkat(4, n_ant=10, n_steps=60, nchan=3, N=256, Nw=6, n_src=10)
+    dev = to_device(obs)
+    outs = []
+    for budget in (0, 3 * img.N * img.N * 8, 2 * img.N * img.N * 8 * img.Nw):
+        plan = rk.Plan(plan_config(img, 3, grid_budget_bytes=budget))
+        im = torch.zeros((3, img.N, img.N), dtype=torch.float32, device="cuda")
+        plan.dirty_image(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"],
+                         dev["nrow"], im)
+        outs.append(im.cpu().numpy())
+    for o in outs[1:]:
+        assert rel_err(o, outs[0]) <= 1e-6
+    refs = _oracle_images(orc, img, obs, [1])
+    assert rel_err(outs[1][1], refs[0].real) <= TOL
+
+
+def test_host_entry_point_matches_device_path(rk, orc):
+    img, obs = meerkat(5, n_ant=8, n_steps=40, nchan=2, N=256, Nw=4, n_src=8)
+    plan = rk.Plan(plan_config(img, 2))
+    out = np.zeros((2, img.N, img.N), np.float32)
+    ws = np.zeros(2)
+    cnt = np.zeros(2, np.int64)
+    plan.dirty_image_host(obs.uvw, obs.chan_scale, obs.vis, obs.weight, obs.flag, out, ws, cnt)
+    I_g, _, ws_g, cnt_g = run_path(plan, to_device(obs), 2, img.N, img.Nw)
+    assert rel_err(out, I_g) <= 1e-6
+    np.testing.assert_allclose(ws, ws_g, rtol=1e-12)
+    assert cnt.tolist() == cnt_g.tolist()
+
+
+# ----------------------------------------------------------------------------
+# invariants and edge cases on the GPU
+# ----------------------------------------------------------------------------
+
+def test_empty_input(rk):
+    img, obs = tiny_wstack(14, nvis=10, N=128)
+    plan = rk.Plan(plan_config(img, 1))
+    dev = to_device(obs)
+    dev["nrow"] = 0
+    I_g, _, ws, counts = run_path(plan, dev, 1, img.N, img.Nw)
+    assert ws[0] == 0.0 and counts.tolist() == [0, 0] and np.all(I_g == 0)
+
+
+def test_all_visibilities_off_grid(rk):
+    img, obs = tiny_wstack(15, nvis=500, N=128)
+    obs.uvw[:, 0] += 10 * img.N / img.fov   # every footprint far outside the grid
+    plan = rk.Plan(plan_config(img, 1))
+    I_g, _, ws, counts = run_path(plan, to_device(obs), 1, img.N, img.Nw)
+    assert counts.tolist() == [0, 500] and ws[0] == 0.0 and np.all(I_g == 0)
+
+
+def test_unit_source_at_phase_centre_gpu(rk):
+    img, obs = tiny_wstack(16, nvis=5000, N=256)
+    obs.vis[:] = 1.0
+    plan = rk.Plan(plan_config(img, 1))
+    I_g, _, _, _ = run_path(plan, to_device(obs), 1, img.N, img.Nw)
+    N = img.N
+    assert np.unravel_index(np.argmax(I_g[0]), I_g[0].shape) == (N // 2, N // 2)
+    assert abs(I_g[0, N // 2, N // 2] - 1.0) < 4e-3
+
+
+def test_hermitian_input_gives_real_image_gpu(rk):
+    img, obs = tiny_wstack(17, nvis=6000, N=256)
+    obs.uvw = np.concatenate([obs.uvw, -obs.uvw])
+    obs.vis = np.concatenate([obs.vis, np.conj(obs.vis)])
+    obs.weight = np.concatenate([obs.weight, obs.weight])
+    plan = rk.Plan(plan_config(img, 1))
+    _, C_g, _, _ = run_path(plan, to_device(obs), 1, img.N, img.Nw, complex_out=True)
+    assert np.abs(C_g.imag).max() <= 1e-6 * np.abs(C_g.real).max()
+
+
+def test_linearity_gpu(rk):
+    img, obs = tiny_wstack(18, nvis=4000, N=128)
+    g = np.random.default_rng(1)
+    V1 = ((g.integers(-64, 64, obs.vis.shape) + 1j * g.integers(-64, 64, obs.vis.shape)) / 8).astype(np.complex64)
+    V2 = ((g.integers(-64, 64, obs.vis.shape) + 1j * g.integers(-64, 64, obs.vis.shape)) / 8).astype(np.complex64)
+    plan = rk.Plan(plan_config(img, 1))
+    outs = []
+    for V in (V1, V2, (2 * V1 - 0.5 * V2).astype(np.complex64)):
+        obs.vis = V
+        outs.append(run_path(plan, to_device(obs), 1, img.N, img.Nw)[0])
+    assert rel_err(outs[2], 2 * outs[0] - 0.5 * outs[1]) <= 1e-6
+
+
+def test_all_fp32_variant_error_is_reported(rk, orc):
+    """The all-FP32 variant computes index and phase in single precision; its
+    error against the FP64 oracle is reported, and must stay sane."""
+    img, obs = meerkat(6, n_ant=16, n_steps=80, nchan=2, N=1024, Nw=8, n_src=10)
+    (I_o,) = _oracle_images(orc, img, obs, [1])
+    errs = {}
+    for prec in ("fp64idx", "fp32"):
+        plan = rk.Plan(plan_config(img, 2, precision=prec))
+        I_g, _, _, _ = run_path(plan, to_device(obs), 2, img.N, img.Nw)
+        errs[prec] = rel_err(I_g[1], I_o.real)
+    print(f"max|delta|/peak vs FP64 oracle: {errs}")
+    assert errs["fp64idx"] <= TOL
+    assert errs["fp32"] < 1e-2
+
+
+def test_invalid_arguments_are_rejected(rk):
+    img, _ = tiny_wstack(19, nvis=10, N=128)
+    bad = [dict(N=100), dict(support=0), dict(tile=48), dict(n_wplanes=0), dict(fov_rad=1.5)]
+    for b in bad:
+        cfg = plan_config(img, 1)
+        for k, v in b.items():
+            setattr(cfg, k, v)
+        with pytest.raises(rk.RickError) as e:
+            rk.Plan(cfg)
+        assert e.value.status == 1
+
+
+def test_launch_count_is_tracked(rk):
+    img, obs = tiny_wstack(20, nvis=1000, N=128)
+    plan = rk.Plan(plan_config(img, 1))
+    n0 = plan.launch_count()
+    run_path(plan, to_device(obs), 1, img.N, img.Nw)
+    # place, 3 scan kernels, scatter, grid, phase
+    assert plan.launch_count() - n0 == 7
