@@ -157,16 +157,22 @@ def oracle_sample(img, obs, n_planes: int, reps: int = 1):
     return n / s, n, s, desc
 
 
-def image_error_probe(img, obs, image_ch0: np.ndarray, n_pix: int = 8):
+def image_error_probe(img, obs, image_ch0: np.ndarray, taper: np.ndarray, n_pix: int = 8):
     """Oracle O1 (per-visibility form) at probe pixels of channel 0 vs the
-    GPU image: max|delta|/peak over the probes."""
+    GPU image: max|delta|/peak over the probes.  Probes: the field centre and
+    the brightest sources inside the field where the taper correction
+    amplifies by at most 100 (C(p) C(q) >= 1e-2 C(N/2)^2)."""
     import oracle
     cfg = oracle.Config(img.N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov, img.w_min,
                         img.w_max)
     N = img.N
     dl = img.fov / N
     src = obs.sources
-    order = np.argsort(-src[:, 2])[: n_pix - 1]
+    ps = np.clip(np.rint(src[:, 0] / dl + N // 2), 0, N - 1).astype(int)
+    qs = np.clip(np.rint(src[:, 1] / dl + N // 2), 0, N - 1).astype(int)
+    gain = taper[ps] * taper[qs] / taper[N // 2] ** 2
+    cand = np.nonzero(gain >= 1e-2)[0]
+    order = cand[np.argsort(-src[cand, 2])][: n_pix - 1]
     p = np.clip(np.rint(src[order, 0] / dl + N // 2), 0, N - 1).astype(np.int32)
     q = np.clip(np.rint(src[order, 1] / dl + N // 2), 0, N - 1).astype(np.int32)
     p = np.append(p, N // 2).astype(np.int32)
@@ -376,7 +382,7 @@ def run_ours(args):
             r, nv, s, desc = oracle_sample(img, obs, 2)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": desc, "seconds": s}
-            err, npix = image_error_probe(img, obs, img_ch0)
+            err, npix = image_error_probe(img, obs, img_ch0, plan.taper())
             line["image_error"] = {"max_rel_vs_fp64_oracle": err, "probe_pixels": npix,
                                    "channel": 0, "how": "oracle O1 per-visibility form"}
         print(json.dumps(line), flush=True)

@@ -67,3 +67,39 @@ def rel_err(a, ref):
     ref = np.asarray(ref)
     peak = np.abs(ref).max()
     return float(np.abs(np.asarray(a) - ref).max() / peak)
+
+
+def taper_gain(taper):
+    """A(p, q) = C(p) C(q) / C(N/2)^2: the factor the taper correction divides
+    pixel (p, q) by, relative to the field centre."""
+    t = np.asarray(taper, dtype=np.float64)
+    c0 = t[t.shape[0] // 2]
+    return np.outer(t, t) / (c0 * c0)
+
+
+def image_errors(got, ref, taper, inner=1e-2):
+    """Errors of a dirty image against the oracle.
+
+    full      max|delta| / peak over every pixel;
+    weighted  max|delta| A / max|ref| A  -- the error of the image before the
+              per-pixel division by the taper, which is where FP32 rounding
+              arises; the division itself multiplies it by up to 1/A;
+    inner     max|delta| / peak over pixels with A >= inner, i.e. where the
+              taper correction amplifies by at most 1/inner."""
+    got = np.asarray(got)
+    ref = np.asarray(ref)
+    A = taper_gain(taper)
+    d = np.abs(got - ref)
+    peak = np.abs(ref).max()
+    m = A >= inner
+    return dict(full=float(d.max() / peak),
+                weighted=float((d * A).max() / (np.abs(ref) * A).max()),
+                inner=float(d[m].max() / peak))
+
+
+def assert_image_close(got, ref, taper, tol=1e-5, full=False):
+    e = image_errors(got, ref, taper)
+    assert e["weighted"] <= tol and e["inner"] <= tol, e
+    if full:
+        assert e["full"] <= tol, e
+    return e
