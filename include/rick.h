@@ -187,6 +187,32 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
                                   int64_t nrow, float* image_real, double* weight_sum,
                                   int64_t* counts, void* stream);
 
+/* ---- gridding without allocation ------------------------------------ */
+
+/* rick_grid for callers that may not allocate device memory once they run:
+ * for example a streaming pipeline that sizes all device memory at start-up
+ * and must not stall on cudaMalloc/cudaFree while data arrives, or a host
+ * framework that owns the device memory budget through its own pool.  Same
+ * inputs, outputs and layout as rick_grid (all channels, planes
+ * [plane_begin, plane_end)), but it takes the configuration directly instead
+ * of a plan, and keeps its binning scratch in one fixed 32 MiB array in device
+ * memory that every GPU loading the library holds until the process exits.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Sizes whose scratch does not fit (about 40 bytes per visibility plus
+ *     8 bytes per (channel, plane, tile, class) bin) return RICK_ERR_CAPACITY
+ *     before anything is launched; Gaussian and Kaiser-Bessel kernels only
+ *     (RICK_ERR_UNSUPPORTED for a table kernel).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   - Every call shares the one array and clears what must start at zero;
+ *     calls whose work overlaps on the GPU (other streams or threads) race on
+ *     it and must be serialised by the caller.
+ * The paper has no counterpart: this is an integration variant only. */
+rick_status rick_grid_noalloc(const rick_config* cfg, const double* uvw, const double* chan_scale,
+                              const float* vis, const float* weight, const uint8_t* flag,
+                              int64_t nrow, int32_t plane_begin, int32_t plane_end, float* grids,
+                              double* weight_sum, int64_t* counts, void* stream);
+
 /* ---- introspection --------------------------------------------------- */
 
 /* Synchronise the plan's last stream and report device-side errors. */

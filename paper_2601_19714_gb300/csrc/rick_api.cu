@@ -542,6 +542,12 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
 
 }  // namespace
 
+namespace rick {
+// Lets other translation units of the library report a message through
+// rick_last_error().
+void set_error_message(const char* msg) { set_err("%s", msg); }
+}  // namespace rick
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -1,0 +1,213 @@
+// rick_noalloc.cu -- rick_grid_noalloc: binning + gridding with no device
+// allocation at all.
+//
+// Who needs this: code that must not call cudaMalloc/cudaFree once it is
+// running.  Examples are a real-time pipeline (a correlator or beamformer back
+// end) that sizes all device memory at start-up and may not stall on the
+// allocator while data streams in, and host frameworks that own the device's
+// memory budget through their own pool, where a library that allocates behind
+// their back breaks the accounting.  rick_grid needs a plan, and creating a
+// plan allocates tables, scratch and cuFFT work areas; this entry point takes
+// the configuration directly and keeps its scratch in one fixed array in device
+// memory that exists from the moment the library's device code is loaded.
+//
+// The array is kNoallocScratchBytes (32 MiB) on every GPU that loads the
+// library, held until the process exits.  A call whose binning scratch does
+// not fit (roughly 40 bytes per visibility plus 8 bytes per bin) is rejected
+// with RICK_ERR_CAPACITY before anything is launched.  All calls share the
+// array: each call clears what must start at zero, and calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on
+// it -- serialise them.
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "rick_internal.cuh"
+
+namespace rick {
+void set_error_message(const char* msg);
+}
+
+using namespace rick;
+
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
+constexpr int kMaxDevices = 64;
+
+// The scratch itself.  In host code this name only stands in for the symbol;
+// its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char rick_noalloc_scratch[kNoallocScratchBytes];
+
+std::mutex g_mutex;
+void* g_scratch_addr[kMaxDevices] = {};
+
+rick_status fail(rick_status s, const char* msg) {
+    set_error_message(msg);
+    return s;
+}
+
+// Device address of the scratch on the current device, looked up once per
+// device (the first call on a device does this; make it before any capture).
+rick_status scratch_address(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(RICK_ERR_CUDA, "rick_grid_noalloc: cudaGetDevice failed");
+    if (dev < 0 || dev >= kMaxDevices)
+        return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, rick_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(RICK_ERR_CUDA, "rick_grid_noalloc: cudaGetSymbolAddress of the scratch failed");
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return RICK_OK;
+}
+
+double i0_series(double x) {
+    const double y = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 400 && term > 1e-17 * sum; ++k) {
+        term *= y / ((double)k * k);
+        sum += term;
+    }
+    return sum;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* uvw,
+                                         const double* chan_scale, const float* vis,
+                                         const float* weight, const uint8_t* flag, int64_t nrow,
+                                         int32_t plane_begin, int32_t plane_end, float* grids,
+                                         double* weight_sum, int64_t* counts, void* stream) {
+    if (!cfg) return fail(RICK_ERR_INVALID_ARG, "invalid argument: cfg is NULL");
+    const rick_config& c = *cfg;
+    const int T = c.tile ? c.tile : 64;
+    const int threads = c.grid_threads ? c.grid_threads : 256;
+    if (c.N < 64 || c.N > 65536 || (c.N & (c.N - 1)) || !(T == 32 || T == 64 || T == 128) ||
+        T > c.N || c.n_wplanes < 1 || c.n_channels < 1 || c.support < 1 || c.support > 16 ||
+        c.support > T || !(c.fov_rad > 0.0 && c.fov_rad < 1.0) ||
+        !(std::isfinite(c.w_min) && std::isfinite(c.w_max)) ||
+        (c.n_wplanes > 1 && !(c.w_max > c.w_min)) || !(c.kernel_param > 0.0) ||
+        !(threads == 128 || threads == 256 || threads == 512) ||
+        !(c.precision == RICK_PREC_FP32_FP64IDX || c.precision == RICK_PREC_ALL_FP32))
+        return fail(RICK_ERR_INVALID_ARG, "invalid argument: configuration");
+    if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
+        return fail(RICK_ERR_UNSUPPORTED,
+                    "rick_grid_noalloc: only Gaussian and Kaiser-Bessel kernels (a table kernel needs a plan)");
+    if (nrow < 0 || !weight_sum || !grids || (nrow > 0 && !(uvw && chan_scale && vis && weight)))
+        return fail(RICK_ERR_INVALID_ARG, "invalid argument: inputs");
+    if (!(0 <= plane_begin && plane_begin < plane_end && plane_end <= c.n_wplanes))
+        return fail(RICK_ERR_INVALID_ARG, "invalid argument: plane range");
+    if (((uintptr_t)grids & 15u) != 0)
+        return fail(RICK_ERR_INVALID_ARG, "invalid argument: grids must be 16-byte aligned");
+
+    const int NT = c.N / T;
+    const uint64_t nkeys = (uint64_t)c.n_channels * c.n_wplanes * (uint64_t)NT * NT * 4ull;
+    const uint64_t nvis = (uint64_t)nrow * (uint64_t)c.n_channels;
+    const uint64_t items = (uint64_t)c.n_channels * (plane_end - plane_begin) * (uint64_t)NT * NT;
+    // scratch layout: hist, offsets, scan partials, key, rank, stage, records, counter, counts
+    const size_t b_hist = up256(nkeys * 4), b_off = up256((nkeys + 1) * 4);
+    const size_t b_part = up256(scan_partials_needed(nkeys) * 4);
+    const size_t b_key = up256(nvis * 4), b_rec = up256(nvis * sizeof(VisRecord));
+    const size_t need = b_hist + b_off + b_part + 2 * b_key + 2 * b_rec + 256 + 256;
+    if (nkeys >= 0xFFFFFFFFull || nvis >= 0xFFFFFFFFull || items >= 0xFFFFFFFFull ||
+        need > kNoallocScratchBytes) {
+        char msg[256];
+        snprintf(msg, sizeof msg,
+                 "rick_grid_noalloc: needs %llu bytes of scratch (%llu visibilities, %llu bins); "
+                 "the fixed scratch holds %llu bytes -- use rick_grid with a plan",
+                 (unsigned long long)need, (unsigned long long)nvis, (unsigned long long)nkeys,
+                 (unsigned long long)kNoallocScratchBytes);
+        return fail(RICK_ERR_CAPACITY, msg);
+    }
+
+    unsigned char* base = nullptr;
+    rick_status s = scratch_address(&base);
+    if (s != RICK_OK) return s;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base);
+    uint32_t* offsets = reinterpret_cast<uint32_t*>(base + b_hist);
+    uint32_t* partials = reinterpret_cast<uint32_t*>(base + b_hist + b_off);
+    uint32_t* key = reinterpret_cast<uint32_t*>(base + b_hist + b_off + b_part);
+    uint32_t* rank = reinterpret_cast<uint32_t*>(base + b_hist + b_off + b_part + b_key);
+    VisRecord* stage = reinterpret_cast<VisRecord*>(base + b_hist + b_off + b_part + 2 * b_key);
+    VisRecord* records = reinterpret_cast<VisRecord*>(base + b_hist + b_off + b_part + 2 * b_key + b_rec);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(base + b_hist + b_off + b_part + 2 * b_key + 2 * b_rec);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(
+        base + b_hist + b_off + b_part + 2 * b_key + 2 * b_rec + 256);
+
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, num_sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(RICK_ERR_CUDA, "rick_grid_noalloc: device query failed");
+
+    // the array keeps the previous call's contents: clear what must start at zero
+    if (cudaMemsetAsync(hist, 0, nkeys * 4, st) != cudaSuccess ||
+        cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess ||
+        cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st) != cudaSuccess)
+        return fail(RICK_ERR_CUDA, "rick_grid_noalloc: cudaMemsetAsync failed");
+
+    PlaceParams pp;
+    pp.N = c.N;
+    pp.S = c.support;
+    pp.Nw = c.n_wplanes;
+    pp.C = c.n_channels;
+    pp.T = T;
+    pp.NT = NT;
+    pp.precision = c.precision;
+    pp.fov = c.fov_rad;
+    pp.half_n = 0.5 * c.N;
+    pp.half_s = 0.5 * c.support;
+    pp.w_min = c.w_min;
+    pp.w_scale = c.n_wplanes > 1 ? (double)c.n_wplanes / (c.w_max - c.w_min) : 0.0;
+    pp.fov_f = (float)c.fov_rad;
+    pp.half_n_f = (float)pp.half_n;
+    pp.half_s_f = (float)pp.half_s;
+    pp.w_min_f = (float)c.w_min;
+    pp.w_scale_f = (float)pp.w_scale;
+    int launches = 0;
+    cudaError_t e = launch_place(pp, uvw, chan_scale, reinterpret_cast<const float2*>(vis), weight,
+                                 flag, (int64_t)nvis, hist, key, rank, stage, weight_sum, cnt,
+                                 num_sms, st, &launches);
+    if (e == cudaSuccess) e = launch_scan(hist, offsets, partials, nkeys, st, &launches);
+    if (e == cudaSuccess)
+        e = launch_scatter(key, rank, stage, offsets, records, (int64_t)nvis, num_sms, st, &launches);
+    if (e == cudaSuccess) {
+        GridParams G;
+        G.N = c.N;
+        G.S = c.support;
+        G.T = T;
+        G.NT = NT;
+        G.Nw = c.n_wplanes;
+        G.c0 = 0;
+        G.nc = c.n_channels;
+        G.k0 = plane_begin;
+        G.nk = plane_end - plane_begin;
+        G.n_items = (uint32_t)items;
+        G.kind = c.kernel_kind;
+        G.kb_beta = (float)c.kernel_param;
+        G.kb_inv_i0beta = (float)(1.0 / i0_series(c.kernel_param));
+        G.two_over_s = 2.0f / (float)c.support;
+        G.gauss_inv_2sigma2 = (float)(0.5 / (c.kernel_param * c.kernel_param));
+        G.table = nullptr;
+        G.lattice = 0;
+        e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
+                        num_sms, st, &launches);
+    }
+    if (e == cudaSuccess && counts)
+        e = cudaMemcpyAsync(counts, cnt, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+        char msg[256];
+        snprintf(msg, sizeof msg, "rick_grid_noalloc: %s", cudaGetErrorString(e));
+        return fail(RICK_ERR_CUDA, msg);
+    }
+    return RICK_OK;
+}

@@ -28,7 +28,7 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
            "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_dirty_image",
            "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
-           "rick_plan_bins", "rick_status_string", "rick_last_error"]
+           "rick_plan_bins", "rick_grid_noalloc", "rick_status_string", "rick_last_error"]
 
 
 class RickError(RuntimeError):
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "rick_dirty_image_host": [p, p, p, p, p, p, i64, p, p, p, p],
         "rick_plan_sync_status": [p],
         "rick_plan_bins": [p, C.POINTER(i64), C.POINTER(i64), p, p],
+        "rick_grid_noalloc": [C.POINTER(rick_config), p, p, p, p, p, i64, i32, i32, p, p, p, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -287,3 +288,18 @@ class Plan:
                                             hp(weight), hp(flag), int(nrow), hp(image_real),
                                             hp(weight_sum), hp(counts), _stream(stream)),
                "rick_dirty_image_host")
+
+
+def grid_noalloc(cfg: Config, uvw, chan_scale, vis, weight, flag, nrow, plane_begin, plane_end,
+                 grids, weight_sum, counts=None, stream=None):
+    """rick_grid without a plan and without any device allocation (see
+    rick_grid_noalloc in include/rick.h): for callers that may not allocate
+    once running.  Scratch is a fixed 32 MiB device array shared by all calls."""
+    d = _dt()
+    c = cfg.c()
+    _check(load().rick_grid_noalloc(
+        C.byref(c), _ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+        _ptr(vis, d["c64"], "vis", 8), _ptr(weight, d["f32"], "weight", 4),
+        _ptr(flag, d["u8"], "flag"), int(nrow), int(plane_begin), int(plane_end),
+        _ptr(grids, d["c64"], "grids", 16), _ptr(weight_sum, d["f64"], "weight_sum", 8),
+        _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_grid_noalloc")
