@@ -90,7 +90,7 @@ typedef struct rick_config {
     int32_t tile;         /* gridder tile side T: 32, 64 or 128 (0 = 64); T <= N */
     int32_t grid_threads; /* gridder CTA size: 128, 256 or 512 (0 = 256) */
     int32_t fft_batch;    /* planes per cuFFT execution (0 = up to 4 GiB of planes) */
-    int32_t reserved;     /* must be 0 */
+    int32_t tiles_per_grab; /* tiles a gridder CTA takes from the work queue at once: 1..64 (0 = 8) */
     int64_t grid_budget_bytes; /* rick_dirty_image: device bytes for plane groups (0 = all) */
 } rick_config;
 
@@ -186,6 +186,55 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
                                   const float* vis, const float* weight, const uint8_t* flag,
                                   int64_t nrow, float* image_real, double* weight_sum,
                                   int64_t* counts, void* stream);
+
+/* ---- batched launch: graph capture and autotuning (pattern 2) -------- */
+
+typedef struct rick_graph rick_graph;
+
+/* Capture the whole path for ALL channels and planes of the plan into one
+ * CUDA graph: zero image_real, rick_bin, one persistent rick_grid_binned over
+ * every (channel, plane, tile), rick_fft_wplanes over every plane, and
+ * rick_phase_correct_reduce.  Channels may have any (uneven, flagged)
+ * visibility counts; the gridder's work queue spans all of them.  Pointers are
+ * the device buffers the graph will use on every launch (their contents may
+ * change between launches, their addresses may not): grids must hold
+ * [C][Nw][N][N] complex64, image_real [C][N][N], weight_sum [C], counts[2]
+ * (nullable).  With grids = NULL the graph instead streams channel/plane
+ * groups through plan-owned grid memory of grid_budget_bytes (allocated
+ * before the capture), exactly as rick_dirty_image does.  The plan must have
+ * been reserved (rick_plan_reserve) for at
+ * least nrow rows, else RICK_ERR_CAPACITY.  The graph references the plan,
+ * which must outlive it. */
+rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double* chan_scale,
+                               const float* vis, const float* weight, const uint8_t* flag,
+                               int64_t nrow, float* grids, double* weight_sum, float* image_real,
+                               int64_t* counts, rick_graph** out);
+
+/* Launch a captured graph on a stream (asynchronous). */
+rick_status rick_graph_launch(rick_graph* graph, void* stream);
+
+/* Destroy a captured graph.  NULL is accepted. */
+rick_status rick_graph_destroy(rick_graph* graph);
+
+typedef struct rick_tune_entry {
+    int32_t tile, grid_threads, tiles_per_grab;
+    float grid_ms; /* median time of rick_grid_binned over the timed region */
+} rick_tune_entry;
+
+/* Autotune the gridder for this data: for every valid tile side T (32, 64,
+ * 128 with S <= T <= N), CTA size (128, 256, 512) and tiles per grab (2, 8,
+ * 32), bin the visibilities with T and time rick_grid_binned over channels
+ * [chan_begin, chan_end) and planes [plane_begin, plane_end) (grids sized for
+ * that region), reps times after one warm-up.  Writes up to max_results
+ * entries to results (nullable), their number to *n_results, and the base
+ * configuration with the fastest (tile, grid_threads, tiles_per_grab) to
+ * *best.  Synchronous; allocates a plan per tile side. */
+rick_status rick_autotune(const rick_config* base, const double* uvw, const double* chan_scale,
+                          const float* vis, const float* weight, const uint8_t* flag,
+                          int64_t nrow, int32_t chan_begin, int32_t chan_end,
+                          int32_t plane_begin, int32_t plane_end, float* grids, int32_t reps,
+                          rick_tune_entry* results, int32_t max_results, int32_t* n_results,
+                          rick_config* best);
 
 /* ---- gridding without allocation ------------------------------------ */
 

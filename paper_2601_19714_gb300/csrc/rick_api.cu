@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -127,7 +128,7 @@ void make_taper(int kind, double param, int S, int N, std::vector<double>& C) {
 struct rick_plan {
     rick_config cfg;
     int device = 0, num_sms = 0;
-    int T = 64, NT = 0, threads = 256;
+    int T = 64, NT = 0, threads = 256, grab = 8;
     uint64_t nkeys = 0;
     double w_scale = 0.0, dw = 0.0;
     std::vector<double> taper;
@@ -161,6 +162,8 @@ struct rick_plan {
     size_t img_cap = 0;
     int64_t launches = 0;
     cudaStream_t last_stream = nullptr;
+    float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
+    double tap_fit_error = 0.0;
 };
 
 namespace {
@@ -216,7 +219,7 @@ rick_status validate(const rick_config* c) {
     const int th = c->grid_threads ? c->grid_threads : 256;
     RK_ARG(th == 128 || th == 256 || th == 512, "grid_threads must be 128, 256 or 512");
     RK_ARG(c->fft_batch >= 0, "fft_batch must be >= 0");
-    RK_ARG(c->reserved == 0, "reserved must be 0");
+    RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 64, "tiles_per_grab must be in [0, 64]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     const uint64_t NT = (uint64_t)(c->N / T);
     const uint64_t nkeys = (uint64_t)c->n_channels * c->n_wplanes * NT * NT * 4ull;
@@ -269,6 +272,8 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     c.tile = P->T;
     P->threads = c.grid_threads ? c.grid_threads : 256;
     c.grid_threads = P->threads;
+    P->grab = c.tiles_per_grab ? c.tiles_per_grab : 8;
+    c.tiles_per_grab = P->grab;
     P->NT = c.N / P->T;
     P->nkeys = (uint64_t)c.n_channels * c.n_wplanes * (uint64_t)P->NT * P->NT * 4ull;
     if (c.n_wplanes > 1) {
@@ -278,6 +283,17 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaGetDevice(&P->device));
     RK_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
 
+    if (c.kernel_kind != RICK_KERNEL_TABLE) {
+        GridParams fit;
+        P->tap_fit_error = fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, fit);
+        std::memcpy(P->tap_coef, fit.coef, sizeof P->tap_coef);
+        if (!(P->tap_fit_error <= 1e-6)) {
+            set_err("kernel_param %g: the degree-%d tap polynomials reach only %.2e of the kernel "
+                    "(limit 1e-6); the kernel is too narrow for this support",
+                    c.kernel_param, kPolyDegree, P->tap_fit_error);
+            return RICK_ERR_UNSUPPORTED;
+        }
+    }
     const int taper_kind = c.kernel_kind == RICK_KERNEL_TABLE ? RICK_KERNEL_KAISER_BESSEL : c.kernel_kind;
     make_taper(taper_kind, c.kernel_param, c.support, c.N, P->taper);
     std::vector<float> inv(c.N);
@@ -404,12 +420,10 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.nk = k1 - k0;
     G.n_items = (uint32_t)items;
     G.kind = c.kernel_kind;
-    G.kb_beta = (float)c.kernel_param;
-    G.kb_inv_i0beta = (float)(1.0 / bessel_i0(c.kernel_param));
-    G.two_over_s = 2.0f / (float)c.support;
-    G.gauss_inv_2sigma2 = (float)(0.5 / (c.kernel_param * c.kernel_param));
+    std::memcpy(G.coef, P->tap_coef, sizeof G.coef);
     G.table = P->d_table;
     G.lattice = P->lattice;
+    G.grab = (uint32_t)P->grab;
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
     int launches = 0;
@@ -508,6 +522,20 @@ void plan_groups(const rick_plan* P, int* gc, int* gk) {
     }
 }
 
+rick_status ensure_group_grid(rick_plan* P) {
+    const rick_config& c = P->cfg;
+    int gc, gk;
+    plan_groups(P, &gc, &gk);
+    const size_t need = (size_t)gc * gk * (size_t)c.N * c.N * sizeof(float2);
+    if (need > P->grid_cap) {
+        dfree(P->d_grid);
+        P->grid_cap = 0;
+        RK_CUDA(cudaMalloc(&P->d_grid, need));
+        P->grid_cap = need;
+    }
+    return RICK_OK;
+}
+
 rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan_scale,
                              const float* vis, const float* weight, const uint8_t* flag,
                              int64_t nrow, float* image_real, float* image_complex,
@@ -519,13 +547,7 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
     int gc, gk;
     plan_groups(P, &gc, &gk);
     const size_t NN = (size_t)c.N * c.N;
-    const size_t need = (size_t)gc * gk * NN * sizeof(float2);
-    if (need > P->grid_cap) {
-        dfree(P->d_grid);
-        P->grid_cap = 0;
-        RK_CUDA(cudaMalloc(&P->d_grid, need));
-        P->grid_cap = need;
-    }
+    RK_TRY(ensure_group_grid(P));
     float* g = reinterpret_cast<float*>(P->d_grid);
     for (int c0 = 0; c0 < c.n_channels; c0 += gc) {
         const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
@@ -750,6 +772,179 @@ rick_status rick_plan_bins(rick_plan* plan, int64_t* n_keys, int64_t* n_records,
     if (records && total)
         RK_CUDA(cudaMemcpy(records, plan->d_records, sizeof(VisRecord) * total, cudaMemcpyDeviceToHost));
     return RICK_OK;
+}
+
+struct rick_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    rick_plan* plan = nullptr;
+    int64_t kernels = 0;  // this library's kernels per launch
+};
+
+rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double* chan_scale,
+                               const float* vis, const float* weight, const uint8_t* flag,
+                               int64_t nrow, float* grids, double* weight_sum, float* image_real,
+                               int64_t* counts, rick_graph** out) {
+    RK_ARG(plan && out && weight_sum && image_real, "plan, out, weight_sum and image_real are required");
+    *out = nullptr;
+    const rick_config& c = plan->cfg;
+    const int64_t nvis = nrow * (int64_t)c.n_channels;
+    RK_ARG(nrow >= 0, "nrow must be >= 0");
+    if (nvis > plan->cap_vis) {
+        set_err("graph capture: the plan is reserved for %lld visibilities, %lld requested; call "
+                "rick_plan_reserve first (nothing may allocate during capture)",
+                (long long)plan->cap_vis, (long long)nvis);
+        return RICK_ERR_CAPACITY;
+    }
+    if (!grids) RK_TRY(ensure_group_grid(plan));  // nothing may allocate during capture
+    cudaStream_t st = nullptr;
+    RK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(st);
+        set_err("cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+        return RICK_ERR_CUDA;
+    }
+    const size_t NN = (size_t)c.N * c.N;
+    const int64_t launches_before = plan->launches;
+    rick_status s = RICK_OK;
+    if (cudaMemsetAsync(image_real, 0, sizeof(float) * NN * c.n_channels, st) != cudaSuccess) {
+        set_err("cudaMemsetAsync of the image during capture failed");
+        s = RICK_ERR_CUDA;
+    }
+    if (grids) {
+        if (s == RICK_OK) s = bin_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts, st);
+        if (s == RICK_OK) s = grid_impl(plan, 0, c.n_channels, 0, c.n_wplanes, grids, st);
+        if (s == RICK_OK) s = fft_impl(plan, grids, (int64_t)c.n_channels * c.n_wplanes, st);
+        if (s == RICK_OK)
+            s = phase_impl(plan, grids, 0, c.n_channels, 0, c.n_wplanes, weight_sum, image_real, nullptr, st);
+    } else if (s == RICK_OK) {
+        s = dirty_image_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, image_real, nullptr,
+                             weight_sum, counts, st);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st, &g);
+    cudaStreamDestroy(st);
+    if (s != RICK_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    if (e != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        set_err("cudaStreamEndCapture: %s", cudaGetErrorString(e));
+        return RICK_ERR_CUDA;
+    }
+    rick_graph* G = new (std::nothrow) rick_graph();
+    if (!G) {
+        cudaGraphDestroy(g);
+        set_err("host allocation failed");
+        return RICK_ERR_OOM;
+    }
+    G->graph = g;
+    G->plan = plan;
+    G->kernels = plan->launches - launches_before;
+    plan->launches = launches_before;  // capturing launches nothing
+    e = cudaGraphInstantiate(&G->exec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        delete G;
+        set_err("cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        return RICK_ERR_CUDA;
+    }
+    *out = G;
+    return RICK_OK;
+}
+
+rick_status rick_graph_launch(rick_graph* graph, void* stream) {
+    RK_ARG(graph != nullptr, "graph is NULL");
+    RK_CUDA(cudaGraphLaunch(graph->exec, as_stream(stream)));
+    graph->plan->last_stream = as_stream(stream);
+    graph->plan->launches += graph->kernels;
+    return RICK_OK;
+}
+
+rick_status rick_graph_destroy(rick_graph* graph) {
+    if (!graph) return RICK_OK;
+    if (graph->exec) cudaGraphExecDestroy(graph->exec);
+    if (graph->graph) cudaGraphDestroy(graph->graph);
+    delete graph;
+    return RICK_OK;
+}
+
+rick_status rick_autotune(const rick_config* base, const double* uvw, const double* chan_scale,
+                          const float* vis, const float* weight, const uint8_t* flag,
+                          int64_t nrow, int32_t chan_begin, int32_t chan_end,
+                          int32_t plane_begin, int32_t plane_end, float* grids, int32_t reps,
+                          rick_tune_entry* results, int32_t max_results, int32_t* n_results,
+                          rick_config* best) {
+    RK_TRY(validate(base));
+    RK_ARG(n_results && best && grids, "n_results, best and grids are required");
+    RK_ARG(reps >= 1 && reps <= 100, "reps must be in [1, 100]");
+    RK_ARG(0 <= chan_begin && chan_begin < chan_end && chan_end <= base->n_channels, "channel range");
+    RK_ARG(0 <= plane_begin && plane_begin < plane_end && plane_end <= base->n_wplanes, "plane range");
+    *n_results = 0;
+    *best = *base;
+    float best_ms = 1e30f;
+    const int tiles[3] = {32, 64, 128};
+    const int threads[3] = {128, 256, 512};
+    const int grabs[3] = {2, 8, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    RK_CUDA(cudaEventCreate(&e0));
+    RK_CUDA(cudaEventCreate(&e1));
+    rick_status result = RICK_OK;
+    double* wsum = nullptr;
+    if (cudaMalloc(&wsum, sizeof(double) * base->n_channels) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        set_err("autotune: allocation failed");
+        return RICK_ERR_OOM;
+    }
+    for (int ti = 0; ti < 3 && result == RICK_OK; ++ti) {
+        rick_config cfg = *base;
+        cfg.tile = tiles[ti];
+        if (cfg.tile > cfg.N || cfg.support > cfg.tile) continue;
+        if (validate(&cfg) != RICK_OK) continue;  // e.g. bin space too large for this tile
+        rick_plan* P = nullptr;
+        result = rick_plan_create(&cfg, &P);
+        if (result != RICK_OK) break;
+        result = bin_impl(P, uvw, chan_scale, vis, weight, flag, nrow, wsum, nullptr, nullptr);
+        for (int hi = 0; hi < 3 && result == RICK_OK; ++hi) {
+            for (int gi = 0; gi < 3 && result == RICK_OK; ++gi) {
+                P->threads = threads[hi];
+                P->grab = grabs[gi];
+                std::vector<float> ms;
+                for (int r = 0; r <= reps && result == RICK_OK; ++r) {
+                    cudaEventRecord(e0, nullptr);
+                    result = grid_impl(P, chan_begin, chan_end, plane_begin, plane_end, grids, nullptr);
+                    cudaEventRecord(e1, nullptr);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) {
+                        set_err("autotune: a timed launch failed");
+                        result = RICK_ERR_CUDA;
+                    }
+                    float t = 0.f;
+                    cudaEventElapsedTime(&t, e0, e1);
+                    if (r > 0) ms.push_back(t);  // the first launch is the warm-up
+                }
+                if (result != RICK_OK) break;
+                std::sort(ms.begin(), ms.end());
+                const float med = ms[ms.size() / 2];
+                if (results && *n_results < max_results)
+                    results[*n_results] = rick_tune_entry{tiles[ti], threads[hi], grabs[gi], med};
+                ++*n_results;
+                if (med < best_ms) {
+                    best_ms = med;
+                    best->tile = tiles[ti];
+                    best->grid_threads = threads[hi];
+                    best->tiles_per_grab = grabs[gi];
+                }
+            }
+        }
+        rick_plan_destroy(P);
+    }
+    cudaFree(wsum);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
 }
 
 const char* rick_status_string(rick_status s) {

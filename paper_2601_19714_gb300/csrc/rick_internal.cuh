@@ -46,16 +46,28 @@ struct PlaceParams {
     float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
 };
 
+// Separable kernels are evaluated per footprint tap a from a polynomial in
+// t = 2 f - 1 (f = fractional offset in [0, 1)): g(a + 1 - S/2 - f) ~= sum_k
+// coef[a][k] t^k, degree kPolyDegree, fitted on the host in FP64 (Chebyshev
+// interpolation) and checked there against g to 1e-6 (typically 6e-8).
+constexpr int kMaxSupport = 16;
+constexpr int kPolyDegree = 11;
+
 struct GridParams {
     int N, S, T, NT, Nw;
     int c0, nc, k0, nk;
     uint32_t n_items;     // nc * nk * NT * NT tiles
     int kind;             // rick_kernel_kind
-    float kb_beta, kb_inv_i0beta, two_over_s;  // Kaiser-Bessel
-    float gauss_inv_2sigma2;                   // Gaussian
     const float* table;   // RICK_KERNEL_TABLE: [Nw][L+1][L+1][16]
     int lattice;
+    uint32_t grab;        // tiles taken from the work queue per atomic
+    float coef[kMaxSupport][kPolyDegree + 1];
 };
+
+// Fit the tap polynomials of a Gaussian or Kaiser-Bessel kernel of support S
+// (param = sigma or beta) into G.coef; returns the largest deviation from the
+// kernel found on a fine grid with FP32 Horner evaluation.
+double fit_tap_polynomials(int kind, double param, int S, GridParams& G);
 
 struct PhaseParams {
     int N, nc, nk;

@@ -67,16 +67,6 @@ rick_status scratch_address(unsigned char** out) {
     return RICK_OK;
 }
 
-double i0_series(double x) {
-    const double y = 0.25 * x * x;
-    double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 400 && term > 1e-17 * sum; ++k) {
-        term *= y / ((double)k * k);
-        sum += term;
-    }
-    return sum;
-}
-
 size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -193,12 +183,11 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         G.nk = plane_end - plane_begin;
         G.n_items = (uint32_t)items;
         G.kind = c.kernel_kind;
-        G.kb_beta = (float)c.kernel_param;
-        G.kb_inv_i0beta = (float)(1.0 / i0_series(c.kernel_param));
-        G.two_over_s = 2.0f / (float)c.support;
-        G.gauss_inv_2sigma2 = (float)(0.5 / (c.kernel_param * c.kernel_param));
+        if (!(fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, G) <= 1e-6))
+            return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: kernel too narrow for its support");
         G.table = nullptr;
         G.lattice = 0;
+        G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 64 ? (uint32_t)c.tiles_per_grab : 8u;
         e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
                         num_sms, st, &launches);
     }

@@ -28,7 +28,8 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
            "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_dirty_image",
            "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
-           "rick_plan_bins", "rick_grid_noalloc", "rick_status_string", "rick_last_error"]
+           "rick_plan_bins", "rick_grid_noalloc", "rick_graph_capture", "rick_graph_launch",
+           "rick_graph_destroy", "rick_autotune", "rick_status_string", "rick_last_error"]
 
 
 class RickError(RuntimeError):
@@ -42,8 +43,13 @@ class rick_config(C.Structure):
                 ("n_channels", C.c_int32), ("fov_rad", C.c_double), ("w_min", C.c_double),
                 ("w_max", C.c_double), ("kernel_param", C.c_double), ("kernel_kind", C.c_int32),
                 ("precision", C.c_int32), ("tile", C.c_int32), ("grid_threads", C.c_int32),
-                ("fft_batch", C.c_int32), ("reserved", C.c_int32),
+                ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
                 ("grid_budget_bytes", C.c_int64)]
+
+
+class rick_tune_entry(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("grid_threads", C.c_int32), ("tiles_per_grab", C.c_int32),
+                ("grid_ms", C.c_float)]
 
 
 _lib = None
@@ -74,6 +80,11 @@ def load(path: str = LIB_PATH):
         "rick_plan_sync_status": [p],
         "rick_plan_bins": [p, C.POINTER(i64), C.POINTER(i64), p, p],
         "rick_grid_noalloc": [C.POINTER(rick_config), p, p, p, p, p, i64, i32, i32, p, p, p, p],
+        "rick_graph_capture": [p, p, p, p, p, p, i64, p, p, p, p, C.POINTER(p)],
+        "rick_graph_launch": [p, p],
+        "rick_graph_destroy": [p],
+        "rick_autotune": [C.POINTER(rick_config), p, p, p, p, p, i64, i32, i32, i32, i32, p, i32,
+                          C.POINTER(rick_tune_entry), i32, C.POINTER(i32), C.POINTER(rick_config)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -147,13 +158,14 @@ class Config:
     tile: int = 0
     grid_threads: int = 0
     fft_batch: int = 0
+    tiles_per_grab: int = 0
     grid_budget_bytes: int = 0
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
                            self.w_min, self.w_max, self.kernel_param, KERNELS[self.kernel],
                            PRECISIONS[self.precision], self.tile, self.grid_threads,
-                           self.fft_batch, 0, self.grid_budget_bytes)
+                           self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes)
 
 
 class Plan:
@@ -270,6 +282,18 @@ class Plan:
             _ptr(weight_sum, d["f64"], "weight_sum", 8), _ptr(counts, d["i64"], "counts", 8),
             _stream(stream)), "rick_dirty_image")
 
+    def capture_graph(self, uvw, chan_scale, vis, weight, flag, nrow, grids, weight_sum,
+                      image_real, counts=None):
+        """Capture the whole path (all channels and planes) into a CUDA graph."""
+        d = _dt()
+        h = C.c_void_p()
+        _check(load().rick_graph_capture(
+            self.handle, *self._vis_args(uvw, chan_scale, vis, weight, flag), int(nrow),
+            _ptr(grids, d["c64"], "grids", 16), _ptr(weight_sum, d["f64"], "weight_sum", 8),
+            _ptr(image_real, d["f32"], "image_real", 8), _ptr(counts, d["i64"], "counts", 8),
+            C.byref(h)), "rick_graph_capture")
+        return Graph(h, self)
+
     def dirty_image_host(self, uvw, chan_scale, vis, weight, flag, image_real, weight_sum=None,
                          counts=None, stream=None):
         """Host buffers in and out (numpy arrays or CPU tensors, contiguous)."""
@@ -303,3 +327,46 @@ def grid_noalloc(cfg: Config, uvw, chan_scale, vis, weight, flag, nrow, plane_be
         _ptr(flag, d["u8"], "flag"), int(nrow), int(plane_begin), int(plane_end),
         _ptr(grids, d["c64"], "grids", 16), _ptr(weight_sum, d["f64"], "weight_sum", 8),
         _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_grid_noalloc")
+
+
+class Graph:
+    """A captured rick graph (keeps its plan alive)."""
+
+    def __init__(self, handle, plan):
+        self.handle = handle
+        self.plan = plan
+
+    def launch(self, stream=None):
+        _check(load().rick_graph_launch(self.handle, _stream(stream)), "rick_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rick_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def autotune(cfg: Config, uvw, chan_scale, vis, weight, flag, nrow, chan_range, plane_range,
+             grids, reps: int = 3):
+    """rick_autotune: returns (best Config, [(tile, threads, grab, ms), ...])."""
+    d = _dt()
+    c = cfg.c()
+    res = (rick_tune_entry * 64)()
+    n = C.c_int32()
+    best = rick_config()
+    _check(load().rick_autotune(
+        C.byref(c), _ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+        _ptr(vis, d["c64"], "vis", 8), _ptr(weight, d["f32"], "weight", 4),
+        _ptr(flag, d["u8"], "flag"), int(nrow), int(chan_range[0]), int(chan_range[1]),
+        int(plane_range[0]), int(plane_range[1]), _ptr(grids, d["c64"], "grids", 16), int(reps),
+        res, 64, C.byref(n), C.byref(best)), "rick_autotune")
+    from dataclasses import replace
+    out = replace(cfg, tile=best.tile, grid_threads=best.grid_threads,
+                  tiles_per_grab=best.tiles_per_grab)
+    table = [(r.tile, r.grid_threads, r.tiles_per_grab, float(r.grid_ms)) for r in res[:min(n.value, 64)]]
+    return out, table

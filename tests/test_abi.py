@@ -53,7 +53,7 @@ def test_status_strings(lib):
 @pytest.mark.parametrize("field,value", [("N", 100), ("N", 32), ("support", 0), ("support", 17),
                                          ("tile", 48), ("n_wplanes", 0), ("n_channels", 0),
                                          ("fov_rad", 1.5), ("kernel_param", -1.0),
-                                         ("grid_threads", 96), ("reserved", 1)])
+                                         ("grid_threads", 96), ("tiles_per_grab", 65)])
 def test_invalid_configs_rejected_on_host(lib, field, value):
     from paper_2601_19714_gb300 import rick
     cfg = rick.Config(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
