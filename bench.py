@@ -275,11 +275,13 @@ def run_ours(args):
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stage_events = []
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         start.record(stream)
         for _ in range(args.steps):
             stage_events.append(step(record=True))
         stop.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     launches = plan.launch_count() - launches0

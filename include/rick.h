@@ -236,6 +236,73 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
                           rick_tune_entry* results, int32_t max_results, int32_t* n_results,
                           rick_config* best);
 
+/* ---- learned support-4 kernel (pattern 4) ---------------------------- */
+
+/* A multilayer perceptron in[3] = (dx, dy, w-plane in [-1, 1]) -> H GELU ->
+ * H GELU -> 16 taps (tap t = 4b + a weighs footprint cell (i0 + a, j0 + b)),
+ * FP32, GELU in its tanh form.  Parameters are packed W1[H][3], b1[H],
+ * W2[H][H], b2[H], W3[16][H], b3[16]; H is 16, 32 or 64.  The paper grids with
+ * a Kaiser-Bessel kernel (Sec. 2, Eq. 3); the network replaces its taps at
+ * support 4, and the image is still divided by the support-4 Kaiser-Bessel
+ * taper, so the image stays linear in the taps. */
+int64_t rick_mlp_param_count(int32_t hidden);
+
+/* out[n][16] = mlp(in[n][3]).  work (nullable) receives [n][6H] saved values
+ * for rick_mlp_backward.  All device pointers. */
+rick_status rick_mlp_forward(const float* params, int32_t hidden, const float* in, int64_t n,
+                             float* out, float* work, void* stream);
+
+/* grad[P] += d(sum_i gout[i] . mlp(in[i]))/dparams for the n points
+ * (forward recomputed).  work: [n][6H] floats, scratch: [n][16] floats. */
+rick_status rick_mlp_backward(const float* params, int32_t hidden, const float* in, int64_t n,
+                              const float* gout, float* grad, float* work, float* scratch,
+                              void* stream);
+
+/* One Adam update (Kingma & Ba 2015) of n parameters; step counts from 1. */
+rick_status rick_adam_step(float* params, const float* grad, float* m, float* v, int64_t n,
+                           float lr, float beta1, float beta2, float eps, int32_t step,
+                           void* stream);
+
+/* The inputs of the baked table: out[Nw][L+1][L+1][3] = (ix/L, iy/L, plane
+ * coordinate (2k - (Nw-1))/(Nw-1)).  rick_mlp_forward on them gives the table
+ * rick_set_kernel_table takes. */
+rick_status rick_mlp_lattice_inputs(int32_t n_wplanes, int32_t lattice, float* out, void* stream);
+
+typedef struct rick_learn rick_learn;
+
+/* Training set-up: one channel of visibilities (uvw[nvis][3] in wavelengths
+ * and weight[nvis], device) placed once with the plan rules of cfg
+ * (kernel_kind RICK_KERNEL_TABLE, support 4, one channel, kernel_param = beta
+ * of the support-4 Kaiser-Bessel taper) and sorted by w-plane.  The tap table
+ * has lattice L (1..64). */
+rick_status rick_learn_create(const rick_config* cfg, int32_t lattice, const double* uvw,
+                              const float* weight, int64_t nvis, rick_learn** out);
+rick_status rick_learn_destroy(rick_learn* learn);
+
+/* Number of visibilities placed on the grid (the rest are skipped/dropped). */
+int64_t rick_learn_placed(const rick_learn* learn);
+
+/* One training field: sources[ns][3] = (pixel p, pixel q, flux) on pixel
+ * centres (host, 1..64), probes[np][2] pixels (host, 1..64).  Predicts the
+ * field's visibilities (Eq. 1), evaluates at the probes the w-stacking image
+ * that gridding with the tap table (device [Nw][L+1][L+1][16]) would give
+ * (Eq. 2, 3) and the direct Fourier inversion, and writes the loss
+ * sum_P (I_P - D_P)^2 / sum_P D_P^2 to loss[0] (device), grad_scale times
+ * its gradient with respect to the table to table_grad (device, same shape;
+ * overwritten, or added to if accumulate != 0, so that a batch of fields can
+ * be summed; nullable) and (I_P, D_P) pairs to image_dft[np][2] (device,
+ * nullable). */
+rick_status rick_learn_field_grad(rick_learn* learn, const float* table, const float* sources,
+                                  int32_t ns, const int32_t* probes, int32_t np,
+                                  float* table_grad, int32_t accumulate, float grad_scale,
+                                  float* loss, float* image_dft, void* stream);
+
+/* Supervised start: loss = mean (table - KB4 taps)^2 over the lattice and its
+ * gradient (device), where KB4 taps are g(a + 1 - 2 - dx) g(b + 1 - 2 - dy)
+ * of the support-4 Kaiser-Bessel. */
+rick_status rick_learn_pretrain_grad(rick_learn* learn, const float* table, float* table_grad,
+                                     float* loss, void* stream);
+
 /* ---- gridding without allocation ------------------------------------ */
 
 /* rick_grid for callers that may not allocate device memory once they run:

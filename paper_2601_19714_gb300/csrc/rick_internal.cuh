@@ -102,4 +102,14 @@ cudaError_t launch_phase_reduce(const PhaseParams& P, const float2* grids, const
 
 uint64_t scan_partials_needed(uint64_t n);
 
+// learned kernel network (rick_mlp.cu)
+int64_t mlp_param_count(int H);
+cudaError_t mlp_forward(const float* params, int H, const float* in, int64_t n, float* out,
+                        float* work, cudaStream_t st);
+cudaError_t mlp_backward(const float* params, int H, const float* in, int64_t n, const float* gout,
+                         float* grad, float* work, float* scratch_out, cudaStream_t st);
+cudaError_t adam_step(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1,
+                      float b2, float eps, int step, cudaStream_t st);
+cudaError_t lattice_inputs(int Nw, int L, float* out, cudaStream_t st);
+
 }  // namespace rick

@@ -1,0 +1,157 @@
+"""Learned support-4 gridding kernel (pattern 4): training loop, fields,
+checkpoints.
+
+The network (3 -> H GELU -> H GELU -> 16 taps) is trained on the GPU by the
+library's own kernels: ``rick_mlp_forward`` bakes the tap table on the
+lattice, ``rick_learn_field_grad`` images a point-source field with that table
+and measures it against the direct Fourier inversion at the source pixels,
+``rick_mlp_backward`` carries the table gradient into the network and
+``rick_adam_step`` updates it.  This module only orders those calls, draws the
+seeded fields, and saves/resumes the state (parameters, Adam moments, step).
+
+Start: a supervised fit of the support-4 Kaiser-Bessel taps (so the untrained
+starting point is the method without the learned part), then fields.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import rick
+
+
+def init_params(hidden: int, seed: int) -> np.ndarray:
+    """He-scaled normal weights, zero biases, packed W1, b1, W2, b2, W3, b3."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 0x4D4C50]))
+    H = hidden
+    W1 = g.normal(0, math.sqrt(2.0 / 3.0), (H, 3))
+    W2 = g.normal(0, math.sqrt(2.0 / H), (H, H))
+    W3 = g.normal(0, math.sqrt(1.0 / H), (16, H))
+    return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(),
+                           np.zeros(16)]).astype(np.float32)
+
+
+def training_field(seed: int, N: int, margin: int = 4, n_range=(1, 50),
+                   flux=(0.01, 1.0)) -> np.ndarray:
+    """A point-source field: 1-50 sources on pixel centres anywhere in the
+    image (margin pixels from the edge), fluxes log-uniform.  [ns, 3] (p, q, A)."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 0x46494C44]))
+    ns = int(g.integers(n_range[0], n_range[1] + 1))
+    pq = g.integers(margin, N - margin, size=(ns, 2))
+    a = np.exp(math.log(flux[0]) + g.random(ns) * (math.log(flux[1]) - math.log(flux[0])))
+    return np.concatenate([pq.astype(np.float64), a[:, None]], axis=1)
+
+
+@dataclass
+class TrainState:
+    step: int = 0
+    pretrain_step: int = 0
+    seed: int = 0
+    losses: list | None = None
+
+
+class LearnedKernel:
+    def __init__(self, n_wplanes: int, hidden: int = 64, lattice: int = 32, seed: int = 0):
+        import torch
+        self.Nw, self.H, self.L = n_wplanes, hidden, lattice
+        self.n_params = rick.mlp_param_count(hidden)
+        self.params = torch.from_numpy(init_params(hidden, seed)).cuda()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.grad = torch.zeros_like(self.params)
+        npts = n_wplanes * (lattice + 1) ** 2
+        self.lattice_in = torch.empty((npts, 3), dtype=torch.float32, device="cuda")
+        rick.mlp_lattice_inputs(n_wplanes, lattice, self.lattice_in)
+        self.table = torch.empty((npts, 16), dtype=torch.float32, device="cuda")
+        self.table_grad = torch.empty_like(self.table)
+        self.work = torch.empty((npts, 6 * hidden), dtype=torch.float32, device="cuda")
+        self.scratch = torch.empty((npts, 16), dtype=torch.float32, device="cuda")
+        self.loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self.state = TrainState(seed=seed, losses=[])
+        self.adam_t = 0
+
+    def bake(self):
+        """Evaluate the network on the lattice: the table the gridder reads."""
+        rick.mlp_forward(self.params, self.H, self.lattice_in, self.table)
+        return self.table
+
+    def _update(self, lr):
+        self.grad.zero_()
+        rick.mlp_backward(self.params, self.H, self.lattice_in, self.table_grad, self.grad,
+                          self.work, self.scratch)
+        self.adam_t += 1
+        rick.adam_step(self.params, self.grad, self.m, self.v, lr, self.adam_t)
+
+    def pretrain(self, learn: rick.Learn, steps: int, lr: float = 3e-3, log_every: int = 0):
+        for _ in range(steps):
+            self.bake()
+            learn.pretrain_grad(self.table, self.table_grad, self.loss)
+            self._update(lr)
+            self.state.pretrain_step += 1
+            if log_every and self.state.pretrain_step % log_every == 0:
+                self.state.losses.append(("pretrain", self.state.pretrain_step, float(self.loss.item())))
+        return float(self.loss.item())
+
+    def train(self, learn: rick.Learn, updates: int, lr: float = 1e-5, batch: int = 8,
+              N: int | None = None, log_every: int = 0, field_seed0: int = 1_000_000,
+              lr_final: float | None = None):
+        """``updates`` Adam steps, each on the mean gradient of ``batch`` fields
+        (field seeds field_seed0 + 0, 1, 2, ... in order, so a resumed run
+        sees the same sequence).  The learning rate decays on a cosine from lr
+        to lr_final (default lr / 10)."""
+        N = N or learn.cfg.N
+        lr_final = lr / 10 if lr_final is None else lr_final
+        last = []
+        for u in range(updates):
+            self.bake()
+            total = 0.0
+            for b in range(batch):
+                src = training_field(field_seed0 + self.state.step, N)
+                learn.field_grad(self.table, src, src[:, :2].astype(np.int32), self.table_grad,
+                                 self.loss, accumulate=b > 0, grad_scale=1.0 / batch)
+                self.state.step += 1
+                if log_every:
+                    total += float(self.loss.item())
+            c = 0.5 * (1 + math.cos(math.pi * u / max(1, updates)))
+            self._update(lr_final + (lr - lr_final) * c)
+            if log_every and (u + 1) % log_every == 0:
+                last.append(total / batch)
+                self.state.losses.append(("field", self.state.step, total / batch))
+        return last
+
+    def heldout_loss(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000):
+        """Mean and median loss over n held-out fields (seeds never trained on)."""
+        self.bake()
+        out = []
+        for s in range(n):
+            src = training_field(seed0 + s, learn.cfg.N)
+            learn.field_grad(self.table, src, src[:, :2].astype(np.int32), None, self.loss)
+            out.append(float(self.loss.item()))
+        return float(np.mean(out)), float(np.median(out))
+
+    # ---- checkpoint / resume ------------------------------------------------
+    def save(self, path: str):
+        np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(),
+                 v=self.v.cpu().numpy())
+        with open(path + ".json", "w") as f:
+            json.dump({"step": self.state.step, "pretrain_step": self.state.pretrain_step,
+                       "adam_t": self.adam_t, "seed": self.state.seed, "H": self.H,
+                       "L": self.L, "Nw": self.Nw}, f)
+
+    @classmethod
+    def load(cls, path: str) -> "LearnedKernel":
+        import torch
+        with open(path + ".json") as f:
+            meta = json.load(f)
+        k = cls(meta["Nw"], meta["H"], meta["L"], meta["seed"])
+        z = np.load(path if path.endswith(".npz") else path + ".npz")
+        k.params.copy_(torch.from_numpy(z["params"]))
+        k.m.copy_(torch.from_numpy(z["m"]))
+        k.v.copy_(torch.from_numpy(z["v"]))
+        k.state.step, k.state.pretrain_step = meta["step"], meta["pretrain_step"]
+        k.adam_t = meta["adam_t"]
+        return k

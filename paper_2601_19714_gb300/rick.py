@@ -29,7 +29,10 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_dirty_image",
            "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
            "rick_plan_bins", "rick_grid_noalloc", "rick_graph_capture", "rick_graph_launch",
-           "rick_graph_destroy", "rick_autotune", "rick_status_string", "rick_last_error"]
+           "rick_graph_destroy", "rick_autotune", "rick_mlp_param_count", "rick_mlp_forward",
+           "rick_mlp_backward", "rick_adam_step", "rick_mlp_lattice_inputs", "rick_learn_create",
+           "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
+           "rick_learn_pretrain_grad", "rick_status_string", "rick_last_error"]
 
 
 class RickError(RuntimeError):
@@ -90,6 +93,24 @@ def load(path: str = LIB_PATH):
         f = getattr(L, name)
         f.argtypes = args
         f.restype = st
+    f32 = C.c_float
+    for name, args in {
+        "rick_mlp_forward": [p, i32, p, i64, p, p, p],
+        "rick_mlp_backward": [p, i32, p, i64, p, p, p, p, p],
+        "rick_adam_step": [p, p, p, p, i64, f32, f32, f32, f32, i32, p],
+        "rick_mlp_lattice_inputs": [i32, i32, p, p],
+        "rick_learn_create": [C.POINTER(rick_config), i32, p, p, i64, C.POINTER(p)],
+        "rick_learn_destroy": [p],
+        "rick_learn_field_grad": [p, p, p, i32, p, i32, p, i32, f32, p, p, p],
+        "rick_learn_pretrain_grad": [p, p, p, p, p],
+    }.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = st
+    L.rick_mlp_param_count.argtypes = [i32]
+    L.rick_mlp_param_count.restype = i64
+    L.rick_learn_placed.argtypes = [p]
+    L.rick_learn_placed.restype = i64
     L.rick_plan_launch_count.argtypes = [p]
     L.rick_plan_launch_count.restype = i64
     L.rick_status_string.argtypes = [st]
@@ -370,3 +391,92 @@ def autotune(cfg: Config, uvw, chan_scale, vis, weight, flag, nrow, chan_range, 
                   tiles_per_grab=best.tiles_per_grab)
     table = [(r.tile, r.grid_threads, r.tiles_per_grab, float(r.grid_ms)) for r in res[:min(n.value, 64)]]
     return out, table
+
+
+# ---- learned kernel (pattern 4) -------------------------------------------
+
+def mlp_param_count(hidden: int) -> int:
+    return int(load().rick_mlp_param_count(hidden))
+
+
+def mlp_forward(params, hidden, inp, out, work=None, stream=None):
+    d = _dt()
+    n = inp.shape[0]
+    _check(load().rick_mlp_forward(_ptr(params, d["f32"], "params", 4), hidden,
+                                   _ptr(inp, d["f32"], "in", 4), int(n),
+                                   _ptr(out, d["f32"], "out", 4), _ptr(work, d["f32"], "work", 4),
+                                   _stream(stream)), "rick_mlp_forward")
+
+
+def mlp_backward(params, hidden, inp, gout, grad, work, scratch, stream=None):
+    d = _dt()
+    n = inp.shape[0]
+    _check(load().rick_mlp_backward(_ptr(params, d["f32"], "params", 4), hidden,
+                                    _ptr(inp, d["f32"], "in", 4), int(n),
+                                    _ptr(gout, d["f32"], "gout", 4), _ptr(grad, d["f32"], "grad", 4),
+                                    _ptr(work, d["f32"], "work", 4),
+                                    _ptr(scratch, d["f32"], "scratch", 4), _stream(stream)),
+           "rick_mlp_backward")
+
+
+def adam_step(params, grad, m, v, lr, step, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    d = _dt()
+    _check(load().rick_adam_step(_ptr(params, d["f32"]), _ptr(grad, d["f32"]), _ptr(m, d["f32"]),
+                                 _ptr(v, d["f32"]), int(params.numel()), float(lr), float(beta1),
+                                 float(beta2), float(eps), int(step), _stream(stream)),
+           "rick_adam_step")
+
+
+def mlp_lattice_inputs(n_wplanes, lattice, out, stream=None):
+    d = _dt()
+    _check(load().rick_mlp_lattice_inputs(int(n_wplanes), int(lattice), _ptr(out, d["f32"]),
+                                          _stream(stream)), "rick_mlp_lattice_inputs")
+
+
+class Learn:
+    """Training set-up of the learned kernel on a fixed visibility sample."""
+
+    def __init__(self, cfg: Config, lattice: int, uvw, weight):
+        d = _dt()
+        self._c = cfg.c()
+        h = C.c_void_p()
+        _check(load().rick_learn_create(C.byref(self._c), int(lattice), _ptr(uvw, d["f64"], "uvw", 8),
+                                        _ptr(weight, d["f32"], "weight", 4), int(uvw.shape[0]),
+                                        C.byref(h)), "rick_learn_create")
+        self.handle = h
+        self.cfg = cfg
+        self.lattice = lattice
+
+    def placed(self) -> int:
+        return int(load().rick_learn_placed(self.handle))
+
+    def field_grad(self, table, sources, probes, table_grad, loss, image_dft=None,
+                   accumulate=False, grad_scale=1.0, stream=None):
+        """sources: numpy [ns, 3] (p, q, flux); probes: numpy [np, 2] int pixels."""
+        import numpy as np
+        d = _dt()
+        src = np.ascontiguousarray(sources, dtype=np.float32)
+        prb = np.ascontiguousarray(probes, dtype=np.int32)
+        _check(load().rick_learn_field_grad(self.handle, _ptr(table, d["f32"]), src.ctypes.data,
+                                            src.shape[0], prb.ctypes.data, prb.shape[0],
+                                            _ptr(table_grad, d["f32"]), int(bool(accumulate)),
+                                            float(grad_scale), _ptr(loss, d["f32"]),
+                                            _ptr(image_dft, d["f32"]), _stream(stream)),
+               "rick_learn_field_grad")
+
+    def pretrain_grad(self, table, table_grad, loss, stream=None):
+        d = _dt()
+        _check(load().rick_learn_pretrain_grad(self.handle, _ptr(table, d["f32"]),
+                                               _ptr(table_grad, d["f32"]), _ptr(loss, d["f32"]),
+                                               _stream(stream)), "rick_learn_pretrain_grad")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().rick_learn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
