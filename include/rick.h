@@ -67,9 +67,10 @@ typedef enum {
 typedef enum {
     RICK_KERNEL_GAUSS = 0,          /* exp(-s^2/(2 sigma^2)), kernel_param = sigma in cells */
     RICK_KERNEL_KAISER_BESSEL = 1,  /* I0(beta sqrt(1-(2s/S)^2))/I0(beta), kernel_param = beta */
-    RICK_KERNEL_TABLE = 2           /* learned support-4 taps from rick_set_kernel_table;
-                                       kernel_param = beta of the support-4 Kaiser-Bessel
-                                       whose taper divides the image */
+    RICK_KERNEL_TABLE = 2           /* learned support 4: the Kaiser-Bessel taps (beta =
+                                       kernel_param) plus a correction table set by
+                                       rick_set_kernel_table; the image is divided by the
+                                       support-4 Kaiser-Bessel taper */
 } rick_kernel_kind;
 
 typedef enum {
@@ -116,11 +117,14 @@ rick_status rick_plan_reserve(rick_plan* plan, int64_t max_rows);
  * C(p) = integral_{-S/2}^{S/2} g(s) cos(2 pi s (p - N/2)/N) ds.  Host out. */
 rick_status rick_plan_taper(const rick_plan* plan, double* taper_host);
 
-/* Learned kernel: taps[Nw][L+1][L+1][16] (device, float32, copied into the
- * plan) on an (L+1)x(L+1) lattice of fractional offsets (dx, dy) in [0,1]^2
- * per w-plane; tap t = 4b + a weighs footprint cell (i0 + a, j0 + b).  The
- * gridder interpolates bilinearly between lattice points.  Only for plans
- * with kernel_kind = RICK_KERNEL_TABLE; 1 <= L <= 256. */
+/* Learned kernel: the correction taps[Nw][L+1][L+1][16] (device, float32,
+ * copied into the plan) on an (L+1)x(L+1) lattice of fractional offsets
+ * (dx, dy) in [0,1]^2 per w-plane; tap t = 4b + a weighs footprint cell
+ * (i0 + a, j0 + b).  The gridder interpolates the correction bilinearly
+ * between lattice points and adds it to the separable support-4
+ * Kaiser-Bessel taps g(a + 1 - 2 - dx) g(b + 1 - 2 - dy), so an all-zero table
+ * is exactly the Kaiser-Bessel kernel.  Only for plans with kernel_kind =
+ * RICK_KERNEL_TABLE; 1 <= L <= 256. */
 rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t lattice, void* stream);
 
 /* ---- the hot path ---------------------------------------------------- */
@@ -239,12 +243,13 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
 /* ---- learned support-4 kernel (pattern 4) ---------------------------- */
 
 /* A multilayer perceptron in[3] = (dx, dy, w-plane in [-1, 1]) -> H GELU ->
- * H GELU -> 16 taps (tap t = 4b + a weighs footprint cell (i0 + a, j0 + b)),
+ * H GELU -> 16 outputs (output t = 4b + a for footprint cell (i0 + a, j0 + b)),
  * FP32, GELU in its tanh form.  Parameters are packed W1[H][3], b1[H],
  * W2[H][H], b2[H], W3[16][H], b3[16]; H is 16, 32 or 64.  The paper grids with
- * a Kaiser-Bessel kernel (Sec. 2, Eq. 3); the network replaces its taps at
- * support 4, and the image is still divided by the support-4 Kaiser-Bessel
- * taper, so the image stays linear in the taps. */
+ * a Kaiser-Bessel kernel (Sec. 2, Eq. 3); the network's outputs are a
+ * correction to its support-4 taps (the Kaiser-Bessel stays as the fallback
+ * and as the untrained starting point), and the image is still divided by
+ * the support-4 Kaiser-Bessel taper, so it stays linear in the taps. */
 int64_t rick_mlp_param_count(int32_t hidden);
 
 /* out[n][16] = mlp(in[n][3]).  work (nullable) receives [n][6H] saved values
@@ -264,8 +269,8 @@ rick_status rick_adam_step(float* params, const float* grad, float* m, float* v,
                            void* stream);
 
 /* The inputs of the baked table: out[Nw][L+1][L+1][3] = (ix/L, iy/L, plane
- * coordinate (2k - (Nw-1))/(Nw-1)).  rick_mlp_forward on them gives the table
- * rick_set_kernel_table takes. */
+ * coordinate (2k - (Nw-1))/(Nw-1)).  rick_mlp_forward on them gives the
+ * correction table rick_set_kernel_table takes. */
 rick_status rick_mlp_lattice_inputs(int32_t n_wplanes, int32_t lattice, float* out, void* stream);
 
 typedef struct rick_learn rick_learn;
@@ -297,11 +302,6 @@ rick_status rick_learn_field_grad(rick_learn* learn, const float* table, const f
                                   float* table_grad, int32_t accumulate, float grad_scale,
                                   float* loss, float* image_dft, void* stream);
 
-/* Supervised start: loss = mean (table - KB4 taps)^2 over the lattice and its
- * gradient (device), where KB4 taps are g(a + 1 - 2 - dx) g(b + 1 - 2 - dy)
- * of the support-4 Kaiser-Bessel. */
-rick_status rick_learn_pretrain_grad(rick_learn* learn, const float* table, float* table_grad,
-                                     float* loss, void* stream);
 
 /* ---- gridding without allocation ------------------------------------ */
 

@@ -57,8 +57,9 @@
 enum { ORACLE_GAUSS = 0, ORACLE_KAISER_BESSEL = 1, ORACLE_LEARNED = 2 };
 
 /* Learned kernel: a multilayer perceptron 3 -> H -> H -> 16 with GELU
- * activations, whose 16 outputs are the taps of a support-4 kernel.  Its
- * weights are laid out in one FP64 array:
+ * activations, whose 16 outputs correct the 16 taps of the support-4
+ * Kaiser-Bessel kernel (beta = kernel_param): tap(a, b) = g(a + 1 - 2 - fx)
+ * g(b + 1 - 2 - fy) + out[4b + a].  Its weights are laid out in one FP64 array:
  *   W1[H][3], b1[H], W2[H][H], b2[H], W3[16][H], b3[16]. */
 #define ORACLE_MLP_IN 3
 #define ORACLE_MLP_OUT 16
@@ -286,9 +287,9 @@ static double plane_coordinate(int k, int Nw)
     return (2.0 * k - (Nw - 1)) / (double)(Nw - 1);
 }
 
-/* Taps of the learned kernel for fractional offsets (fx, fy) on plane k:
- * t[b*4 + a] weighs cell (i0 + a, j0 + b).  With a lattice L > 0 the network
- * is evaluated on the (L+1)^2 lattice points around (fx, fy) and the taps are
+/* Network correction of the learned kernel for fractional offsets (fx, fy)
+ * on plane k: t[b*4 + a] for cell (i0 + a, j0 + b).  With a lattice L > 0 the
+ * network is evaluated on the (L+1)^2 lattice points around (fx, fy) and
  * interpolated bilinearly; with L = 0 it is evaluated at (fx, fy) itself. */
 static void learned_taps(const oracle_cfg* cfg, double fx, double fy, int k, double t[16])
 {
@@ -465,9 +466,15 @@ static void footprint_weights(const oracle_cfg* cfg, const placement* P, double*
 {
     int S = cfg->S;
     if (cfg->kernel == ORACLE_LEARNED) {
+        /* Kaiser-Bessel support-4 taps plus the network's correction */
         double t[16];
         learned_taps(cfg, P->fx, P->fy, P->k, t);
-        for (int i = 0; i < 16 && i < S * S; ++i) gw[i] = t[i];
+        for (int b = 0; b < 4; ++b)
+            for (int a = 0; a < 4; ++a)
+                gw[b * 4 + a] =
+                    oracle_kernel_value(ORACLE_KAISER_BESSEL, cfg->kernel_param, 4, (double)(P->i0 + a) - P->x) *
+                        oracle_kernel_value(ORACLE_KAISER_BESSEL, cfg->kernel_param, 4, (double)(P->j0 + b) - P->y) +
+                    t[b * 4 + a];
         return;
     }
     double gxa[64], gyb[64];

@@ -283,9 +283,11 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaGetDevice(&P->device));
     RK_CUDA(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
 
-    if (c.kernel_kind != RICK_KERNEL_TABLE) {
+    {
+        // a table kernel is a learned correction added to the Kaiser-Bessel taps
+        const int fit_kind = c.kernel_kind == RICK_KERNEL_TABLE ? RICK_KERNEL_KAISER_BESSEL : c.kernel_kind;
         GridParams fit;
-        P->tap_fit_error = fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, fit);
+        P->tap_fit_error = fit_tap_polynomials(fit_kind, c.kernel_param, c.support, fit);
         std::memcpy(P->tap_coef, fit.coef, sizeof P->tap_coef);
         if (!(P->tap_fit_error <= 1e-6)) {
             set_err("kernel_param %g: the degree-%d tap polynomials reach only %.2e of the kernel "

@@ -14,7 +14,8 @@
 // the binning stores each visibility once with its halo class).
 //
 // Kernel taps: separable g(i - x) g(j - y) (Gaussian, Kaiser-Bessel), or the
-// learned non-separable 4x4 taps interpolated from a per-plane table.  Each
+// learned support-4 kernel: Kaiser-Bessel taps plus a non-separable 4x4
+// correction interpolated from a per-plane table.  Each
 // lane evaluates the 2S (or 16) taps of one record into a warp-private
 // staging area; then the warp walks the 32 records, lanes spread over the
 // footprint cells, and adds into shared memory (red.shared.add.f32).
@@ -104,7 +105,20 @@ __device__ __forceinline__ void accumulate_range(const GridParams& G,
         const float fy = (float)(rec.py & kFracMask) * kInvFrac;
         float* my = wstage + lane * stg;
         if (KIND == RICK_KERNEL_TABLE) {
+            // learned kernel: Kaiser-Bessel support-4 taps plus the network's
+            // correction, interpolated from the plane's lattice
             table_taps(G, k, fx, fy, my);
+            const float tx = fmaf(2.0f, fx, -1.0f), ty = fmaf(2.0f, fy, -1.0f);
+            float gx[4], gy[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                gx[a] = tap_poly<4>(G, a, tx);
+                gy[a] = tap_poly<4>(G, a, ty);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int a = 0; a < 4; ++a) my[4 * b + a] += gx[a] * gy[b];
         } else {
             const float tx = fmaf(2.0f, fx, -1.0f), ty = fmaf(2.0f, fy, -1.0f);
 #pragma unroll

@@ -11,6 +11,8 @@
 //   3. form the loss sum_P (I_P - D_P)^2 / sum_P D_P^2, and
 //   4. back-propagate it to the tap table (bilinear lattice, per plane),
 // after which rick_mlp_backward carries the table gradient into the network.
+// The table holds a correction added to the support-4 Kaiser-Bessel taps (so a
+// zero table is the Kaiser-Bessel kernel); its gradient is the tap gradient.
 //
 // Phases: with x = u fov + N/2 the continuous cell position, u l_p =
 // (x - N/2)(p - N/2)/N turns.  x - N/2 = X + f with X integer, so the turn is
@@ -142,9 +144,22 @@ __global__ void k_learn_predict(const LearnVis* __restrict__ vis, LearnConst C,
     wv[j] = make_float2(v.W * acc.x, v.W * acc.y);
 }
 
-// Taps of visibility v from the table (bilinear), t[b*4 + a].
+// The support-4 Kaiser-Bessel taps as polynomials in 2f - 1 (fitted on the host).
+struct KbTaps {
+    float coef[4][kPolyDegree + 1];
+};
+
+__device__ __forceinline__ float kb_tap(const KbTaps& K, int a, float t) {
+    float acc = K.coef[a][kPolyDegree];
+#pragma unroll
+    for (int q = kPolyDegree - 1; q >= 0; --q) acc = fmaf(acc, t, K.coef[a][q]);
+    return acc;
+}
+
+// Taps of visibility v: the Kaiser-Bessel products plus the correction
+// interpolated (bilinearly) from the table, t[b*4 + a].
 __device__ __forceinline__ void learn_taps(const float* __restrict__ table, int L, const LearnVis& v,
-                                           float* t) {
+                                           const KbTaps& K, float* t) {
     const float X = v.fx * L, Y = v.fy * L;
     const int ix = min((int)X, L - 1), iy = min((int)Y, L - 1);
     const float ax = X - ix, ay = Y - iy;
@@ -152,9 +167,17 @@ __device__ __forceinline__ void learn_taps(const float* __restrict__ table, int 
     const float* t00 = table + (((size_t)v.k * row + iy) * row + ix) * 16;
     const float* t01 = t00 + row * 16;
     const float w00 = (1.f - ax) * (1.f - ay), w10 = ax * (1.f - ay), w01 = (1.f - ax) * ay, w11 = ax * ay;
+    const float tx = fmaf(2.0f, v.fx, -1.0f), ty = fmaf(2.0f, v.fy, -1.0f);
+    float gx[4], gy[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        gx[a] = kb_tap(K, a, tx);
+        gy[a] = kb_tap(K, a, ty);
+    }
 #pragma unroll
     for (int q = 0; q < 16; ++q)
-        t[q] = w00 * __ldg(t00 + q) + w10 * __ldg(t00 + 16 + q) + w01 * __ldg(t01 + q) + w11 * __ldg(t01 + 16 + q);
+        t[q] = gx[q & 3] * gy[q >> 2] + w00 * __ldg(t00 + q) + w10 * __ldg(t00 + 16 + q) +
+               w01 * __ldg(t01 + q) + w11 * __ldg(t01 + 16 + q);
 }
 
 // Probe data in shared memory: per probe p, q (absolute), P = p - N/2, Q,
@@ -235,7 +258,7 @@ __device__ __forceinline__ void load_probes(ProbeSmem& pr, float2* s_ph, const i
 // I_P and D_P accumulated over all visibilities (out[2P], out[2P+1]).
 __global__ void __launch_bounds__(256)
 k_learn_forward(const LearnVis* __restrict__ vis, const float2* __restrict__ wv,
-                const float* __restrict__ table, LearnConst C, const int* __restrict__ pq,
+                const float* __restrict__ table, LearnConst C, KbTaps K, const int* __restrict__ pq,
                 const float4* __restrict__ pconst, const float2* __restrict__ ph,
                 float* __restrict__ out) {
     __shared__ ProbeSmem pr;
@@ -254,7 +277,7 @@ k_learn_forward(const LearnVis* __restrict__ vis, const float2* __restrict__ wv,
         if (ok) {
             v = vis[j];
             w2 = wv[j];
-            learn_taps(table, C.L, v, taps);
+            learn_taps(table, C.L, v, K, taps);
         } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) taps[q] = 0.f;
@@ -338,32 +361,6 @@ k_learn_backward(const LearnVis* __restrict__ vis, const float2* __restrict__ wv
         if (s_tg[i] != 0.f) atomicAdd(&g[i], s_tg[i]);
 }
 
-// Supervised start: taps of the support-4 Kaiser-Bessel, g_a(dx) g_b(dy), on the
-// lattice; gradient of mean squared difference.
-__global__ void k_learn_pretrain(const float* __restrict__ table, int Nw, int L, GridParams G,
-                                 float* __restrict__ grad, float* __restrict__ loss) {
-    const int64_t n = (int64_t)Nw * (L + 1) * (L + 1) * 16;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    float e2 = 0.f;
-    if (i < n) {
-        const int t = (int)(i % 16);
-        const int64_t pt = i / 16;
-        const int ix = (int)(pt % (L + 1)), iy = (int)((pt / (L + 1)) % (L + 1));
-        const float tx = 2.0f * ix / L - 1.0f, ty = 2.0f * iy / L - 1.0f;
-        const int a = t % 4, b = t / 4;
-        float ga = G.coef[a][kPolyDegree], gb = G.coef[b][kPolyDegree];
-        for (int q = kPolyDegree - 1; q >= 0; --q) {
-            ga = fmaf(ga, tx, G.coef[a][q]);
-            gb = fmaf(gb, ty, G.coef[b][q]);
-        }
-        const float d = table[i] - ga * gb;
-        grad[i] = 2.f * d / (float)n;
-        e2 = d * d / (float)n;
-    }
-    for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-    if ((threadIdx.x & 31) == 0 && e2 != 0.f) atomicAdd(loss, e2);
-}
-
 }  // namespace
 
 // ============================================================================
@@ -385,7 +382,7 @@ struct rick_learn {
     float2* d_ph = nullptr;
     float* d_idft = nullptr;  // [2 * kMaxProbes]
     float* d_ge = nullptr;
-    GridParams kb4;  // fitted KB taps for the supervised start
+    KbTaps kb4;  // fitted support-4 Kaiser-Bessel taps the correction adds to
 };
 
 namespace {
@@ -540,7 +537,12 @@ rick_status rick_learn_create(const rick_config* cfg, int32_t lattice, const dou
             Lr->taper[p] = acc;
         }
     }
-    fit_tap_polynomials(RICK_KERNEL_KAISER_BESSEL, c.kernel_param, kLearnS, Lr->kb4);
+    {
+        GridParams fit;
+        fit_tap_polynomials(RICK_KERNEL_KAISER_BESSEL, c.kernel_param, kLearnS, fit);
+        for (int a = 0; a < 4; ++a)
+            for (int q = 0; q <= kPolyDegree; ++q) Lr->kb4.coef[a][q] = fit.coef[a][q];
+    }
     *out = Lr;
     return RICK_OK;
 }
@@ -609,7 +611,7 @@ rick_status rick_learn_field_grad(rick_learn* Lr, const float* table, const floa
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int blocks = std::min((Lr->nvis + 255) / 256, sms * 4);
         const size_t ph_bytes = sizeof(float2) * Nw * kMaxProbes;
-        k_learn_forward<<<blocks, 256, ph_bytes, st>>>(Lr->d_vis, Lr->d_wv, table, C, Lr->d_pq,
+        k_learn_forward<<<blocks, 256, ph_bytes, st>>>(Lr->d_vis, Lr->d_wv, table, C, Lr->kb4, Lr->d_pq,
                                                        Lr->d_pconst, Lr->d_ph, Lr->d_idft);
         k_learn_loss<<<1, 32, 0, st>>>(Lr->d_idft, np, C.inv_wsum * grad_scale, loss, Lr->d_ge);
         chk(cudaGetLastError());
@@ -632,19 +634,6 @@ rick_status rick_learn_field_grad(rick_learn* Lr, const float* table, const floa
         snprintf(m, sizeof m, "rick_learn_field_grad: %s", cudaGetErrorString(e));
         return lfail(RICK_ERR_CUDA, m);
     }
-    return RICK_OK;
-}
-
-rick_status rick_learn_pretrain_grad(rick_learn* Lr, const float* table, float* table_grad,
-                                     float* loss, void* stream) {
-    if (!Lr || !table || !table_grad || !loss) return lfail(RICK_ERR_INVALID_ARG, "invalid argument");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int Nw = Lr->cfg.n_wplanes, L = Lr->L;
-    const int64_t n = (int64_t)Nw * (L + 1) * (L + 1) * 16;
-    if (cudaMemsetAsync(loss, 0, sizeof(float), st) != cudaSuccess)
-        return lfail(RICK_ERR_CUDA, "rick_learn_pretrain_grad: memset failed");
-    k_learn_pretrain<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(table, Nw, L, Lr->kb4, table_grad, loss);
-    if (cudaGetLastError() != cudaSuccess) return lfail(RICK_ERR_CUDA, "rick_learn_pretrain_grad: launch failed");
     return RICK_OK;
 }
 

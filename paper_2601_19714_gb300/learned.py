@@ -1,16 +1,18 @@
 """Learned support-4 gridding kernel (pattern 4): training loop, fields,
 checkpoints.
 
-The network (3 -> H GELU -> H GELU -> 16 taps) is trained on the GPU by the
-library's own kernels: ``rick_mlp_forward`` bakes the tap table on the
-lattice, ``rick_learn_field_grad`` images a point-source field with that table
-and measures it against the direct Fourier inversion at the source pixels,
-``rick_mlp_backward`` carries the table gradient into the network and
-``rick_adam_step`` updates it.  This module only orders those calls, draws the
-seeded fields, and saves/resumes the state (parameters, Adam moments, step).
+The network (3 -> H GELU -> H GELU -> 16 outputs) gives a correction to the
+support-4 Kaiser-Bessel taps.  It is trained on the GPU by the library's own
+kernels: ``rick_mlp_forward`` bakes the correction table on the lattice,
+``rick_learn_field_grad`` images a point-source field with Kaiser-Bessel taps
+plus that correction and measures it against the direct Fourier inversion at
+the source pixels, ``rick_mlp_backward`` carries the table gradient into the
+network and ``rick_adam_step`` updates it.  This module only orders those
+calls, draws the seeded fields, and saves/resumes the state (parameters, Adam
+moments, step).
 
-Start: a supervised fit of the support-4 Kaiser-Bessel taps (so the untrained
-starting point is the method without the learned part), then fields.
+Start: the output layer is zero, so the untrained kernel is exactly the
+support-4 Kaiser-Bessel -- the method without the learned part.
 """
 from __future__ import annotations
 
@@ -24,13 +26,16 @@ import numpy as np
 from . import rick
 
 
-def init_params(hidden: int, seed: int) -> np.ndarray:
-    """He-scaled normal weights, zero biases, packed W1, b1, W2, b2, W3, b3."""
+def init_params(hidden: int, seed: int, zero_output: bool = True) -> np.ndarray:
+    """He-scaled normal hidden weights, zero biases and (by default) a zero
+    output layer, packed W1, b1, W2, b2, W3, b3."""
     g = np.random.Generator(np.random.Philox(key=[seed, 0x4D4C50]))
     H = hidden
     W1 = g.normal(0, math.sqrt(2.0 / 3.0), (H, 3))
     W2 = g.normal(0, math.sqrt(2.0 / H), (H, H))
     W3 = g.normal(0, math.sqrt(1.0 / H), (16, H))
+    if zero_output:
+        W3[:] = 0.0
     return np.concatenate([W1.ravel(), np.zeros(H), W2.ravel(), np.zeros(H), W3.ravel(),
                            np.zeros(16)]).astype(np.float32)
 
@@ -49,17 +54,17 @@ def training_field(seed: int, N: int, margin: int = 4, n_range=(1, 50),
 @dataclass
 class TrainState:
     step: int = 0
-    pretrain_step: int = 0
     seed: int = 0
     losses: list | None = None
 
 
 class LearnedKernel:
-    def __init__(self, n_wplanes: int, hidden: int = 64, lattice: int = 32, seed: int = 0):
+    def __init__(self, n_wplanes: int, hidden: int = 64, lattice: int = 32, seed: int = 0,
+                 zero_output: bool = True):
         import torch
         self.Nw, self.H, self.L = n_wplanes, hidden, lattice
         self.n_params = rick.mlp_param_count(hidden)
-        self.params = torch.from_numpy(init_params(hidden, seed)).cuda()
+        self.params = torch.from_numpy(init_params(hidden, seed, zero_output)).cuda()
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
         self.grad = torch.zeros_like(self.params)
@@ -75,7 +80,7 @@ class LearnedKernel:
         self.adam_t = 0
 
     def bake(self):
-        """Evaluate the network on the lattice: the table the gridder reads."""
+        """Evaluate the network on the lattice: the correction table the gridder reads."""
         rick.mlp_forward(self.params, self.H, self.lattice_in, self.table)
         return self.table
 
@@ -85,16 +90,6 @@ class LearnedKernel:
                           self.work, self.scratch)
         self.adam_t += 1
         rick.adam_step(self.params, self.grad, self.m, self.v, lr, self.adam_t)
-
-    def pretrain(self, learn: rick.Learn, steps: int, lr: float = 3e-3, log_every: int = 0):
-        for _ in range(steps):
-            self.bake()
-            learn.pretrain_grad(self.table, self.table_grad, self.loss)
-            self._update(lr)
-            self.state.pretrain_step += 1
-            if log_every and self.state.pretrain_step % log_every == 0:
-                self.state.losses.append(("pretrain", self.state.pretrain_step, float(self.loss.item())))
-        return float(self.loss.item())
 
     def train(self, learn: rick.Learn, updates: int, lr: float = 1e-5, batch: int = 8,
               N: int | None = None, log_every: int = 0, field_seed0: int = 1_000_000,
@@ -138,8 +133,7 @@ class LearnedKernel:
         np.savez(path, params=self.params.cpu().numpy(), m=self.m.cpu().numpy(),
                  v=self.v.cpu().numpy())
         with open(path + ".json", "w") as f:
-            json.dump({"step": self.state.step, "pretrain_step": self.state.pretrain_step,
-                       "adam_t": self.adam_t, "seed": self.state.seed, "H": self.H,
+            json.dump({"step": self.state.step, "adam_t": self.adam_t, "seed": self.state.seed, "H": self.H,
                        "L": self.L, "Nw": self.Nw}, f)
 
     @classmethod
@@ -152,6 +146,6 @@ class LearnedKernel:
         k.params.copy_(torch.from_numpy(z["params"]))
         k.m.copy_(torch.from_numpy(z["m"]))
         k.v.copy_(torch.from_numpy(z["v"]))
-        k.state.step, k.state.pretrain_step = meta["step"], meta["pretrain_step"]
+        k.state.step = meta["step"]
         k.adam_t = meta["adam_t"]
         return k

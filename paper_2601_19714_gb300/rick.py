@@ -32,7 +32,7 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_graph_destroy", "rick_autotune", "rick_mlp_param_count", "rick_mlp_forward",
            "rick_mlp_backward", "rick_adam_step", "rick_mlp_lattice_inputs", "rick_learn_create",
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
-           "rick_learn_pretrain_grad", "rick_status_string", "rick_last_error"]
+           "rick_status_string", "rick_last_error"]
 
 
 class RickError(RuntimeError):
@@ -102,7 +102,6 @@ def load(path: str = LIB_PATH):
         "rick_learn_create": [C.POINTER(rick_config), i32, p, p, i64, C.POINTER(p)],
         "rick_learn_destroy": [p],
         "rick_learn_field_grad": [p, p, p, i32, p, i32, p, i32, f32, p, p, p],
-        "rick_learn_pretrain_grad": [p, p, p, p, p],
     }.items():
         f = getattr(L, name)
         f.argtypes = args
@@ -463,12 +462,6 @@ class Learn:
                                             float(grad_scale), _ptr(loss, d["f32"]),
                                             _ptr(image_dft, d["f32"]), _stream(stream)),
                "rick_learn_field_grad")
-
-    def pretrain_grad(self, table, table_grad, loss, stream=None):
-        d = _dt()
-        _check(load().rick_learn_pretrain_grad(self.handle, _ptr(table, d["f32"]),
-                                               _ptr(table_grad, d["f32"]), _ptr(loss, d["f32"]),
-                                               _stream(stream)), "rick_learn_pretrain_grad")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -362,23 +362,29 @@ def test_mlp_backward_matches_finite_differences(orc):
     np.testing.assert_allclose(grad, fd, atol=1e-7)
 
 
-def test_learned_kernel_taps_enter_the_grid(orc):
+def test_learned_kernel_is_kaiser_bessel_plus_its_correction(orc):
     """With a network whose only non-zero parameter is b3 = e_t, every
-    visibility puts W V (-1)^(i+j) on exactly footprint cell t."""
+    visibility adds W V (-1)^(i+j) on exactly footprint cell t on top of the
+    support-4 Kaiser-Bessel grid; with an all-zero network the learned kernel
+    is that Kaiser-Bessel."""
     H = 4
     n = orc.mlp_param_count(H)
     img, obs = tiny_wstack(9, nvis=50, N=64)
-    for t in (0, 5, 15):
+    kb = orc.Config(64, img.Nw, 4, "kb", KB_BETA_S4, img.fov, img.w_min, img.w_max)
+    G_kb = sum(orc.grid_plane(kb, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k)
+               for k in range(img.Nw))
+    for t in (None, 0, 5, 15):
         prm = np.zeros(n)
-        prm[n - 16 + t] = 1.0
+        if t is not None:
+            prm[n - 16 + t] = 1.0
         cfg = orc.Config(64, img.Nw, 4, "learned", KB_BETA_S4, img.fov, img.w_min, img.w_max,
                          mlp=prm, mlp_hidden=H)
         pl = orc.place(cfg, obs.uvw, obs.chan_scale, obs.weight)
         G = sum(orc.grid_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k)
                 for k in range(img.Nw))
-        ref = np.zeros((64, 64), complex)
+        ref = G_kb.copy()
         for r in range(50):
-            if pl["status"][r, 0] != 1:
+            if t is None or pl["status"][r, 0] != 1:
                 continue
             i = pl["i0"][r, 0] + t % 4
             j = pl["j0"][r, 0] + t // 4
