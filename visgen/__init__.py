@@ -234,11 +234,17 @@ def disk_observation(seed: int, nvis: int, N: int, fov: float, w_range: float, n
 
 def array_observation(seed: int, enu: np.ndarray, lat_deg: float, n_steps: int, duration_h: float,
                       freqs: np.ndarray, sources: np.ndarray, flag_fractions, weights: str = "unit",
-                      device: str | None = None, w_limit: float | None = None) -> Observation:
+                      device: str | None = None, w_limit: float | None = None,
+                      row_fraction: float = 1.0) -> Observation:
     """Earth-rotation synthesis of an array pointed at dec = latitude (the
     field transits the zenith), time-major rows.  With ``device`` the
-    visibilities are predicted by ``predict_torch`` on that device."""
+    visibilities are predicted by ``predict_torch`` on that device.  With
+    row_fraction < 1 a seeded subset of the rows is kept (before flags,
+    weights and visibilities are drawn)."""
     uvw_m = earth_rotation_uvw(baselines(enu), lat_deg, lat_deg, n_steps, duration_h)
+    if row_fraction < 1.0:
+        keep = rng(seed, "row-subset").random(uvw_m.shape[0]) < row_fraction
+        uvw_m = uvw_m[keep]
     lam0 = C_LIGHT / freqs[0]
     uvw = uvw_m / lam0
     scale = freqs / freqs[0]

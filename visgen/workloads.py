@@ -15,7 +15,7 @@ from dataclasses import dataclass, replace
 
 import numpy as np
 
-from . import (LOFAR_LAT_DEG, MEERKAT_LAT_DEG, Observation, array_observation, band,
+from . import (C_LIGHT, LOFAR_LAT_DEG, MEERKAT_LAT_DEG, Observation, array_observation, band,
                disk_observation, point_sources, stations_enu, w_extent)
 
 # Kaiser-Bessel shape for a grid with no oversampling (alpha = 1), from
@@ -55,18 +55,21 @@ def tiny_wstack(seed: int = 0, nvis: int = 20_000, N: int = 256, Nw: int = 8,
 
 def meerkat(seed: int = 0, n_ant: int = 64, n_steps: int = 1000, nchan: int = 16,
             N: int = 4096, Nw: int = 32, n_src: int = 200, fov_deg: float = 1.5,
-            device: str | None = None, flag_fraction: float = 0.05):
+            device: str | None = None, flag_fraction: float = 0.05,
+            freqs: np.ndarray | None = None, row_fraction: float = 1.0,
+            w_extent_lambda: float | None = None):
     """MeerKAT-shaped: 64 antennas uniform within 8 km (2016 baselines), an
     8 h track of 1000 steps, 16 channels over 856-1712 MHz (~32 M
     visibilities), float32 weights, 5 % flagged, 200 point sources with
     power-law fluxes; 4096^2 grid, 32 w-planes, Kaiser-Bessel S = 8, FoV 1.5 deg."""
     fov = math.radians(fov_deg)
     enu = stations_enu(seed, n_ant, 8000.0)
-    freqs = band(856e6, 1712e6, nchan)
+    freqs = band(856e6, 1712e6, nchan) if freqs is None else np.asarray(freqs, np.float64)
     src = point_sources(seed, n_src, fov, "powerlaw", 0.01, 10.0)
     obs = array_observation(seed, enu, MEERKAT_LAT_DEG, n_steps, 8.0, freqs, src,
-                            [flag_fraction] * nchan, weights="random", device=device)
-    wmax = w_extent(obs)
+                            [flag_fraction] * len(freqs), weights="random", device=device,
+                            row_fraction=row_fraction)
+    wmax = w_extent(obs) if w_extent_lambda is None else w_extent_lambda
     img = Imaging(N, Nw, 8, "kb", KB_BETA_S8, fov, -wmax, wmax)
     return img, obs
 
@@ -107,7 +110,7 @@ def learned_field(seed: int, nvis: int = 2_000_000, N: int = 2048, Nw: int = 16,
     return img, obs
 
 
-def test_positions(N: int, count: int = 64, seed: int = 1234) -> np.ndarray:
+def evaluation_positions(N: int, count: int = 64, seed: int = 1234) -> np.ndarray:
     """Pixel positions (p, q) used to judge the learned kernel: the four
     corners and four edge midpoints of the field (8 pixels in from the edge),
     the centre, and seeded random positions for the rest."""
@@ -121,8 +124,17 @@ def test_positions(N: int, count: int = 64, seed: int = 1234) -> np.ndarray:
 
 
 def meerkat_large(seed: int = 0, n_steps: int = 5800, nchan: int = 128, N: int = 16384,
-                  Nw: int = 32, n_src: int = 200, device: str | None = None):
+                  Nw: int = 32, n_src: int = 200, device: str | None = None,
+                  channels: slice | None = None, row_fraction: float = 1.0):
     """Large precision stress: MeerKAT layout, 8 h track of ~5800 steps, 128
-    channels (~1.5 G visibilities), 16384^2 grid, 32 w-planes streamed in
-    groups, FoV 1.5 deg, Kaiser-Bessel S = 8."""
-    return meerkat(seed, 64, n_steps, nchan, N, Nw, n_src, 1.5, device)
+    channels over 856-1712 MHz (~1.5 G visibilities), 16384^2 grid, 32
+    w-planes streamed in groups, FoV 1.5 deg, Kaiser-Bessel S = 8.
+    ``channels`` selects a block of the 128 channels (uvw then refer to the
+    block's first channel) and ``row_fraction`` a seeded subset of rows; the w
+    range of the planes is that of the whole band, so every block shares the
+    same planes."""
+    freqs = band(856e6, 1712e6, nchan)
+    wmax = 8000.0 / (C_LIGHT / freqs[-1])   # longest baseline at the top of the band
+    sel = freqs[channels] if channels is not None else freqs
+    return meerkat(seed, 64, n_steps, nchan, N, Nw, n_src, 1.5, device, freqs=sel,
+                   row_fraction=row_fraction, w_extent_lambda=wmax)
