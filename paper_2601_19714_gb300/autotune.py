@@ -47,6 +47,7 @@ def tuned(cfg: rick.Config, n_vis: int, cache_path: str, tune_fn=None, gpu_name:
     e = {"tile": best.tile, "grid_threads": best.grid_threads,
          "tiles_per_grab": best.tiles_per_grab, "table": table}
     cache[key] = e
+    os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
     tmp = cache_path + ".tmp"
     with open(tmp, "w") as f:
         json.dump(cache, f, indent=1)
