@@ -12,13 +12,17 @@ device->host copy of the images inside the timed region.
 Workload (default): the MeerKAT-shaped configuration -- 64 antennas, 2016
 baselines x 1000 steps x 16 channels (856-1712 MHz) = 32.3 M visibilities,
 5 % flagged, 200 point sources, 4096^2 grid, 32 w-planes, Kaiser-Bessel S = 8,
-FoV 1.5 deg.  Synthetic, seeded.
+FoV 1.5 deg.  Synthetic, seeded.  The headline path uses the Hermitian fold
+(the 32 w-planes held as 16 stored planes, exact for the real image; see
+hermitian_fold in include/rick.h); the path without it is timed beside it
+and reported under "other_variant" (--no-fold swaps the two).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -119,11 +123,11 @@ def make_workload(seed: int, device: str, world: int = 1, rank: int = 0):
     return img, obs
 
 
-def plan_config(img, nchan):
+def plan_config(img, nchan, fold=False):
     from paper_2601_19714_gb300 import rick
     return rick.Config(N=img.N, n_wplanes=img.Nw, support=img.S, n_channels=nchan,
                        fov_rad=img.fov, w_min=img.w_min, w_max=img.w_max, kernel="kb",
-                       kernel_param=img.kernel_param)
+                       kernel_param=img.kernel_param, hermitian_fold=fold)
 
 
 # --------------------------------------------------------------------------
@@ -240,75 +244,95 @@ def run_ours(args):
                vis=obs.vis, weight=torch.from_numpy(obs.weight).cuda(),
                flag=torch.from_numpy(obs.flag).cuda())
     nrow = obs.nrow
-    # launch shape of the gridder: autotuned on two channels of this data
-    # (pattern 2), cached per problem class; untimed set-up
     from paper_2601_19714_gb300 import autotune
-    base = plan_config(img, C)
-    g2 = torch.empty((2, Nw, N, N), dtype=torch.complex64, device="cuda")
-    tuned, entry = autotune.tuned(
-        base, nrow * C, os.path.join(ROOT, "_build_cache", "autotune.json"),
-        lambda: rick.autotune(base, dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"],
-                              dev["flag"], nrow, (0, 2), (0, Nw), g2, reps=2))
-    del g2
-    torch.cuda.empty_cache()
-    plan = rick.Plan(tuned)
-    plan.reserve(nrow)
-    grids = torch.empty((C, Nw, N, N), dtype=torch.complex64, device="cuda")
-    image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
-    wsum = torch.empty(C, dtype=torch.float64, device="cuda")
-    counts = torch.empty(2, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    ev = {k: [] for k in ("t0", "t1", "t2", "t3", "t4")}
+    def tuned_config(fold):
+        # launch shape of the gridder: autotuned on two channels of this data
+        # (pattern 2), cached per problem class; untimed set-up
+        base = plan_config(img, C, fold)
+        ns = base.stored_planes
+        g2 = torch.empty((2, ns, N, N), dtype=torch.complex64, device="cuda")
+        cfg, _ = autotune.tuned(
+            base, nrow * C, os.path.join(ROOT, "_build_cache", "autotune.json"),
+            lambda: rick.autotune(base, dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"],
+                                  dev["flag"], nrow, (0, 2), (0, ns), g2, reps=2))
+        del g2
+        torch.cuda.empty_cache()
+        return cfg
 
-    def step(record=False):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
-        image.zero_()
-        if e: e[0].record(stream)
-        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], nrow,
-                 wsum, counts)
-        if e: e[1].record(stream)
-        plan.grid_binned(0, C, 0, Nw, grids)
-        if e: e[2].record(stream)
-        plan.fft_wplanes(grids, C * Nw)
-        if e: e[3].record(stream)
-        plan.phase_correct_reduce(grids, 0, C, 0, Nw, wsum, image)
-        if e: e[4].record(stream)
-        return e
+    def measure(cfg, steps, warmup, clocks):
+        """Time `steps` whole-path steps (bin, grid, FFT, phase/reduce) of the
+        plan for cfg; per-stage CUDA events on the launching stream."""
+        plan = rick.Plan(cfg)
+        plan.reserve(nrow)
+        ns = cfg.stored_planes
+        grids = torch.empty((C, ns, N, N), dtype=torch.complex64, device="cuda")
+        image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+        wsum = torch.empty(C, dtype=torch.float64, device="cuda")
+        counts = torch.empty(2, dtype=torch.int64, device="cuda")
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    n_grid, n_drop = counts.cpu().tolist()
+        def step(record=False):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+            image.zero_()
+            if e: e[0].record(stream)
+            plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], nrow,
+                     wsum, counts)
+            if e: e[1].record(stream)
+            plan.grid_binned(0, C, 0, ns, grids)
+            if e: e[2].record(stream)
+            plan.fft_wplanes(grids, C * ns)
+            if e: e[3].record(stream)
+            plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+            if e: e[4].record(stream)
+            return e
 
-    launches0 = plan.launch_count()
-    rdist.barrier()
-    torch.cuda.synchronize()
-    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stage_events = []
-    with ClockSampler(local) as clk:
-        torch.cuda.nvtx.range_push("timed")
-        start.record(stream)
-        for _ in range(args.steps):
-            stage_events.append(step(record=True))
-        stop.record(stream)
+        for _ in range(warmup):
+            step()
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    rdist.barrier()
-    launches = plan.launch_count() - launches0
-    ms_max = rdist.max_over_ranks(start.elapsed_time(stop) / args.steps, device="cuda")
+        n_grid, n_drop = counts.cpu().tolist()
+        launches0 = plan.launch_count()
+        rdist.barrier()
+        torch.cuda.synchronize()
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stage_events = []
+        with (ClockSampler(local) if clocks else contextlib.nullcontext()) as clk:
+            torch.cuda.nvtx.range_push("timed")
+            start.record(stream)
+            for _ in range(steps):
+                stage_events.append(step(record=True))
+            stop.record(stream)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        rdist.barrier()
+        launches = plan.launch_count() - launches0
+        ms = rdist.max_over_ranks(start.elapsed_time(stop) / steps, device="cuda")
+        stage_ms = {"bin": [], "grid": [], "fft": [], "phase": []}
+        for e in stage_events:
+            stage_ms["bin"].append(e[0].elapsed_time(e[1]))
+            stage_ms["grid"].append(e[1].elapsed_time(e[2]))
+            stage_ms["fft"].append(e[2].elapsed_time(e[3]))
+            stage_ms["phase"].append(e[3].elapsed_time(e[4]))
+        st = {k: statistics.median(v) for k, v in stage_ms.items()}
+        out = dict(ms=ms, st=st, launches=launches, n_grid=n_grid, n_drop=n_drop,
+                   clocks=clk.summary() if clocks else None, img_ch0=image[0].cpu().numpy(),
+                   taper=plan.taper())
+        del grids, image, plan
+        torch.cuda.empty_cache()
+        return out
 
-    stage_ms = {"bin": [], "grid": [], "fft": [], "phase": []}
-    for e in stage_events:
-        stage_ms["bin"].append(e[0].elapsed_time(e[1]))
-        stage_ms["grid"].append(e[1].elapsed_time(e[2]))
-        stage_ms["fft"].append(e[2].elapsed_time(e[3]))
-        stage_ms["phase"].append(e[3].elapsed_time(e[4]))
-    st = {k: statistics.median(v) for k, v in stage_ms.items()}
+    fold = not args.no_fold
+    tuned = tuned_config(fold)
+    other_cfg = tuned_config(not fold)
+    other = measure(other_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
+    res = measure(tuned, args.steps, args.warmup, clocks=True)
+    st, ms_max, launches = res["st"], res["ms"], res["launches"]
+    n_grid, n_drop = res["n_grid"], res["n_drop"]
+    Nst = tuned.stored_planes
 
     hbm, peak_kind = peaks()
     NN = N * N
-    cells = C * Nw * NN
+    cells = C * Nst * NN
     b_grid = 8.0 * cells + 16.0 * n_grid                  # write every cell once + read each record
     b_fft = 2 * 8.0 * cells                               # one read + one write per plane (minimum)
     b_phase = 8.0 * cells + 8.0 * C * NN                  # read planes + image read/write
@@ -320,8 +344,6 @@ def run_ours(args):
     dom_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase}[dominant]
 
     # ---- end to end through the host entry point -------------------------------
-    del grids
-    torch.cuda.empty_cache()
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_uvw, h_sc = pin(obs.uvw), pin(obs.chan_scale)
     h_vis = obs.vis.cpu().pin_memory()
@@ -346,7 +368,7 @@ def run_ours(args):
     h2d = (h_uvw.numel() * 8 + h_sc.numel() * 8 + h_vis.numel() * 8 + h_w.numel() * 4 +
            h_f.numel())
     d2h = h_img.numel() * 4 + h_ws.numel() * 8 + 16
-    img_ch0 = image[0].cpu().numpy()
+    img_ch0 = res["img_ch0"]
     del eplan
 
     if rank == 0:
@@ -359,11 +381,12 @@ def run_ours(args):
             "config": {"workload": "meerkat_4096sq_32w_16ch_kb8", "antennas": 64,
                        "baselines": 2016, "time_steps": 1000, "channels": C,
                        "visibilities": int(nrow * C), "gridded": int(n_grid),
-                       "dropped": int(n_drop), "N": N, "w_planes": Nw, "support": img.S,
+                       "dropped": int(n_drop), "N": N, "w_planes": Nw,
+                       "hermitian_fold": fold, "stored_planes": Nst, "support": img.S,
                        "kernel": "kaiser_bessel", "index_phase": "fp64", "fov_deg": round(math.degrees(img.fov), 4),
                        "tile": tuned.tile, "grid_threads": tuned.grid_threads,
                        "tiles_per_grab": tuned.tiles_per_grab, "launch_shape": "autotuned",
-                       "l2": "inputs larger than L2 (grids 68.7 GB, not flushed)",
+                       "l2": f"inputs larger than L2 (grids {8 * cells / 1e9:.1f} GB, not flushed)",
                        "parallelism": f"channel blocks x{world} (16 channels per rank, no collective on the data path)"},
             "stages_ms": st,
             "stage_gbs": gbs,
@@ -381,13 +404,20 @@ def run_ours(args):
             "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
-            "clocks": clk.summary(),
+            "clocks": res["clocks"],
+            "other_variant": {
+                "hermitian_fold": not fold, "stored_planes": other_cfg.stored_planes,
+                "value": other["n_grid"] * world / (other["ms"] * 1e-3), "unit": UNIT,
+                "ms_per_step": other["ms"], "stages_ms": other["st"],
+                "steps": max(1, min(args.steps, 3)),
+                "tile": other_cfg.tile, "grid_threads": other_cfg.grid_threads,
+                "tiles_per_grab": other_cfg.tiles_per_grab},
         }
         if not args.no_cpu_baseline:
             r, nv, s, desc = oracle_sample(img, obs, 2)
             line["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": desc, "seconds": s}
-            err, npix = image_error_probe(img, obs, img_ch0, plan.taper())
+            err, npix = image_error_probe(img, obs, img_ch0, res["taper"])
             line["image_error"] = {"max_rel_vs_fp64_oracle": err, "probe_pixels": npix,
                                    "channel": 0, "how": "oracle O1 per-visibility form"}
         print(json.dumps(line), flush=True)
@@ -607,6 +637,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fold", action="store_true",
+                    help="headline without the Hermitian fold (all Nw planes stored and "
+                         "transformed); the other variant is always measured beside it")
     ap.add_argument("--workload", default="meerkat",
                     choices=["meerkat", "lofar", "learned", "large"],
                     help="meerkat (default bench line); lofar / learned / large measure the "

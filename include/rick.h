@@ -93,7 +93,26 @@ typedef struct rick_config {
     int32_t fft_batch;    /* planes per cuFFT execution (0 = up to 4 GiB of planes) */
     int32_t tiles_per_grab; /* tiles a gridder CTA takes from the work queue at once: 1..64 (0 = 8) */
     int64_t grid_budget_bytes; /* rick_dirty_image: device bytes for plane groups (0 = all) */
+    /* Hermitian fold (0 = off).  The dirty image is the real part of the sum
+     * over planes in Eq. 2, and Re(z) = Re(conj z), so a visibility V at
+     * (u, v) on plane k contributes exactly what conj(V) at (-u, -v) on the
+     * plane of w = -w_k contributes.  With the fold on, every visibility whose
+     * plane k lies in the upper half (2k > Nw - 1) is gridded as its conjugate
+     * on plane Nw - 1 - k at the mirrored cells (N - i) mod N, (N - j) mod N,
+     * with the same kernel taps.  Only the lower ceil(Nw/2) planes are then
+     * stored, transformed and reduced: every plane index, plane range and
+     * grid array of the API counts stored planes, and the real image equals
+     * the unfolded one up to FP32 rounding (the imaginary part of the
+     * complex image is not the unfolded one).  The placement decisions (plane,
+     * footprint, drop) are those of the unfolded visibility.  Requires
+     * w_min == -w_max (so that plane Nw - 1 - k sits at -w_k) and a
+     * point-symmetric kernel (Gaussian or Kaiser-Bessel, not TABLE). */
+    int32_t hermitian_fold;
 } rick_config;
+
+/* Planes a plan stores for cfg: ceil(Nw / 2) with the Hermitian fold, Nw
+ * without; -1 if cfg is NULL. */
+int32_t rick_stored_planes(const rick_config* cfg);
 
 typedef struct rick_plan rick_plan;
 

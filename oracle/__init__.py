@@ -250,6 +250,37 @@ def grid_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, 
     return out
 
 
+def mirror(G: np.ndarray) -> np.ndarray:
+    """M[j, i] = G[(N - j) mod N, (N - i) mod N]: the cell of (-u, -v) on the
+    mesh (cell i sits at u = (i - N/2)/FoV; cell N, the image of cell 0, is
+    cell 0 again on the periodic mesh the inverse DFT sees)."""
+    G = np.asarray(G)
+    N = G.shape[0]
+    j = (N - np.arange(N)) % N
+    return G[np.ix_(j, j)]
+
+
+def fold_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, plane=0):
+    """Stored plane ``plane`` under the Hermitian fold, complex128 [N, N].
+
+    The dirty image is the real part of the sum over planes in Eq. 2 and
+    Re(z) = Re(conj z); with w_min = -w_max, plane Nw-1-k sits at -w_k, so
+    the contribution of plane k' = Nw-1-k equals that of the conjugate of
+    its grid mirrored to (-u, -v) on plane k.  Definition:
+        H_k = G_k + conj(mirror(G_{Nw-1-k}))   for 2k < Nw - 1,
+        H_k = G_k                              for 2k = Nw - 1 (odd Nw).
+    """
+    if cfg.w_min != -cfg.w_max:
+        raise ValueError("the fold needs w_min == -w_max")
+    if not 0 <= 2 * plane <= cfg.Nw - 1:
+        raise ValueError("stored planes are 0 .. ceil(Nw/2) - 1")
+    G = grid_plane(cfg, uvw, chan_scale, vis, weight, flag, channel, plane)
+    k2 = cfg.Nw - 1 - plane
+    if k2 == plane:
+        return G
+    return G + np.conj(mirror(grid_plane(cfg, uvw, chan_scale, vis, weight, flag, channel, k2)))
+
+
 def image(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0):
     """Complex w-stacking dirty image of one channel (O1), complex128 [N, N]
     indexed [q, p] (m row, l column), and the channel's sum of weights."""

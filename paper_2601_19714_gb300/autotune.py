@@ -3,8 +3,8 @@
 ``rick_autotune`` (native, in librick) times every valid (tile side, CTA size,
 tiles per grab) on the caller's own data.  This module keys the winners by
 what decides them -- grid side, support, planes, channels, kernel, the
-visibility density per 64x64 tile per plane (as a power of two) and the GPU
-name -- and keeps them in a JSON file so that later plans reuse them.
+Hermitian fold, the visibility density per 64x64 tile per stored plane (as a
+power of two) and the GPU name -- and keeps them in a JSON file so that later plans reuse them.
 """
 from __future__ import annotations
 
@@ -17,12 +17,13 @@ from . import rick
 
 
 def density_class(cfg: rick.Config, n_vis: int) -> int:
-    tiles = cfg.n_channels * cfg.n_wplanes * (cfg.N // 64) ** 2
+    tiles = cfg.n_channels * cfg.stored_planes * (cfg.N // 64) ** 2
     return int(round(math.log2(max(n_vis, 1) / tiles + 1e-9)))
 
 
 def cache_key(cfg: rick.Config, n_vis: int, gpu_name: str) -> str:
     return (f"N{cfg.N}-S{cfg.support}-Nw{cfg.n_wplanes}-C{cfg.n_channels}-{cfg.kernel}-"
+            f"{'fold-' if cfg.hermitian_fold else ''}"
             f"d{density_class(cfg, n_vis)}-{gpu_name.replace(' ', '_')}")
 
 

@@ -129,6 +129,7 @@ struct rick_plan {
     rick_config cfg;
     int device = 0, num_sms = 0;
     int T = 64, NT = 0, threads = 256, grab = 8;
+    int planes = 0;  // stored planes: ceil(Nw/2) with the Hermitian fold, else Nw
     uint64_t nkeys = 0;
     double w_scale = 0.0, dw = 0.0;
     std::vector<double> taper;
@@ -196,6 +197,10 @@ void release(rick_plan* P) {
     P->have_b = P->have_1 = false;
 }
 
+int stored_planes(const rick_config& c) {
+    return c.hermitian_fold ? (c.n_wplanes + 1) / 2 : c.n_wplanes;
+}
+
 rick_status validate(const rick_config* c) {
     RK_ARG(c != nullptr, "cfg is NULL");
     RK_ARG(c->N >= 64 && c->N <= 65536 && (c->N & (c->N - 1)) == 0,
@@ -221,8 +226,14 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->fft_batch >= 0, "fft_batch must be >= 0");
     RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 64, "tiles_per_grab must be in [0, 64]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
+    RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
+    if (c->hermitian_fold) {
+        RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE,
+               "hermitian_fold needs a point-symmetric kernel (Gaussian or Kaiser-Bessel)");
+        RK_ARG(c->w_min == -c->w_max, "hermitian_fold needs w_min == -w_max");
+    }
     const uint64_t NT = (uint64_t)(c->N / T);
-    const uint64_t nkeys = (uint64_t)c->n_channels * c->n_wplanes * NT * NT * 4ull;
+    const uint64_t nkeys = (uint64_t)c->n_channels * stored_planes(*c) * NT * NT * 4ull;
     if (nkeys >= 0xFFFFFFFFull) {
         set_err("channels x planes x tiles exceeds the 32-bit bin space; use a larger tile or "
                 "fewer channels per plan");
@@ -275,7 +286,8 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     P->grab = c.tiles_per_grab ? c.tiles_per_grab : 8;
     c.tiles_per_grab = P->grab;
     P->NT = c.N / P->T;
-    P->nkeys = (uint64_t)c.n_channels * c.n_wplanes * (uint64_t)P->NT * P->NT * 4ull;
+    P->planes = stored_planes(c);
+    P->nkeys = (uint64_t)c.n_channels * P->planes * (uint64_t)P->NT * P->NT * 4ull;
     if (c.n_wplanes > 1) {
         P->w_scale = (double)c.n_wplanes / (c.w_max - c.w_min);
         P->dw = (c.w_max - c.w_min) / c.n_wplanes;
@@ -317,7 +329,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     if (B <= 0) {
         const size_t cap = (size_t)4 << 30;
         B = (int)(cap / plane_bytes);
-        const long long total = (long long)c.n_wplanes * c.n_channels;
+        const long long total = (long long)P->planes * c.n_channels;
         if (B > total) B = (int)total;
         if (B < 1) B = 1;
     }
@@ -367,6 +379,8 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     pp.T = P->T;
     pp.NT = P->NT;
     pp.precision = c.precision;
+    pp.fold = c.hermitian_fold;
+    pp.Nw_store = P->planes;
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;
@@ -401,7 +415,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     const rick_config& c = P->cfg;
     RK_ARG(P->binned, "rick_bin must precede gridding");
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
-    RK_ARG(0 <= k0 && k0 < k1 && k1 <= c.n_wplanes, "plane range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
     RK_ARG(grids != nullptr, "grids is NULL");
     RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
     if (c.kernel_kind == RICK_KERNEL_TABLE && !P->d_table) {
@@ -415,7 +429,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.S = c.support;
     G.T = P->T;
     G.NT = P->NT;
-    G.Nw = c.n_wplanes;
+    G.Nw = P->planes;
     G.c0 = c0;
     G.nc = c1 - c0;
     G.k0 = k0;
@@ -480,7 +494,7 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
                        cudaStream_t st) {
     const rick_config& c = P->cfg;
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
-    RK_ARG(0 <= k0 && k0 < k1 && k1 <= c.n_wplanes, "plane range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
     RK_ARG(grids && weight_sum && image_real, "grids, weight_sum and image_real are required");
     RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image_real & 7u) == 0 &&
                ((uintptr_t)image_complex & 15u) == 0,
@@ -510,13 +524,13 @@ void plan_groups(const rick_plan* P, int* gc, int* gk) {
     const rick_config& c = P->cfg;
     const size_t plane = (size_t)c.N * c.N * sizeof(float2);
     const size_t budget = c.grid_budget_bytes > 0 ? (size_t)c.grid_budget_bytes : (size_t)-1;
-    const size_t per_chan = plane * c.n_wplanes;
+    const size_t per_chan = plane * P->planes;
     if (budget / per_chan >= (size_t)c.n_channels) {
         *gc = c.n_channels;
-        *gk = c.n_wplanes;
+        *gk = P->planes;
     } else if (budget >= per_chan) {
         *gc = (int)(budget / per_chan);
-        *gk = c.n_wplanes;
+        *gk = P->planes;
     } else {
         *gc = 1;
         size_t k = budget / plane;
@@ -553,8 +567,8 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
     float* g = reinterpret_cast<float*>(P->d_grid);
     for (int c0 = 0; c0 < c.n_channels; c0 += gc) {
         const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
-        for (int k0 = 0; k0 < c.n_wplanes; k0 += gk) {
-            const int k1 = k0 + gk < c.n_wplanes ? k0 + gk : c.n_wplanes;
+        for (int k0 = 0; k0 < P->planes; k0 += gk) {
+            const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
             RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st));
             RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st));
             RK_TRY(phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
@@ -816,10 +830,10 @@ rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double*
     }
     if (grids) {
         if (s == RICK_OK) s = bin_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts, st);
-        if (s == RICK_OK) s = grid_impl(plan, 0, c.n_channels, 0, c.n_wplanes, grids, st);
-        if (s == RICK_OK) s = fft_impl(plan, grids, (int64_t)c.n_channels * c.n_wplanes, st);
+        if (s == RICK_OK) s = grid_impl(plan, 0, c.n_channels, 0, plan->planes, grids, st);
+        if (s == RICK_OK) s = fft_impl(plan, grids, (int64_t)c.n_channels * plan->planes, st);
         if (s == RICK_OK)
-            s = phase_impl(plan, grids, 0, c.n_channels, 0, c.n_wplanes, weight_sum, image_real, nullptr, st);
+            s = phase_impl(plan, grids, 0, c.n_channels, 0, plan->planes, weight_sum, image_real, nullptr, st);
     } else if (s == RICK_OK) {
         s = dirty_image_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, image_real, nullptr,
                              weight_sum, counts, st);
@@ -883,7 +897,8 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
     RK_ARG(n_results && best && grids, "n_results, best and grids are required");
     RK_ARG(reps >= 1 && reps <= 100, "reps must be in [1, 100]");
     RK_ARG(0 <= chan_begin && chan_begin < chan_end && chan_end <= base->n_channels, "channel range");
-    RK_ARG(0 <= plane_begin && plane_begin < plane_end && plane_end <= base->n_wplanes, "plane range");
+    RK_ARG(0 <= plane_begin && plane_begin < plane_end && plane_end <= stored_planes(*base),
+           "plane range");
     *n_results = 0;
     *best = *base;
     float best_ms = 1e30f;
@@ -965,5 +980,7 @@ const char* rick_status_string(rick_status s) {
 }
 
 const char* rick_last_error(void) { return g_err; }
+
+int32_t rick_stored_planes(const rick_config* cfg) { return cfg ? stored_planes(*cfg) : -1; }
 
 }  // extern "C"

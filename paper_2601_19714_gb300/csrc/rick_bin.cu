@@ -30,6 +30,47 @@ struct Placed {
     int status;  // 1 gridded, 0 skipped, -1 dropped
 };
 
+// The record and bin key of a placed visibility: plane k, footprint start
+// (i0, j0) and fractional offsets fq = round(f * 2^24) in [0, 2^24].
+//
+// Hermitian fold: a visibility of the upper half of the planes (2k > Nw - 1)
+// is stored as conj(W V) on plane Nw - 1 - k.  Its footprint, mirrored
+// through cell i -> N - i, starts at N - i0 - S + 1 with offset 1 - f: tap a
+// of the mirrored footprint sits at distance (a + 1 - S/2 - (1 - f)) =
+// -(S - 1 - a + 1 - S/2 - f) from the mirrored centre, the distance of tap
+// S - 1 - a of the original, so a symmetric kernel gives it the same weight.
+// If i0 = 0 the last mirrored cell is N, which is cell 0 on the periodic
+// mesh; it spills out of the last tile column and the gridder of tile column
+// 0 picks it up as a halo (likewise for rows).
+__device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k, int i0, int j0,
+                                              uint32_t fqx, uint32_t fqy, float W, float2 V,
+                                              Placed& out) {
+    float wv_im = W * V.y;
+    if (P.fold && 2 * k > P.Nw - 1) {
+        k = P.Nw - 1 - k;
+        i0 = P.N - i0 - P.S + 1;  // in [1, N - S + 1]; N only for S = 1, i0 = 0
+        j0 = P.N - j0 - P.S + 1;
+        if (i0 == P.N) i0 = 0;
+        if (j0 == P.N) j0 = 0;
+        fqx = (1u << kFracBits) - fqx;
+        fqy = (1u << kFracBits) - fqy;
+        wv_im = -wv_im;
+    }
+    fqx = min(fqx, kFracMask);
+    fqy = min(fqy, kFracMask);
+    const int tx = i0 / P.T, ty = j0 / P.T;
+    const int il = i0 - tx * P.T, jl = j0 - ty * P.T;
+    const int cls = halo_class(il + P.S - 1 >= P.T, jl + P.S - 1 >= P.T);
+    const uint64_t key =
+        ((((uint64_t)c * P.Nw_store + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
+    out.key = (uint32_t)key;
+    out.rec.wv_re = W * V.x;
+    out.rec.wv_im = wv_im;
+    out.rec.px = ((uint32_t)il << kFracBits) | fqx;
+    out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
+    out.status = 1;
+}
+
 // FP64 placement.  The operations and their order are fixed (no contraction)
 // so that the footprint start and plane index are the IEEE results of
 //   u = uvw * s;  x = u * fov + N/2;  sx = x - S/2;  i0 = floor(sx) + 1
@@ -60,20 +101,8 @@ __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, do
         kf = fmin(fmax(kf, 0.0), (double)(P.Nw - 1));
         k = (int)kf;
     }
-    uint32_t fqx = __double2uint_rn(fx * 16777216.0), fqy = __double2uint_rn(fy * 16777216.0);
-    fqx = min(fqx, kFracMask);
-    fqy = min(fqy, kFracMask);
-    const int tx = i0 / P.T, ty = j0 / P.T;
-    const int il = i0 - tx * P.T, jl = j0 - ty * P.T;
-    const int cls = halo_class(il + P.S - 1 >= P.T, jl + P.S - 1 >= P.T);
-    const uint64_t key =
-        ((((uint64_t)c * P.Nw + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
-    out.key = (uint32_t)key;
-    out.rec.wv_re = W * V.x;
-    out.rec.wv_im = W * V.y;
-    out.rec.px = ((uint32_t)il << kFracBits) | fqx;
-    out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
-    out.status = 1;
+    const uint32_t fqx = __double2uint_rn(fx * 16777216.0), fqy = __double2uint_rn(fy * 16777216.0);
+    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, out);
     return out;
 }
 
@@ -104,20 +133,8 @@ __device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, do
         kf = fminf(fmaxf(kf, 0.0f), (float)(P.Nw - 1));
         k = (int)kf;
     }
-    uint32_t fqx = __float2uint_rn(fx * 16777216.0f), fqy = __float2uint_rn(fy * 16777216.0f);
-    fqx = min(fqx, kFracMask);
-    fqy = min(fqy, kFracMask);
-    const int tx = i0 / P.T, ty = j0 / P.T;
-    const int il = i0 - tx * P.T, jl = j0 - ty * P.T;
-    const int cls = halo_class(il + P.S - 1 >= P.T, jl + P.S - 1 >= P.T);
-    const uint64_t key =
-        ((((uint64_t)c * P.Nw + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
-    out.key = (uint32_t)key;
-    out.rec.wv_re = W * V.x;
-    out.rec.wv_im = W * V.y;
-    out.rec.px = ((uint32_t)il << kFracBits) | fqx;
-    out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
-    out.status = 1;
+    const uint32_t fqx = __float2uint_rn(fx * 16777216.0f), fqy = __float2uint_rn(fy * 16777216.0f);
+    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, out);
     return out;
 }
 

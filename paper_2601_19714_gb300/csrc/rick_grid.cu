@@ -231,23 +231,21 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
             const int kk = (int)(plane % G.nk), cc = (int)(plane / G.nk);
             const int c = G.c0 + cc, k = G.k0 + kk;
             const int ty = (int)(tile / NT), tx = (int)(tile - (uint32_t)ty * NT);
-            const uint64_t key = ((((uint64_t)c * G.Nw + k) * NT + ty) * NT + tx) * 4u;
-            // own bins (all classes), left (classes 2-3), up (1-2), up-left (2)
+            const uint64_t kplane = ((uint64_t)c * G.Nw + k) * NT;
+            const uint64_t key = ((kplane + ty) * NT + tx) * 4u;
+            // own bins (all classes), left (classes 2-3), up (1-2), up-left (2).
+            // Neighbours wrap around the mesh: only the Hermitian fold puts
+            // records in the spill classes of the last tile row or column
+            // (footprints ending on cell N = cell 0); without it those bins
+            // are empty.
+            const int txl = tx > 0 ? tx - 1 : NT - 1, tyu = ty > 0 ? ty - 1 : NT - 1;
+            const uint64_t kl = ((kplane + ty) * NT + txl) * 4u;
+            const uint64_t ku = ((kplane + tyu) * NT + tx) * 4u;
+            const uint64_t kd = ((kplane + tyu) * NT + txl) * 4u;
             const uint32_t o0 = __ldg(offsets + key), o4 = __ldg(offsets + key + 4);
-            uint32_t l2 = 0, l4 = 0, u1 = 0, u3 = 0, d2 = 0, d3 = 0;
-            if (tx > 0) {
-                l2 = __ldg(offsets + key - 2);
-                l4 = __ldg(offsets + key);
-            }
-            if (ty > 0) {
-                const uint64_t ku = key - 4ull * NT;
-                u1 = __ldg(offsets + ku + 1);
-                u3 = __ldg(offsets + ku + 3);
-                if (tx > 0) {
-                    d2 = __ldg(offsets + ku - 2);
-                    d3 = __ldg(offsets + ku - 1);
-                }
-            }
+            const uint32_t l2 = __ldg(offsets + kl + 2), l4 = __ldg(offsets + kl + 4);
+            const uint32_t u1 = __ldg(offsets + ku + 1), u3 = __ldg(offsets + ku + 3);
+            const uint32_t d2 = __ldg(offsets + kd + 2), d3 = __ldg(offsets + kd + 3);
             const uint32_t total = (o4 - o0) + (l4 - l2) + (u3 - u1) + (d3 - d2);
             float2* out = grids + ((uint64_t)plane * N + (uint64_t)ty * T) * N + (uint64_t)tx * T;
             if (total == 0) {

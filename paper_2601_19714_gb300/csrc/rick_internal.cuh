@@ -42,6 +42,9 @@ __host__ __device__ inline int halo_class(bool right, bool down) {
 struct PlaceParams {
     int N, S, Nw, C, T, NT;
     int precision;
+    // Hermitian fold: visibilities on planes 2k > Nw - 1 go to plane Nw - 1 - k
+    // as conj(V) at the mirrored footprint; the keys count Nw_store planes.
+    int fold, Nw_store;
     double fov, half_n, half_s, w_min, w_scale;  // w_scale = Nw/(w_max - w_min), 0 if Nw == 1
     float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
 };
@@ -54,7 +57,7 @@ constexpr int kMaxSupport = 16;
 constexpr int kPolyDegree = 11;
 
 struct GridParams {
-    int N, S, T, NT, Nw;
+    int N, S, T, NT, Nw;  // Nw: stored planes (the bin keys' plane count)
     int c0, nc, k0, nk;
     uint32_t n_items;     // nc * nk * NT * NT tiles
     int kind;             // rick_kernel_kind

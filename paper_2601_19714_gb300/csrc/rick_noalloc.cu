@@ -86,20 +86,22 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         !(std::isfinite(c.w_min) && std::isfinite(c.w_max)) ||
         (c.n_wplanes > 1 && !(c.w_max > c.w_min)) || !(c.kernel_param > 0.0) ||
         !(threads == 128 || threads == 256 || threads == 512) ||
-        !(c.precision == RICK_PREC_FP32_FP64IDX || c.precision == RICK_PREC_ALL_FP32))
+        !(c.precision == RICK_PREC_FP32_FP64IDX || c.precision == RICK_PREC_ALL_FP32) ||
+        !(c.hermitian_fold == 0 || (c.hermitian_fold == 1 && c.w_min == -c.w_max)))
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: configuration");
+    const int planes = rick_stored_planes(cfg);
     if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: only Gaussian and Kaiser-Bessel kernels (a table kernel needs a plan)");
     if (nrow < 0 || !weight_sum || !grids || (nrow > 0 && !(uvw && chan_scale && vis && weight)))
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: inputs");
-    if (!(0 <= plane_begin && plane_begin < plane_end && plane_end <= c.n_wplanes))
+    if (!(0 <= plane_begin && plane_begin < plane_end && plane_end <= planes))
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: plane range");
     if (((uintptr_t)grids & 15u) != 0)
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: grids must be 16-byte aligned");
 
     const int NT = c.N / T;
-    const uint64_t nkeys = (uint64_t)c.n_channels * c.n_wplanes * (uint64_t)NT * NT * 4ull;
+    const uint64_t nkeys = (uint64_t)c.n_channels * planes * (uint64_t)NT * NT * 4ull;
     const uint64_t nvis = (uint64_t)nrow * (uint64_t)c.n_channels;
     const uint64_t items = (uint64_t)c.n_channels * (plane_end - plane_begin) * (uint64_t)NT * NT;
     // scratch layout: hist, offsets, scan partials, key, rank, stage, records, counter, counts
@@ -153,6 +155,8 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     pp.T = T;
     pp.NT = NT;
     pp.precision = c.precision;
+    pp.fold = c.hermitian_fold;
+    pp.Nw_store = planes;
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;
@@ -176,7 +180,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         G.S = c.support;
         G.T = T;
         G.NT = NT;
-        G.Nw = c.n_wplanes;
+        G.Nw = planes;
         G.c0 = 0;
         G.nc = c.n_channels;
         G.k0 = plane_begin;

@@ -32,7 +32,7 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_graph_destroy", "rick_autotune", "rick_mlp_param_count", "rick_mlp_forward",
            "rick_mlp_backward", "rick_adam_step", "rick_mlp_lattice_inputs", "rick_learn_create",
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
-           "rick_status_string", "rick_last_error"]
+           "rick_status_string", "rick_last_error", "rick_stored_planes"]
 
 
 class RickError(RuntimeError):
@@ -47,7 +47,7 @@ class rick_config(C.Structure):
                 ("w_max", C.c_double), ("kernel_param", C.c_double), ("kernel_kind", C.c_int32),
                 ("precision", C.c_int32), ("tile", C.c_int32), ("grid_threads", C.c_int32),
                 ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
-                ("grid_budget_bytes", C.c_int64)]
+                ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32)]
 
 
 class rick_tune_entry(C.Structure):
@@ -116,6 +116,8 @@ def load(path: str = LIB_PATH):
     L.rick_status_string.restype = C.c_char_p
     L.rick_last_error.argtypes = []
     L.rick_last_error.restype = C.c_char_p
+    L.rick_stored_planes.argtypes = [C.POINTER(rick_config)]
+    L.rick_stored_planes.restype = i32
     _lib = L
     return L
 
@@ -180,12 +182,19 @@ class Config:
     fft_batch: int = 0
     tiles_per_grab: int = 0
     grid_budget_bytes: int = 0
+    hermitian_fold: bool = False
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
                            self.w_min, self.w_max, self.kernel_param, KERNELS[self.kernel],
                            PRECISIONS[self.precision], self.tile, self.grid_threads,
-                           self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes)
+                           self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes,
+                           int(bool(self.hermitian_fold)))
+
+    @property
+    def stored_planes(self) -> int:
+        """Planes held per channel: ceil(Nw/2) with the Hermitian fold, else Nw."""
+        return (self.n_wplanes + 1) // 2 if self.hermitian_fold else self.n_wplanes
 
 
 class Plan:

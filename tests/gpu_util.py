@@ -46,8 +46,11 @@ def host_vis(obs):
 
 def run_path(plan, dev, nchan, N, Nw, complex_out=False):
     """grid -> fft -> phase through the three spec calls; returns numpy
-    (image_real [C,N,N], image_complex or None, weight_sum [C], counts [2])."""
+    (image_real [C,N,N], image_complex or None, weight_sum [C], counts [2]).
+    Nw is the number of w-planes; the plan stores ceil(Nw/2) of them when it
+    folds."""
     import torch
+    Nw = plan.cfg.stored_planes if plan.cfg.n_wplanes == Nw else Nw
     grids = torch.empty((nchan, Nw, N, N), dtype=torch.complex64, device="cuda")
     wsum = torch.empty(nchan, dtype=torch.float64, device="cuda")
     counts = torch.empty(2, dtype=torch.int64, device="cuda")

@@ -53,7 +53,8 @@ def test_status_strings(lib):
 @pytest.mark.parametrize("field,value", [("N", 100), ("N", 32), ("support", 0), ("support", 17),
                                          ("tile", 48), ("n_wplanes", 0), ("n_channels", 0),
                                          ("fov_rad", 1.5), ("kernel_param", -1.0),
-                                         ("grid_threads", 96), ("tiles_per_grab", 65)])
+                                         ("grid_threads", 96), ("tiles_per_grab", 65),
+                                         ("hermitian_fold", 2)])
 def test_invalid_configs_rejected_on_host(lib, field, value):
     from paper_2601_19714_gb300 import rick
     cfg = rick.Config(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
@@ -78,3 +79,27 @@ def test_null_plan_is_an_error(lib):
     assert lib.rick_plan_destroy(None) == 0
     assert lib.rick_fft_wplanes(None, None, 0, None) == 1
     assert lib.rick_plan_launch_count(None) == -1
+
+
+def test_hermitian_fold_needs_symmetric_w_and_symmetric_kernel(lib):
+    """The fold maps plane k to plane Nw-1-k, which sits at -w_k only for a
+    w range symmetric about zero, and reuses the taps of the mirrored
+    footprint, which needs a point-symmetric kernel."""
+    from paper_2601_19714_gb300 import rick
+    base = dict(N=256, n_wplanes=8, support=4, n_channels=1, fov_rad=0.03, kernel_param=5.6,
+                hermitian_fold=True)
+    for kw in (dict(w_min=-200, w_max=250, kernel="kb"), dict(w_min=-200, w_max=200, kernel="learned")):
+        cfg = rick.Config(**base, **kw).c()
+        h = C.c_void_p(123)
+        assert lib.rick_plan_create(C.byref(cfg), C.byref(h)) == 1
+        assert h.value is None
+        assert b"hermitian_fold" in lib.rick_last_error()
+
+
+@pytest.mark.parametrize("nw,fold,expect", [(8, 0, 8), (8, 1, 4), (7, 1, 4), (1, 1, 1), (32, 1, 16)])
+def test_stored_planes(lib, nw, fold, expect):
+    from paper_2601_19714_gb300 import rick
+    cfg = rick.Config(N=256, n_wplanes=nw, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                      w_max=200, kernel="gauss", kernel_param=0.94, hermitian_fold=bool(fold))
+    assert lib.rick_stored_planes(C.byref(cfg.c())) == expect == cfg.stored_planes
+    assert lib.rick_stored_planes(None) == -1

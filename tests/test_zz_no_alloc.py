@@ -36,10 +36,10 @@ def rk():
     return rick
 
 
-def _config(rk, img, nchan):
+def _config(rk, img, nchan, fold=False):
     return rk.Config(N=img.N, n_wplanes=img.Nw, support=img.S, n_channels=nchan,
                      fov_rad=img.fov, w_min=img.w_min, w_max=img.w_max, kernel="gauss",
-                     kernel_param=img.kernel_param)
+                     kernel_param=img.kernel_param, hermitian_fold=fold)
 
 
 def _inputs(obs):
@@ -48,29 +48,32 @@ def _inputs(obs):
     return t(obs.uvw), t(obs.chan_scale), t(obs.vis), t(obs.weight), obs.nrow
 
 
-def _with_plan(rk, img, obs):
+def _with_plan(rk, img, obs, fold=False):
     import torch
     uvw, sc, vis, wt, nrow = _inputs(obs)
-    grids = torch.empty((1, img.Nw, img.N, img.N), dtype=torch.complex64, device="cuda")
+    cfg = _config(rk, img, 1, fold)
+    ns = cfg.stored_planes
+    grids = torch.empty((1, ns, img.N, img.N), dtype=torch.complex64, device="cuda")
     wsum = torch.empty(1, dtype=torch.float64, device="cuda")
     counts = torch.empty(2, dtype=torch.int64, device="cuda")
-    with rk.Plan(_config(rk, img, 1)) as plan:
-        plan.grid(uvw, sc, vis, wt, None, nrow, 0, img.Nw, grids, wsum, counts)
+    with rk.Plan(cfg) as plan:
+        plan.grid(uvw, sc, vis, wt, None, nrow, 0, ns, grids, wsum, counts)
         torch.cuda.synchronize()
     return grids.cpu().numpy(), wsum.cpu().numpy(), counts.cpu().numpy()
 
 
-def _without_alloc(rk, img, obs):
+def _without_alloc(rk, img, obs, fold=False):
     """Call rick_grid_noalloc directly through ctypes (the C ABI)."""
     import torch
     uvw, sc, vis, wt, nrow = _inputs(obs)
-    grids = torch.empty((1, img.Nw, img.N, img.N), dtype=torch.complex64, device="cuda")
+    ns = _config(rk, img, 1, fold).stored_planes
+    grids = torch.empty((1, ns, img.N, img.N), dtype=torch.complex64, device="cuda")
     wsum = torch.empty(1, dtype=torch.float64, device="cuda")
     counts = torch.empty(2, dtype=torch.int64, device="cuda")
-    cfg = _config(rk, img, 1).c()
+    cfg = _config(rk, img, 1, fold).c()
     L = rk.load()
     st = L.rick_grid_noalloc(C.byref(cfg), uvw.data_ptr(), sc.data_ptr(), vis.data_ptr(),
-                             wt.data_ptr(), None, nrow, 0, img.Nw, grids.data_ptr(),
+                             wt.data_ptr(), None, nrow, 0, ns, grids.data_ptr(),
                              wsum.data_ptr(), counts.data_ptr(),
                              torch.cuda.current_stream().cuda_stream)
     assert st == 0, L.rick_last_error()
@@ -87,6 +90,16 @@ def test_noalloc_matches_rick_grid_on_two_calls_in_a_row(rk):
         assert err <= TOL, err
         assert cnt.tolist() == cnt_ref.tolist()
         np.testing.assert_allclose(ws, ws_ref, rtol=1e-12)
+
+
+def test_noalloc_with_hermitian_fold_matches_rick_grid(rk):
+    img, obs = tiny_wstack(34, nvis=12_345, N=256, Nw=7)
+    g, ws, cnt = _without_alloc(rk, img, obs, fold=True)
+    g_ref, ws_ref, cnt_ref = _with_plan(rk, img, obs, fold=True)
+    assert g.shape[1] == 4
+    assert np.abs(g - g_ref).max() <= TOL * np.abs(g_ref).max()
+    assert cnt.tolist() == cnt_ref.tolist()
+    np.testing.assert_allclose(ws, ws_ref, rtol=1e-12)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(rk):
