@@ -544,11 +544,35 @@ def run_learned(args):
     out = {}
     grids = torch.empty((1, Nw, N, N), dtype=torch.complex64, device="cuda")
     ws = torch.empty(1, dtype=torch.float64, device="cuda")
-    for name, cfg in (("learned_s4", mk(4, "table", KB_BETA_S4)), ("kb_s4", mk(4, "kb", KB_BETA_S4)),
-                      ("kb_s8", mk(8, "kb", KB_BETA_S8))):
+    table = k.bake()
+
+    def make_plan(name, cfg):
         plan = rick.Plan(cfg)
         if name == "learned_s4":
-            plan.set_kernel_table(k.bake(), L)
+            plan.set_kernel_table(table, L)
+        return plan
+
+    def grid_ms(plan, reps=5):
+        plan.grid(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], None, obs.nrow, 0, Nw,
+                  grids, ws)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            plan.grid_binned(0, 1, 0, Nw, grids)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # each kernel at its fastest launch shape (tile, CTA threads, tiles per grab)
+    shapes = ((16, 128, 4), (16, 256, 4), (32, 128, 4), (32, 256, 4), (32, 512, 4))
+    for name, base in (("learned_s4", mk(4, "table", KB_BETA_S4)), ("kb_s4", mk(4, "kb", KB_BETA_S4)),
+                       ("kb_s8", mk(8, "kb", KB_BETA_S8))):
+        from dataclasses import replace as _replace
+        sweep = {sh: grid_ms(make_plan(name, _replace(base, tile=sh[0], grid_threads=sh[1],
+                                                       tiles_per_grab=sh[2]))) for sh in shapes}
+        best = min(sweep, key=sweep.get)
+        cfg = _replace(base, tile=best[0], grid_threads=best[1], tiles_per_grab=best[2])
+        plan = make_plan(name, cfg)
         for _ in range(max(3, args.warmup)):
             plan.grid(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], None, obs.nrow, 0,
                       Nw, grids, ws)
@@ -563,7 +587,7 @@ def run_learned(args):
         torch.cuda.synchronize()
         mb, mg = e[0].elapsed_time(e[1]) / args.steps, e[1].elapsed_time(e[2]) / args.steps
         out[name] = {"ms_bin": mb, "ms_grid": mg, "grid_vis_per_s": obs.nrow / (mg * 1e-3),
-                     "bin_grid_vis_per_s": obs.nrow / ((mb + mg) * 1e-3)}
+                     "bin_grid_vis_per_s": obs.nrow / ((mb + mg) * 1e-3), "shape": list(best)}
     print(json.dumps({
         "metric": METRIC, "value": out["learned_s4"]["bin_grid_vis_per_s"], "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -598,7 +622,7 @@ def run_large(args):
         for prec in ("fp64idx", "fp32"):
             cfg = rick.Config(N=N, n_wplanes=img.Nw, support=img.S, n_channels=C, fov_rad=img.fov,
                               w_min=img.w_min, w_max=img.w_max, kernel="kb",
-                              kernel_param=img.kernel_param, precision=prec, tile=128,
+                              kernel_param=img.kernel_param, precision=prec, tile=32,
                               grid_budget_bytes=img.Nw * N * N * 8)
             plan = rick.Plan(cfg)
             plan.reserve(obs.nrow)
@@ -629,6 +653,58 @@ def run_large(args):
         "precision": res}), flush=True)
 
 
+def run_profile_small(args):
+    """A small case of the default workload for ncu captures: the MeerKAT
+    recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
+    visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
+    grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
+    Runs warm-up + steps whole-path steps and prints one JSON line."""
+    import torch
+    from paper_2601_19714_gb300 import _build, rick
+    from visgen.workloads import meerkat
+    _build.build()
+    img, obs = meerkat(args.seed, n_steps=500, nchan=2, N=4096, Nw=8, device="cuda")
+    dev = _dev_inputs(obs)
+    C, N = obs.nchan, img.N
+    cfg = rick.Config(N=N, n_wplanes=img.Nw, support=img.S, n_channels=C, fov_rad=img.fov,
+                      w_min=img.w_min, w_max=img.w_max, kernel="kb", kernel_param=img.kernel_param,
+                      tile=32, grid_threads=128, tiles_per_grab=4, hermitian_fold=not args.no_fold)
+    plan = rick.Plan(cfg)
+    ns = cfg.stored_planes
+    grids = torch.empty((C, ns, N, N), dtype=torch.complex64, device="cuda")
+    image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    wsum = torch.empty(C, dtype=torch.float64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+
+    def step():
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
+                 wsum, counts)
+        plan.grid_binned(0, C, 0, ns, grids)
+        plan.fft_wplanes(grids, C * ns)
+        plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    n_grid = int(counts[0].item())
+    print(json.dumps({"metric": METRIC, "value": n_grid / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "impl": "ours", "config": {"workload": "meerkat_small_4096sq_8w_2ch_kb8",
+                                                 "visibilities": int(obs.nrow * C),
+                                                 "gridded": n_grid, "hermitian_fold": cfg.hermitian_fold,
+                                                 "stored_planes": ns, "tile": 32,
+                                                 "grid_threads": 128, "tiles_per_grab": 4}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -641,9 +717,10 @@ def main():
                     help="headline without the Hermitian fold (all Nw planes stored and "
                          "transformed); the other variant is always measured beside it")
     ap.add_argument("--workload", default="meerkat",
-                    choices=["meerkat", "lofar", "learned", "large"],
+                    choices=["meerkat", "lofar", "learned", "large", "profile_small"],
                     help="meerkat (default bench line); lofar / learned / large measure the "
-                         "batched, learned-kernel and precision-stress workloads")
+                         "batched, learned-kernel and precision-stress workloads; "
+                         "profile_small is the small case the ncu captures use")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -653,6 +730,8 @@ def main():
         run_learned(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "profile_small":
+        run_profile_small(args)
     else:
         run_ours(args)
 

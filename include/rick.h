@@ -88,10 +88,11 @@ typedef struct rick_config {
     double kernel_param;  /* see rick_kernel_kind */
     int32_t kernel_kind;  /* rick_kernel_kind */
     int32_t precision;    /* rick_precision */
-    int32_t tile;         /* gridder tile side T: 32, 64 or 128 (0 = 64); T <= N */
-    int32_t grid_threads; /* gridder CTA size: 128, 256 or 512 (0 = 256) */
+    int32_t tile;         /* gridder tile side T: 16, 32 or 64 (0 = 32); T <= N; one warp
+                           * grids one tile at a time, so T = 64 allows 128 grid_threads */
+    int32_t grid_threads; /* gridder CTA size: 128, 256 or 512 (0 = 128) */
     int32_t fft_batch;    /* planes per cuFFT execution (0 = up to 4 GiB of planes) */
-    int32_t tiles_per_grab; /* tiles a gridder CTA takes from the work queue at once: 1..64 (0 = 8) */
+    int32_t tiles_per_grab; /* tiles a gridder warp takes from the work queue at once: 1..8 (0 = 4) */
     int64_t grid_budget_bytes; /* rick_dirty_image: device bytes for plane groups (0 = all) */
     /* Hermitian fold (0 = off).  The dirty image is the real part of the sum
      * over planes in Eq. 2, and Re(z) = Re(conj z), so a visibility V at
@@ -244,9 +245,9 @@ typedef struct rick_tune_entry {
     float grid_ms; /* median time of rick_grid_binned over the timed region */
 } rick_tune_entry;
 
-/* Autotune the gridder for this data: for every valid tile side T (32, 64,
- * 128 with S <= T <= N), CTA size (128, 256, 512) and tiles per grab (2, 8,
- * 32), bin the visibilities with T and time rick_grid_binned over channels
+/* Autotune the gridder for this data: for every valid tile side T (16, 32,
+ * 64 with S <= T <= N), CTA size (128, 256, 512; those that fit shared
+ * memory) and tiles per grab (1, 4, 8), bin the visibilities with T and time rick_grid_binned over channels
  * [chan_begin, chan_end) and planes [plane_begin, plane_end) (grids sized for
  * that region), reps times after one warm-up.  Writes up to max_results
  * entries to results (nullable), their number to *n_results, and the base

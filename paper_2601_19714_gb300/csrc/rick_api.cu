@@ -145,7 +145,9 @@ struct rick_plan {
     uint32_t* d_hist = nullptr;
     uint32_t* d_offsets = nullptr;
     uint32_t* d_partials = nullptr;
-    uint32_t* d_counter = nullptr;
+    uint32_t* d_counter = nullptr;   // gridder queues and list lengths (8 words)
+    uint32_t* d_lists = nullptr;     // longest-first tile lists, 3 x list_cap
+    uint32_t list_cap = 0;
     unsigned long long* d_counts = nullptr;
     int* d_status = nullptr;
     double* d_wsum = nullptr;
@@ -186,6 +188,7 @@ void release(rick_plan* P) {
     dfree(P->d_offsets);
     dfree(P->d_partials);
     dfree(P->d_counter);
+    dfree(P->d_lists);
     dfree(P->d_counts);
     dfree(P->d_status);
     dfree(P->d_wsum);
@@ -205,8 +208,8 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c != nullptr, "cfg is NULL");
     RK_ARG(c->N >= 64 && c->N <= 65536 && (c->N & (c->N - 1)) == 0,
            "N must be a power of two in [64, 65536]");
-    const int T = c->tile ? c->tile : 64;
-    RK_ARG(T == 32 || T == 64 || T == 128, "tile must be 32, 64 or 128");
+    const int T = c->tile ? c->tile : 32;
+    RK_ARG(T == 16 || T == 32 || T == 64, "tile must be 16, 32 or 64");
     RK_ARG(T <= c->N, "tile must not exceed N");
     RK_ARG(c->n_wplanes >= 1, "n_wplanes must be >= 1");
     RK_ARG(c->n_channels >= 1, "n_channels must be >= 1");
@@ -221,10 +224,13 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE || c->support == 4, "table kernels have support 4");
     RK_ARG(c->precision == RICK_PREC_FP32_FP64IDX || c->precision == RICK_PREC_ALL_FP32,
            "unknown precision");
-    const int th = c->grid_threads ? c->grid_threads : 256;
+    const int th = c->grid_threads ? c->grid_threads : 128;
     RK_ARG(th == 128 || th == 256 || th == 512, "grid_threads must be 128, 256 or 512");
+    // every warp of a gridder CTA holds one T x (T + 8) complex tile in shared memory
+    RK_ARG((size_t)(th / 32) * T * (T + 8) * 8 <= (size_t)160 * 1024,
+           "tile 64 allows at most 128 grid_threads (one 37 KB shared tile per warp)");
     RK_ARG(c->fft_batch >= 0, "fft_batch must be >= 0");
-    RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 64, "tiles_per_grab must be in [0, 64]");
+    RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 8, "tiles_per_grab must be in [0, 8]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
     if (c->hermitian_fold) {
@@ -248,12 +254,17 @@ rick_status ensure_vis_capacity(rick_plan* P, int64_t nvis) {
     dfree(P->d_rank);
     dfree(P->d_stage);
     dfree(P->d_records);
+    dfree(P->d_lists);
     P->cap_vis = 0;
+    P->list_cap = 0;
     const size_t n = (size_t)nvis;
     RK_CUDA(cudaMalloc(&P->d_key, n * sizeof(uint32_t)));
     RK_CUDA(cudaMalloc(&P->d_rank, n * sizeof(uint32_t)));
     RK_CUDA(cudaMalloc(&P->d_stage, n * sizeof(VisRecord)));
     RK_CUDA(cudaMalloc(&P->d_records, n * sizeof(VisRecord)));
+    const uint32_t cap = schedule_list_cap(nvis, P->T);
+    RK_CUDA(cudaMalloc(&P->d_lists, 3 * (size_t)cap * sizeof(uint32_t)));
+    P->list_cap = cap;
     P->cap_vis = nvis;
     return RICK_OK;
 }
@@ -279,11 +290,11 @@ rick_status make_fft_plan(cufftHandle* h, bool* have, int N, int batch) {
 rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     P->cfg = *cfg;
     rick_config& c = P->cfg;
-    P->T = c.tile ? c.tile : 64;
+    P->T = c.tile ? c.tile : 32;
     c.tile = P->T;
-    P->threads = c.grid_threads ? c.grid_threads : 256;
+    P->threads = c.grid_threads ? c.grid_threads : 128;
     c.grid_threads = P->threads;
-    P->grab = c.tiles_per_grab ? c.tiles_per_grab : 8;
+    P->grab = c.tiles_per_grab ? c.tiles_per_grab : 4;
     c.tiles_per_grab = P->grab;
     P->NT = c.N / P->T;
     P->planes = stored_planes(c);
@@ -318,7 +329,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaMalloc(&P->d_hist, sizeof(uint32_t) * P->nkeys));
     RK_CUDA(cudaMalloc(&P->d_offsets, sizeof(uint32_t) * (P->nkeys + 1)));
     RK_CUDA(cudaMalloc(&P->d_partials, sizeof(uint32_t) * scan_partials_needed(P->nkeys)));
-    RK_CUDA(cudaMalloc(&P->d_counter, sizeof(uint32_t)));
+    RK_CUDA(cudaMalloc(&P->d_counter, 8 * sizeof(uint32_t)));
     RK_CUDA(cudaMalloc(&P->d_counts, 2 * sizeof(unsigned long long)));
     RK_CUDA(cudaMalloc(&P->d_status, sizeof(int)));
     RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
@@ -440,8 +451,10 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.table = P->d_table;
     G.lattice = P->lattice;
     G.grab = (uint32_t)P->grab;
+    G.lists = P->d_lists;
+    G.list_cap = P->list_cap;
     P->last_stream = st;
-    RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
+    RK_CUDA(cudaMemsetAsync(P->d_counter, 0, 8 * sizeof(uint32_t), st));
     int launches = 0;
     rick_status s = check_launch(launch_grid(G, P->d_offsets, P->d_records,
                                              reinterpret_cast<float2*>(grids), P->d_counter,
@@ -644,6 +657,10 @@ rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t la
     RK_ARG(plan->cfg.kernel_kind == RICK_KERNEL_TABLE, "plan does not use a table kernel");
     RK_ARG(lattice >= 1 && lattice <= 256, "lattice must be in [1, 256]");
     const size_t n = (size_t)plan->cfg.n_wplanes * (lattice + 1) * (lattice + 1) * 16;
+    if (n >= ((size_t)1 << 31)) {
+        set_err("kernel table of %zu floats exceeds the gridder's 32-bit table index", n);
+        return RICK_ERR_UNSUPPORTED;
+    }
     if (lattice != plan->lattice) {
         dfree(plan->d_table);
         plan->lattice = 0;
@@ -902,9 +919,9 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
     *n_results = 0;
     *best = *base;
     float best_ms = 1e30f;
-    const int tiles[3] = {32, 64, 128};
+    const int tiles[3] = {16, 32, 64};
     const int threads[3] = {128, 256, 512};
-    const int grabs[3] = {2, 8, 32};
+    const int grabs[3] = {1, 4, 8};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     RK_CUDA(cudaEventCreate(&e0));
     RK_CUDA(cudaEventCreate(&e1));
@@ -927,6 +944,11 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
         result = bin_impl(P, uvw, chan_scale, vis, weight, flag, nrow, wsum, nullptr, nullptr);
         for (int hi = 0; hi < 3 && result == RICK_OK; ++hi) {
             for (int gi = 0; gi < 3 && result == RICK_OK; ++gi) {
+                {
+                    rick_config shape = cfg;
+                    shape.grid_threads = threads[hi];
+                    if (validate(&shape) != RICK_OK) continue;  // too much shared memory
+                }
                 P->threads = threads[hi];
                 P->grab = grabs[gi];
                 std::vector<float> ms;

@@ -63,9 +63,23 @@ struct GridParams {
     int kind;             // rick_kernel_kind
     const float* table;   // RICK_KERNEL_TABLE: [Nw][L+1][L+1][16]
     int lattice;
-    uint32_t grab;        // tiles taken from the work queue per atomic
+    uint32_t grab;        // tiles a warp takes from the work queue per atomic
+    // Longest-first order (optional): three lists, list_cap entries each, of
+    // the tiles with at least 64T, 16T and 4T records (own bins plus the
+    // neighbours' spill), filled by a scheduling pass; work_counter[1..3]
+    // hold their lengths.  The gridder takes those tiles first, heaviest list
+    // first, then every other tile in natural order.  nullptr: natural order.
+    uint32_t* lists;
+    uint32_t list_cap;
     float coef[kMaxSupport][kPolyDegree + 1];
 };
+
+// Entries per longest-first list for a plan binning up to max_vis
+// visibilities with tile side T: a record is counted by at most 4 tiles (its
+// own and 3 neighbours), so at most 4 max_vis / (4T) tiles reach 4T records.
+inline uint32_t schedule_list_cap(int64_t max_vis, int T) {
+    return (uint32_t)(max_vis / T + 64);
+}
 
 // Fit the tap polynomials of a Gaussian or Kaiser-Bessel kernel of support S
 // (param = sigma or beta) into G.coef; returns the largest deviation from the
@@ -95,6 +109,7 @@ cudaError_t launch_scatter(const uint32_t* key, const uint32_t* rank, const VisR
                            const uint32_t* offsets, VisRecord* records, int64_t nvis,
                            int num_sms, cudaStream_t stream, int* launches);
 
+// work_counter: 8 words, zero on entry (queue positions, list lengths).
 cudaError_t launch_grid(const GridParams& G, const uint32_t* offsets, const VisRecord* records,
                         float2* grids, uint32_t* work_counter, int threads, int num_sms,
                         cudaStream_t stream, int* launches);

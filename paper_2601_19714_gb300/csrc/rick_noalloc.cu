@@ -78,9 +78,10 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
                                          double* weight_sum, int64_t* counts, void* stream) {
     if (!cfg) return fail(RICK_ERR_INVALID_ARG, "invalid argument: cfg is NULL");
     const rick_config& c = *cfg;
-    const int T = c.tile ? c.tile : 64;
-    const int threads = c.grid_threads ? c.grid_threads : 256;
-    if (c.N < 64 || c.N > 65536 || (c.N & (c.N - 1)) || !(T == 32 || T == 64 || T == 128) ||
+    const int T = c.tile ? c.tile : 32;
+    const int threads = c.grid_threads ? c.grid_threads : 128;
+    if (c.N < 64 || c.N > 65536 || (c.N & (c.N - 1)) || !(T == 16 || T == 32 || T == 64) ||
+        (size_t)(threads / 32) * T * (T + 8) * 8 > (size_t)160 * 1024 ||
         T > c.N || c.n_wplanes < 1 || c.n_channels < 1 || c.support < 1 || c.support > 16 ||
         c.support > T || !(c.fov_rad > 0.0 && c.fov_rad < 1.0) ||
         !(std::isfinite(c.w_min) && std::isfinite(c.w_max)) ||
@@ -143,7 +144,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     // the array keeps the previous call's contents: clear what must start at zero
     if (cudaMemsetAsync(hist, 0, nkeys * 4, st) != cudaSuccess ||
         cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), st) != cudaSuccess ||
-        cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(counter, 0, 8 * sizeof(uint32_t), st) != cudaSuccess ||
         cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st) != cudaSuccess)
         return fail(RICK_ERR_CUDA, "rick_grid_noalloc: cudaMemsetAsync failed");
 
@@ -191,7 +192,9 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
             return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: kernel too narrow for its support");
         G.table = nullptr;
         G.lattice = 0;
-        G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 64 ? (uint32_t)c.tiles_per_grab : 8u;
+        G.lists = nullptr;  // natural tile order (no scheduling scratch)
+        G.list_cap = 0;
+        G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 8 ? (uint32_t)c.tiles_per_grab : 4u;
         e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
                         num_sms, st, &launches);
     }
