@@ -297,7 +297,8 @@ def run_ours(args):
         start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         stage_events = []
         with (ClockSampler(local) if clocks else contextlib.nullcontext()) as clk:
-            torch.cuda.nvtx.range_push("timed")
+            # "timed" marks the headline's timed steps (ncu --nvtx-include timed/)
+            torch.cuda.nvtx.range_push("timed" if clocks else "timed_other_variant")
             start.record(stream)
             for _ in range(steps):
                 stage_events.append(step(record=True))
