@@ -343,6 +343,13 @@ def run_ours(args):
            (("bin", b_bin), ("grid", b_grid), ("fft", b_fft), ("phase", b_phase))}
     dominant = max(st, key=st.get)
     dom_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase}[dominant]
+    # DRAM traffic of the dominant stage, from one ncu capture of the small
+    # 4096^2 case (dram__bytes_read.sum + dram__bytes_write.sum of cuFFT's three
+    # kernels: 46.7 bytes per cell per transform, proportional to the planes)
+    dom_traffic, traffic_how = None, None
+    if dominant == "fft" and N == 4096:
+        dom_traffic = 46.7 * cells
+        traffic_how = "ncu capture of the 4096^2 small case, scaled by planes (46.7 B/cell)"
 
     # ---- end to end through the host entry point -------------------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -397,7 +404,8 @@ def run_ours(args):
                          "achieved": dom_bytes / (st[dominant] * 1e-3) / 1e9,
                          "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                          "frac": dom_bytes / (st[dominant] * 1e-3) / 1e9 / hbm,
-                         "traffic": None},
+                         "traffic": dom_traffic, "traffic_unit": "bytes per step",
+                         "traffic_how": traffic_how},
             "roofline_grid": {"bound": "hbm", "achieved": gbs["grid"], "peak": hbm,
                               "unit": "GB/s", "frac": gbs["grid"] / hbm},
             "roofline_phase": {"bound": "hbm", "achieved": gbs["phase"], "peak": hbm,

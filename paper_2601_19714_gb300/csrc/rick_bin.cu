@@ -71,37 +71,97 @@ __device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k
     out.status = 1;
 }
 
-// FP64 placement.  The operations and their order are fixed (no contraction)
-// so that the footprint start and plane index are the IEEE results of
+// floor(s) and round-half-even((s - floor(s)) 2^24) of an FP64 value s >= 0,
+// read exactly from its bits with integer operations: s = m 2^(e-52), so
+// s 2^24 = m 2^(e-28) is m shifted, and the bits shifted out decide the
+// rounding.  These equal the FP64 results of floor, s - floor(s) (exact) and
+// __double2uint_rn((s - floor(s)) * 2^24).  False if s is not finite or s >= 2^30.
+__device__ __forceinline__ bool split_cell(double s, int& fl, uint32_t& fq) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    const int be = (int)((b >> 52) & 0x7ffu);
+    if (be == 0x7ff) return false;
+    const int e = be - 1023;
+    if (e >= 30) return false;
+    if (be == 0) {  // zero or subnormal: below 2^-1022, rounds to 0
+        fl = 0;
+        fq = 0;
+        return true;
+    }
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    unsigned long long qf, qr;
+    if (e >= 28) {
+        qf = qr = m << (e - 28);
+    } else if (28 - e >= 64) {
+        qf = qr = 0;  // s 2^24 < 2^53 2^-64 < 1/2
+    } else {
+        const int sh = 28 - e;
+        qf = m >> sh;
+        const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        qr = qf + ((rem > half || (rem == half && (qf & 1ull))) ? 1ull : 0ull);
+    }
+    fl = (int)(qf >> 24);
+    fq = (uint32_t)(qr - ((unsigned long long)(uint32_t)fl << 24));
+    return true;
+}
+
+__device__ __forceinline__ bool finite_bits(double s) {
+    return (((unsigned long long)__double_as_longlong(s) >> 52) & 0x7ffu) != 0x7ffu;
+}
+
+// One axis of the placement from sx = x - S/2: footprint start i0 and 24-bit
+// fraction; false if the visibility leaves the grid or sx is not finite.
+// sx >= 0 (all but footprints starting at cell 0) takes the integer path;
+// sx < 0 the FP64 operations floor, subtraction and conversion.
+__device__ __forceinline__ bool place_axis(const PlaceParams& P, double sx, int& i0, uint32_t& fq) {
+    int fl;
+    if (!(__double_as_longlong(sx) < 0)) {
+        if (!split_cell(sx, fl, fq)) return false;
+    } else {
+        if (!finite_bits(sx)) return false;
+        const double f = floor(sx);
+        if (f < -1.0) return false;
+        fl = (int)f;
+        fq = __double2uint_rn(__dsub_rn(sx, f) * 16777216.0);
+    }
+    if (fl + P.S > P.N - 1) return false;
+    i0 = fl + 1;
+    return true;
+}
+
+// FP64 placement.  The FP64 operations and their order are fixed (no
+// contraction) so that the footprint start, fraction and plane index are the
+// IEEE results of
 //   u = uvw * s;  x = u * fov + N/2;  sx = x - S/2;  i0 = floor(sx) + 1
 //   k = floor((w - w_min) * (Nw / (w_max - w_min)))   (clamped)
+// Only the multiplications and additions run on the FP64 pipe (11 per
+// visibility, GB300's FP64 rate being a small fraction of its FP32 rate); the
+// floors, fractions, 24-bit rounding, range and finiteness tests are read from
+// the bit patterns with integer operations (exactly the same results).
 __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, double v0, double w0,
                                              double sc, int c, float W, float2 V) {
     Placed out;
     out.key = kInvalidKey;
-    out.status = 0;
+    out.status = -1;
     const double u = __dmul_rn(u0, sc), v = __dmul_rn(v0, sc), w = __dmul_rn(w0, sc);
     const double x = __dadd_rn(__dmul_rn(u, P.fov), P.half_n);
     const double y = __dadd_rn(__dmul_rn(v, P.fov), P.half_n);
-    if (!isfinite(x) || !isfinite(y) || !isfinite(w)) {
-        out.status = -1;
-        return out;
-    }
-    const double sx = __dsub_rn(x, P.half_s), sy = __dsub_rn(y, P.half_s);
-    const double flx = floor(sx), fly = floor(sy);
-    if (flx < -1.0 || fly < -1.0 || flx + P.S > P.N - 1 || fly + P.S > P.N - 1) {
-        out.status = -1;
-        return out;
-    }
-    const int i0 = (int)flx + 1, j0 = (int)fly + 1;
-    const double fx = __dsub_rn(sx, flx), fy = __dsub_rn(sy, fly);
+    if (!finite_bits(w)) return out;
+    int i0, j0;
+    uint32_t fqx, fqy;
+    if (!place_axis(P, __dsub_rn(x, P.half_s), i0, fqx)) return out;
+    if (!place_axis(P, __dsub_rn(y, P.half_s), j0, fqy)) return out;
     int k = 0;
     if (P.Nw > 1) {
-        double kf = floor(__dmul_rn(__dsub_rn(w, P.w_min), P.w_scale));
-        kf = fmin(fmax(kf, 0.0), (double)(P.Nw - 1));
-        k = (int)kf;
+        const double t = __dmul_rn(__dsub_rn(w, P.w_min), P.w_scale);
+        const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
+        int fl;
+        uint32_t unused;
+        if (tb >> 63) k = 0;                                        // t < 0 or -0: clamp low
+        else if ((tb & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull) k = 0;  // NaN: fmax gives 0
+        else if (!split_cell(t, fl, unused)) k = P.Nw - 1;          // +inf or >= 2^30: clamp high
+        else k = min(fl, P.Nw - 1);
     }
-    const uint32_t fqx = __double2uint_rn(fx * 16777216.0), fqy = __double2uint_rn(fy * 16777216.0);
+    out.status = 0;
     finish_record(P, c, k, i0, j0, fqx, fqy, W, V, out);
     return out;
 }

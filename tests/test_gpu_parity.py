@@ -110,6 +110,58 @@ def test_binning_is_bit_exact(rk, orc, T):
     assert wsum.item() == pytest.approx(ws_o, rel=1e-12) and ws_o < ws_e
 
 
+def test_placement_rounding_ties_and_edges_are_bit_exact(rk, orc):
+    """Footprint starts and 24-bit fractions on exact half-way points of the
+    rounding (fraction (2j+1) 2^-25), on the first cell (x - S/2 in [-1, 0),
+    the FP64 branch of the placement), on the last valid cell, just off the grid
+    and at non-finite positions.  With fov = 2^-5 rad, x = u fov + N/2 is exact,
+    so each position is the intended one."""
+    import torch
+    from visgen.workloads import Imaging
+    N, S, fov = 256, 8, 2.0 ** -5
+    img = Imaging(N, 4, S, "kb", 12.25, fov, -100.0, 100.0)
+    xs = []
+    for cell in (40, 41, 128, 200):
+        for j in (0, 1, 2, 3, 1 << 20, (1 << 23) - 1, (1 << 24) - 1):
+            xs.append(cell + S / 2 + (2 * j + 1) * 2.0 ** -25)      # ties at bit 25
+        xs.append(cell + S / 2 + 0.5)
+        xs.append(cell + S / 2)
+    for f in (0.0, 2.0 ** -25, 0.25, 0.5, 1 - 2.0 ** -25):
+        xs.append(S / 2 - 1 + f)                                     # x - S/2 in [-1, 0)
+    xs += [S / 2 - 1 - 2.0 ** -30, N - S / 2 - 2.0 ** -25, N - S / 2, N - S / 2 + 1e-9]
+    xs = np.array(xs)
+    n = len(xs)
+    g = np.random.default_rng(3)
+    ys = xs[g.permutation(n)]
+    uvw = np.stack([(xs - N / 2) / fov, (ys - N / 2) / fov, g.uniform(-99, 99, n)], axis=1)
+    uvw[-1, 0] = np.inf
+    uvw[-2, 2] = np.nan
+    from types import SimpleNamespace
+    obs = SimpleNamespace(uvw=uvw, chan_scale=np.ones(1), vis=np.ones((n, 1), np.complex64),
+                          weight=np.ones((n, 1), np.float32), flag=None)
+    for fold in (False, True):
+        plan = rk.Plan(plan_config(img, 1, tile=32, hermitian_fold=fold))
+        dev = to_device(obs)
+        wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+        counts = torch.empty(2, dtype=torch.int64, device="cuda")
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], None, dev["nrow"], wsum,
+                 counts)
+        off, rec = plan.bins()
+        if not fold:
+            key_e, px_e, py_e, wv_e, ng, nd = _expected_records(orc, img, obs, 32)
+            assert counts.cpu().tolist() == [ng, nd] and nd >= 4
+            key_g = np.repeat(np.arange(len(off) - 1), np.diff(off.astype(np.int64)))
+            o_g = np.lexsort((rec[:, 3], rec[:, 2], key_g))
+            o_e = np.lexsort((py_e, px_e, key_e))
+            np.testing.assert_array_equal(key_g[o_g], key_e[o_e])
+            np.testing.assert_array_equal(rec[o_g, 2].astype(np.int64), px_e[o_e])
+            np.testing.assert_array_equal(rec[o_g, 3].astype(np.int64), py_e[o_e])
+            fq = rec[:, 2].astype(np.int64) & ((1 << 24) - 1)
+            assert (fq % 2 == 0).sum() > 0 and (fq == 0).sum() > 0
+        else:
+            assert counts.cpu().tolist()[0] == ng
+
+
 # ----------------------------------------------------------------------------
 # stage by stage against the oracle
 # ----------------------------------------------------------------------------
