@@ -380,10 +380,32 @@ __global__ void __launch_bounds__(256)
 k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
           const VisRecord* __restrict__ stage, const uint32_t* __restrict__ offsets,
           VisRecord* __restrict__ records, int64_t nvis) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvis; i += stride) {
-        const uint32_t k = key[i];
-        if (k != kInvalidKey) records[offsets[k] + rank[i]] = stage[i];
+    // four visibilities per thread and step, their loads issued together: the
+    // key -> offset -> store chain is latency-bound, so this keeps 4x more
+    // requests in flight
+    constexpr int kU = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kU;
+    for (int64_t base = ((int64_t)blockIdx.x * blockDim.x) * kU + threadIdx.x; base < nvis;
+         base += stride) {
+        uint32_t k[kU], r[kU], o[kU];
+        VisRecord v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x;
+            k[u] = i < nvis ? key[i] : kInvalidKey;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = base + (int64_t)u * blockDim.x;
+            if (k[u] != kInvalidKey) {
+                o[u] = offsets[k[u]];
+                r[u] = rank[i];
+                v[u] = stage[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (k[u] != kInvalidKey) records[o[u] + r[u]] = v[u];
     }
 }
 
@@ -435,8 +457,8 @@ cudaError_t launch_scatter(const uint32_t* key, const uint32_t* rank, const VisR
                            const uint32_t* offsets, VisRecord* records, int64_t nvis,
                            int num_sms, cudaStream_t stream, int* launches) {
     if (nvis <= 0) return cudaSuccess;
-    int64_t blocks = (nvis + 255) / 256;
-    const int64_t cap = (int64_t)num_sms * 16;
+    int64_t blocks = (nvis + 1023) / 1024;
+    const int64_t cap = (int64_t)num_sms * 8;
     if (blocks > cap) blocks = cap;
     k_scatter<<<(unsigned)blocks, 256, 0, stream>>>(key, rank, stage, offsets, records, nvis);
     ++*launches;
