@@ -116,6 +116,12 @@ def _declare(L):
     L.oracle_image_at.argtypes = vis_args + [C.c_int, C.c_int, i64, p, p, p]
     L.oracle_dft_at.restype = C.c_int
     L.oracle_dft_at.argtypes = vis_args + [C.c_int, i64, p, p, p]
+    novis = [cfgp, p, p, C.c_int, p, p, i64, C.c_int]
+    L.oracle_predict.restype = C.c_int
+    L.oracle_predict.argtypes = novis + [p, p]
+    for name in ("oracle_predict_at", "oracle_predict_dft"):
+        getattr(L, name).restype = C.c_int
+        getattr(L, name).argtypes = novis + [i64, p, p, p, i64, p, p]
     del i32
 
 
@@ -322,3 +328,58 @@ def dft_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=()
     if rc != 0:
         raise ValueError(f"oracle_dft_at failed ({rc})")
     return out
+
+
+# --------------------------------------------------------------------- #
+# prediction (degridding)                                                 #
+# --------------------------------------------------------------------- #
+
+def _novis_args(uvw, chan_scale, weight, flag):
+    nrow = len(uvw)
+    v = _Vis(uvw, chan_scale, np.zeros((nrow, len(np.atleast_1d(chan_scale))), np.complex64),
+             weight, flag)
+    return v, [_ptr(v.uvw), _ptr(v.scale), v.C, _ptr(v.weight), _ptr(v.flag), v.nrow]
+
+
+def predict(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0, image=None):
+    """O1 prediction of channel ``channel`` from the real model image [N, N]
+    (row q, column p): complex128 [nrow], zero where a visibility is not gridded."""
+    v, args = _novis_args(uvw, chan_scale, weight, flag)
+    J = np.ascontiguousarray(image, dtype=np.float64)
+    assert J.shape == (cfg.N, cfg.N)
+    out = np.zeros(v.nrow, np.complex128)
+    c = cfg.c()
+    rc = lib().oracle_predict(C.byref(c), *args, channel, _ptr(J), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_predict failed ({rc})")
+    return out
+
+
+def _sources_call(fn, cfg, uvw, chan_scale, weight, flag, channel, p, q, flux, rows):
+    v, args = _novis_args(uvw, chan_scale, weight, flag)
+    pp = np.ascontiguousarray(p, dtype=np.int32)
+    qq = np.ascontiguousarray(q, dtype=np.int32)
+    ff = np.ascontiguousarray(flux, dtype=np.float64)
+    rr = np.ascontiguousarray(np.arange(v.nrow) if rows is None else rows, dtype=np.int64)
+    out = np.zeros(rr.shape[0], np.complex128)
+    c = cfg.c()
+    rc = fn(C.byref(c), *args, channel, pp.shape[0], _ptr(pp), _ptr(qq), _ptr(ff), rr.shape[0],
+            _ptr(rr), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"prediction failed ({rc})")
+    return out
+
+
+def predict_at(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0, p=(), q=(), flux=(),
+               rows=None):
+    """O1 prediction for a point-source model on pixel centres, visibility by
+    visibility (no FFT): the same values as ``predict`` on that image."""
+    return _sources_call(lib().oracle_predict_at, cfg, uvw, chan_scale, weight, flag, channel,
+                         p, q, flux, rows)
+
+
+def predict_dft(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0, p=(), q=(), flux=(),
+                rows=None):
+    """O2 prediction: Eq. 1 summed over the point sources directly."""
+    return _sources_call(lib().oracle_predict_dft, cfg, uvw, chan_scale, weight, flag, channel,
+                         p, q, flux, rows)

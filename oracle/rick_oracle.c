@@ -733,3 +733,158 @@ int oracle_dft_at(const oracle_cfg* cfg, const double* uvw, const double* scale,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Prediction (degridding): the adjoint direction of Eq. 2 and 3       */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper only images (Sec. 2); prediction is the other half of an imaging
+ * cycle and is written here from the same statement of the problem.  For a
+ * real model image J of one channel, Eq. 1 discretised on the pixels reads
+ *   V(u, v, w) = sum_{p,q} J(p, q) / n * exp(-2 pi i (u l + v m + w (n - 1)))
+ * (O2 below, the plain definition).  Its w-stacking form, with the same
+ * readings R1-R7 as the imaging path, is (O1):
+ *   M_k(p, q) = J(p, q) exp(-2 pi i w_k (n - 1)) / (n C(p) C(q))
+ *   F_k(i, j) = sum_{p,q} M_k(p, q) exp(-2 pi i ((i - N/2)(p - N/2) + (j - N/2)(q - N/2)) / N)
+ *             = (-1)^(i+j) * [forward DFT of (-1)^(p+q) M_k](i, j)           (R6)
+ *   V        ~ sum_{a,b} g(i0 + a - x) g(j0 + b - y) F_k(i0 + a, j0 + b)
+ * for every visibility the gridder keeps (R3, R4, R10), k its plane; the
+ * others are 0.  The convolution with g in (u, v) is undone by the division by
+ * C in (l, m), as in the imaging path.  This operator is the adjoint of the
+ * imaging operator up to the weights and the n^2 factor:
+ *   sum W V conj(pred(J)) = sum W * sum_p J(p) I(V)(p) / n(p)^2.
+ */
+
+/* Forward 2-D DFT (exponent -), unnormalised: conj(ifft2(conj(A))). */
+static void fft2_forward(int N, double complex* A)
+{
+    size_t NN = (size_t)N * N;
+    for (size_t t = 0; t < NN; ++t) A[t] = conj(A[t]);
+    oracle_ifft2(N, A);
+    for (size_t t = 0; t < NN; ++t) A[t] = conj(A[t]);
+}
+
+/* O1 prediction for channel c from the real model image J [N][N] (row q, column
+ * p): out[r] for every row r of the visibilities (zero where not gridded).
+ * Planes are built, transformed and sampled one at a time.  Returns 0. */
+int oracle_predict(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
+                   const float* weight, const uint8_t* flag, long nrow, int c, const double* J,
+                   double complex* out)
+{
+    if (check_cfg(cfg)) return 1;
+    if (cfg->kernel == ORACLE_LEARNED) return 3;
+    int N = cfg->N, S = cfg->S;
+    size_t NN = (size_t)N * N;
+    double complex* F = (double complex*)malloc(sizeof(double complex) * NN);
+    double* Ct = (double*)malloc(sizeof(double) * N);
+    double* gw = (double*)malloc(sizeof(double) * S * S);
+    if (!F || !Ct || !gw) { free(F); free(Ct); free(gw); return 2; }
+    cfg_taper(cfg, Ct);
+    for (long r = 0; r < nrow; ++r) out[r] = 0.0;
+    for (int k = 0; k < cfg->Nw; ++k) {
+        double wk = oracle_plane_w(cfg, k);
+        for (int q = 0; q < N; ++q)
+            for (int p = 0; p < N; ++p) {
+                double n, d;
+                pixel_n(cfg, p, q, &n, &d);
+                double sgn = ((p + q) & 1) ? -1.0 : 1.0;
+                F[(size_t)q * N + p] = sgn * J[(size_t)q * N + p] * turn_phasor(-wk * d) / (n * Ct[p] * Ct[q]);
+            }
+        fft2_forward(N, F);
+        for (long r = 0; r < nrow; ++r) {
+            placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
+            if (P.ok != 1 || P.k != k) continue;
+            footprint_weights(cfg, &P, gw);
+            double complex acc = 0.0;
+            for (int b = 0; b < S; ++b)
+                for (int a = 0; a < S; ++a) {
+                    long i = P.i0 + a, j = P.j0 + b;
+                    double sgn = ((i + j) & 1) ? -1.0 : 1.0;
+                    acc += gw[b * S + a] * sgn * F[(size_t)j * N + i];
+                }
+            out[r] = acc;
+        }
+    }
+    free(F);
+    free(Ct);
+    free(gw);
+    return 0;
+}
+
+/* O1 prediction for a model of point sources on pixel centres (p_s, q_s) with
+ * fluxes A_s, evaluated visibility by visibility without the FFT (the same
+ * value as oracle_predict on that image):
+ *   V = sum_{a,b} g_a g_b sum_s A_s exp(-2 pi i w_k (n_s - 1)) / (n_s C(p_s) C(q_s))
+ *         * exp(-2 pi i ((i - N/2)(p_s - N/2) + (j - N/2)(q_s - N/2)) / N)
+ * with the exponent reduced exactly mod N.  rows[t] selects the visibility
+ * (rows[t], c); out[t] = 0 if it is not gridded. */
+int oracle_predict_at(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
+                      const float* weight, const uint8_t* flag, long nrow, int c, long nsrc,
+                      const int32_t* sp, const int32_t* sq, const double* flux, long nsel,
+                      const int64_t* rows, double complex* out)
+{
+    if (check_cfg(cfg)) return 1;
+    if (cfg->kernel == ORACLE_LEARNED) return 3;
+    int N = cfg->N, S = cfg->S;
+    double* Ct = (double*)malloc(sizeof(double) * N);
+    double* gw = (double*)malloc(sizeof(double) * S * S);
+    if (!Ct || !gw) { free(Ct); free(gw); return 2; }
+    cfg_taper(cfg, Ct);
+    for (long t = 0; t < nsel; ++t) {
+        out[t] = 0.0;
+        long r = (long)rows[t];
+        if (r < 0 || r >= nrow) continue;
+        placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
+        if (P.ok != 1) continue;
+        footprint_weights(cfg, &P, gw);
+        double wk = oracle_plane_w(cfg, P.k);
+        double complex acc = 0.0;
+        for (long s = 0; s < nsrc; ++s) {
+            double n, d;
+            pixel_n(cfg, sp[s], sq[s], &n, &d);
+            double complex Ms = flux[s] * turn_phasor(-wk * d) / (n * Ct[sp[s]] * Ct[sq[s]]);
+            long ps = sp[s] - N / 2, qs = sq[s] - N / 2;
+            for (int b = 0; b < S; ++b) {
+                long j = P.j0 + b - N / 2;
+                long jq = ((j * qs) % N + N) % N;
+                for (int a = 0; a < S; ++a) {
+                    long i = P.i0 + a - N / 2;
+                    long ip = ((i * ps) % N + N) % N;
+                    acc += gw[b * S + a] * Ms * turn_phasor(-(double)((ip + jq) % N) / N);
+                }
+            }
+        }
+        out[t] = acc;
+    }
+    free(Ct);
+    free(gw);
+    return 0;
+}
+
+/* O2 prediction: Eq. 1 summed directly over point sources on pixel centres,
+ *   V = sum_s A_s / n_s exp(-2 pi i (u l_s + v m_s + w (n_s - 1))),
+ * for the selected visibilities that the gridder keeps (others 0). */
+int oracle_predict_dft(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
+                       const float* weight, const uint8_t* flag, long nrow, int c, long nsrc,
+                       const int32_t* sp, const int32_t* sq, const double* flux, long nsel,
+                       const int64_t* rows, double complex* out)
+{
+    if (check_cfg(cfg)) return 1;
+    double dl = cfg->fov / cfg->N;
+    for (long t = 0; t < nsel; ++t) {
+        out[t] = 0.0;
+        long r = (long)rows[t];
+        if (r < 0 || r >= nrow) continue;
+        placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
+        if (P.ok != 1) continue;
+        double complex acc = 0.0;
+        for (long s = 0; s < nsrc; ++s) {
+            double l = (sp[s] - cfg->N / 2) * dl, m = (sq[s] - cfg->N / 2) * dl;
+            double n, d;
+            pixel_n(cfg, sp[s], sq[s], &n, &d);
+            acc += flux[s] / n * turn_phasor(-(P.u * l + P.v * m + P.w * d));
+        }
+        out[t] = acc;
+    }
+    return 0;
+}
