@@ -260,6 +260,55 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
                           rick_tune_entry* results, int32_t max_results, int32_t* n_results,
                           rick_config* best);
 
+/* ---- prediction (degridding) ------------------------------------------
+ *
+ * The adjoint direction of the imaging path, for major cycles: a real model
+ * image per channel to model visibilities.  The paper images only (Sec. 2);
+ * the prediction is Eq. 1 discretised on the pixels,
+ *   V(u, v, w) = sum_{p,q} J(p, q) / n exp(-2 pi i (u l + v m + w (n - 1))),
+ * in w-stacking form with the readings of the imaging path (cell and pixel
+ * maps, footprint, planes, checkerboard, taper):
+ *   M_k = (-1)^(p+q) J exp(-2 pi i w_k (n - 1)) / (n C(p) C(q))   (per plane)
+ *   F_k = forward 2-D DFT of M_k (cuFFT, exponent -)
+ *   V   = sum over the footprint of g(i - x) g(j - y) (-1)^(i+j) F_k(i, j).
+ * With the Hermitian fold, visibilities of the upper half of the planes are
+ * predicted on the mirrored plane at the mirrored cells and conjugated (exact
+ * for a real image).  Gaussian and Kaiser-Bessel kernels (not TABLE). */
+
+/* Place and bin every visibility for prediction: the same selection as
+ * rick_bin (flags, zero weights and footprints off the grid are skipped;
+ * counts[2] (device, nullable) receives (predicted, dropped)).  Replaces any
+ * binning of the plan made for gridding, and vice versa. */
+rick_status rick_bin_predict(rick_plan* plan, const double* uvw, const double* chan_scale,
+                             const float* weight, const uint8_t* flag, int64_t nrow, int64_t* counts,
+                             void* stream);
+
+/* M_k for channels [chan_begin, chan_end) and stored planes [plane_begin,
+ * plane_end): image_real[chan_end-chan_begin][N][N] (device, f32, row q major)
+ * to grids laid out as for rick_grid_binned; every cell is written. */
+rick_status rick_model_to_wplanes(rick_plan* plan, const float* image_real, int32_t chan_begin,
+                                  int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                  float* grids, void* stream);
+
+/* In place, unnormalised 2-D forward FFT (exponent -) of n_planes planes. */
+rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
+
+/* V for every visibility binned by rick_bin_predict whose channel and plane lie
+ * in the ranges, from the transformed planes `grids` (layout as for
+ * rick_grid_binned): vis_out[nrow][C] complex64 (device) receives those
+ * entries; the others are left untouched. */
+rick_status rick_degrid_binned(rick_plan* plan, const float* grids, int32_t chan_begin,
+                               int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                               float* vis_out, void* stream);
+
+/* The whole prediction: rick_bin_predict, then per plane group of the
+ * plan-owned grid rick_model_to_wplanes + rick_fft_wplanes_forward +
+ * rick_degrid_binned.  vis_out[nrow][C] (device) is zeroed first, so skipped
+ * visibilities read 0.  image_real[C][N][N] device f32. */
+rick_status rick_predict(rick_plan* plan, const double* uvw, const double* chan_scale,
+                         const float* weight, const uint8_t* flag, int64_t nrow,
+                         const float* image_real, float* vis_out, int64_t* counts, void* stream);
+
 /* ---- learned support-4 kernel (pattern 4) ---------------------------- */
 
 /* A multilayer perceptron in[3] = (dx, dy, w-plane in [-1, 1]) -> H GELU ->

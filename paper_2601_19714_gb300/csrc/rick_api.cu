@@ -152,6 +152,7 @@ struct rick_plan {
     int* d_status = nullptr;
     double* d_wsum = nullptr;
     bool binned = false;
+    bool binned_for_predict = false;  // records hold (index, conj) instead of W V
     // cuFFT: batch B and single-plane plans
     cufftHandle fft_b = 0, fft_1 = 0;
     bool have_b = false, have_1 = false;
@@ -363,7 +364,7 @@ rick_status check_launch(cudaError_t e, const char* what) {
 
 rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
                      const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
-                     int64_t* counts, cudaStream_t st) {
+                     int64_t* counts, cudaStream_t st, bool predict = false) {
     const rick_config& c = P->cfg;
     RK_ARG(nrow >= 0, "nrow must be >= 0");
     RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
@@ -374,7 +375,8 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
         return RICK_ERR_UNSUPPORTED;
     }
     if (nrow > 0) {
-        RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
+        RK_ARG(uvw && chan_scale && (vis || predict) && weight,
+               "uvw, chan_scale, vis and weight are required");
     }
     RK_TRY(ensure_vis_capacity(P, nvis));
     P->last_stream = st;
@@ -392,6 +394,7 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     pp.precision = c.precision;
     pp.fold = c.hermitian_fold;
     pp.Nw_store = P->planes;
+    pp.predict = predict ? 1 : 0;
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;
@@ -419,12 +422,13 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     if (counts)
         RK_CUDA(cudaMemcpyAsync(counts, P->d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     P->binned = true;
+    P->binned_for_predict = predict;
     return RICK_OK;
 }
 
 rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids, cudaStream_t st) {
     const rick_config& c = P->cfg;
-    RK_ARG(P->binned, "rick_bin must precede gridding");
+    RK_ARG(P->binned && !P->binned_for_predict, "rick_bin must precede gridding");
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
     RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
     RK_ARG(grids != nullptr, "grids is NULL");
@@ -464,7 +468,8 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     return s;
 }
 
-rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st) {
+rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st,
+                     int direction = CUFFT_INVERSE) {
     RK_ARG(n_planes >= 0, "n_planes must be >= 0");
     RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
     const size_t NN = (size_t)P->cfg.N * P->cfg.N;
@@ -478,7 +483,7 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
         }
         for (; done + P->fft_B <= n_planes; done += P->fft_B) {
             cufftComplex* d = g + (size_t)done * NN;
-            const cufftResult r = cufftExecC2C(P->fft_b, d, d, CUFFT_INVERSE);
+            const cufftResult r = cufftExecC2C(P->fft_b, d, d, direction);
             if (r != CUFFT_SUCCESS) {
                 set_err("cufftExecC2C (batch) failed: %d", (int)r);
                 return RICK_ERR_CUFFT;
@@ -492,7 +497,7 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
         }
         for (; done < n_planes; ++done) {
             cufftComplex* d = g + (size_t)done * NN;
-            const cufftResult r = cufftExecC2C(P->fft_1, d, d, CUFFT_INVERSE);
+            const cufftResult r = cufftExecC2C(P->fft_1, d, d, direction);
             if (r != CUFFT_SUCCESS) {
                 set_err("cufftExecC2C failed: %d", (int)r);
                 return RICK_ERR_CUFFT;
@@ -527,6 +532,73 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
                             P->d_inv_taper, image_real, reinterpret_cast<float2*>(image_complex),
                             st, &launches),
         "phase kernel");
+    P->launches += launches;
+    return s;
+}
+
+PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
+    const rick_config& c = P->cfg;
+    PhaseParams pp;
+    pp.N = c.N;
+    pp.nc = c1 - c0;
+    pp.nk = k1 - k0;
+    pp.dl = c.fov_rad / c.N;
+    pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
+    pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
+    pp.precision = c.precision;
+    return pp;
+}
+
+rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
+                       cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_ARG(image && grids, "image and grids are required");
+    RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image & 7u) == 0,
+           "grids must be 16-byte and image 8-byte aligned");
+    P->last_stream = st;
+    int launches = 0;
+    rick_status s = check_launch(
+        launch_model_planes(phase_params(P, c0, c1, k0, k1), image, P->d_inv_taper,
+                            reinterpret_cast<float2*>(grids), st, &launches),
+        "model kernel");
+    P->launches += launches;
+    return s;
+}
+
+rick_status degrid_impl(rick_plan* P, const float* grids, int c0, int c1, int k0, int k1,
+                        float* vis_out, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(P->binned && P->binned_for_predict, "rick_bin_predict must precede degridding");
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_ARG(grids && vis_out, "grids and vis_out are required");
+    RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)vis_out & 7u) == 0,
+           "grids must be 16-byte and vis_out 8-byte aligned");
+    const uint64_t items = (uint64_t)(c1 - c0) * (k1 - k0) * (uint64_t)P->NT * P->NT;
+    RK_ARG(items < 0xFFFFFFFFull, "too many tiles in one call");
+    GridParams G;
+    std::memset(&G, 0, sizeof G);
+    G.N = c.N;
+    G.S = c.support;
+    G.T = P->T;
+    G.NT = P->NT;
+    G.Nw = P->planes;
+    G.c0 = c0;
+    G.nc = c1 - c0;
+    G.k0 = k0;
+    G.nk = k1 - k0;
+    G.n_items = (uint32_t)items;
+    G.kind = c.kernel_kind;
+    std::memcpy(G.coef, P->tap_coef, sizeof G.coef);
+    P->last_stream = st;
+    RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
+    int launches = 0;
+    rick_status s = check_launch(
+        launch_degrid(G, P->d_offsets, P->d_records, reinterpret_cast<const float2*>(grids),
+                      reinterpret_cast<float2*>(vis_out), P->d_counter, 128, P->num_sms, st, &launches),
+        "degridding kernel");
     P->launches += launches;
     return s;
 }
@@ -586,6 +658,31 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
             RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st));
             RK_TRY(phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
                               image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st));
+        }
+    }
+    return RICK_OK;
+}
+
+rick_status predict_impl(rick_plan* P, const double* uvw, const double* chan_scale,
+                         const float* weight, const uint8_t* flag, int64_t nrow, const float* image,
+                         float* vis_out, int64_t* counts, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    RK_ARG(image != nullptr && vis_out != nullptr, "image and vis_out are required");
+    RK_TRY(bin_impl(P, uvw, chan_scale, nullptr, weight, flag, nrow, P->d_wsum, counts, st, true));
+    if (nrow > 0)
+        RK_CUDA(cudaMemsetAsync(vis_out, 0, sizeof(float2) * (size_t)nrow * c.n_channels, st));
+    int gc, gk;
+    plan_groups(P, &gc, &gk);
+    const size_t NN = (size_t)c.N * c.N;
+    RK_TRY(ensure_group_grid(P));
+    float* g = reinterpret_cast<float*>(P->d_grid);
+    for (int c0 = 0; c0 < c.n_channels; c0 += gc) {
+        const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
+        for (int k0 = 0; k0 < P->planes; k0 += gk) {
+            const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
+            RK_TRY(model_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, st));
+            RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st, CUFFT_FORWARD));
+            RK_TRY(degrid_impl(P, g, c0, c1, k0, k1, vis_out, st));
         }
     }
     return RICK_OK;
@@ -984,6 +1081,51 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return result;
+}
+
+rick_status rick_bin_predict(rick_plan* plan, const double* uvw, const double* chan_scale,
+                             const float* weight, const uint8_t* flag, int64_t nrow, int64_t* counts,
+                             void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    if (plan->cfg.kernel_kind == RICK_KERNEL_TABLE) {
+        set_err("prediction supports the Gaussian and Kaiser-Bessel kernels");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    return bin_impl(plan, uvw, chan_scale, nullptr, weight, flag, nrow, plan->d_wsum, counts,
+                    as_stream(stream), true);
+}
+
+rick_status rick_model_to_wplanes(rick_plan* plan, const float* image_real, int32_t chan_begin,
+                                  int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                  float* grids, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return model_impl(plan, image_real, chan_begin, chan_end, plane_begin, plane_end, grids,
+                      as_stream(stream));
+}
+
+rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return fft_impl(plan, grids, n_planes, as_stream(stream), CUFFT_FORWARD);
+}
+
+rick_status rick_degrid_binned(rick_plan* plan, const float* grids, int32_t chan_begin,
+                               int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                               float* vis_out, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return degrid_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, vis_out,
+                       as_stream(stream));
+}
+
+rick_status rick_predict(rick_plan* plan, const double* uvw, const double* chan_scale,
+                         const float* weight, const uint8_t* flag, int64_t nrow,
+                         const float* image_real, float* vis_out, int64_t* counts, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    if (plan->cfg.kernel_kind == RICK_KERNEL_TABLE) {
+        set_err("prediction supports the Gaussian and Kaiser-Bessel kernels");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    return predict_impl(plan, uvw, chan_scale, weight, flag, nrow, image_real, vis_out, counts,
+                        as_stream(stream));
 }
 
 const char* rick_status_string(rick_status s) {

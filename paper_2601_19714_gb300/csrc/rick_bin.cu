@@ -44,9 +44,11 @@ struct Placed {
 // 0 picks it up as a halo (likewise for rows).
 __device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k, int i0, int j0,
                                               uint32_t fqx, uint32_t fqy, float W, float2 V,
-                                              Placed& out) {
+                                              uint32_t vidx, Placed& out) {
     float wv_im = W * V.y;
+    bool folded = false;
     if (P.fold && 2 * k > P.Nw - 1) {
+        folded = true;
         k = P.Nw - 1 - k;
         i0 = P.N - i0 - P.S + 1;  // in [1, N - S + 1]; N only for S = 1, i0 = 0
         j0 = P.N - j0 - P.S + 1;
@@ -64,8 +66,8 @@ __device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k
     const uint64_t key =
         ((((uint64_t)c * P.Nw_store + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
     out.key = (uint32_t)key;
-    out.rec.wv_re = W * V.x;
-    out.rec.wv_im = wv_im;
+    out.rec.wv_re = P.predict ? __uint_as_float(vidx) : W * V.x;
+    out.rec.wv_im = P.predict ? __uint_as_float(folded ? 1u : 0u) : wv_im;
     out.rec.px = ((uint32_t)il << kFracBits) | fqx;
     out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
     out.status = 1;
@@ -138,7 +140,7 @@ __device__ __forceinline__ bool place_axis(const PlaceParams& P, double sx, int&
 // floors, fractions, 24-bit rounding, range and finiteness tests are read from
 // the bit patterns with integer operations (exactly the same results).
 __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, double v0, double w0,
-                                             double sc, int c, float W, float2 V) {
+                                             double sc, int c, float W, float2 V, uint32_t vidx) {
     Placed out;
     out.key = kInvalidKey;
     out.status = -1;
@@ -162,13 +164,13 @@ __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, do
         else k = min(fl, P.Nw - 1);
     }
     out.status = 0;
-    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, out);
+    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, vidx, out);
     return out;
 }
 
 // All-FP32 placement (precision study): same steps in single precision.
 __device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, double v0, double w0,
-                                             double sc, int c, float W, float2 V) {
+                                             double sc, int c, float W, float2 V, uint32_t vidx) {
     Placed out;
     out.key = kInvalidKey;
     out.status = 0;
@@ -194,7 +196,7 @@ __device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, do
         k = (int)kf;
     }
     const uint32_t fqx = __float2uint_rn(fx * 16777216.0f), fqy = __float2uint_rn(fy * 16777216.0f);
-    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, out);
+    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, vidx, out);
     return out;
 }
 
@@ -233,9 +235,9 @@ k_place(PlaceParams P, const double* __restrict__ uvw, const double* __restrict_
             if (!flagged && W != 0.0f && isfinite(W)) {
                 const int64_t r = idx / P.C;
                 const double u0 = uvw[3 * r], v0 = uvw[3 * r + 1], w0 = uvw[3 * r + 2];
-                const float2 V = vis[idx];
-                pl = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc, c, W, V)
-                                                : place_fp64(P, u0, v0, w0, sc, c, W, V);
+                const float2 V = vis != nullptr ? vis[idx] : make_float2(0.f, 0.f);
+                pl = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc, c, W, V, (uint32_t)idx)
+                                                : place_fp64(P, u0, v0, w0, sc, c, W, V, (uint32_t)idx);
                 if (pl.status == 1) {
                     my_wsum += (double)W;
                     ++n_grid;

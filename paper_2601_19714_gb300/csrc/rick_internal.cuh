@@ -20,7 +20,9 @@ namespace rick {
 
 // One binned visibility: W*V (FP32) and, per axis, the first footprint cell
 // relative to the anchor tile (top 8 bits) and the fractional offset
-// f = (x - S/2) - floor(x - S/2) in units of 2^-24 (low 24 bits).
+// f = (x - S/2) - floor(x - S/2) in units of 2^-24 (low 24 bits).  Records
+// binned for prediction hold the visibility index and a conjugation flag in
+// the bits of wv_re and wv_im.
 struct __align__(16) VisRecord {
     float wv_re, wv_im;
     uint32_t px, py;
@@ -45,6 +47,10 @@ struct PlaceParams {
     // Hermitian fold: visibilities on planes 2k > Nw - 1 go to plane Nw - 1 - k
     // as conj(V) at the mirrored footprint; the keys count Nw_store planes.
     int fold, Nw_store;
+    // Prediction binning: records carry the visibility's index (bits of
+    // wv_re) and whether its prediction is to be conjugated (wv_im bits 0/1,
+    // set by the fold) instead of W V.
+    int predict;
     double fov, half_n, half_s, w_min, w_scale;  // w_scale = Nw/(w_max - w_min), 0 if Nw == 1
     float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
 };
@@ -117,6 +123,18 @@ cudaError_t launch_grid(const GridParams& G, const uint32_t* offsets, const VisR
 cudaError_t launch_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                 const float* taper, float* image_real, float2* image_complex,
                                 cudaStream_t stream, int* launches);
+
+// prediction (degridding)
+cudaError_t launch_model_planes(const PhaseParams& P, const float* image, const float* inv_taper,
+                                float2* grids, cudaStream_t stream, int* launches);
+
+// Gathers the prediction of every record binned for prediction whose
+// (channel, plane) lies in G's range from the transformed planes `grids`
+// (layout as for the gridder) into vis_out[index] (conjugated where flagged).
+// work_counter: 1 word, zero on entry.
+cudaError_t launch_degrid(const GridParams& G, const uint32_t* offsets, const VisRecord* records,
+                          const float2* grids, float2* vis_out, uint32_t* work_counter, int threads,
+                          int num_sms, cudaStream_t stream, int* launches);
 
 uint64_t scan_partials_needed(uint64_t n);
 

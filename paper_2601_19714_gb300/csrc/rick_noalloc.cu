@@ -158,6 +158,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     pp.precision = c.precision;
     pp.fold = c.hermitian_fold;
     pp.Nw_store = planes;
+    pp.predict = 0;
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;

@@ -134,7 +134,94 @@ k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __
     }
 }
 
+// Prediction, first step: the model image of each channel spread onto the
+// w-planes (the adjoint of the reduction above),
+//   M_k[q][p] = (-1)^(p+q) J_c[q][p] exp(-2 pi i w_k (n - 1)) / (n C(p) C(q)),
+// every plane written once (16-byte streaming stores of two pixels).  The
+// phase is the conjugate of the one the reduction applies, formed the same
+// way (FP64 per pixel, Q0.64 turns, exact anchors every 8 planes).
+template <int PREC>
+__global__ void __launch_bounds__(kPhaseThreads)
+k_model_planes(PhaseParams P, const float* __restrict__ image, const float* __restrict__ inv_taper,
+               float2* __restrict__ grids) {
+    const int N = P.N, halfN = N / 2;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)N * halfN) return;
+    const int q = (int)(tid / halfN);
+    const int p = (int)(tid - (int64_t)q * halfN) * 2;
+    const size_t NN = (size_t)N * N;
+
+    uint64_t t0[2], dt[2];
+    float t0f[2], dtf[2];
+    float scale[2];
+    for (int e = 0; e < 2; ++e) {
+        const double l = (double)(p + e - halfN) * P.dl, m = (double)(q - halfN) * P.dl;
+        const double r2 = l * l + m * m;
+        const double n = sqrt(1.0 - r2);
+        const double delta = -r2 / (1.0 + n);
+        if (PREC == RICK_PREC_ALL_FP32) {
+            const float lf = (float)(p + e - halfN) * (float)P.dl, mf = (float)(q - halfN) * (float)P.dl;
+            const float r2f = lf * lf + mf * mf;
+            const float nf = sqrtf(1.0f - r2f);
+            const float df = -r2f / (1.0f + nf);
+            t0f[e] = (float)P.w_first * df;
+            dtf[e] = (float)P.dw * df;
+        } else {
+            t0[e] = turns_q64(P.w_first * delta);
+            dt[e] = turns_q64(P.dw * delta);
+        }
+        const float sg = ((p + e + q) & 1) ? -1.f : 1.f;
+        scale[e] = sg * inv_taper[p + e] * inv_taper[q] / (float)n;
+    }
+
+    for (int cc = 0; cc < P.nc; ++cc) {
+        const float2 J = *reinterpret_cast<const float2*>(image + (size_t)cc * NN + (size_t)q * N + p);
+        const float a0 = J.x * scale[0], a1 = J.y * scale[1];
+        float4* g = reinterpret_cast<float4*>(grids + (size_t)cc * P.nk * NN + (size_t)q * N + p);
+        if (PREC == RICK_PREC_ALL_FP32) {
+            for (int k = 0; k < P.nk; ++k) {
+                float s0, c0, s1, c1;
+                const float b0 = t0f[0] + (float)k * dtf[0], b1 = t0f[1] + (float)k * dtf[1];
+                sincospif(2.0f * (b0 - rintf(b0)), &s0, &c0);
+                sincospif(2.0f * (b1 - rintf(b1)), &s1, &c1);
+                __stcs(g + (size_t)k * (NN / 2), make_float4(a0 * c0, -a0 * s0, a1 * c1, -a1 * s1));
+            }
+        } else {
+            const float2 r0 = phasor_q64(dt[0]), r1 = phasor_q64(dt[1]);
+            uint64_t tk0 = t0[0], tk1 = t0[1];
+            for (int kb = 0; kb < P.nk; kb += kAnchor) {
+                const int kn = min(kAnchor, P.nk - kb);
+                float2 z0 = phasor_q64(tk0), z1 = phasor_q64(tk1);
+#pragma unroll
+                for (int j = 0; j < kAnchor; ++j) {
+                    if (j < kn) {
+                        __stcs(g + (size_t)(kb + j) * (NN / 2),
+                               make_float4(a0 * z0.x, -a0 * z0.y, a1 * z1.x, -a1 * z1.y));
+                        z0 = cmul(z0, r0);
+                        z1 = cmul(z1, r1);
+                    }
+                }
+                tk0 += (uint64_t)kAnchor * dt[0];
+                tk1 += (uint64_t)kAnchor * dt[1];
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_model_planes(const PhaseParams& P, const float* image, const float* inv_taper,
+                                float2* grids, cudaStream_t stream, int* launches) {
+    const int64_t threads = (int64_t)P.N * (P.N / 2);
+    const int64_t blocks = (threads + kPhaseThreads - 1) / kPhaseThreads;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (P.precision == RICK_PREC_ALL_FP32)
+        k_model_planes<RICK_PREC_ALL_FP32><<<(unsigned)blocks, kPhaseThreads, 0, stream>>>(P, image, inv_taper, grids);
+    else
+        k_model_planes<RICK_PREC_FP32_FP64IDX><<<(unsigned)blocks, kPhaseThreads, 0, stream>>>(P, image, inv_taper, grids);
+    ++*launches;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                 const float* inv_taper, float* image_real, float2* image_complex,

@@ -32,7 +32,9 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_graph_destroy", "rick_autotune", "rick_mlp_param_count", "rick_mlp_forward",
            "rick_mlp_backward", "rick_adam_step", "rick_mlp_lattice_inputs", "rick_learn_create",
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
-           "rick_status_string", "rick_last_error", "rick_stored_planes"]
+           "rick_status_string", "rick_last_error", "rick_stored_planes", "rick_bin_predict",
+           "rick_model_to_wplanes", "rick_fft_wplanes_forward", "rick_degrid_binned",
+           "rick_predict"]
 
 
 class RickError(RuntimeError):
@@ -88,6 +90,11 @@ def load(path: str = LIB_PATH):
         "rick_graph_destroy": [p],
         "rick_autotune": [C.POINTER(rick_config), p, p, p, p, p, i64, i32, i32, i32, i32, p, i32,
                           C.POINTER(rick_tune_entry), i32, C.POINTER(i32), C.POINTER(rick_config)],
+        "rick_bin_predict": [p, p, p, p, p, i64, p, p],
+        "rick_model_to_wplanes": [p, p, i32, i32, i32, i32, p, p],
+        "rick_fft_wplanes_forward": [p, p, i64, p],
+        "rick_degrid_binned": [p, p, i32, i32, i32, i32, p, p],
+        "rick_predict": [p, p, p, p, p, i64, p, p, p, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -310,6 +317,44 @@ class Plan:
             _ptr(image_complex, d["c64"], "image_complex", 16),
             _ptr(weight_sum, d["f64"], "weight_sum", 8), _ptr(counts, d["i64"], "counts", 8),
             _stream(stream)), "rick_dirty_image")
+
+    # ---- prediction (degridding) ---------------------------------------------
+    def bin_predict(self, uvw, chan_scale, weight, flag, nrow, counts=None, stream=None):
+        d = _dt()
+        _check(load().rick_bin_predict(
+            self.handle, _ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+            _ptr(weight, d["f32"], "weight", 4), _ptr(flag, d["u8"], "flag"), int(nrow),
+            _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_bin_predict")
+
+    def model_to_wplanes(self, image_real, chan_begin, chan_end, plane_begin, plane_end, grids,
+                         stream=None):
+        d = _dt()
+        _check(load().rick_model_to_wplanes(
+            self.handle, _ptr(image_real, d["f32"], "image_real", 8), chan_begin, chan_end,
+            plane_begin, plane_end, _ptr(grids, d["c64"], "grids", 16), _stream(stream)),
+            "rick_model_to_wplanes")
+
+    def fft_wplanes_forward(self, grids, n_planes, stream=None):
+        d = _dt()
+        _check(load().rick_fft_wplanes_forward(self.handle, _ptr(grids, d["c64"], "grids", 16),
+                                               int(n_planes), _stream(stream)),
+               "rick_fft_wplanes_forward")
+
+    def degrid_binned(self, grids, chan_begin, chan_end, plane_begin, plane_end, vis_out,
+                      stream=None):
+        d = _dt()
+        _check(load().rick_degrid_binned(
+            self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
+            plane_end, _ptr(vis_out, d["c64"], "vis_out", 8), _stream(stream)), "rick_degrid_binned")
+
+    def predict(self, uvw, chan_scale, weight, flag, nrow, image_real, vis_out, counts=None,
+                stream=None):
+        d = _dt()
+        _check(load().rick_predict(
+            self.handle, _ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+            _ptr(weight, d["f32"], "weight", 4), _ptr(flag, d["u8"], "flag"), int(nrow),
+            _ptr(image_real, d["f32"], "image_real", 8), _ptr(vis_out, d["c64"], "vis_out", 8),
+            _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_predict")
 
     def capture_graph(self, uvw, chan_scale, vis, weight, flag, nrow, grids, weight_sum,
                       image_real, counts=None):
