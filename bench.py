@@ -667,12 +667,122 @@ def run_large(args):
         "precision": res}), flush=True)
 
 
+def run_predict(args):
+    """Prediction (degridding) on the default workload's observation: the
+    MeerKAT-shaped 16 channels (32.3 M visibilities), 4096^2, 32 w-planes (16
+    stored with the fold), KB S = 8; the model is the observation's point
+    sources inside the field where the taper gain is >= 1e-2, placed on their
+    nearest pixels (the same model in every channel).
+    A step = rick_bin_predict + rick_model_to_wplanes + rick_fft_wplanes_forward
+    + rick_degrid_binned over all channels and planes; `value` = predicted
+    visibilities / s."""
+    import torch
+    from paper_2601_19714_gb300 import _build, rick
+    _build.build()
+    img, obs = make_workload(args.seed, "cuda")
+    dev = _dev_inputs(obs)
+    C, N = obs.nchan, img.N
+    cfg = plan_config(img, C, not args.no_fold)
+    ns = cfg.stored_planes
+    plan = rick.Plan(cfg)
+    plan.reserve(obs.nrow)
+    dl = img.fov / N
+    src = obs.sources
+    p = np.clip(np.rint(src[:, 0] / dl + N // 2), 0, N - 1).astype(np.int64)
+    q = np.clip(np.rint(src[:, 1] / dl + N // 2), 0, N - 1).astype(np.int64)
+    # sources where the taper gain C(p) C(q) / C(N/2)^2 >= 1e-2: without padding
+    # the division by the taper multiplies FP32 rounding by up to ~5e9 at the
+    # field edges (Kaiser-Bessel, beta 12.25), as for imaging
+    taper = plan.taper()
+    gain = taper[p] * taper[q] / taper[N // 2] ** 2
+    sel = gain >= 1e-2
+    J1 = np.zeros((N, N), np.float32)
+    np.add.at(J1, (q[sel], p[sel]), src[sel, 2].astype(np.float32))
+    J = torch.from_numpy(J1).cuda().unsqueeze(0).repeat(C, 1, 1).contiguous()
+    grids = torch.empty((C, ns, N, N), dtype=torch.complex64, device="cuda")
+    vis = torch.zeros((obs.nrow, C), dtype=torch.complex64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(record=False):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        if e: e[0].record(stream)
+        plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow, counts)
+        if e: e[1].record(stream)
+        plan.model_to_wplanes(J, 0, C, 0, ns, grids)
+        if e: e[2].record(stream)
+        plan.fft_wplanes_forward(grids, C * ns)
+        if e: e[3].record(stream)
+        plan.degrid_binned(grids, 0, C, 0, ns, vis)
+        if e: e[4].record(stream)
+        return e
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    n_pred, n_drop = counts.cpu().tolist()
+    off, _ = plan.bins()
+    own = np.diff(off.astype(np.int64)[::4])   # records per tile (own bins, all classes)
+    tiles_used = int((own > 0).sum())
+    n0 = plan.launch_count()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = []
+    with ClockSampler(0) as clk:
+        a.record(stream)
+        for _ in range(args.steps):
+            evs.append(step(record=True))
+        b.record(stream)
+        torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    launches = plan.launch_count() - n0
+    st = {k: statistics.median([e[i].elapsed_time(e[i + 1]) for e in evs])
+          for i, k in enumerate(("bin", "model", "fft", "degrid"))}
+    hbm, peak_kind = peaks()
+    cells = C * ns * N * N
+    R = cfg.tile or 32
+    b_model = 8.0 * cells + 4.0 * C * N * N
+    b_degrid = 24.0 * n_pred + 8.0 * tiles_used * (R + img.S - 1) ** 2
+    gbs = {"model": b_model / (st["model"] * 1e-3) / 1e9, "degrid": b_degrid / (st["degrid"] * 1e-3) / 1e9,
+           "fft": 16.0 * cells / (st["fft"] * 1e-3) / 1e9}
+    # spot check against Eq. 1 summed over the sources (O2) on a few visibilities
+    import oracle
+    ocfg = oracle.Config(N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov, img.w_min, img.w_max)
+    g = np.random.default_rng(args.seed)
+    rows = g.choice(obs.nrow, 64, replace=False)
+    keep = J1 != 0
+    qq, pp = np.nonzero(keep)
+    Vo = oracle.predict_at(ocfg, obs.uvw, obs.chan_scale, obs.weight, obs.flag, channel=0,
+                           p=pp, q=qq, flux=J1[keep].astype(np.float64), rows=rows)
+    Vg = vis[torch.from_numpy(rows).cuda(), 0].cpu().numpy()
+    err = float(np.abs(Vg - Vo).max() / np.abs(Vo).max())
+    print(json.dumps({
+        "metric": "predicted visibilities/sec at 1 GB300 (degridding); error vs FP64 oracle",
+        "value": n_pred / (ms * 1e-3), "unit": "vis/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+        "config": {"workload": "meerkat_4096sq_32w_16ch_kb8_predict", "visibilities": int(obs.nrow * C),
+                   "predicted": int(n_pred), "dropped": int(n_drop), "hermitian_fold": cfg.hermitian_fold,
+                   "stored_planes": ns,
+                   "model": f"{int(sel.sum())} of the 200 point sources (taper gain >= 1e-2) on pixels, every channel",
+                   "tiles_with_records": tiles_used},
+        "stages_ms": st, "stage_gbs": gbs,
+        "roofline_model": {"bound": "hbm", "achieved": gbs["model"], "peak": hbm, "unit": "GB/s",
+                           "frac": gbs["model"] / hbm, "peak_kind": peak_kind},
+        "roofline_degrid": {"bound": "hbm", "achieved": gbs["degrid"], "peak": hbm, "unit": "GB/s",
+                            "frac": gbs["degrid"] / hbm, "peak_kind": peak_kind},
+        "degrid_vis_per_s": n_pred / (st["degrid"] * 1e-3),
+        "error_vs_oracle": {"max_rel": err, "sampled_visibilities": 64, "channel": 0},
+        "gpu_launches": int(launches), "clocks": clk.summary()}), flush=True)
+
+
 def run_profile_small(args):
     """A small case of the default workload for ncu captures: the MeerKAT
     recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
     grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
-    Runs warm-up + steps whole-path steps and prints one JSON line."""
+    A step images the 2 channels and then predicts visibilities from the
+    dirty images (the degridding path).  Runs warm-up + steps steps and
+    prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
     from visgen.workloads import meerkat
@@ -690,12 +800,21 @@ def run_profile_small(args):
     wsum = torch.empty(C, dtype=torch.float64, device="cuda")
     counts = torch.empty(2, dtype=torch.int64, device="cuda")
 
+    pvis = torch.zeros((obs.nrow, C), dtype=torch.complex64, device="cuda")
+
     def step():
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
         plan.grid_binned(0, C, 0, ns, grids)
         plan.fft_wplanes(grids, C * ns)
         plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        # prediction from the dirty image just made (exercises the degridder)
+        plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow)
+        plan.model_to_wplanes(image, 0, C, 0, ns, grids)
+        plan.fft_wplanes_forward(grids, C * ns)
+        plan.degrid_binned(grids, 0, C, 0, ns, pvis)
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
+                 wsum, counts)
 
     for _ in range(args.warmup):
         step()
@@ -731,7 +850,7 @@ def main():
                     help="headline without the Hermitian fold (all Nw planes stored and "
                          "transformed); the other variant is always measured beside it")
     ap.add_argument("--workload", default="meerkat",
-                    choices=["meerkat", "lofar", "learned", "large", "profile_small"],
+                    choices=["meerkat", "lofar", "learned", "large", "predict", "profile_small"],
                     help="meerkat (default bench line); lofar / learned / large measure the "
                          "batched, learned-kernel and precision-stress workloads; "
                          "profile_small is the small case the ncu captures use")
@@ -744,6 +863,8 @@ def main():
         run_learned(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "predict":
+        run_predict(args)
     elif args.workload == "profile_small":
         run_profile_small(args)
     else:
