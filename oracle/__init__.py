@@ -43,7 +43,8 @@ class _Cfg(C.Structure):
     _fields_ = [("N", C.c_int32), ("Nw", C.c_int32), ("S", C.c_int32), ("kernel", C.c_int32),
                 ("kernel_param", C.c_double), ("fov", C.c_double), ("w_min", C.c_double),
                 ("w_max", C.c_double), ("mlp", C.POINTER(C.c_double)),
-                ("mlp_hidden", C.c_int32), ("mlp_lattice", C.c_int32)]
+                ("mlp_hidden", C.c_int32), ("mlp_lattice", C.c_int32),
+                ("w_support", C.c_int32), ("w_kernel_param", C.c_double)]
 
 
 @dataclass
@@ -61,11 +62,14 @@ class Config:
     mlp: np.ndarray | None = None
     mlp_hidden: int = 64
     mlp_lattice: int = 0
+    w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
+    w_kernel_param: float = 0.0
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Cfg:
         cfg = _Cfg(self.N, self.Nw, self.S, _KINDS[self.kernel], self.kernel_param, self.fov,
-                   self.w_min, self.w_max, None, self.mlp_hidden, self.mlp_lattice)
+                   self.w_min, self.w_max, None, self.mlp_hidden, self.mlp_lattice,
+                   self.w_support, self.w_kernel_param)
         if self.mlp is not None:
             arr = np.ascontiguousarray(self.mlp, dtype=np.float64)
             self._keep = [arr]
@@ -106,7 +110,11 @@ def _declare(L):
     L.oracle_plane_w.restype = d
     L.oracle_plane_w.argtypes = [cfgp, C.c_int]
     vis_args = [cfgp, p, p, C.c_int, p, p, p, i64]
-    L.oracle_place.argtypes = [cfgp, p, p, C.c_int, p, p, i64, p, p, p, p, p, p]
+    L.oracle_place.argtypes = [cfgp, p, p, C.c_int, p, p, i64, p, p, p, p, p, p, p]
+    L.oracle_planes_total.restype = C.c_int
+    L.oracle_planes_total.argtypes = [cfgp]
+    L.oracle_kernel_ft.restype = d
+    L.oracle_kernel_ft.argtypes = [C.c_int, d, C.c_int, d]
     L.oracle_grid_plane.restype = i64
     L.oracle_grid_plane.argtypes = vis_args + [C.c_int, C.c_int, p]
     L.oracle_channel_stats.argtypes = [cfgp, p, p, C.c_int, p, p, i64, C.c_int, p, p, p]
@@ -226,11 +234,22 @@ def place(cfg: Config, uvw, chan_scale, weight, flag=None):
              weight, flag)
     shape = (v.nrow, v.C)
     st, k, i0, j0 = (np.zeros(shape, np.int32) for _ in range(4))
-    fx, fy = np.zeros(shape), np.zeros(shape)
+    fx, fy, fw = np.zeros(shape), np.zeros(shape), np.zeros(shape)
     c = cfg.c()
     lib().oracle_place(C.byref(c), _ptr(v.uvw), _ptr(v.scale), v.C, _ptr(v.weight), _ptr(v.flag),
-                       v.nrow, _ptr(st), _ptr(k), _ptr(i0), _ptr(j0), _ptr(fx), _ptr(fy))
-    return dict(status=st, k=k, i0=i0, j0=j0, fx=fx, fy=fy)
+                       v.nrow, _ptr(st), _ptr(k), _ptr(i0), _ptr(j0), _ptr(fx), _ptr(fy), _ptr(fw))
+    return dict(status=st, k=k, i0=i0, j0=j0, fx=fx, fy=fy, fw=fw)
+
+
+def planes_total(cfg: Config) -> int:
+    """Planes imaged: Nw, or Nw + Sw with a w-kernel."""
+    c = cfg.c()
+    return lib().oracle_planes_total(C.byref(c))
+
+
+def kernel_ft(kind: str, param: float, S: int, nu: float) -> float:
+    """Continuous Fourier transform of a kernel at frequency nu (cycles per cell)."""
+    return lib().oracle_kernel_ft(_KINDS[kind], float(param), int(S), float(nu))
 
 
 def channel_stats(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0):

@@ -79,6 +79,10 @@ typedef struct {
     int32_t mlp_lattice;  /* taps are baked on an (L+1)x(L+1) lattice of (dx, dy)
                              per plane and bilinearly interpolated; 0 = evaluate
                              the network at the exact offsets */
+    int32_t w_support;    /* 0 or 1: each visibility on its closest plane (R4);
+                             even Sw >= 2: convolved in w onto Sw planes with a
+                             Kaiser-Bessel kernel (R14) */
+    double w_kernel_param;/* beta of the w-direction Kaiser-Bessel kernel */
 } oracle_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -384,7 +388,8 @@ typedef struct {
     long i0, j0;   /* first footprint cell along u and along v (R3) */
     double x, y;   /* continuous position in cells (R1) */
     double fx, fy; /* (x - S/2) - floor(x - S/2), in [0, 1) */
-    int k;         /* w-plane (R4) */
+    int k;         /* w-plane (R4); with a w-kernel, the first of its Sw planes (R14) */
+    double fw;     /* with a w-kernel: (z - Sw/2) - floor(z - Sw/2), z = plane coordinate */
     double u, v, w;/* wavelengths at this channel */
 } placement;
 
@@ -394,12 +399,22 @@ static double wplane_scale(const oracle_cfg* cfg)
     return (double)cfg->Nw / (cfg->w_max - cfg->w_min);
 }
 
-/* w_k: centre of plane k (R4). */
+static int w_improved(const oracle_cfg* cfg) { return cfg->w_support >= 2; }
+
+/* Planes imaged: Nw, or Nw + Sw with a w-kernel (Sw/2 more at each end, R14). */
+int oracle_planes_total(const oracle_cfg* cfg)
+{
+    return cfg->Nw + (w_improved(cfg) ? cfg->w_support : 0);
+}
+
+/* w_k: centre of plane k (R4); with a w-kernel, plane k of the extended set,
+ * whose first Sw/2 planes lie below w_min (R14). */
 double oracle_plane_w(const oracle_cfg* cfg, int k)
 {
     if (cfg->Nw <= 1) return 0.5 * (cfg->w_min + cfg->w_max);
     double dw = (cfg->w_max - cfg->w_min) / cfg->Nw;
-    return cfg->w_min + (k + 0.5) * dw;
+    int off = w_improved(cfg) ? cfg->w_support / 2 : 0;
+    return cfg->w_min + (k - off + 0.5) * dw;
 }
 
 static placement place(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
@@ -430,6 +445,17 @@ static placement place(const oracle_cfg* cfg, const double* uvw, const double* s
     P.fy = sy - fly;
     if (cfg->Nw <= 1) {
         P.k = 0;
+    } else if (w_improved(cfg)) {
+        /* R14: plane coordinate z (plane k centred at z = k), clamped to the
+         * w range; footprint of Sw planes as R3 in u and v, shifted by Sw/2 */
+        int Sw = cfg->w_support;
+        double z = (P.w - cfg->w_min) * wplane_scale(cfg) - 0.5;
+        if (z < -0.5) z = -0.5;
+        if (z > cfg->Nw - 0.5) z = cfg->Nw - 0.5;
+        double sz = z - 0.5 * Sw;
+        double fl = floor(sz);
+        P.k = (int)fl + 1 + Sw / 2;
+        P.fw = sz - fl;
     } else {
         double t = (P.w - cfg->w_min) * wplane_scale(cfg);
         double kf = floor(t);
@@ -441,12 +467,50 @@ static placement place(const oracle_cfg* cfg, const double* uvw, const double* s
     return P;
 }
 
+/* Weight of plane k for a placed visibility: 1 on its plane (R4), or the
+ * w-kernel g_w(k - z) on its Sw planes (R14); 0 elsewhere. */
+static double plane_weight(const oracle_cfg* cfg, const placement* P, int k)
+{
+    if (!w_improved(cfg)) return k == P->k ? 1.0 : 0.0;
+    int s = k - P->k;
+    if (s < 0 || s >= cfg->w_support) return 0.0;
+    return oracle_kernel_value(ORACLE_KAISER_BESSEL, cfg->w_kernel_param, cfg->w_support,
+                               (double)s + 1.0 - 0.5 * cfg->w_support - P->fw);
+}
+
+/* Continuous Fourier transform of a separable kernel, C(nu) = int g(s) cos(2 pi s nu) ds
+ * over [-S/2, S/2], by composite Gauss-Legendre quadrature (24 nodes per unit). */
+double oracle_kernel_ft(int kind, double param, int S, double nu)
+{
+    double gx[24], gwt[24];
+    oracle_gauss_legendre(24, gx, gwt);
+    double acc = 0.0;
+    for (int seg = 0; seg < S; ++seg) {
+        double a = -0.5 * S + seg;
+        for (int i = 0; i < 24; ++i) {
+            double si = a + 0.5 + 0.5 * gx[i];
+            acc += 0.5 * gwt[i] * oracle_kernel_value(kind, param, S, si) * cos(2.0 * ORACLE_PI * si * nu);
+        }
+    }
+    return acc;
+}
+
+/* The w-taper C_w((n - 1) dw) that the image is divided by (R14); 1 without a
+ * w-kernel. */
+static double w_taper(const oracle_cfg* cfg, double delta)
+{
+    if (!w_improved(cfg) || cfg->Nw <= 1) return 1.0;
+    double dw = (cfg->w_max - cfg->w_min) / cfg->Nw;
+    return oracle_kernel_ft(ORACLE_KAISER_BESSEL, cfg->w_kernel_param, cfg->w_support, delta * dw);
+}
+
 /* Per-visibility placement, exported so that tests can compare index work
  * exactly.  For each visibility (r, c), r < nrow, c < C, row-major:
- *   status (1 gridded, 0 skipped, -1 dropped), k, i0, j0, fx, fy. */
+ *   status (1 gridded, 0 skipped, -1 dropped), k, i0, j0, fx, fy, and with a
+ *   w-kernel the plane fraction fw (k is then the first of its Sw planes). */
 void oracle_place(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
                   const float* weight, const uint8_t* flag, long nrow, int32_t* status, int32_t* k,
-                  int32_t* i0, int32_t* j0, double* fx, double* fy)
+                  int32_t* i0, int32_t* j0, double* fx, double* fy, double* fw)
 {
     for (long r = 0; r < nrow; ++r)
         for (int c = 0; c < C; ++c) {
@@ -458,6 +522,7 @@ void oracle_place(const oracle_cfg* cfg, const double* uvw, const double* scale,
             j0[idx] = P.ok == 1 ? (int32_t)P.j0 : 0;
             fx[idx] = P.ok == 1 ? P.fx : 0.0;
             fy[idx] = P.ok == 1 ? P.fy : 0.0;
+            if (fw) fw[idx] = P.ok == 1 ? P.fw : 0.0;
         }
 }
 
@@ -493,6 +558,8 @@ static int check_cfg(const oracle_cfg* cfg)
     if (cfg->Nw > 1 && !(cfg->w_max > cfg->w_min)) return 1;
     if (!(cfg->fov > 0.0) || cfg->fov >= 1.0) return 1;
     if (cfg->kernel == ORACLE_LEARNED && (cfg->S != 4 || !cfg->mlp || cfg->mlp_hidden < 1)) return 1;
+    if (cfg->w_support < 0 || cfg->w_support > 16) return 1;
+    if (w_improved(cfg) && ((cfg->w_support & 1) || cfg->Nw < 2 || !(cfg->w_kernel_param > 0.0))) return 1;
     return 0;
 }
 
@@ -522,9 +589,11 @@ long oracle_grid_plane(const oracle_cfg* cfg, const double* uvw, const double* s
     long n = 0;
     for (long r = 0; r < nrow; ++r) {
         placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
-        if (P.ok != 1 || P.k != k) continue;
+        if (P.ok != 1) continue;
+        double pw = plane_weight(cfg, &P, k);
+        if (pw == 0.0) continue;
         size_t idx = (size_t)r * C + c;
-        double complex WV = (double)weight[idx] * ((double)vis[2 * idx] + I * (double)vis[2 * idx + 1]);
+        double complex WV = pw * (double)weight[idx] * ((double)vis[2 * idx] + I * (double)vis[2 * idx + 1]);
         footprint_weights(cfg, &P, gw);
         for (int b = 0; b < S; ++b) {
             long j = P.j0 + b;
@@ -602,7 +671,7 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
     long ng, nd;
     oracle_channel_stats(cfg, uvw, scale, C, weight, flag, nrow, c, &ws, &ng, &nd);
     memset(img, 0, sizeof(double complex) * NN);
-    for (int k = 0; k < cfg->Nw; ++k) {
+    for (int k = 0; k < oracle_planes_total(cfg); ++k) {
         long nk = oracle_grid_plane(cfg, uvw, scale, C, vis, weight, flag, nrow, c, k, G);
         if (nk <= 0) continue;
         oracle_ifft2(N, G);
@@ -619,7 +688,7 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
             double n, d;
             pixel_n(cfg, p, q, &n, &d);
             double sgn = ((p + q) & 1) ? -1.0 : 1.0;
-            double s = ws != 0.0 ? sgn * n / (ws * Ct[p] * Ct[q]) : 0.0;
+            double s = ws != 0.0 ? sgn * n / (ws * Ct[p] * Ct[q] * w_taper(cfg, d)) : 0.0;
             img[(size_t)q * N + p] *= s;
         }
     if (weight_sum_out) *weight_sum_out = ws;
@@ -654,11 +723,12 @@ int oracle_image_at(const oracle_cfg* cfg, const double* uvw, const double* scal
     for (long r = 0; r < nrow; ++r) {
         placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
         if (P.ok != 1) continue;
-        if (plane >= 0 && P.k != plane) continue;
+        if (plane >= 0 && plane_weight(cfg, &P, plane) == 0.0) continue;
         size_t idx = (size_t)r * C + c;
         double complex WV = (double)weight[idx] * ((double)vis[2 * idx] + I * (double)vis[2 * idx + 1]);
         footprint_weights(cfg, &P, gw);
-        double wk = oracle_plane_w(cfg, P.k);
+        /* the visibility's planes: its own (R4) or its Sw planes (R14) */
+        int kfirst = P.k, kn = w_improved(cfg) ? cfg->w_support : 1;
         for (long t = 0; t < npix; ++t) {
             int p = pp[t], q = qq[t];
             for (int a = 0; a < S; ++a) {
@@ -678,7 +748,12 @@ int oracle_image_at(const oracle_cfg* cfg, const double* uvw, const double* scal
             if (plane < 0) {
                 double n, d;
                 pixel_n(cfg, p, q, &n, &d);
-                acc *= turn_phasor(wk * d);
+                double complex ph = 0.0;
+                for (int s = 0; s < kn; ++s)
+                    ph += plane_weight(cfg, &P, kfirst + s) * turn_phasor(oracle_plane_w(cfg, kfirst + s) * d);
+                acc *= ph;
+            } else {
+                acc *= plane_weight(cfg, &P, plane);
             }
             out[t] += WV * acc;
         }
@@ -689,7 +764,7 @@ int oracle_image_at(const oracle_cfg* cfg, const double* uvw, const double* scal
             double n, d;
             pixel_n(cfg, p, q, &n, &d);
             double sgn = ((p + q) & 1) ? -1.0 : 1.0;
-            out[t] *= ws != 0.0 ? sgn * n / (ws * Ct[p] * Ct[q]) : 0.0;
+            out[t] *= ws != 0.0 ? sgn * n / (ws * Ct[p] * Ct[q] * w_taper(cfg, d)) : 0.0;
         }
     free(Ct);
     free(gw);
@@ -781,19 +856,22 @@ int oracle_predict(const oracle_cfg* cfg, const double* uvw, const double* scale
     if (!F || !Ct || !gw) { free(F); free(Ct); free(gw); return 2; }
     cfg_taper(cfg, Ct);
     for (long r = 0; r < nrow; ++r) out[r] = 0.0;
-    for (int k = 0; k < cfg->Nw; ++k) {
+    for (int k = 0; k < oracle_planes_total(cfg); ++k) {
         double wk = oracle_plane_w(cfg, k);
         for (int q = 0; q < N; ++q)
             for (int p = 0; p < N; ++p) {
                 double n, d;
                 pixel_n(cfg, p, q, &n, &d);
                 double sgn = ((p + q) & 1) ? -1.0 : 1.0;
-                F[(size_t)q * N + p] = sgn * J[(size_t)q * N + p] * turn_phasor(-wk * d) / (n * Ct[p] * Ct[q]);
+                F[(size_t)q * N + p] = sgn * J[(size_t)q * N + p] * turn_phasor(-wk * d) /
+                                       (n * Ct[p] * Ct[q] * w_taper(cfg, d));
             }
         fft2_forward(N, F);
         for (long r = 0; r < nrow; ++r) {
             placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
-            if (P.ok != 1 || P.k != k) continue;
+            if (P.ok != 1) continue;
+            double pw = plane_weight(cfg, &P, k);
+            if (pw == 0.0) continue;
             footprint_weights(cfg, &P, gw);
             double complex acc = 0.0;
             for (int b = 0; b < S; ++b)
@@ -802,7 +880,7 @@ int oracle_predict(const oracle_cfg* cfg, const double* uvw, const double* scale
                     double sgn = ((i + j) & 1) ? -1.0 : 1.0;
                     acc += gw[b * S + a] * sgn * F[(size_t)j * N + i];
                 }
-            out[r] = acc;
+            out[r] += pw * acc;
         }
     }
     free(F);
@@ -837,12 +915,15 @@ int oracle_predict_at(const oracle_cfg* cfg, const double* uvw, const double* sc
         placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
         if (P.ok != 1) continue;
         footprint_weights(cfg, &P, gw);
-        double wk = oracle_plane_w(cfg, P.k);
+        int kn = w_improved(cfg) ? cfg->w_support : 1;
         double complex acc = 0.0;
         for (long s = 0; s < nsrc; ++s) {
             double n, d;
             pixel_n(cfg, sp[s], sq[s], &n, &d);
-            double complex Ms = flux[s] * turn_phasor(-wk * d) / (n * Ct[sp[s]] * Ct[sq[s]]);
+            double complex ph = 0.0;  /* sum over the visibility's planes (R4 / R14) */
+            for (int t2 = 0; t2 < kn; ++t2)
+                ph += plane_weight(cfg, &P, P.k + t2) * turn_phasor(-oracle_plane_w(cfg, P.k + t2) * d);
+            double complex Ms = flux[s] * ph / (n * Ct[sp[s]] * Ct[sq[s]] * w_taper(cfg, d));
             long ps = sp[s] - N / 2, qs = sq[s] - N / 2;
             for (int b = 0; b < S; ++b) {
                 long j = P.j0 + b - N / 2;
