@@ -97,22 +97,38 @@ typedef struct rick_config {
     /* Hermitian fold (0 = off).  The dirty image is the real part of the sum
      * over planes in Eq. 2, and Re(z) = Re(conj z), so a visibility V at
      * (u, v) on plane k contributes exactly what conj(V) at (-u, -v) on the
-     * plane of w = -w_k contributes.  With the fold on, every visibility whose
-     * plane k lies in the upper half (2k > Nw - 1) is gridded as its conjugate
-     * on plane Nw - 1 - k at the mirrored cells (N - i) mod N, (N - j) mod N,
-     * with the same kernel taps.  Only the lower ceil(Nw/2) planes are then
+     * plane of w = -w_k contributes.  With the fold on, every record whose
+     * plane k lies in the upper half (2k > Nt - 1, Nt the plane count: Nw, or
+     * Nw + Sw with a w-kernel) is gridded as its conjugate on plane Nt - 1 - k
+     * at the mirrored cells (N - i) mod N, (N - j) mod N, with the same kernel
+     * taps and plane weight.  Only the lower ceil(Nt/2) planes are then
      * stored, transformed and reduced: every plane index, plane range and
      * grid array of the API counts stored planes, and the real image equals
      * the unfolded one up to FP32 rounding (the imaginary part of the
      * complex image is not the unfolded one).  The placement decisions (plane,
      * footprint, drop) are those of the unfolded visibility.  Requires
-     * w_min == -w_max (so that plane Nw - 1 - k sits at -w_k) and a
+     * w_min == -w_max (so that plane Nt - 1 - k sits at -w_k) and a
      * point-symmetric kernel (Gaussian or Kaiser-Bessel, not TABLE). */
     int32_t hermitian_fold;
+    /* w-direction kernel ("improved w-stacking"; 0 or 1 = off).  Eq. 3 writes
+     * the gridding kernel as a function of (u, v, w); the paper's method puts
+     * each visibility on its closest plane.  With an even w_support Sw in
+     * [2, 8] each visibility is spread over Sw consecutive planes with
+     * Kaiser-Bessel weights g_w(k - z) (beta = w_kernel_param, z the continuous
+     * plane coordinate (w - w_min)/dw - 1/2, clamped to the w range), the
+     * planes extend Sw/2 beyond [w_min, w_max] at each end (Nw + Sw planes
+     * before the fold, plane k centred at w_min + (k - Sw/2 + 1/2) dw), and the
+     * image is also divided by the kernel's transform C_w((n - 1) dw).  The
+     * prediction uses the same weights and taper.  Gridding work and records
+     * grow by Sw, and nrow * C * Sw must stay below 2^32 - 1 per plan call.
+     * Not with a TABLE kernel nor in rick_grid_noalloc or the learned-kernel
+     * trainer (RICK_ERR_INVALID_ARG / RICK_ERR_UNSUPPORTED). */
+    int32_t w_support;
+    double w_kernel_param;
 } rick_config;
 
-/* Planes a plan stores for cfg: ceil(Nw / 2) with the Hermitian fold, Nw
- * without; -1 if cfg is NULL. */
+/* Planes a plan stores for cfg: P = Nw, or Nw + Sw with a w-kernel; ceil(P / 2)
+ * with the Hermitian fold; -1 if cfg is NULL. */
 int32_t rick_stored_planes(const rick_config* cfg);
 
 typedef struct rick_plan rick_plan;
@@ -268,9 +284,11 @@ rick_status rick_autotune(const rick_config* base, const double* uvw, const doub
  *   V(u, v, w) = sum_{p,q} J(p, q) / n exp(-2 pi i (u l + v m + w (n - 1))),
  * in w-stacking form with the readings of the imaging path (cell and pixel
  * maps, footprint, planes, checkerboard, taper):
- *   M_k = (-1)^(p+q) J exp(-2 pi i w_k (n - 1)) / (n C(p) C(q))   (per plane)
+ *   M_k = (-1)^(p+q) J exp(-2 pi i w_k (n - 1)) / (n C(p) C(q) C_w)   (per plane)
  *   F_k = forward 2-D DFT of M_k (cuFFT, exponent -)
- *   V   = sum over the footprint of g(i - x) g(j - y) (-1)^(i+j) F_k(i, j).
+ *   V   = sum over the footprint of g(i - x) g(j - y) (-1)^(i+j) F_k(i, j)
+ * (C_w = 1 and the closest plane without a w-kernel; with one, V sums the Sw
+ * planes' values times their weights g_w).
  * With the Hermitian fold, visibilities of the upper half of the planes are
  * predicted on the mirrored plane at the mirrored cells and conjugated (exact
  * for a real image).  Gaussian and Kaiser-Bessel kernels (not TABLE). */
@@ -296,7 +314,8 @@ rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_pl
 /* V for every visibility binned by rick_bin_predict whose channel and plane lie
  * in the ranges, from the transformed planes `grids` (layout as for
  * rick_grid_binned): vis_out[nrow][C] complex64 (device) receives those
- * entries; the others are left untouched. */
+ * entries; the others are left untouched.  With a w-kernel a visibility has
+ * Sw planes and each adds its share (+=), so the caller zeroes vis_out. */
 rick_status rick_degrid_binned(rick_plan* plan, const float* grids, int32_t chan_begin,
                                int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                float* vis_out, void* stream);

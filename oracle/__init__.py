@@ -291,16 +291,19 @@ def fold_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, 
     The dirty image is the real part of the sum over planes in Eq. 2 and
     Re(z) = Re(conj z); with w_min = -w_max, plane Nw-1-k sits at -w_k, so
     the contribution of plane k' = Nw-1-k equals that of the conjugate of
-    its grid mirrored to (-u, -v) on plane k.  Definition:
-        H_k = G_k + conj(mirror(G_{Nw-1-k}))   for 2k < Nw - 1,
-        H_k = G_k                              for 2k = Nw - 1 (odd Nw).
+    its grid mirrored to (-u, -v) on plane k.  Definition, with Nt the
+    number of planes imaged (Nw, or Nw + Sw with a w-kernel, whose extended
+    set is symmetric about w = 0 as well):
+        H_k = G_k + conj(mirror(G_{Nt-1-k}))   for 2k < Nt - 1,
+        H_k = G_k                              for 2k = Nt - 1 (odd Nt).
     """
     if cfg.w_min != -cfg.w_max:
         raise ValueError("the fold needs w_min == -w_max")
-    if not 0 <= 2 * plane <= cfg.Nw - 1:
-        raise ValueError("stored planes are 0 .. ceil(Nw/2) - 1")
+    nt = planes_total(cfg)
+    if not 0 <= 2 * plane <= nt - 1:
+        raise ValueError("stored planes are 0 .. ceil(Nt/2) - 1")
     G = grid_plane(cfg, uvw, chan_scale, vis, weight, flag, channel, plane)
-    k2 = cfg.Nw - 1 - plane
+    k2 = nt - 1 - plane
     if k2 == plane:
         return G
     return G + np.conj(mirror(grid_plane(cfg, uvw, chan_scale, vis, weight, flag, channel, k2)))

@@ -129,14 +129,16 @@ struct rick_plan {
     rick_config cfg;
     int device = 0, num_sms = 0;
     int T = 64, NT = 0, threads = 256, grab = 8;
-    int planes = 0;  // stored planes: ceil(Nw/2) with the Hermitian fold, else Nw
+    int planes = 0;  // stored planes: ceil(Nt/2) with the Hermitian fold, else Nt
+                     // (Nt = Nw, or Nw + Sw with a w-kernel)
+    int nrec_per_vis = 1;  // records per visibility: Sw with a w-kernel, else 1
     uint64_t nkeys = 0;
     double w_scale = 0.0, dw = 0.0;
     std::vector<double> taper;
     float* d_inv_taper = nullptr;
     float* d_table = nullptr;
     int lattice = 0;
-    // binning scratch
+    // binning scratch, sized in records (visibilities x records per visibility)
     int64_t cap_vis = 0;
     uint32_t* d_key = nullptr;
     uint32_t* d_rank = nullptr;
@@ -152,7 +154,7 @@ struct rick_plan {
     int* d_status = nullptr;
     double* d_wsum = nullptr;
     bool binned = false;
-    bool binned_for_predict = false;  // records hold (index, conj) instead of W V
+    bool binned_for_predict = false;  // records hold (index, signed weight) instead of W V
     // cuFFT: batch B and single-plane plans
     cufftHandle fft_b = 0, fft_1 = 0;
     bool have_b = false, have_1 = false;
@@ -168,6 +170,9 @@ struct rick_plan {
     cudaStream_t last_stream = nullptr;
     float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
     double tap_fit_error = 0.0;
+    // w-kernel: tap polynomials and the constants of its transform C_w
+    float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
+    double w_c0 = 1.0, w_s_i0 = 1.0;
 };
 
 namespace {
@@ -201,8 +206,11 @@ void release(rick_plan* P) {
     P->have_b = P->have_1 = false;
 }
 
+int planes_total(const rick_config& c) { return c.n_wplanes + (c.w_support >= 2 ? c.w_support : 0); }
+
 int stored_planes(const rick_config& c) {
-    return c.hermitian_fold ? (c.n_wplanes + 1) / 2 : c.n_wplanes;
+    const int t = planes_total(c);
+    return c.hermitian_fold ? (t + 1) / 2 : t;
 }
 
 rick_status validate(const rick_config* c) {
@@ -234,6 +242,16 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 8, "tiles_per_grab must be in [0, 8]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
+    RK_ARG(c->w_support == 0 || c->w_support == 1 ||
+               (c->w_support >= 2 && c->w_support <= 8 && (c->w_support & 1) == 0),
+           "w_support must be 0, 1 or even in [2, 8]");
+    if (c->w_support >= 2) {
+        RK_ARG(c->n_wplanes >= 2, "a w-kernel needs n_wplanes >= 2");
+        RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE,
+               "a w-kernel needs a Gaussian or Kaiser-Bessel uv kernel (not a table kernel)");
+        RK_ARG(c->w_kernel_param > 0.0 && std::isfinite(c->w_kernel_param),
+               "w_kernel_param must be > 0 with a w-kernel");
+    }
     if (c->hermitian_fold) {
         RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE,
                "hermitian_fold needs a point-symmetric kernel (Gaussian or Kaiser-Bessel)");
@@ -320,6 +338,28 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
             return RICK_ERR_UNSUPPORTED;
         }
     }
+    if (c.w_support >= 2) {
+        // the w-kernel: Kaiser-Bessel of support Sw; its taps by the same
+        // polynomial fit, and C_w(0) = Sw sinh(beta) / (beta I0(beta))
+        GridParams fit;
+        const double err = fit_tap_polynomials(RICK_KERNEL_KAISER_BESSEL, c.w_kernel_param, c.w_support, fit);
+        if (!(err <= 1e-6)) {
+            set_err("w_kernel_param %g: the w-kernel's tap polynomials reach only %.2e (limit 1e-6)",
+                    c.w_kernel_param, err);
+            return RICK_ERR_UNSUPPORTED;
+        }
+        for (int a = 0; a < c.w_support; ++a)
+            for (int q = 0; q <= kPolyDegree; ++q) P->w_coef[a][q] = fit.coef[a][q];
+        const double b = c.w_kernel_param;
+        double term = 1.0, i0 = 1.0;
+        for (int k = 1; k < 400 && term > 1e-17 * i0; ++k) {
+            term *= 0.25 * b * b / ((double)k * k);
+            i0 += term;
+        }
+        P->w_s_i0 = c.w_support / i0;
+        P->w_c0 = P->w_s_i0 * std::sinh(b) / b;
+        P->nrec_per_vis = c.w_support;
+    }
     const int taper_kind = c.kernel_kind == RICK_KERNEL_TABLE ? RICK_KERNEL_KAISER_BESSEL : c.kernel_kind;
     make_taper(taper_kind, c.kernel_param, c.support, c.N, P->taper);
     std::vector<float> inv(c.N);
@@ -370,15 +410,17 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
     const int64_t nvis = nrow * (int64_t)c.n_channels;
     RK_ARG(nrow == 0 || nvis / nrow == c.n_channels, "nrow * C overflows");
-    if (nvis >= (int64_t)0xFFFFFFFFLL) {
-        set_err("nrow * C = %lld exceeds 2^32 - 2 visibilities per plan call", (long long)nvis);
+    const int64_t nrec = nvis * P->nrec_per_vis;
+    if (nrec >= (int64_t)0xFFFFFFFFLL) {
+        set_err("nrow * C%s = %lld exceeds 2^32 - 2 records per plan call",
+                P->nrec_per_vis > 1 ? " * w_support" : "", (long long)nrec);
         return RICK_ERR_UNSUPPORTED;
     }
     if (nrow > 0) {
         RK_ARG(uvw && chan_scale && (vis || predict) && weight,
                "uvw, chan_scale, vis and weight are required");
     }
-    RK_TRY(ensure_vis_capacity(P, nvis));
+    RK_TRY(ensure_vis_capacity(P, nrec));
     P->last_stream = st;
     int launches = 0;
     RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
@@ -395,6 +437,9 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     pp.fold = c.hermitian_fold;
     pp.Nw_store = P->planes;
     pp.predict = predict ? 1 : 0;
+    pp.w_support = c.w_support >= 2 ? c.w_support : 0;
+    pp.Nw_total = planes_total(c);
+    std::memcpy(pp.wcoef, P->w_coef, sizeof pp.wcoef);
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;
@@ -415,7 +460,7 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
                          "scan kernels");
     if (s == RICK_OK)
         s = check_launch(launch_scatter(P->d_key, P->d_rank, P->d_stage, P->d_offsets,
-                                        P->d_records, nvis, P->num_sms, st, &launches),
+                                        P->d_records, nrec, P->num_sms, st, &launches),
                          "scatter kernel");
     P->launches += launches;
     RK_TRY(s);
@@ -457,6 +502,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.grab = (uint32_t)P->grab;
     G.lists = P->d_lists;
     G.list_cap = P->list_cap;
+    G.w_support = 0;
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, 8 * sizeof(uint32_t), st));
     int launches = 0;
@@ -507,6 +553,28 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
     return RICK_OK;
 }
 
+// Phase-screen parameters of planes [k0, k1) (stored indices) of channels
+// [c0, c1): plane k is centred at w_min + (k - off + 1/2) dw, off = Sw/2 with
+// a w-kernel (its extended plane set starts below w_min), else 0.
+PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
+    const rick_config& c = P->cfg;
+    PhaseParams pp;
+    pp.N = c.N;
+    pp.nc = c1 - c0;
+    pp.nk = k1 - k0;
+    pp.dl = c.fov_rad / c.N;
+    pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
+    const int off = c.w_support >= 2 ? c.w_support / 2 : 0;
+    pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 - off + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
+    pp.precision = c.precision;
+    pp.w_support = c.w_support >= 2 && c.n_wplanes > 1 ? c.w_support : 0;
+    pp.w_beta = c.w_kernel_param;
+    pp.w_c0 = (float)P->w_c0;
+    pp.w_s_i0 = (float)P->w_s_i0;
+    pp.w_exp2b = (float)std::exp(-2.0 * c.w_kernel_param);
+    return pp;
+}
+
 rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0, int k1,
                        const double* weight_sum, float* image_real, float* image_complex,
                        cudaStream_t st) {
@@ -517,14 +585,7 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
     RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image_real & 7u) == 0 &&
                ((uintptr_t)image_complex & 15u) == 0,
            "grids/image_complex must be 16-byte and image_real 8-byte aligned");
-    PhaseParams pp;
-    pp.N = c.N;
-    pp.nc = c1 - c0;
-    pp.nk = k1 - k0;
-    pp.dl = c.fov_rad / c.N;
-    pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
-    pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
-    pp.precision = c.precision;
+    const PhaseParams pp = phase_params(P, c0, c1, k0, k1);
     P->last_stream = st;
     int launches = 0;
     rick_status s = check_launch(
@@ -534,19 +595,6 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
         "phase kernel");
     P->launches += launches;
     return s;
-}
-
-PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
-    const rick_config& c = P->cfg;
-    PhaseParams pp;
-    pp.N = c.N;
-    pp.nc = c1 - c0;
-    pp.nk = k1 - k0;
-    pp.dl = c.fov_rad / c.N;
-    pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
-    pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
-    pp.precision = c.precision;
-    return pp;
 }
 
 rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
@@ -591,6 +639,7 @@ rick_status degrid_impl(rick_plan* P, const float* grids, int c0, int c1, int k0
     G.nk = k1 - k0;
     G.n_items = (uint32_t)items;
     G.kind = c.kernel_kind;
+    G.w_support = c.w_support >= 2 ? c.w_support : 0;
     std::memcpy(G.coef, P->tap_coef, sizeof G.coef);
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
@@ -734,10 +783,11 @@ rick_status rick_plan_destroy(rick_plan* plan) {
 rick_status rick_plan_reserve(rick_plan* plan, int64_t max_rows) {
     RK_ARG(plan != nullptr, "plan is NULL");
     RK_ARG(max_rows >= 0, "max_rows must be >= 0");
-    const int64_t nvis = max_rows * (int64_t)plan->cfg.n_channels;
-    RK_ARG(max_rows == 0 || nvis / max_rows == plan->cfg.n_channels, "overflow");
+    const int64_t nvis = max_rows * (int64_t)plan->cfg.n_channels * plan->nrec_per_vis;
+    RK_ARG(max_rows == 0 || nvis / max_rows == (int64_t)plan->cfg.n_channels * plan->nrec_per_vis,
+           "overflow");
     if (nvis >= (int64_t)0xFFFFFFFFLL) {
-        set_err("reservation exceeds 2^32 - 2 visibilities");
+        set_err("reservation exceeds 2^32 - 2 records");
         return RICK_ERR_UNSUPPORTED;
     }
     return ensure_vis_capacity(plan, nvis);
@@ -918,10 +968,10 @@ rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double*
     RK_ARG(plan && out && weight_sum && image_real, "plan, out, weight_sum and image_real are required");
     *out = nullptr;
     const rick_config& c = plan->cfg;
-    const int64_t nvis = nrow * (int64_t)c.n_channels;
+    const int64_t nvis = nrow * (int64_t)c.n_channels * plan->nrec_per_vis;
     RK_ARG(nrow >= 0, "nrow must be >= 0");
     if (nvis > plan->cap_vis) {
-        set_err("graph capture: the plan is reserved for %lld visibilities, %lld requested; call "
+        set_err("graph capture: the plan is reserved for %lld records, %lld requested; call "
                 "rick_plan_reserve first (nothing may allocate during capture)",
                 (long long)plan->cap_vis, (long long)nvis);
         return RICK_ERR_CAPACITY;

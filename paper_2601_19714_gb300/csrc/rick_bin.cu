@@ -30,6 +30,16 @@ struct Placed {
     int status;  // 1 gridded, 0 skipped, -1 dropped
 };
 
+// Placement of one visibility before its records are formed: footprint start,
+// 24-bit fractions, first plane (of the extended set with a w-kernel) and the
+// w fraction.
+struct Base {
+    int status;  // 1 placed, 0 skipped, -1 dropped
+    int i0, j0, k;
+    uint32_t fqx, fqy;
+    float fw;
+};
+
 // The record and bin key of a placed visibility: plane k, footprint start
 // (i0, j0) and fractional offsets fq = round(f * 2^24) in [0, 2^24].
 //
@@ -44,12 +54,13 @@ struct Placed {
 // 0 picks it up as a halo (likewise for rows).
 __device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k, int i0, int j0,
                                               uint32_t fqx, uint32_t fqy, float W, float2 V,
-                                              uint32_t vidx, Placed& out) {
-    float wv_im = W * V.y;
+                                              float gw, uint32_t vidx, Placed& out) {
+    const float Wg = W * gw;
+    float wv_im = Wg * V.y;
     bool folded = false;
-    if (P.fold && 2 * k > P.Nw - 1) {
+    if (P.fold && 2 * k > P.Nw_total - 1) {
         folded = true;
-        k = P.Nw - 1 - k;
+        k = P.Nw_total - 1 - k;
         i0 = P.N - i0 - P.S + 1;  // in [1, N - S + 1]; N only for S = 1, i0 = 0
         j0 = P.N - j0 - P.S + 1;
         if (i0 == P.N) i0 = 0;
@@ -66,8 +77,8 @@ __device__ __forceinline__ void finish_record(const PlaceParams& P, int c, int k
     const uint64_t key =
         ((((uint64_t)c * P.Nw_store + k) * P.NT + ty) * P.NT + tx) * 4u + (uint64_t)cls;
     out.key = (uint32_t)key;
-    out.rec.wv_re = P.predict ? __uint_as_float(vidx) : W * V.x;
-    out.rec.wv_im = P.predict ? __uint_as_float(folded ? 1u : 0u) : wv_im;
+    out.rec.wv_re = P.predict ? __uint_as_float(vidx) : Wg * V.x;
+    out.rec.wv_im = P.predict ? (folded ? -gw : gw) : wv_im;
     out.rec.px = ((uint32_t)il << kFracBits) | fqx;
     out.rec.py = ((uint32_t)jl << kFracBits) | fqy;
     out.status = 1;
@@ -139,11 +150,11 @@ __device__ __forceinline__ bool place_axis(const PlaceParams& P, double sx, int&
 // visibility, GB300's FP64 rate being a small fraction of its FP32 rate); the
 // floors, fractions, 24-bit rounding, range and finiteness tests are read from
 // the bit patterns with integer operations (exactly the same results).
-__device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, double v0, double w0,
-                                             double sc, int c, float W, float2 V, uint32_t vidx) {
-    Placed out;
-    out.key = kInvalidKey;
+__device__ __forceinline__ Base place_fp64(const PlaceParams& P, double u0, double v0, double w0,
+                                           double sc) {
+    Base out;
     out.status = -1;
+    out.fw = 0.f;
     const double u = __dmul_rn(u0, sc), v = __dmul_rn(v0, sc), w = __dmul_rn(w0, sc);
     const double x = __dadd_rn(__dmul_rn(u, P.fov), P.half_n);
     const double y = __dadd_rn(__dmul_rn(v, P.fov), P.half_n);
@@ -153,7 +164,18 @@ __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, do
     if (!place_axis(P, __dsub_rn(x, P.half_s), i0, fqx)) return out;
     if (!place_axis(P, __dsub_rn(y, P.half_s), j0, fqy)) return out;
     int k = 0;
-    if (P.Nw > 1) {
+    if (P.Nw > 1 && P.w_support >= 2) {
+        // w-kernel: plane coordinate z = t - 1/2 clamped to the w range, first
+        // plane floor(z - Sw/2) + 1 (+ Sw/2 in the extended set), fraction fw
+        const double t = __dmul_rn(__dsub_rn(w, P.w_min), P.w_scale);
+        double z = __dsub_rn(t, 0.5);
+        if (z < -0.5) z = -0.5;
+        if (z > P.Nw - 0.5) z = P.Nw - 0.5;
+        const double sz = __dsub_rn(z, 0.5 * P.w_support);
+        const double fl = floor(sz);
+        k = (int)fl + 1 + P.w_support / 2;
+        out.fw = (float)__dsub_rn(sz, fl);
+    } else if (P.Nw > 1) {
         const double t = __dmul_rn(__dsub_rn(w, P.w_min), P.w_scale);
         const unsigned long long tb = (unsigned long long)__double_as_longlong(t);
         int fl;
@@ -163,17 +185,21 @@ __device__ __forceinline__ Placed place_fp64(const PlaceParams& P, double u0, do
         else if (!split_cell(t, fl, unused)) k = P.Nw - 1;          // +inf or >= 2^30: clamp high
         else k = min(fl, P.Nw - 1);
     }
-    out.status = 0;
-    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, vidx, out);
+    out.status = 1;
+    out.i0 = i0;
+    out.j0 = j0;
+    out.k = k;
+    out.fqx = fqx;
+    out.fqy = fqy;
     return out;
 }
 
 // All-FP32 placement (precision study): same steps in single precision.
-__device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, double v0, double w0,
-                                             double sc, int c, float W, float2 V, uint32_t vidx) {
-    Placed out;
-    out.key = kInvalidKey;
+__device__ __forceinline__ Base place_fp32(const PlaceParams& P, double u0, double v0, double w0,
+                                           double sc) {
+    Base out;
     out.status = 0;
+    out.fw = 0.f;
     const float s = (float)sc;
     const float u = (float)u0 * s, v = (float)v0 * s, w = (float)w0 * s;
     const float x = u * P.fov_f + P.half_n_f, y = v * P.fov_f + P.half_n_f;
@@ -190,13 +216,24 @@ __device__ __forceinline__ Placed place_fp32(const PlaceParams& P, double u0, do
     const int i0 = (int)flx + 1, j0 = (int)fly + 1;
     const float fx = sx - flx, fy = sy - fly;
     int k = 0;
-    if (P.Nw > 1) {
+    if (P.Nw > 1 && P.w_support >= 2) {
+        float z = (w - P.w_min_f) * P.w_scale_f - 0.5f;
+        z = fminf(fmaxf(z, -0.5f), (float)P.Nw - 0.5f);
+        const float sz = z - 0.5f * P.w_support;
+        const float fl = floorf(sz);
+        k = (int)fl + 1 + P.w_support / 2;
+        out.fw = sz - fl;
+    } else if (P.Nw > 1) {
         float kf = floorf((w - P.w_min_f) * P.w_scale_f);
         kf = fminf(fmaxf(kf, 0.0f), (float)(P.Nw - 1));
         k = (int)kf;
     }
-    const uint32_t fqx = __float2uint_rn(fx * 16777216.0f), fqy = __float2uint_rn(fy * 16777216.0f);
-    finish_record(P, c, k, i0, j0, fqx, fqy, W, V, vidx, out);
+    out.status = 1;
+    out.i0 = i0;
+    out.j0 = j0;
+    out.k = k;
+    out.fqx = __float2uint_rn(fx * 16777216.0f);
+    out.fqy = __float2uint_rn(fy * 16777216.0f);
     return out;
 }
 
@@ -224,39 +261,56 @@ k_place(PlaceParams P, const double* __restrict__ uvw, const double* __restrict_
 
     double my_wsum = 0.0;
     uint32_t n_grid = 0, n_drop = 0;
+    const int nrec = P.w_support >= 2 ? P.w_support : 1;   // records per visibility
     for (int64_t base = tid0 - lane; base < nvis; base += stride) {
         const int64_t idx = base + lane;
-        Placed pl;
-        pl.key = kInvalidKey;
-        pl.status = 0;
+        Base b;
+        b.status = 0;
+        float W = 0.f;
+        float2 V = make_float2(0.f, 0.f);
         if (idx < nvis) {
             const bool flagged = flag != nullptr && flag[idx] != 0;
-            const float W = weight[idx];
+            W = weight[idx];
             if (!flagged && W != 0.0f && isfinite(W)) {
                 const int64_t r = idx / P.C;
                 const double u0 = uvw[3 * r], v0 = uvw[3 * r + 1], w0 = uvw[3 * r + 2];
-                const float2 V = vis != nullptr ? vis[idx] : make_float2(0.f, 0.f);
-                pl = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc, c, W, V, (uint32_t)idx)
-                                                : place_fp64(P, u0, v0, w0, sc, c, W, V, (uint32_t)idx);
-                if (pl.status == 1) {
+                if (vis != nullptr) V = vis[idx];
+                b = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc)
+                                               : place_fp64(P, u0, v0, w0, sc);
+                if (b.status == 1) {
                     my_wsum += (double)W;
                     ++n_grid;
-                } else if (pl.status == -1) {
+                } else if (b.status == -1) {
                     ++n_drop;
                 }
             }
         }
-        // rank within the bin: one atomic per distinct key in the warp
-        const unsigned peers = __match_any_sync(0xffffffffu, pl.key);
-        const int leader = __ffs(peers) - 1;
-        uint32_t first = 0;
-        if (lane == leader && pl.key != kInvalidKey) first = atomicAdd(&hist[pl.key], __popc(peers));
-        first = __shfl_sync(0xffffffffu, first, leader);
-        if (idx < nvis) {
-            key_out[idx] = pl.key;
-            if (pl.key != kInvalidKey) {
-                rank_out[idx] = first + __popc(peers & ((1u << lane) - 1u));
-                stage[idx] = pl.rec;
+        const float tw = fmaf(2.0f, b.fw, -1.0f);
+        for (int sw = 0; sw < nrec; ++sw) {
+            Placed pl;
+            pl.key = kInvalidKey;
+            if (b.status == 1) {
+                float gw = 1.0f;
+                if (P.w_support >= 2) {
+                    gw = P.wcoef[sw][kPolyDegree];
+#pragma unroll
+                    for (int q = kPolyDegree - 1; q >= 0; --q) gw = fmaf(gw, tw, P.wcoef[sw][q]);
+                }
+                finish_record(P, c, b.k + sw, b.i0, b.j0, b.fqx, b.fqy, W, V, gw, (uint32_t)idx, pl);
+            }
+            // rank within the bin: one atomic per distinct key in the warp
+            const unsigned peers = __match_any_sync(0xffffffffu, pl.key);
+            const int leader = __ffs(peers) - 1;
+            uint32_t first = 0;
+            if (lane == leader && pl.key != kInvalidKey) first = atomicAdd(&hist[pl.key], __popc(peers));
+            first = __shfl_sync(0xffffffffu, first, leader);
+            if (idx < nvis) {
+                const int64_t o = idx * nrec + sw;
+                key_out[o] = pl.key;
+                if (pl.key != kInvalidKey) {
+                    rank_out[o] = first + __popc(peers & ((1u << lane) - 1u));
+                    stage[o] = pl.rec;
+                }
             }
         }
     }

@@ -4,8 +4,10 @@
 //   V = sum_{a,b} g(i0 + a - x) g(j0 + b - y) (-1)^(i+j) F_k(i0 + a, j0 + b),
 // where F_k is the forward transform of the model planes built by
 // k_model_planes (so that (-1)^(i+j) F_k is the plane of the w-stacking
-// prediction, see the oracle's oracle_predict), conjugated for visibilities
-// that the Hermitian fold mapped onto the mirrored plane.
+// prediction), times the record's plane weight and conjugated for records
+// that the Hermitian fold mapped onto the mirrored plane.  Without a w-kernel
+// a visibility has one record and its prediction is stored; with one
+// (improved w-stacking) its Sw records each add their plane's part.
 //
 // One warp per tile of one (channel, plane): the warp copies the tile's
 // (T + S - 1)^2 region of the plane (rows and columns taken mod N, which only
@@ -102,11 +104,14 @@ __global__ void k_degrid(GridParams G, const uint32_t* __restrict__ offsets,
                             acc.y = fmaf(gy[b], rs.y, acc.y);
                         }
                     }
-                    // (-1)^(i0 + j0) of the footprint's first cell (T is even)
+                    // (-1)^(i0 + j0) of the footprint's first cell (T is even),
+                    // the plane weight, and its sign bit: conjugate
                     const float s0 = ((il + jl) & 1) ? -1.f : 1.f;
-                    const bool conj = __float_as_uint(rec.wv_im) != 0u;
-                    vis_out[__float_as_uint(rec.wv_re)] =
-                        make_float2(s0 * acc.x, conj ? -s0 * acc.y : s0 * acc.y);
+                    const float gw = s0 * fabsf(rec.wv_im);
+                    const float2 out = make_float2(gw * acc.x, signbit(rec.wv_im) ? -gw * acc.y : gw * acc.y);
+                    float2* dst = vis_out + __float_as_uint(rec.wv_re);
+                    if (G.w_support >= 2) atomicAdd(dst, out);
+                    else *dst = out;
                 }
             }
             __syncwarp();  // the region is rewritten for the next tile

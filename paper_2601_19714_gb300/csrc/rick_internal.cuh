@@ -3,9 +3,11 @@
 // Data layout in HBM (all device memory):
 //   inputs   uvw[nrow][3] f64, chan_scale[C] f64, vis[nrow][C] complex64,
 //            weight[nrow][C] f32, flag[nrow][C] u8
-//   binning  key[nvis] u32, rank[nvis] u32, stage[nvis] VisRecord (unsorted),
-//            hist[nkeys] u32, offsets[nkeys+1] u32, records[nvis] VisRecord
-//            (sorted by key = (((c*Nw + k)*NT + ty)*NT + tx)*4 + halo class)
+//   binning  key[nrec] u32, rank[nrec] u32, stage[nrec] VisRecord (unsorted),
+//            hist[nkeys] u32, offsets[nkeys+1] u32, records[nrec] VisRecord
+//            (sorted by key = (((c*Nw + k)*NT + ty)*NT + tx)*4 + halo class);
+//            nrec = nvis, or nvis * Sw with a w-kernel (Sw records per
+//            visibility, record s of visibility v at v * Sw + s before sorting)
 //   grids    [channels][planes][N][N] complex64, checkerboard-signed
 //   images   [channels][N][N] f32
 #pragma once
@@ -21,8 +23,9 @@ namespace rick {
 // One binned visibility: W*V (FP32) and, per axis, the first footprint cell
 // relative to the anchor tile (top 8 bits) and the fractional offset
 // f = (x - S/2) - floor(x - S/2) in units of 2^-24 (low 24 bits).  Records
-// binned for prediction hold the visibility index and a conjugation flag in
-// the bits of wv_re and wv_im.
+// binned for prediction hold the visibility index in the bits of wv_re and
+// the record's plane weight in wv_im (1, or the w-kernel tap), negative where
+// the prediction is to be conjugated.
 struct __align__(16) VisRecord {
     float wv_re, wv_im;
     uint32_t px, py;
@@ -41,6 +44,14 @@ __host__ __device__ inline int halo_class(bool right, bool down) {
     return right ? (down ? 2 : 3) : (down ? 1 : 0);
 }
 
+// Separable kernels are evaluated per footprint tap a from a polynomial in
+// t = 2 f - 1 (f = fractional offset in [0, 1)): g(a + 1 - S/2 - f) ~= sum_k
+// coef[a][k] t^k, degree kPolyDegree, fitted on the host in FP64 (Chebyshev
+// interpolation) and checked there against g to 1e-6 (typically 6e-8).
+constexpr int kMaxSupport = 16;
+constexpr int kPolyDegree = 11;
+constexpr int kMaxWSupport = 8;   // w-kernel support
+
 struct PlaceParams {
     int N, S, Nw, C, T, NT;
     int precision;
@@ -48,19 +59,18 @@ struct PlaceParams {
     // as conj(V) at the mirrored footprint; the keys count Nw_store planes.
     int fold, Nw_store;
     // Prediction binning: records carry the visibility's index (bits of
-    // wv_re) and whether its prediction is to be conjugated (wv_im bits 0/1,
-    // set by the fold) instead of W V.
+    // wv_re) and its plane weight, negated if its prediction is to be
+    // conjugated (set by the fold), in wv_im, instead of W V.
     int predict;
+    // w-kernel (w_support >= 2): Sw records per visibility on planes k0 .. k0 +
+    // Sw - 1 of the extended set of Nw_total = Nw + Sw planes (the first Sw/2
+    // below w_min), weights from the fitted tap polynomials wcoef (t = 2 fw - 1).
+    // Nw_total is also the plane count the fold mirrors.
+    int w_support, Nw_total;
+    float wcoef[kMaxWSupport][kPolyDegree + 1];
     double fov, half_n, half_s, w_min, w_scale;  // w_scale = Nw/(w_max - w_min), 0 if Nw == 1
     float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
 };
-
-// Separable kernels are evaluated per footprint tap a from a polynomial in
-// t = 2 f - 1 (f = fractional offset in [0, 1)): g(a + 1 - S/2 - f) ~= sum_k
-// coef[a][k] t^k, degree kPolyDegree, fitted on the host in FP64 (Chebyshev
-// interpolation) and checked there against g to 1e-6 (typically 6e-8).
-constexpr int kMaxSupport = 16;
-constexpr int kPolyDegree = 11;
 
 struct GridParams {
     int N, S, T, NT, Nw;  // Nw: stored planes (the bin keys' plane count)
@@ -77,6 +87,7 @@ struct GridParams {
     // first, then every other tile in natural order.  nullptr: natural order.
     uint32_t* lists;
     uint32_t list_cap;
+    int w_support;        // prediction: >= 2 accumulates the Sw partial predictions
     float coef[kMaxSupport][kPolyDegree + 1];
 };
 
@@ -98,6 +109,14 @@ struct PhaseParams {
     double w_first;       // w of plane plane_begin (plane centre)
     double dw;            // plane spacing (0 if Nw == 1)
     int precision;
+    // w-kernel (w_support >= 2): every pixel is also divided by the kernel's
+    // transform C_w((n - 1) dw) (Kaiser-Bessel, beta = w_beta):
+    //   C_w(nu) = w_c0 (beta / r) sinh(r) / sinh(beta),  r^2 = beta^2 - (pi Sw nu)^2 > 0
+    //           = w_s_i0 sin(r) / r,                     r^2 = (pi Sw nu)^2 - beta^2 >= 0
+    // with w_c0 = C_w(0) and w_s_i0 = Sw / I0(beta) from the host in FP64.
+    int w_support;
+    double w_beta;
+    float w_c0, w_s_i0, w_exp2b;  // w_exp2b = exp(-2 beta)
 };
 
 // --- launchers (one per kernel family), all asynchronous on `stream` -------

@@ -94,6 +94,9 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: only Gaussian and Kaiser-Bessel kernels (a table kernel needs a plan)");
+    if (c.w_support >= 2)
+        return fail(RICK_ERR_UNSUPPORTED,
+                    "rick_grid_noalloc: a w-kernel (w_support >= 2) needs a plan (Sw records per visibility)");
     if (nrow < 0 || !weight_sum || !grids || (nrow > 0 && !(uvw && chan_scale && vis && weight)))
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: inputs");
     if (!(0 <= plane_begin && plane_begin < plane_end && plane_end <= planes))
@@ -159,6 +162,8 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     pp.fold = c.hermitian_fold;
     pp.Nw_store = planes;
     pp.predict = 0;
+    pp.w_support = 0;
+    pp.Nw_total = c.n_wplanes;
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;
@@ -195,6 +200,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         G.lattice = 0;
         G.lists = nullptr;  // natural tile order (no scheduling scratch)
         G.list_cap = 0;
+        G.w_support = 0;
         G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 8 ? (uint32_t)c.tiles_per_grab : 4u;
         e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
                         num_sms, st, &launches);

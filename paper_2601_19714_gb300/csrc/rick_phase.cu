@@ -15,6 +15,10 @@
 // formed exactly from the top 32 bits (sincospif of a value in [-1, 1)); in
 // between it advances by one FP32 complex multiply with exp(2 pi i dt).  The
 // only FP64 work is a handful of operations per pixel, never per plane.
+//
+// With a w-kernel (improved w-stacking) the planes are those of the extended
+// set (w_first is the centre of the launch's first plane in it) and every
+// pixel is also divided by the w-kernel's transform C_w((n - 1) dw).
 #include "rick_internal.cuh"
 
 namespace rick {
@@ -38,6 +42,30 @@ __device__ __forceinline__ float2 phasor_q64(uint64_t t) {
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// 1 / C_w(delta dw) for the Kaiser-Bessel w-kernel of support Sw (1 without
+// one), from its closed-form transform
+//   C_w(nu) = Sw sinh(r) / (r I0(beta)),  r = sqrt(beta^2 - (pi Sw nu)^2),
+// (sin for r^2 < 0).  Inside the main lobe it is written relative to C_w(0):
+//   C_w(nu) / C_w(0) = (beta / r) e^(-eps) (1 - e^(-2 r)) / (1 - e^(-2 beta)),
+// eps = beta - r = a^2 / (beta + r), a = pi Sw nu, so that FP32 sees no
+// large argument and no cancellation; r and eps come from FP64 once per pixel.
+__device__ __forceinline__ float w_taper_inv(const PhaseParams& P, double delta) {
+    if (P.w_support < 2) return 1.0f;
+    const double a = 3.141592653589793 * P.w_support * (delta * P.dw);
+    const double b = P.w_beta;
+    const double x2 = b * b - a * a;
+    if (x2 > 0.0) {
+        const double r = sqrt(x2);
+        const float eps = (float)(a * a / (b + r));
+        const float ratio = (float)(b / r) * expf(-eps) * (1.0f - expf(-2.0f * (float)r)) /
+                            (1.0f - P.w_exp2b);
+        return 1.0f / (P.w_c0 * ratio);
+    }
+    const float r = (float)sqrt(-x2);
+    const float h = r < 1e-4f ? 1.0f : sinf(r) / r;
+    return 1.0f / (P.w_s_i0 * h);
 }
 
 template <int PREC, bool COMPLEX_OUT>
@@ -72,7 +100,7 @@ k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __
             dt[e] = turns_q64(P.dw * delta);
         }
         const float sg = ((p + e + q) & 1) ? -1.f : 1.f;
-        scale[e] = sg * (float)n * inv_taper[p + e] * inv_taper[q];
+        scale[e] = sg * (float)n * inv_taper[p + e] * inv_taper[q] * w_taper_inv(P, delta);
     }
 
     for (int cc = 0; cc < P.nc; ++cc) {
@@ -136,7 +164,7 @@ k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __
 
 // Prediction, first step: the model image of each channel spread onto the
 // w-planes (the adjoint of the reduction above),
-//   M_k[q][p] = (-1)^(p+q) J_c[q][p] exp(-2 pi i w_k (n - 1)) / (n C(p) C(q)),
+//   M_k[q][p] = (-1)^(p+q) J_c[q][p] exp(-2 pi i w_k (n - 1)) / (n C(p) C(q) C_w),
 // every plane written once (16-byte streaming stores of two pixels).  The
 // phase is the conjugate of the one the reduction applies, formed the same
 // way (FP64 per pixel, Q0.64 turns, exact anchors every 8 planes).
@@ -171,7 +199,7 @@ k_model_planes(PhaseParams P, const float* __restrict__ image, const float* __re
             dt[e] = turns_q64(P.dw * delta);
         }
         const float sg = ((p + e + q) & 1) ? -1.f : 1.f;
-        scale[e] = sg * inv_taper[p + e] * inv_taper[q] / (float)n;
+        scale[e] = sg * inv_taper[p + e] * inv_taper[q] * w_taper_inv(P, delta) / (float)n;
     }
 
     for (int cc = 0; cc < P.nc; ++cc) {

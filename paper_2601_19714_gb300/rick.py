@@ -49,7 +49,8 @@ class rick_config(C.Structure):
                 ("w_max", C.c_double), ("kernel_param", C.c_double), ("kernel_kind", C.c_int32),
                 ("precision", C.c_int32), ("tile", C.c_int32), ("grid_threads", C.c_int32),
                 ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
-                ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32)]
+                ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32),
+                ("w_support", C.c_int32), ("w_kernel_param", C.c_double)]
 
 
 class rick_tune_entry(C.Structure):
@@ -190,18 +191,27 @@ class Config:
     tiles_per_grab: int = 0
     grid_budget_bytes: int = 0
     hermitian_fold: bool = False
+    w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
+    w_kernel_param: float = 0.0
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
                            self.w_min, self.w_max, self.kernel_param, KERNELS[self.kernel],
                            PRECISIONS[self.precision], self.tile, self.grid_threads,
                            self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes,
-                           int(bool(self.hermitian_fold)))
+                           int(bool(self.hermitian_fold)), int(self.w_support),
+                           float(self.w_kernel_param))
+
+    @property
+    def planes_total(self) -> int:
+        """Planes imaged: Nw, or Nw + Sw with a w-kernel."""
+        return self.n_wplanes + (self.w_support if self.w_support >= 2 else 0)
 
     @property
     def stored_planes(self) -> int:
-        """Planes held per channel: ceil(Nw/2) with the Hermitian fold, else Nw."""
-        return (self.n_wplanes + 1) // 2 if self.hermitian_fold else self.n_wplanes
+        """Planes held per channel: ceil(planes_total/2) with the Hermitian fold."""
+        t = self.planes_total
+        return (t + 1) // 2 if self.hermitian_fold else t
 
 
 class Plan:

@@ -103,3 +103,32 @@ def test_stored_planes(lib, nw, fold, expect):
                       w_max=200, kernel="gauss", kernel_param=0.94, hermitian_fold=bool(fold))
     assert lib.rick_stored_planes(C.byref(cfg.c())) == expect == cfg.stored_planes
     assert lib.rick_stored_planes(None) == -1
+
+
+@pytest.mark.parametrize("kw", [dict(w_support=3, w_kernel_param=6.0),
+                                dict(w_support=10, w_kernel_param=6.0),
+                                dict(w_support=4, w_kernel_param=0.0),
+                                dict(w_support=4, w_kernel_param=6.0, n_wplanes=1),
+                                dict(w_support=4, w_kernel_param=6.0, kernel="learned", support=4,
+                                     kernel_param=5.6)])
+def test_w_kernel_configs_rejected_on_host(lib, kw):
+    """The w-kernel needs an even support in [2, 8], a positive beta, at least
+    two planes, and a separable uv kernel (the table kernel is per plane)."""
+    from paper_2601_19714_gb300 import rick
+    base = dict(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                w_max=200, kernel="gauss", kernel_param=0.94)
+    base.update(kw)
+    h = C.c_void_p(123)
+    assert lib.rick_plan_create(C.byref(rick.Config(**base).c()), C.byref(h)) == 1
+    assert h.value is None
+    assert b"w_" in lib.rick_last_error() or b"w-kernel" in lib.rick_last_error()
+
+
+@pytest.mark.parametrize("nw,sw,fold,expect", [(8, 4, 0, 12), (8, 4, 1, 6), (7, 4, 1, 6),
+                                               (7, 2, 0, 9), (32, 8, 1, 20), (8, 1, 0, 8)])
+def test_stored_planes_with_w_kernel(lib, nw, sw, fold, expect):
+    from paper_2601_19714_gb300 import rick
+    cfg = rick.Config(N=256, n_wplanes=nw, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                      w_max=200, kernel="gauss", kernel_param=0.94, hermitian_fold=bool(fold),
+                      w_support=sw, w_kernel_param=6.0)
+    assert lib.rick_stored_planes(C.byref(cfg.c())) == expect == cfg.stored_planes

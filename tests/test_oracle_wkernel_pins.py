@@ -150,3 +150,45 @@ def test_w_kernel_hermitian_partner_predicts_the_conjugate(orc):
     A = orc.predict(cfg, obs.uvw, obs.chan_scale, obs.weight, image=J)
     B = orc.predict(cfg, -obs.uvw, obs.chan_scale, obs.weight, image=J)
     np.testing.assert_allclose(B, np.conj(A), atol=1e-9 * np.abs(A).max())
+
+
+def test_w_kernel_real_image_is_unchanged_by_hermitian_partners(orc):
+    """Every visibility replaced by its partner conj V at (-u, -v, -w): with a
+    w range symmetric about 0 the extended plane set, the w-kernel weights and
+    the w-taper are symmetric too, so the real image stays (to rounding of the
+    mirrored positions) while the imaginary part flips.  Plane centres off by
+    one in the extended set, or an odd taper, break it."""
+    img, obs = tiny_wstack(66, nvis=3000, N=64, Nw=8, w_range=800.0)
+    obs.uvw[:, :2] *= 0.8   # footprints off the mesh border
+    cfg = cfg_of(orc, img, w_support=4, w_kernel_param=8.0)
+    I1, w1 = orc.image(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight)
+    I2, w2 = orc.image(cfg, -obs.uvw, obs.chan_scale, np.conj(obs.vis), obs.weight)
+    assert w1 == w2
+    np.testing.assert_allclose(I2.real, I1.real, atol=1e-9 * np.abs(I1.real).max())
+    np.testing.assert_allclose(I2.imag, -I1.imag, atol=1e-9 * np.abs(I1.real).max())
+    assert np.abs(I1.imag).max() > 1e-3 * np.abs(I1.real).max()
+
+
+@pytest.mark.parametrize("Nw", [7, 8])
+def test_w_kernel_fold_planes_add_the_partner_planes(orc, Nw):
+    """The fold over the extended plane set (Nt = Nw + Sw planes): stored
+    plane H_k equals the grid of the data plus the grid of the partner data on
+    plane k (the partner's records on plane k are the mirrored conjugates of
+    the data's records on plane Nt - 1 - k), for 2k < Nt - 1; the middle plane
+    of an odd Nt keeps the data's grid alone."""
+    img, obs = tiny_wstack(67, nvis=1500, N=64, Nw=Nw, w_range=800.0)
+    obs.uvw[:, :2] *= 0.8
+    cfg = cfg_of(orc, img, w_support=4, w_kernel_param=8.0)
+    nt = orc.planes_total(cfg)
+    assert nt == Nw + 4
+    pu, pv = -obs.uvw, np.conj(obs.vis)
+    for k in range((nt + 1) // 2):
+        H = orc.fold_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k)
+        G = orc.grid_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=k)
+        if 2 * k == nt - 1:
+            np.testing.assert_array_equal(H, G)
+            continue
+        P = orc.grid_plane(cfg, pu, obs.chan_scale, pv, obs.weight, plane=k)
+        np.testing.assert_allclose(H, G + P, atol=1e-9 * np.abs(G + P).max())
+    with pytest.raises(ValueError):
+        orc.fold_plane(cfg, obs.uvw, obs.chan_scale, obs.vis, obs.weight, plane=(nt + 1) // 2)
