@@ -173,7 +173,7 @@ __device__ __forceinline__ Base place_fp64(const PlaceParams& P, double u0, doub
         if (z > P.Nw - 0.5) z = P.Nw - 0.5;
         const double sz = __dsub_rn(z, 0.5 * P.w_support);
         const double fl = floor(sz);
-        k = (int)fl + 1 + P.w_support / 2;
+        k = min(max((int)fl + 1 + P.w_support / 2, 0), P.Nw);  // in [0, Nw] by the clamp
         out.fw = (float)__dsub_rn(sz, fl);
     } else if (P.Nw > 1) {
         const double t = __dmul_rn(__dsub_rn(w, P.w_min), P.w_scale);
@@ -221,7 +221,7 @@ __device__ __forceinline__ Base place_fp32(const PlaceParams& P, double u0, doub
         z = fminf(fmaxf(z, -0.5f), (float)P.Nw - 0.5f);
         const float sz = z - 0.5f * P.w_support;
         const float fl = floorf(sz);
-        k = (int)fl + 1 + P.w_support / 2;
+        k = min(max((int)fl + 1 + P.w_support / 2, 0), P.Nw);
         out.fw = sz - fl;
     } else if (P.Nw > 1) {
         float kf = floorf((w - P.w_min_f) * P.w_scale_f);
