@@ -121,6 +121,10 @@ typedef struct rick_config {
      * image is also divided by the kernel's transform C_w((n - 1) dw).  The
      * prediction uses the same weights and taper.  Gridding work and records
      * grow by Sw, and nrow * C * Sw must stay below 2^32 - 1 per plan call.
+     * The plane spacing must keep the first zero of C_w outside the field:
+     * pi Sw dw max|n - 1| < sqrt(beta^2 + pi^2), max over the field corners
+     * (else RICK_ERR_INVALID_ARG; the method needs dw max|n - 1| well below
+     * 1/2 anyway).
      * Not with a TABLE kernel nor in rick_grid_noalloc or the learned-kernel
      * trainer (RICK_ERR_INVALID_ARG / RICK_ERR_UNSUPPORTED). */
     int32_t w_support;

@@ -251,6 +251,17 @@ rick_status validate(const rick_config* c) {
                "a w-kernel needs a Gaussian or Kaiser-Bessel uv kernel (not a table kernel)");
         RK_ARG(c->w_kernel_param > 0.0 && std::isfinite(c->w_kernel_param),
                "w_kernel_param must be > 0 with a w-kernel");
+        // the image is divided by C_w((n - 1) dw); its first zero, at
+        // pi Sw |nu| = sqrt(beta^2 + pi^2), must lie outside the field (the
+        // field corner has the largest |n - 1|)
+        const double half = 0.5 * c->fov_rad, r2 = 2.0 * half * half;
+        const double delta = r2 / (1.0 + std::sqrt(1.0 - r2));
+        const double dw = (c->w_max - c->w_min) / c->n_wplanes;
+        const double pi = 3.141592653589793;
+        const double b = c->w_kernel_param;
+        RK_ARG(pi * c->w_support * dw * delta < std::sqrt(b * b + pi * pi),
+               "w-kernel: the planes are too sparse for the field (C_w has a zero inside it); "
+               "use more w-planes or a smaller w_support");
     }
     if (c->hermitian_fold) {
         RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE,

@@ -110,7 +110,11 @@ def test_stored_planes(lib, nw, fold, expect):
                                 dict(w_support=4, w_kernel_param=0.0),
                                 dict(w_support=4, w_kernel_param=6.0, n_wplanes=1),
                                 dict(w_support=4, w_kernel_param=6.0, kernel="learned", support=4,
-                                     kernel_param=5.6)])
+                                     kernel_param=5.6),
+                                # dw max|n - 1| = 0.6 (pi Sw 0.6 = 7.5 > sqrt(6^2 + pi^2) = 6.8)
+                                dict(w_support=4, w_kernel_param=6.0, fov_rad=0.2,
+                                     w_min=-0.6 / 0.0100503781525921 * 4,
+                                     w_max=0.6 / 0.0100503781525921 * 4)])
 def test_w_kernel_configs_rejected_on_host(lib, kw):
     """The w-kernel needs an even support in [2, 8], a positive beta, at least
     two planes, and a separable uv kernel (the table kernel is per plane)."""

@@ -160,8 +160,10 @@ def test_w_kernel_tiny_image_matches_oracle(rk, orc, fold):
 @pytest.mark.parametrize("fold", [False, True])
 def test_w_kernel_multichannel_kaiser_bessel(rk, orc, fold):
     """MeerKAT-shaped, 3 channels with uneven flags, KB S = 8 in uv and
-    Sw = 6 in w, odd plane count."""
-    img, obs = meerkat(74, n_ant=12, n_steps=97, nchan=3, N=512, Nw=7, n_src=20)
+    Sw = 6 in w, odd plane count (25 planes: dw max|n - 1| = 0.30 at the
+    field corners of this w range; with 7 planes it would be 1.09, beyond the
+    sampling limit, where C_w passes through zero)."""
+    img, obs = meerkat(74, n_ant=12, n_steps=97, nchan=3, N=512, Nw=25, n_src=20)
     plan = rk.Plan(plan_config(img, 3, fft_batch=4, hermitian_fold=fold, w_support=6,
                                w_kernel_param=10.0))
     I_g, _, _, cnt = run_path(plan, to_device(obs), 3, img.N, img.Nw)
