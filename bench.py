@@ -3,8 +3,11 @@
 
 One step = the whole path over one batch: rick_bin + rick_grid_binned
 (placement, binning and gridding of every visibility of every channel onto
-its w-plane), rick_fft_wplanes (every plane), rick_phase_correct_reduce
-(phase screen + sum over planes into the dirty images).  Inputs are resident
+its w-plane), then the inverse 2-D DFT of every plane and Eq. 2's phase
+screen + sum over planes into the dirty images: the library's own transform
+as rick_fft_wplanes_columns (column pass) + rick_rows_phase_correct_reduce
+(row pass fused with the reduction); the cuFFT path (rick_fft_wplanes +
+rick_phase_correct_reduce) is timed beside it as "cufft_variant".  Inputs are resident
 in HBM when the timed region starts; `e2e` repeats the measurement through
 rick_dirty_image_host, with the host->device copy of the inputs and the
 device->host copy of the images inside the timed region.
@@ -272,6 +275,8 @@ def run_ours(args):
         wsum = torch.empty(C, dtype=torch.float64, device="cuda")
         counts = torch.empty(2, dtype=torch.int64, device="cuda")
 
+        own = cfg.fft_impl == "own"
+
         def step(record=False):
             e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
             image.zero_()
@@ -281,9 +286,14 @@ def run_ours(args):
             if e: e[1].record(stream)
             plan.grid_binned(0, C, 0, ns, grids)
             if e: e[2].record(stream)
-            plan.fft_wplanes(grids, C * ns)
-            if e: e[3].record(stream)
-            plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+            if own:   # the own transform: column pass, then rows fused with Eq. 2's reduction
+                plan.fft_wplanes_columns(grids, C * ns)
+                if e: e[3].record(stream)
+                plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+            else:     # cuFFT, then the reduction
+                plan.fft_wplanes(grids, C * ns)
+                if e: e[3].record(stream)
+                plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
             if e: e[4].record(stream)
             return e
 
@@ -308,12 +318,11 @@ def run_ours(args):
         rdist.barrier()
         launches = plan.launch_count() - launches0
         ms = rdist.max_over_ranks(start.elapsed_time(stop) / steps, device="cuda")
-        stage_ms = {"bin": [], "grid": [], "fft": [], "phase": []}
+        names = ("bin", "grid", "columns", "rows_phase") if own else ("bin", "grid", "fft", "phase")
+        stage_ms = {k: [] for k in names}
         for e in stage_events:
-            stage_ms["bin"].append(e[0].elapsed_time(e[1]))
-            stage_ms["grid"].append(e[1].elapsed_time(e[2]))
-            stage_ms["fft"].append(e[2].elapsed_time(e[3]))
-            stage_ms["phase"].append(e[3].elapsed_time(e[4]))
+            for i, k in enumerate(names):
+                stage_ms[k].append(e[i].elapsed_time(e[i + 1]))
         st = {k: statistics.median(v) for k, v in stage_ms.items()}
         out = dict(ms=ms, st=st, launches=launches, n_grid=n_grid, n_drop=n_drop,
                    clocks=clk.summary() if clocks else None, img_ch0=image[0].cpu().numpy(),
@@ -323,9 +332,12 @@ def run_ours(args):
         return out
 
     fold = not args.no_fold
+    from dataclasses import replace
     tuned = tuned_config(fold)
     other_cfg = tuned_config(not fold)
     other = measure(other_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
+    cufft_cfg = replace(tuned, fft_impl="cufft")
+    cufft = measure(cufft_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
     res = measure(tuned, args.steps, args.warmup, clocks=True)
     st, ms_max, launches = res["st"], res["ms"], res["launches"]
     n_grid, n_drop = res["n_grid"], res["n_drop"]
@@ -339,17 +351,23 @@ def run_ours(args):
     b_phase = 8.0 * cells + 8.0 * C * NN                  # read planes + image read/write
     b_bin = (24.0 * nrow + C * nrow * (8 + 4 + 1)         # inputs
              + C * nrow * (4 + 4 + 16) * 2 + 16.0 * n_grid)  # key/rank/stage write+read, records
-    gbs = {k: b / (st[k] * 1e-3) / 1e9 for k, b in
-           (("bin", b_bin), ("grid", b_grid), ("fft", b_fft), ("phase", b_phase))}
+    # the own transform: the column pass reads and writes every cell (the FFT's
+    # algorithmic 16 B/cell); the fused row pass reads every cell once (the
+    # reduction's 8 B/cell) and the image, and writes no plane
+    stage_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase,
+                   "columns": b_fft, "rows_phase": b_phase}
+    gbs = {k: stage_bytes[k] / (st[k] * 1e-3) / 1e9 for k in st}
     dominant = max(st, key=st.get)
-    dom_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase}[dominant]
-    # DRAM traffic of the dominant stage, from one ncu capture of the small
-    # 4096^2 case (dram__bytes_read.sum + dram__bytes_write.sum of cuFFT's three
-    # kernels: 46.7 bytes per cell per transform, proportional to the planes)
+    dom_bytes = stage_bytes[dominant]
+    # DRAM traffic of the dominant stage per step, from one ncu capture of the
+    # small 4096^2 case (dram__bytes_read.sum + dram__bytes_write.sum per
+    # launch), scaled by the planes (traffic proportional to cells)
+    per_cell = {"fft": 46.7}
     dom_traffic, traffic_how = None, None
-    if dominant == "fft" and N == 4096:
-        dom_traffic = 46.7 * cells
-        traffic_how = "ncu capture of the 4096^2 small case, scaled by planes (46.7 B/cell)"
+    if dominant in per_cell and N == 4096:
+        dom_traffic = per_cell[dominant] * cells
+        traffic_how = (f"ncu capture of the 4096^2 small case, scaled by planes "
+                       f"({per_cell[dominant]} B/cell)")
 
     # ---- end to end through the host entry point -------------------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -406,10 +424,8 @@ def run_ours(args):
                          "frac": dom_bytes / (st[dominant] * 1e-3) / 1e9 / hbm,
                          "traffic": dom_traffic, "traffic_unit": "bytes per step",
                          "traffic_how": traffic_how},
-            "roofline_grid": {"bound": "hbm", "achieved": gbs["grid"], "peak": hbm,
-                              "unit": "GB/s", "frac": gbs["grid"] / hbm},
-            "roofline_phase": {"bound": "hbm", "achieved": gbs["phase"], "peak": hbm,
-                               "unit": "GB/s", "frac": gbs["phase"] / hbm},
+            "roofline_stages": {k: {"bound": "hbm", "achieved": gbs[k], "peak": hbm, "unit": "GB/s",
+                                    "frac": gbs[k] / hbm} for k in st},
             "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -421,6 +437,11 @@ def run_ours(args):
                 "steps": max(1, min(args.steps, 3)),
                 "tile": other_cfg.tile, "grid_threads": other_cfg.grid_threads,
                 "tiles_per_grab": other_cfg.tiles_per_grab},
+            "cufft_variant": {
+                "fft_impl": "cufft", "hermitian_fold": fold,
+                "value": cufft["n_grid"] * world / (cufft["ms"] * 1e-3), "unit": UNIT,
+                "ms_per_step": cufft["ms"], "stages_ms": cufft["st"],
+                "steps": max(1, min(args.steps, 3))},
         }
         if not args.no_cpu_baseline:
             r, nv, s, desc = oracle_sample(img, obs, 2)
@@ -839,9 +860,9 @@ def run_wkernel(args):
             if e: e[1].record(stream)
             plan.grid_binned(0, C, 0, ns, grids)
             if e: e[2].record(stream)
-            plan.fft_wplanes(grids, C * ns)
+            plan.fft_wplanes_columns(grids, C * ns)
             if e: e[3].record(stream)
-            plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+            plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
             if e: e[4].record(stream)
             return e
 
@@ -860,7 +881,7 @@ def run_wkernel(args):
             torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
         st = {k: statistics.median([e[i].elapsed_time(e[i + 1]) for e in evs])
-              for i, k in enumerate(("bin", "grid", "fft", "phase"))}
+              for i, k in enumerate(("bin", "grid", "columns", "rows_phase"))}
         I = image[c_top].cpu().numpy()
         got = I[probes[1], probes[0]]
         err = float(np.abs(got - D).max() / np.abs(D).max())
@@ -869,7 +890,7 @@ def run_wkernel(args):
              "vis_per_s": n_grid / (ms * 1e-3), "stages_ms": st,
              "records": int(n_grid * max(1, sw)),
              "error_vs_eq1_direct": err, "launches": int(plan.launch_count() - n0),
-             "phase_gbs": (8.0 * cells + 8.0 * C * N * N) / (st["phase"] * 1e-3) / 1e9,
+             "rows_phase_gbs": (8.0 * cells + 8.0 * C * N * N) / (st["rows_phase"] * 1e-3) / 1e9,
              "clocks": clk.summary()}
         r["_got"] = got
         results[name] = r
@@ -900,8 +921,9 @@ def run_wkernel(args):
                    "launch_shape": "default (tile 32, 128 threads, 4 tiles per grab)",
                    "l2": "inputs larger than L2"},
         "variants": results,
-        "roofline_phase": {"bound": "hbm", "achieved": rb["phase_gbs"], "peak": hbm,
-                           "unit": "GB/s", "frac": rb["phase_gbs"] / hbm, "peak_kind": peak_kind},
+        "roofline_rows_phase": {"bound": "hbm", "achieved": rb["rows_phase_gbs"], "peak": hbm,
+                                "unit": "GB/s", "frac": rb["rows_phase_gbs"] / hbm,
+                                "peak_kind": peak_kind},
         "gpu_launches": rb["launches"], "clocks": rb["clocks"]}), flush=True)
 
 
@@ -910,8 +932,9 @@ def run_profile_small(args):
     recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
     grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
-    A step images the 2 channels and then predicts visibilities from the
-    dirty images (the degridding path).  Runs warm-up + steps steps and
+    A step images the 2 channels (the own transform: column pass, then the
+    row pass fused with the reduction) and then predicts visibilities from
+    the dirty images (the degridding path).  Runs warm-up + steps steps and
     prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
@@ -936,8 +959,8 @@ def run_profile_small(args):
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
         plan.grid_binned(0, C, 0, ns, grids)
-        plan.fft_wplanes(grids, C * ns)
-        plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        plan.fft_wplanes_columns(grids, C * ns)
+        plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
         # prediction from the dirty image just made (exercises the degridder)
         plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow)
         plan.model_to_wplanes(image, 0, C, 0, ns, grids)

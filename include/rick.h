@@ -129,6 +129,11 @@ typedef struct rick_config {
      * trainer (RICK_ERR_INVALID_ARG / RICK_ERR_UNSUPPORTED). */
     int32_t w_support;
     double w_kernel_param;
+    /* 2-D DFT of the w-planes: 0 = the library's own two-pass transform for
+     * power-of-two 256 <= N <= 8192 (columns, then rows; the imaging path fuses
+     * the row pass with the phase screen and reduction), cuFFT for other N;
+     * 1 = cuFFT for every N (batched, fft_batch planes per execution). */
+    int32_t fft_impl;
 } rick_config;
 
 /* Planes a plan stores for cfg: P = Nw, or Nw + Sw with a w-kernel; ceil(P / 2)
@@ -195,7 +200,8 @@ rick_status rick_grid(rick_plan* plan, const double* uvw, const double* chan_sca
                       int64_t* counts, void* stream);
 
 /* In place, unnormalised 2-D inverse FFT (exponent +) of n_planes
- * consecutive N x N complex64 planes (cuFFT, batched). */
+ * consecutive N x N complex64 planes: the library's own transform (a column
+ * pass and a row pass, 2 kernel launches) or cuFFT, see fft_impl. */
 rick_status rick_fft_wplanes(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
 
 /* Phase screen and reduction over planes (Eq. 2): for channels
@@ -211,6 +217,31 @@ rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32
                                       int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                       const double* weight_sum, float* image_real,
                                       float* image_complex, void* stream);
+
+/* rick_fft_wplanes followed by rick_phase_correct_reduce over channels
+ * [chan_begin, chan_end) and planes [plane_begin, plane_end) of the gridded
+ * (untransformed) planes in grids, with the same result up to FP32 rounding.
+ * With the library's own transform the row pass is fused with the phase
+ * screen and the reduction (2 kernel launches; the transformed planes are
+ * never written): grids is left holding the column-transformed planes, not
+ * the transformed ones.  With cuFFT it is exactly the two calls. */
+rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t chan_begin,
+                                          int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                          const double* weight_sum, float* image_real,
+                                          float* image_complex, void* stream);
+
+/* The two passes of rick_fft_phase_correct_reduce with the library's own
+ * transform, as separate calls (RICK_ERR_UNSUPPORTED with cuFFT):
+ * rick_fft_wplanes_columns: the length-N inverse DFT down every column of
+ *   n_planes planes, in place (pass 1; one launch);
+ * rick_rows_phase_correct_reduce: the row DFTs of column-transformed planes
+ *   fused with the phase screen and reduction, arguments as for
+ *   rick_phase_correct_reduce (pass 2; one launch; grids is only read). */
+rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
+rick_status rick_rows_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
+                                           int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                           const double* weight_sum, float* image_real,
+                                           float* image_complex, void* stream);
 
 /* The whole path on device buffers: bin, then for each group of channels and
  * planes that fits grid_budget_bytes grid, transform and reduce into
@@ -237,8 +268,8 @@ typedef struct rick_graph rick_graph;
 
 /* Capture the whole path for ALL channels and planes of the plan into one
  * CUDA graph: zero image_real, rick_bin, one persistent rick_grid_binned over
- * every (channel, plane, tile), rick_fft_wplanes over every plane, and
- * rick_phase_correct_reduce.  Channels may have any (uneven, flagged)
+ * every (channel, plane, tile), and rick_fft_phase_correct_reduce over every
+ * plane.  Channels may have any (uneven, flagged)
  * visibility counts; the gridder's work queue spans all of them.  Pointers are
  * the device buffers the graph will use on every launch (their contents may
  * change between launches, their addresses may not): grids must hold

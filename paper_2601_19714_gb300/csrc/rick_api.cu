@@ -170,6 +170,9 @@ struct rick_plan {
     cudaStream_t last_stream = nullptr;
     float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
     double tap_fit_error = 0.0;
+    // the library's own 2-D DFT (fft_impl 0 and 256 <= N <= 8192): twiddle tables
+    bool own_fft = false;
+    float2* d_twid = nullptr;
     // w-kernel: tap polynomials and the constants of its transform C_w
     float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
     double w_c0 = 1.0, w_s_i0 = 1.0;
@@ -185,6 +188,7 @@ void dfree(T*& p) {
 
 void release(rick_plan* P) {
     dfree(P->d_inv_taper);
+    dfree(P->d_twid);
     dfree(P->d_table);
     dfree(P->d_key);
     dfree(P->d_rank);
@@ -242,6 +246,7 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 8, "tiles_per_grab must be in [0, 8]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
+    RK_ARG(c->fft_impl == 0 || c->fft_impl == 1, "fft_impl must be 0 or 1");
     RK_ARG(c->w_support == 0 || c->w_support == 1 ||
                (c->w_support >= 2 && c->w_support <= 8 && (c->w_support & 1) == 0),
            "w_support must be 0, 1 or even in [2, 8]");
@@ -387,6 +392,14 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
     RK_CUDA(cudaMalloc(&P->d_wsum, sizeof(double) * c.n_channels));
 
+    P->own_fft = c.fft_impl == 0 && fft_supported(c.N);
+    if (P->own_fft) {
+        std::vector<float2> tw;
+        fft_twiddles(c.N, tw);
+        RK_CUDA(cudaMalloc(&P->d_twid, sizeof(float2) * tw.size()));
+        RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+        return RICK_OK;   // no cuFFT plans
+    }
     const size_t plane_bytes = (size_t)c.N * c.N * sizeof(float2);
     int B = c.fft_batch;
     if (B <= 0) {
@@ -530,9 +543,18 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
     RK_ARG(n_planes >= 0, "n_planes must be >= 0");
     RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
     const size_t NN = (size_t)P->cfg.N * P->cfg.N;
+    P->last_stream = st;
+    if (P->own_fft) {
+        RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
+        int launches = 0;
+        rick_status s = check_launch(launch_fft2d(reinterpret_cast<float2*>(grids), n_planes, P->cfg.N,
+                                                  direction == CUFFT_INVERSE, P->d_twid, st, &launches),
+                                     "FFT kernels");
+        P->launches += launches;
+        return s;
+    }
     cufftComplex* g = reinterpret_cast<cufftComplex*>(grids);
     int64_t done = 0;
-    P->last_stream = st;
     if (P->have_b) {
         if (cufftSetStream(P->fft_b, st) != CUFFT_SUCCESS) {
             set_err("cufftSetStream failed");
@@ -606,6 +628,70 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
         "phase kernel");
     P->launches += launches;
     return s;
+}
+
+// Pass 1 of the own transform (inverse DFT down every column), in place.
+rick_status columns_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st) {
+    if (!P->own_fft) {
+        set_err("the column pass needs the library's own transform (fft_impl 0, 256 <= N <= 8192)");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    RK_ARG(n_planes >= 0, "n_planes must be >= 0");
+    RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
+    RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
+    P->last_stream = st;
+    int launches = 0;
+    rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids), n_planes, P->cfg.N,
+                                                    true, P->d_twid, st, &launches),
+                                 "FFT column kernel");
+    P->launches += launches;
+    return s;
+}
+
+// Pass 2 fused with the phase screen and reduction, on column-transformed planes.
+rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0, int k1,
+                            const double* weight_sum, float* image_real, float* image_complex,
+                            cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    if (!P->own_fft) {
+        set_err("the fused row pass needs the library's own transform (fft_impl 0, 256 <= N <= 8192)");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_ARG(grids && weight_sum && image_real, "grids, weight_sum and image_real are required");
+    RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image_real & 3u) == 0 &&
+               ((uintptr_t)image_complex & 7u) == 0,
+           "grids must be 16-byte, image_real 4-byte and image_complex 8-byte aligned");
+    P->last_stream = st;
+    int launches = 0;
+    rick_status s = check_launch(launch_rows_phase_reduce(phase_params(P, c0, c1, k0, k1),
+                                                          reinterpret_cast<const float2*>(grids),
+                                                          weight_sum + c0, P->d_inv_taper, P->d_twid,
+                                                          image_real,
+                                                          reinterpret_cast<float2*>(image_complex), st,
+                                                          &launches),
+                                 "fused row FFT / phase kernel");
+    P->launches += launches;
+    return s;
+}
+
+// Transform + phase screen + reduction of gridded planes [k0, k1) of channels
+// [c0, c1): with the own transform, the column pass and the fused row pass.
+rick_status fft_phase_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int k1,
+                           const double* weight_sum, float* image_real, float* image_complex,
+                           cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    if (!P->own_fft) {
+        RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+        RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+        RK_TRY(fft_impl(P, grids, (int64_t)(c1 - c0) * (k1 - k0), st));
+        return phase_impl(P, grids, c0, c1, k0, k1, weight_sum, image_real, image_complex, st);
+    }
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_TRY(columns_impl(P, grids, (int64_t)(c1 - c0) * (k1 - k0), st));
+    return rows_phase_impl(P, grids, c0, c1, k0, k1, weight_sum, image_real, image_complex, st);
 }
 
 rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
@@ -715,9 +801,8 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
         for (int k0 = 0; k0 < P->planes; k0 += gk) {
             const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
             RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st));
-            RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st));
-            RK_TRY(phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
-                              image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st));
+            RK_TRY(fft_phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
+                                  image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st));
         }
     }
     return RICK_OK;
@@ -869,6 +954,29 @@ rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32
                       image_real, image_complex, as_stream(stream));
 }
 
+rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t chan_begin,
+                                          int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                          const double* weight_sum, float* image_real,
+                                          float* image_complex, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return fft_phase_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, weight_sum,
+                          image_real, image_complex, as_stream(stream));
+}
+
+rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return columns_impl(plan, grids, n_planes, as_stream(stream));
+}
+
+rick_status rick_rows_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
+                                           int32_t chan_end, int32_t plane_begin, int32_t plane_end,
+                                           const double* weight_sum, float* image_real,
+                                           float* image_complex, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return rows_phase_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, weight_sum,
+                           image_real, image_complex, as_stream(stream));
+}
+
 rick_status rick_dirty_image(rick_plan* plan, const double* uvw, const double* chan_scale,
                              const float* vis, const float* weight, const uint8_t* flag,
                              int64_t nrow, float* image_real, float* image_complex,
@@ -1006,9 +1114,9 @@ rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double*
     if (grids) {
         if (s == RICK_OK) s = bin_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, weight_sum, counts, st);
         if (s == RICK_OK) s = grid_impl(plan, 0, c.n_channels, 0, plan->planes, grids, st);
-        if (s == RICK_OK) s = fft_impl(plan, grids, (int64_t)c.n_channels * plan->planes, st);
         if (s == RICK_OK)
-            s = phase_impl(plan, grids, 0, c.n_channels, 0, plan->planes, weight_sum, image_real, nullptr, st);
+            s = fft_phase_impl(plan, grids, 0, c.n_channels, 0, plan->planes, weight_sum, image_real,
+                               nullptr, st);
     } else if (s == RICK_OK) {
         s = dirty_image_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, image_real, nullptr,
                              weight_sum, counts, st);

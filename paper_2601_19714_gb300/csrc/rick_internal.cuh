@@ -16,6 +16,8 @@
 #include <cufft.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "rick.h"
 
 namespace rick {
@@ -119,6 +121,30 @@ struct PhaseParams {
     float w_c0, w_s_i0, w_exp2b;  // w_exp2b = exp(-2 beta)
 };
 
+// 1 / C_w(delta dw) for the Kaiser-Bessel w-kernel of support Sw (1 without
+// one), from its closed-form transform
+//   C_w(nu) = Sw sinh(r) / (r I0(beta)),  r = sqrt(beta^2 - (pi Sw nu)^2),
+// (sin for r^2 < 0).  Inside the main lobe it is written relative to C_w(0):
+//   C_w(nu) / C_w(0) = (beta / r) e^(-eps) (1 - e^(-2 r)) / (1 - e^(-2 beta)),
+// eps = beta - r = a^2 / (beta + r), a = pi Sw nu, so that FP32 sees no
+// large argument and no cancellation; r and eps come from FP64 once per pixel.
+__device__ __forceinline__ float w_taper_inv(const PhaseParams& P, double delta) {
+    if (P.w_support < 2) return 1.0f;
+    const double a = 3.141592653589793 * P.w_support * (delta * P.dw);
+    const double b = P.w_beta;
+    const double x2 = b * b - a * a;
+    if (x2 > 0.0) {
+        const double r = sqrt(x2);
+        const float eps = (float)(a * a / (b + r));
+        const float ratio = (float)(b / r) * expf(-eps) * (1.0f - expf(-2.0f * (float)r)) /
+                            (1.0f - P.w_exp2b);
+        return 1.0f / (P.w_c0 * ratio);
+    }
+    const float r = (float)sqrt(-x2);
+    const float h = r < 1e-4f ? 1.0f : sinf(r) / r;
+    return 1.0f / (P.w_s_i0 * h);
+}
+
 // --- launchers (one per kernel family), all asynchronous on `stream` -------
 
 cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* chan_scale,
@@ -156,6 +182,22 @@ cudaError_t launch_degrid(const GridParams& G, const uint32_t* offsets, const Vi
                           int num_sms, cudaStream_t stream, int* launches);
 
 uint64_t scan_partials_needed(uint64_t n);
+
+// The library's own 2-D DFT of the w-planes (rick_fft.cu), 256 <= N <= 8192
+// (powers of two).  twid: the table fft_twiddles(N) in device memory.
+bool fft_supported(int N);
+void fft_twiddles(int N, std::vector<float2>& out);
+// In place, unnormalised, over n_planes planes [N][N]: columns then rows.
+cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
+                         cudaStream_t stream, int* launches);
+// Pass 1 alone (the inverse DFT down every column), in place.
+cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
+                               cudaStream_t stream, int* launches);
+// Pass 2 fused with the phase screen and reduction: grids must hold the
+// column-transformed planes [nc][nk][N][N]; image_real [nc][N][N] (+=).
+cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
+                                     const float* inv_taper, const float2* twid, float* image_real,
+                                     float2* image_complex, cudaStream_t stream, int* launches);
 
 // learned kernel network (rick_mlp.cu)
 int64_t mlp_param_count(int H);

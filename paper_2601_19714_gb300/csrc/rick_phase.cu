@@ -44,29 +44,6 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// 1 / C_w(delta dw) for the Kaiser-Bessel w-kernel of support Sw (1 without
-// one), from its closed-form transform
-//   C_w(nu) = Sw sinh(r) / (r I0(beta)),  r = sqrt(beta^2 - (pi Sw nu)^2),
-// (sin for r^2 < 0).  Inside the main lobe it is written relative to C_w(0):
-//   C_w(nu) / C_w(0) = (beta / r) e^(-eps) (1 - e^(-2 r)) / (1 - e^(-2 beta)),
-// eps = beta - r = a^2 / (beta + r), a = pi Sw nu, so that FP32 sees no
-// large argument and no cancellation; r and eps come from FP64 once per pixel.
-__device__ __forceinline__ float w_taper_inv(const PhaseParams& P, double delta) {
-    if (P.w_support < 2) return 1.0f;
-    const double a = 3.141592653589793 * P.w_support * (delta * P.dw);
-    const double b = P.w_beta;
-    const double x2 = b * b - a * a;
-    if (x2 > 0.0) {
-        const double r = sqrt(x2);
-        const float eps = (float)(a * a / (b + r));
-        const float ratio = (float)(b / r) * expf(-eps) * (1.0f - expf(-2.0f * (float)r)) /
-                            (1.0f - P.w_exp2b);
-        return 1.0f / (P.w_c0 * ratio);
-    }
-    const float r = (float)sqrt(-x2);
-    const float h = r < 1e-4f ? 1.0f : sinf(r) / r;
-    return 1.0f / (P.w_s_i0 * h);
-}
 
 template <int PREC, bool COMPLEX_OUT>
 __global__ void __launch_bounds__(kPhaseThreads)

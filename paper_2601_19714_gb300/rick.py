@@ -23,10 +23,13 @@ STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_E
           7: "RICK_ERR_INTERNAL", 8: "RICK_ERR_CAPACITY"}
 KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
 PRECISIONS = {"fp64idx": 0, "fp32": 1}
+FFT_IMPLS = {"own": 0, "cufft": 1}
 
 EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
            "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
-           "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_dirty_image",
+           "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_fft_phase_correct_reduce",
+           "rick_fft_wplanes_columns", "rick_rows_phase_correct_reduce",
+           "rick_dirty_image",
            "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
            "rick_plan_bins", "rick_grid_noalloc", "rick_graph_capture", "rick_graph_launch",
            "rick_graph_destroy", "rick_autotune", "rick_mlp_param_count", "rick_mlp_forward",
@@ -50,7 +53,8 @@ class rick_config(C.Structure):
                 ("precision", C.c_int32), ("tile", C.c_int32), ("grid_threads", C.c_int32),
                 ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
                 ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32),
-                ("w_support", C.c_int32), ("w_kernel_param", C.c_double)]
+                ("w_support", C.c_int32), ("w_kernel_param", C.c_double),
+                ("fft_impl", C.c_int32)]
 
 
 class rick_tune_entry(C.Structure):
@@ -81,6 +85,9 @@ def load(path: str = LIB_PATH):
         "rick_grid": [p, p, p, p, p, p, i64, i32, i32, p, p, p, p],
         "rick_fft_wplanes": [p, p, i64, p],
         "rick_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
+        "rick_fft_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
+        "rick_fft_wplanes_columns": [p, p, i64, p],
+        "rick_rows_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
         "rick_dirty_image": [p, p, p, p, p, p, i64, p, p, p, p, p],
         "rick_dirty_image_host": [p, p, p, p, p, p, i64, p, p, p, p],
         "rick_plan_sync_status": [p],
@@ -193,6 +200,7 @@ class Config:
     hermitian_fold: bool = False
     w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
     w_kernel_param: float = 0.0
+    fft_impl: str = "own"       # "own": the library's two-pass DFT (256 <= N <= 8192); "cufft"
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
@@ -200,7 +208,7 @@ class Config:
                            PRECISIONS[self.precision], self.tile, self.grid_threads,
                            self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes,
                            int(bool(self.hermitian_fold)), int(self.w_support),
-                           float(self.w_kernel_param))
+                           float(self.w_kernel_param), FFT_IMPLS[self.fft_impl])
 
     @property
     def planes_total(self) -> int:
@@ -317,6 +325,32 @@ class Plan:
             _ptr(image_real, d["f32"], "image_real", 8),
             _ptr(image_complex, d["c64"], "image_complex", 16), _stream(stream)),
             "rick_phase_correct_reduce")
+
+    def fft_phase_correct_reduce(self, grids, chan_begin, chan_end, plane_begin, plane_end,
+                                 weight_sum, image_real, image_complex=None, stream=None):
+        d = _dt()
+        _check(load().rick_fft_phase_correct_reduce(
+            self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
+            plane_end, _ptr(weight_sum, d["f64"], "weight_sum", 8),
+            _ptr(image_real, d["f32"], "image_real", 4),
+            _ptr(image_complex, d["c64"], "image_complex", 8), _stream(stream)),
+            "rick_fft_phase_correct_reduce")
+
+    def fft_wplanes_columns(self, grids, n_planes, stream=None):
+        d = _dt()
+        _check(load().rick_fft_wplanes_columns(self.handle, _ptr(grids, d["c64"], "grids", 16),
+                                               int(n_planes), _stream(stream)),
+               "rick_fft_wplanes_columns")
+
+    def rows_phase_correct_reduce(self, grids, chan_begin, chan_end, plane_begin, plane_end,
+                                  weight_sum, image_real, image_complex=None, stream=None):
+        d = _dt()
+        _check(load().rick_rows_phase_correct_reduce(
+            self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
+            plane_end, _ptr(weight_sum, d["f64"], "weight_sum", 8),
+            _ptr(image_real, d["f32"], "image_real", 4),
+            _ptr(image_complex, d["c64"], "image_complex", 8), _stream(stream)),
+            "rick_rows_phase_correct_reduce")
 
     def dirty_image(self, uvw, chan_scale, vis, weight, flag, nrow, image_real,
                     image_complex=None, weight_sum=None, counts=None, stream=None):
