@@ -3,11 +3,11 @@
 
 One step = the whole path over one batch: rick_bin + rick_grid_binned
 (placement, binning and gridding of every visibility of every channel onto
-its w-plane), then the inverse 2-D DFT of every plane and Eq. 2's phase
-screen + sum over planes into the dirty images: the library's own transform
-as rick_fft_wplanes_columns (column pass) + rick_rows_phase_correct_reduce
-(row pass fused with the reduction); the cuFFT path (rick_fft_wplanes +
-rick_phase_correct_reduce) is timed beside it as "cufft_variant".  Inputs are resident
+its w-plane), rick_fft_wplanes (cuFFT, every plane), rick_phase_correct_reduce
+(phase screen + sum over planes into the dirty images).  The library's own
+transform (rick_fft_wplanes_columns + rick_rows_phase_correct_reduce, the row
+pass fused with the reduction) is timed beside it as "own_fft_variant".
+Inputs are resident
 in HBM when the timed region starts; `e2e` repeats the measurement through
 rick_dirty_image_host, with the host->device copy of the inputs and the
 device->host copy of the images inside the timed region.
@@ -336,8 +336,8 @@ def run_ours(args):
     tuned = tuned_config(fold)
     other_cfg = tuned_config(not fold)
     other = measure(other_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
-    cufft_cfg = replace(tuned, fft_impl="cufft")
-    cufft = measure(cufft_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
+    own_cfg = replace(tuned, fft_impl="own")
+    own_fft = measure(own_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
     res = measure(tuned, args.steps, args.warmup, clocks=True)
     st, ms_max, launches = res["st"], res["ms"], res["launches"]
     n_grid, n_drop = res["n_grid"], res["n_drop"]
@@ -437,10 +437,11 @@ def run_ours(args):
                 "steps": max(1, min(args.steps, 3)),
                 "tile": other_cfg.tile, "grid_threads": other_cfg.grid_threads,
                 "tiles_per_grab": other_cfg.tiles_per_grab},
-            "cufft_variant": {
-                "fft_impl": "cufft", "hermitian_fold": fold,
-                "value": cufft["n_grid"] * world / (cufft["ms"] * 1e-3), "unit": UNIT,
-                "ms_per_step": cufft["ms"], "stages_ms": cufft["st"],
+            "own_fft_variant": {
+                "fft_impl": "own (column pass + row pass fused with the reduction)",
+                "hermitian_fold": fold,
+                "value": own_fft["n_grid"] * world / (own_fft["ms"] * 1e-3), "unit": UNIT,
+                "ms_per_step": own_fft["ms"], "stages_ms": own_fft["st"],
                 "steps": max(1, min(args.steps, 3))},
         }
         if not args.no_cpu_baseline:
@@ -860,9 +861,9 @@ def run_wkernel(args):
             if e: e[1].record(stream)
             plan.grid_binned(0, C, 0, ns, grids)
             if e: e[2].record(stream)
-            plan.fft_wplanes_columns(grids, C * ns)
+            plan.fft_wplanes(grids, C * ns)
             if e: e[3].record(stream)
-            plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+            plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
             if e: e[4].record(stream)
             return e
 
@@ -881,7 +882,7 @@ def run_wkernel(args):
             torch.cuda.synchronize()
         ms = a.elapsed_time(b) / args.steps
         st = {k: statistics.median([e[i].elapsed_time(e[i + 1]) for e in evs])
-              for i, k in enumerate(("bin", "grid", "columns", "rows_phase"))}
+              for i, k in enumerate(("bin", "grid", "fft", "phase"))}
         I = image[c_top].cpu().numpy()
         got = I[probes[1], probes[0]]
         err = float(np.abs(got - D).max() / np.abs(D).max())
@@ -890,7 +891,7 @@ def run_wkernel(args):
              "vis_per_s": n_grid / (ms * 1e-3), "stages_ms": st,
              "records": int(n_grid * max(1, sw)),
              "error_vs_eq1_direct": err, "launches": int(plan.launch_count() - n0),
-             "rows_phase_gbs": (8.0 * cells + 8.0 * C * N * N) / (st["rows_phase"] * 1e-3) / 1e9,
+             "phase_gbs": (8.0 * cells + 8.0 * C * N * N) / (st["phase"] * 1e-3) / 1e9,
              "clocks": clk.summary()}
         r["_got"] = got
         results[name] = r
@@ -921,9 +922,8 @@ def run_wkernel(args):
                    "launch_shape": "default (tile 32, 128 threads, 4 tiles per grab)",
                    "l2": "inputs larger than L2"},
         "variants": results,
-        "roofline_rows_phase": {"bound": "hbm", "achieved": rb["rows_phase_gbs"], "peak": hbm,
-                                "unit": "GB/s", "frac": rb["rows_phase_gbs"] / hbm,
-                                "peak_kind": peak_kind},
+        "roofline_phase": {"bound": "hbm", "achieved": rb["phase_gbs"], "peak": hbm,
+                           "unit": "GB/s", "frac": rb["phase_gbs"] / hbm, "peak_kind": peak_kind},
         "gpu_launches": rb["launches"], "clocks": rb["clocks"]}), flush=True)
 
 
@@ -932,9 +932,8 @@ def run_profile_small(args):
     recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
     grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
-    A step images the 2 channels (the own transform: column pass, then the
-    row pass fused with the reduction) and then predicts visibilities from
-    the dirty images (the degridding path).  Runs warm-up + steps steps and
+    A step images the 2 channels and then predicts visibilities from the
+    dirty images (the degridding path).  Runs warm-up + steps steps and
     prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
@@ -959,8 +958,8 @@ def run_profile_small(args):
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
         plan.grid_binned(0, C, 0, ns, grids)
-        plan.fft_wplanes_columns(grids, C * ns)
-        plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        plan.fft_wplanes(grids, C * ns)
+        plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
         # prediction from the dirty image just made (exercises the degridder)
         plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow)
         plan.model_to_wplanes(image, 0, C, 0, ns, grids)

@@ -129,10 +129,10 @@ typedef struct rick_config {
      * trainer (RICK_ERR_INVALID_ARG / RICK_ERR_UNSUPPORTED). */
     int32_t w_support;
     double w_kernel_param;
-    /* 2-D DFT of the w-planes: 0 = the library's own two-pass transform for
-     * power-of-two 256 <= N <= 8192 (columns, then rows; the imaging path fuses
-     * the row pass with the phase screen and reduction), cuFFT for other N;
-     * 1 = cuFFT for every N (batched, fft_batch planes per execution). */
+    /* 2-D DFT of the w-planes: 0 = cuFFT (batched, fft_batch planes per
+     * execution); 1 = the library's own two-pass transform for power-of-two
+     * 256 <= N <= 8192 (columns, then rows; the imaging path fuses the row
+     * pass with the phase screen and reduction; cuFFT for other N). */
     int32_t fft_impl;
 } rick_config;
 

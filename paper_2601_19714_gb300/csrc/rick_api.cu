@@ -392,7 +392,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
     RK_CUDA(cudaMalloc(&P->d_wsum, sizeof(double) * c.n_channels));
 
-    P->own_fft = c.fft_impl == 0 && fft_supported(c.N);
+    P->own_fft = c.fft_impl == 1 && fft_supported(c.N);
     if (P->own_fft) {
         std::vector<float2> tw;
         fft_twiddles(c.N, tw);
@@ -633,7 +633,7 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
 // Pass 1 of the own transform (inverse DFT down every column), in place.
 rick_status columns_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st) {
     if (!P->own_fft) {
-        set_err("the column pass needs the library's own transform (fft_impl 0, 256 <= N <= 8192)");
+        set_err("the column pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(n_planes >= 0, "n_planes must be >= 0");
@@ -654,7 +654,7 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
                             cudaStream_t st) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
-        set_err("the fused row pass needs the library's own transform (fft_impl 0, 256 <= N <= 8192)");
+        set_err("the fused row pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");

@@ -23,7 +23,7 @@ STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_E
           7: "RICK_ERR_INTERNAL", 8: "RICK_ERR_CAPACITY"}
 KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
 PRECISIONS = {"fp64idx": 0, "fp32": 1}
-FFT_IMPLS = {"own": 0, "cufft": 1}
+FFT_IMPLS = {"cufft": 0, "own": 1}
 
 EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
            "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
@@ -200,7 +200,7 @@ class Config:
     hermitian_fold: bool = False
     w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
     w_kernel_param: float = 0.0
-    fft_impl: str = "own"       # "own": the library's two-pass DFT (256 <= N <= 8192); "cufft"
+    fft_impl: str = "cufft"     # or "own": the library's two-pass DFT (256 <= N <= 8192)
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,

@@ -32,6 +32,7 @@ def rk():
 
 
 def _plan(rk, N, n_planes=1, **kw):
+    kw.setdefault("fft_impl", "own")
     return rk.Plan(rk.Config(N=N, n_wplanes=n_planes, support=8, n_channels=1, fov_rad=0.02,
                              w_min=-100.0, w_max=100.0, kernel="kb", kernel_param=12.25, **kw))
 
@@ -107,10 +108,11 @@ def _gridded(rk, cfg, dev, C):
                                 dict(hermitian_fold=True, w_support=4, w_kernel_param=8.0)])
 def test_fused_equals_separate_calls(rk, kw):
     import torch
-    img, obs = meerkat(81, n_ant=10, n_steps=60, nchan=3, N=1024, Nw=8, n_src=10)
+    # 24 planes: with a w-kernel of support 4, fewer would put a zero of C_w in the field
+    img, obs = meerkat(81, n_ant=10, n_steps=60, nchan=3, N=1024, Nw=24, n_src=10)
     dev = to_device(obs)
     C, N = 3, img.N
-    cfg = plan_config(img, C, **kw)
+    cfg = plan_config(img, C, fft_impl="own", **kw)
     plan, grids, wsum = _gridded(rk, cfg, dev, C)
     ns = cfg.stored_planes
     sep = grids.clone()
@@ -124,10 +126,14 @@ def test_fused_equals_separate_calls(rk, kw):
     torch.cuda.synchronize()
     a, b = i_fus.cpu().numpy() - 0.5, i_sep.cpu().numpy()
     peak = np.abs(b).max()
+    # the all-FP32 variant forms the phase differently in the two kernels (FP32
+    # turns per plane there, FP32 turns to Q0.32 once per pixel here): it is a
+    # precision study with no gate, so only agreement to its own error is asked
+    tol = 2e-5 if kw.get("precision") == "fp32" else 2e-6
     print(kw, np.abs(a - b).max() / peak)
-    assert np.abs(a - b).max() <= 2e-6 * peak
+    assert np.abs(a - b).max() <= tol * peak
     ca, cb = c_fus.cpu().numpy(), c_sep.cpu().numpy()
-    assert np.abs(ca - cb).max() <= 2e-6 * np.abs(cb).max()
+    assert np.abs(ca - cb).max() <= tol * np.abs(cb).max()
 
 
 def test_fused_channel_and_plane_ranges(rk):
@@ -137,7 +143,7 @@ def test_fused_channel_and_plane_ranges(rk):
     img, obs = meerkat(82, n_ant=10, n_steps=40, nchan=4, N=512, Nw=8, n_src=10)
     dev = to_device(obs)
     C, N = 4, img.N
-    cfg = plan_config(img, C)
+    cfg = plan_config(img, C, fft_impl="own")
     plan, grids, wsum = _gridded(rk, cfg, dev, C)
     sub = grids[1:3, 2:6].contiguous()
     ref = sub.clone()
