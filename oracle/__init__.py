@@ -24,6 +24,7 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 GAUSS, KAISER_BESSEL, LEARNED = 0, 1, 2
 _KINDS = {"gauss": GAUSS, "kb": KAISER_BESSEL, "kaiser_bessel": KAISER_BESSEL, "learned": LEARNED}
+_WEIGHTINGS = {"natural": 0, "uniform": 1, "briggs": 2}
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,8 @@ class _Cfg(C.Structure):
                 ("kernel_param", C.c_double), ("fov", C.c_double), ("w_min", C.c_double),
                 ("w_max", C.c_double), ("mlp", C.POINTER(C.c_double)),
                 ("mlp_hidden", C.c_int32), ("mlp_lattice", C.c_int32),
-                ("w_support", C.c_int32), ("w_kernel_param", C.c_double)]
+                ("w_support", C.c_int32), ("w_kernel_param", C.c_double),
+                ("weighting", C.c_int32), ("robust", C.c_double)]
 
 
 @dataclass
@@ -64,12 +66,15 @@ class Config:
     mlp_lattice: int = 0
     w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
     w_kernel_param: float = 0.0
+    weighting: str = "natural"  # or "uniform", "briggs" (R15)
+    robust: float = 0.0         # Briggs robustness R
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Cfg:
         cfg = _Cfg(self.N, self.Nw, self.S, _KINDS[self.kernel], self.kernel_param, self.fov,
                    self.w_min, self.w_max, None, self.mlp_hidden, self.mlp_lattice,
-                   self.w_support, self.w_kernel_param)
+                   self.w_support, self.w_kernel_param, _WEIGHTINGS[self.weighting],
+                   self.robust)
         if self.mlp is not None:
             arr = np.ascontiguousarray(self.mlp, dtype=np.float64)
             self._keep = [arr]
@@ -111,6 +116,8 @@ def _declare(L):
     L.oracle_plane_w.argtypes = [cfgp, C.c_int]
     vis_args = [cfgp, p, p, C.c_int, p, p, p, i64]
     L.oracle_place.argtypes = [cfgp, p, p, C.c_int, p, p, i64, p, p, p, p, p, p, p]
+    L.oracle_imaging_weights.restype = C.c_int
+    L.oracle_imaging_weights.argtypes = [cfgp, p, p, C.c_int, p, p, i64, p]
     L.oracle_planes_total.restype = C.c_int
     L.oracle_planes_total.argtypes = [cfgp]
     L.oracle_kernel_ft.restype = d
@@ -252,7 +259,31 @@ def kernel_ft(kind: str, param: float, S: int, nu: float) -> float:
     return lib().oracle_kernel_ft(_KINDS[kind], float(param), int(S), float(nu))
 
 
+def imaging_weights(cfg: Config, uvw, chan_scale, weight, flag=None) -> np.ndarray:
+    """Imaging weights W' [nrow, C] in FP64 (R15): W for natural weighting and
+    for visibilities that are not gridded; W / D (uniform) or W / (1 + f^2 D)
+    (Briggs) otherwise, D the Hermitian-completed density on the nearest cell."""
+    v = _Vis(uvw, chan_scale, np.zeros((len(uvw), len(np.atleast_1d(chan_scale))), np.complex64),
+             weight, flag)
+    out = np.zeros((v.nrow, v.C), np.float64)
+    c = cfg.c()
+    rc = lib().oracle_imaging_weights(C.byref(c), _ptr(v.uvw), _ptr(v.scale), v.C, _ptr(v.weight),
+                                      _ptr(v.flag), v.nrow, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_imaging_weights failed ({rc})")
+    return out
+
+
+def _weights(cfg: Config, uvw, chan_scale, weight, flag):
+    """The weights the imaging functions use: the data weights, or the imaging
+    weights W' of R15 stored in FP32 (the C functions take them as given)."""
+    if cfg.weighting == "natural":
+        return weight
+    return imaging_weights(cfg, uvw, chan_scale, weight, flag).astype(np.float32)
+
+
 def channel_stats(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0):
+    weight = _weights(cfg, uvw, chan_scale, weight, flag)
     v = _Vis(uvw, chan_scale, np.zeros((len(uvw), len(np.atleast_1d(chan_scale))), np.complex64),
              weight, flag)
     ws = C.c_double()
@@ -266,7 +297,7 @@ def channel_stats(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0):
 
 def grid_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, plane=0):
     """Gridded plane ``plane`` of channel ``channel`` (Eq. 3), complex128 [N, N]."""
-    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    v = _Vis(uvw, chan_scale, vis, _weights(cfg, uvw, chan_scale, weight, flag), flag)
     out = np.zeros((cfg.N, cfg.N), np.complex128)
     c = cfg.c()
     n = lib().oracle_grid_plane(C.byref(c), *v.args(), channel, plane, _ptr(out))
@@ -312,7 +343,7 @@ def fold_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, 
 def image(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0):
     """Complex w-stacking dirty image of one channel (O1), complex128 [N, N]
     indexed [q, p] (m row, l column), and the channel's sum of weights."""
-    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    v = _Vis(uvw, chan_scale, vis, _weights(cfg, uvw, chan_scale, weight, flag), flag)
     out = np.zeros((cfg.N, cfg.N), np.complex128)
     ws = C.c_double()
     c = cfg.c()
@@ -326,7 +357,7 @@ def image_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=
              plane=-1):
     """O1 at pixels (p, q) evaluated visibility by visibility (no FFT).  With
     ``plane >= 0``: the transformed plane F_plane[q, p] before the phase screen."""
-    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    v = _Vis(uvw, chan_scale, vis, _weights(cfg, uvw, chan_scale, weight, flag), flag)
     pp = np.ascontiguousarray(p, dtype=np.int32)
     qq = np.ascontiguousarray(q, dtype=np.int32)
     out = np.zeros(pp.shape[0], np.complex128)
@@ -339,8 +370,9 @@ def image_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=
 
 
 def dft_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=(), q=()):
-    """O2: direct Fourier inversion of Eq. 1 at pixels (p, q), complex."""
-    v = _Vis(uvw, chan_scale, vis, weight, flag)
+    """O2: direct Fourier inversion of Eq. 1 at pixels (p, q), complex (with
+    the same imaging weights as O1)."""
+    v = _Vis(uvw, chan_scale, vis, _weights(cfg, uvw, chan_scale, weight, flag), flag)
     pp = np.ascontiguousarray(p, dtype=np.int32)
     qq = np.ascontiguousarray(q, dtype=np.int32)
     out = np.zeros(pp.shape[0], np.complex128)

@@ -41,6 +41,17 @@
  *   R7 kernels:       Gaussian g(s) = exp(-s^2/(2 sigma^2)); Kaiser-Bessel
  *                     (Jackson 1991) g(s) = I0(beta sqrt(1-(2s/S)^2))/I0(beta),
  *                     both zero for |s| > S/2.
+ *   R15 weighting:    the paper uses natural weighting (Sec. 4.1.1); uniform
+ *                     and Briggs (robust) weighting are extensions.  The
+ *                     density D is the sum of the weights of the gridded
+ *                     visibilities of one channel on their nearest mesh cell
+ *                     (i, j) = (floor(x + 1/2), floor(y + 1/2)), each counted
+ *                     there and at the cell of its Hermitian partner,
+ *                     ((N - i) mod N, (N - j) mod N).  Uniform: W' = W / D;
+ *                     Briggs with robustness R: W' = W / (1 + f^2 D),
+ *                     f^2 = (5 10^-R)^2 sum(D) / sum(D^2) over the cells.  The
+ *                     weights W' (stored in FP32, like the data weights)
+ *                     then replace W everywhere, including the sum of weights.
  *
  * Floating point: FP64 throughout, compiled without FMA contraction so that
  * the index decisions (footprint start, plane index) are the IEEE results of
@@ -83,7 +94,11 @@ typedef struct {
                              even Sw >= 2: convolved in w onto Sw planes with a
                              Kaiser-Bessel kernel (R14) */
     double w_kernel_param;/* beta of the w-direction Kaiser-Bessel kernel */
+    int32_t weighting;    /* ORACLE_NATURAL / ORACLE_UNIFORM / ORACLE_BRIGGS (R15) */
+    double robust;        /* Briggs robustness R */
 } oracle_cfg;
+
+enum { ORACLE_NATURAL = 0, ORACLE_UNIFORM = 1, ORACLE_BRIGGS = 2 };
 
 /* ------------------------------------------------------------------ */
 /* Kernel functions                                                    */
@@ -560,6 +575,58 @@ static int check_cfg(const oracle_cfg* cfg)
     if (cfg->kernel == ORACLE_LEARNED && (cfg->S != 4 || !cfg->mlp || cfg->mlp_hidden < 1)) return 1;
     if (cfg->w_support < 0 || cfg->w_support > 16) return 1;
     if (w_improved(cfg) && ((cfg->w_support & 1) || cfg->Nw < 2 || !(cfg->w_kernel_param > 0.0))) return 1;
+    if (cfg->weighting < ORACLE_NATURAL || cfg->weighting > ORACLE_BRIGGS) return 1;
+    if (cfg->weighting == ORACLE_BRIGGS && !isfinite(cfg->robust)) return 1;
+    return 0;
+}
+
+/* Imaging weights (R15): out[r][c] = W' for every visibility (W itself for
+ * those that are not gridded, and for natural weighting).  Returns 0, or 1
+ * for an invalid configuration, 2 if memory runs out.  The gridding, imaging
+ * and direct-inversion functions below take the weights they are given; for
+ * uniform or Briggs weighting the caller passes W' (the Python wrapper does). */
+int oracle_imaging_weights(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
+                           const float* weight, const uint8_t* flag, long nrow, double* out)
+{
+    if (check_cfg(cfg)) return 1;
+    for (long r = 0; r < nrow; ++r)
+        for (int c = 0; c < C; ++c) out[(size_t)r * C + c] = (double)weight[(size_t)r * C + c];
+    if (cfg->weighting == ORACLE_NATURAL) return 0;
+    int N = cfg->N;
+    double* D = (double*)malloc(sizeof(double) * (size_t)N * N);
+    long* cell = (long*)malloc(sizeof(long) * (size_t)(nrow > 0 ? nrow : 1));
+    if (!D || !cell) { free(D); free(cell); return 2; }
+    for (int c = 0; c < C; ++c) {
+        memset(D, 0, sizeof(double) * (size_t)N * N);
+        for (long r = 0; r < nrow; ++r) {
+            cell[r] = -1;
+            placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
+            if (P.ok != 1) continue;
+            /* nearest cell; inside [0, N) because the whole footprint is */
+            long i = (long)floor(P.x + 0.5), j = (long)floor(P.y + 0.5);
+            double W = (double)weight[(size_t)r * C + c];
+            D[(size_t)j * N + i] += W;
+            D[(size_t)((N - j) % N) * N + (N - i) % N] += W;
+            cell[r] = j * N + i;
+        }
+        double f2 = 0.0;
+        if (cfg->weighting == ORACLE_BRIGGS) {
+            double s1 = 0.0, s2 = 0.0;
+            for (size_t e = 0; e < (size_t)N * N; ++e) {
+                s1 += D[e];
+                s2 += D[e] * D[e];
+            }
+            double a = 5.0 * pow(10.0, -cfg->robust);
+            f2 = s2 > 0.0 ? a * a * s1 / s2 : 0.0;
+        }
+        for (long r = 0; r < nrow; ++r) {
+            if (cell[r] < 0) continue;
+            double W = (double)weight[(size_t)r * C + c], d = D[cell[r]];
+            out[(size_t)r * C + c] = cfg->weighting == ORACLE_UNIFORM ? W / d : W / (1.0 + f2 * d);
+        }
+    }
+    free(D);
+    free(cell);
     return 0;
 }
 
