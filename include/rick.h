@@ -78,6 +78,22 @@ typedef enum {
     RICK_PREC_ALL_FP32 = 1      /* index and phase in FP32 as well (precision study) */
 } rick_precision;
 
+/* Imaging weights.  The paper images with natural weighting (the data
+ * weights W, Sec. 4.1.1).  Uniform and Briggs weighting replace W by W'
+ * before gridding (and in the sum of weights): with D the density of the
+ * channel's gridded visibilities -- the sum of their W on their nearest mesh
+ * cell (floor(x + 1/2), floor(y + 1/2)), each counted there and at the cell
+ * of its Hermitian partner ((N - i) mod N, (N - j) mod N) --
+ *   uniform: W' = W / D(cell),
+ *   Briggs:  W' = W / (1 + f^2 D(cell)),  f^2 = (5 10^-R)^2 sum D / sum D^2
+ * over the cells of the channel, R = robust (R -> +inf: natural, R -> -inf:
+ * proportional to uniform).  W' is stored in FP32. */
+typedef enum {
+    RICK_WEIGHT_NATURAL = 0,
+    RICK_WEIGHT_UNIFORM = 1,
+    RICK_WEIGHT_BRIGGS = 2
+} rick_weighting;
+
 typedef struct rick_config {
     int32_t N;            /* grid side = image side: power of two, 64..65536 */
     int32_t n_wplanes;    /* Nw >= 1 */
@@ -134,6 +150,8 @@ typedef struct rick_config {
      * 256 <= N <= 8192 (columns, then rows; the imaging path fuses the row
      * pass with the phase screen and reduction; cuFFT for other N). */
     int32_t fft_impl;
+    int32_t weighting;    /* rick_weighting (0 = natural); imaging only, prediction ignores it */
+    double robust;        /* Briggs robustness R (weighting = RICK_WEIGHT_BRIGGS) */
 } rick_config;
 
 /* Planes a plan stores for cfg: P = Nw, or Nw + Sw with a w-kernel; ceil(P / 2)
@@ -191,6 +209,15 @@ rick_status rick_bin(rick_plan* plan, const double* uvw, const double* chan_scal
  * need not be cleared.  Requires a preceding rick_bin on the same plan. */
 rick_status rick_grid_binned(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
                              int32_t plane_begin, int32_t plane_end, float* grids, void* stream);
+
+/* The imaging weights W'[nrow][C] (device, f32) that rick_bin grids with:
+ * the data weights for natural weighting, else uniform or Briggs weights of
+ * the plan's configuration (see rick_weighting); visibilities that are not
+ * gridded keep their weight.  Inputs as for rick_bin.  Uses plan-owned
+ * scratch: a [C][N][N] FP64 density. */
+rick_status rick_imaging_weights(rick_plan* plan, const double* uvw, const double* chan_scale,
+                                 const float* weight, const uint8_t* flag, int64_t nrow,
+                                 float* weight_out, void* stream);
 
 /* rick_bin followed by rick_grid_binned for all channels and planes
  * [plane_begin, plane_end). */

@@ -170,7 +170,12 @@ struct rick_plan {
     cudaStream_t last_stream = nullptr;
     float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
     double tap_fit_error = 0.0;
-    // the library's own 2-D DFT (fft_impl 0 and 256 <= N <= 8192): twiddle tables
+    // imaging weights (uniform / Briggs): density [C][N][N], moments [2C], W' [cap_w]
+    double* d_density = nullptr;
+    double* d_wmom = nullptr;
+    float* d_wbuf = nullptr;
+    int64_t cap_w = 0;
+    // the library's own 2-D DFT (fft_impl 1 and 256 <= N <= 8192): twiddle tables
     bool own_fft = false;
     float2* d_twid = nullptr;
     // w-kernel: tap polynomials and the constants of its transform C_w
@@ -189,6 +194,9 @@ void dfree(T*& p) {
 void release(rick_plan* P) {
     dfree(P->d_inv_taper);
     dfree(P->d_twid);
+    dfree(P->d_density);
+    dfree(P->d_wmom);
+    dfree(P->d_wbuf);
     dfree(P->d_table);
     dfree(P->d_key);
     dfree(P->d_rank);
@@ -247,6 +255,9 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
     RK_ARG(c->fft_impl == 0 || c->fft_impl == 1, "fft_impl must be 0 or 1");
+    RK_ARG(c->weighting >= RICK_WEIGHT_NATURAL && c->weighting <= RICK_WEIGHT_BRIGGS,
+           "weighting must be 0 (natural), 1 (uniform) or 2 (Briggs)");
+    RK_ARG(c->weighting != RICK_WEIGHT_BRIGGS || std::isfinite(c->robust), "robust must be finite");
     RK_ARG(c->w_support == 0 || c->w_support == 1 ||
                (c->w_support >= 2 && c->w_support <= 8 && (c->w_support & 1) == 0),
            "w_support must be 0, 1 or even in [2, 8]");
@@ -301,6 +312,15 @@ rick_status ensure_vis_capacity(rick_plan* P, int64_t nvis) {
     RK_CUDA(cudaMalloc(&P->d_lists, 3 * (size_t)cap * sizeof(uint32_t)));
     P->list_cap = cap;
     P->cap_vis = nvis;
+    return RICK_OK;
+}
+
+rick_status ensure_weight_capacity(rick_plan* P, int64_t nvis) {
+    if (nvis <= P->cap_w) return RICK_OK;
+    dfree(P->d_wbuf);
+    P->cap_w = 0;
+    RK_CUDA(cudaMalloc(&P->d_wbuf, sizeof(float) * (size_t)(nvis > 0 ? nvis : 1)));
+    P->cap_w = nvis;
     return RICK_OK;
 }
 
@@ -391,6 +411,10 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     RK_CUDA(cudaMalloc(&P->d_status, sizeof(int)));
     RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
     RK_CUDA(cudaMalloc(&P->d_wsum, sizeof(double) * c.n_channels));
+    if (c.weighting != RICK_WEIGHT_NATURAL) {
+        RK_CUDA(cudaMalloc(&P->d_density, sizeof(double) * (size_t)c.N * c.N * c.n_channels));
+        RK_CUDA(cudaMalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
+    }
 
     P->own_fft = c.fft_impl == 1 && fft_supported(c.N);
     if (P->own_fft) {
@@ -426,30 +450,9 @@ rick_status check_launch(cudaError_t e, const char* what) {
     return RICK_OK;
 }
 
-rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
-                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
-                     int64_t* counts, cudaStream_t st, bool predict = false) {
+// Placement parameters of the plan (binning for gridding or for prediction).
+PlaceParams place_params(const rick_plan* P, bool predict) {
     const rick_config& c = P->cfg;
-    RK_ARG(nrow >= 0, "nrow must be >= 0");
-    RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
-    const int64_t nvis = nrow * (int64_t)c.n_channels;
-    RK_ARG(nrow == 0 || nvis / nrow == c.n_channels, "nrow * C overflows");
-    const int64_t nrec = nvis * P->nrec_per_vis;
-    if (nrec >= (int64_t)0xFFFFFFFFLL) {
-        set_err("nrow * C%s = %lld exceeds 2^32 - 2 records per plan call",
-                P->nrec_per_vis > 1 ? " * w_support" : "", (long long)nrec);
-        return RICK_ERR_UNSUPPORTED;
-    }
-    if (nrow > 0) {
-        RK_ARG(uvw && chan_scale && (vis || predict) && weight,
-               "uvw, chan_scale, vis and weight are required");
-    }
-    RK_TRY(ensure_vis_capacity(P, nrec));
-    P->last_stream = st;
-    int launches = 0;
-    RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
-    RK_CUDA(cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st));
-    RK_CUDA(cudaMemsetAsync(P->d_counts, 0, 2 * sizeof(unsigned long long), st));
     PlaceParams pp;
     pp.N = c.N;
     pp.S = c.support;
@@ -474,7 +477,45 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     pp.half_s_f = (float)pp.half_s;
     pp.w_min_f = (float)c.w_min;
     pp.w_scale_f = (float)P->w_scale;
-    rick_status s = check_launch(
+    return pp;
+}
+
+rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
+                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
+                     int64_t* counts, cudaStream_t st, bool predict = false) {
+    const rick_config& c = P->cfg;
+    RK_ARG(nrow >= 0, "nrow must be >= 0");
+    RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
+    const int64_t nvis = nrow * (int64_t)c.n_channels;
+    RK_ARG(nrow == 0 || nvis / nrow == c.n_channels, "nrow * C overflows");
+    const int64_t nrec = nvis * P->nrec_per_vis;
+    if (nrec >= (int64_t)0xFFFFFFFFLL) {
+        set_err("nrow * C%s = %lld exceeds 2^32 - 2 records per plan call",
+                P->nrec_per_vis > 1 ? " * w_support" : "", (long long)nrec);
+        return RICK_ERR_UNSUPPORTED;
+    }
+    if (nrow > 0) {
+        RK_ARG(uvw && chan_scale && (vis || predict) && weight,
+               "uvw, chan_scale, vis and weight are required");
+    }
+    RK_TRY(ensure_vis_capacity(P, nrec));
+    if (!predict && c.weighting != RICK_WEIGHT_NATURAL) RK_TRY(ensure_weight_capacity(P, nvis));
+    P->last_stream = st;
+    int launches = 0;
+    RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
+    RK_CUDA(cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st));
+    RK_CUDA(cudaMemsetAsync(P->d_counts, 0, 2 * sizeof(unsigned long long), st));
+    const PlaceParams pp = place_params(P, predict);
+    rick_status s = RICK_OK;
+    if (!predict && c.weighting != RICK_WEIGHT_NATURAL && nvis > 0) {
+        // imaging weights W' into the plan's buffer, gridded in place of W
+        s = check_launch(launch_imaging_weights(pp, uvw, chan_scale, weight, flag, nvis, c.weighting,
+                                                c.robust, P->d_density, P->d_wmom, P->d_wbuf,
+                                                P->num_sms, st, &launches),
+                         "imaging weight kernels");
+        weight = P->d_wbuf;
+    }
+    if (s == RICK_OK) s = check_launch(
         launch_place(pp, uvw, chan_scale, reinterpret_cast<const float2*>(vis), weight, flag, nvis,
                      P->d_hist, P->d_key, P->d_rank, P->d_stage, weight_sum, P->d_counts,
                      P->num_sms, st, &launches),
@@ -886,6 +927,8 @@ rick_status rick_plan_reserve(rick_plan* plan, int64_t max_rows) {
         set_err("reservation exceeds 2^32 - 2 records");
         return RICK_ERR_UNSUPPORTED;
     }
+    if (plan->cfg.weighting != RICK_WEIGHT_NATURAL)
+        RK_TRY(ensure_weight_capacity(plan, max_rows * (int64_t)plan->cfg.n_channels));
     return ensure_vis_capacity(plan, nvis);
 }
 
@@ -938,6 +981,31 @@ rick_status rick_grid(rick_plan* plan, const double* uvw, const double* chan_sca
                     as_stream(stream)));
     return grid_impl(plan, 0, plan->cfg.n_channels, plane_begin, plane_end, grids,
                      as_stream(stream));
+}
+
+rick_status rick_imaging_weights(rick_plan* plan, const double* uvw, const double* chan_scale,
+                                 const float* weight, const uint8_t* flag, int64_t nrow,
+                                 float* weight_out, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    const rick_config& c = plan->cfg;
+    RK_ARG(nrow >= 0, "nrow must be >= 0");
+    const int64_t nvis = nrow * (int64_t)c.n_channels;
+    if (nvis == 0) return RICK_OK;
+    RK_ARG(uvw && chan_scale && weight && weight_out, "uvw, chan_scale, weight and weight_out are required");
+    cudaStream_t st = as_stream(stream);
+    plan->last_stream = st;
+    if (c.weighting == RICK_WEIGHT_NATURAL) {
+        RK_CUDA(cudaMemcpyAsync(weight_out, weight, sizeof(float) * (size_t)nvis, cudaMemcpyDeviceToDevice, st));
+        return RICK_OK;
+    }
+    int launches = 0;
+    rick_status s = check_launch(
+        launch_imaging_weights(place_params(plan, false), uvw, chan_scale, weight, flag, nvis,
+                               c.weighting, c.robust, plan->d_density, plan->d_wmom, weight_out,
+                               plan->num_sms, st, &launches),
+        "imaging weight kernels");
+    plan->launches += launches;
+    return s;
 }
 
 rick_status rick_fft_wplanes(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {

@@ -16,6 +16,8 @@
 //              of the weights per channel.
 //   k_scan_*   exclusive scan of the histogram -> bin offsets.
 //   k_scatter  record -> offsets[key] + rank.
+#include <cmath>
+
 #include "rick_internal.cuh"
 
 namespace rick {
@@ -465,7 +467,165 @@ k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
     }
 }
 
+// ---- imaging weights (uniform / Briggs) ------------------------------------
+//
+// The density of a channel is the sum of the weights of its gridded
+// visibilities on their nearest mesh cell (floor(x + 1/2), floor(y + 1/2)),
+// each added there and at the cell of its Hermitian partner ((N - i) mod N,
+// (N - j) mod N).  Uniform: W' = W / D(cell); Briggs: W' = W / (1 + f^2 D),
+// f^2 = (5 10^-R)^2 sum D / sum D^2.  Same skip and drop decisions as the
+// placement; the cell is taken in the placement's precision.
+
+// True if visibility idx is gridded; its cell and the mirrored cell (flat
+// indices into the channel's N x N density) and its weight.
+template <int PREC>
+__device__ __forceinline__ bool weight_cell(const PlaceParams& P, const double* __restrict__ uvw,
+                                            const double* __restrict__ chan_scale,
+                                            const float* __restrict__ weight,
+                                            const uint8_t* __restrict__ flag, int64_t idx, int& cell,
+                                            int& mcell, float& W) {
+    if (flag != nullptr && flag[idx] != 0) return false;
+    W = weight[idx];
+    if (!(W != 0.0f) || !isfinite(W)) return false;
+    const int64_t r = idx / P.C;
+    const int c = (int)(idx - r * P.C);
+    const double sc = chan_scale[c];
+    const double u0 = uvw[3 * r], v0 = uvw[3 * r + 1], w0 = uvw[3 * r + 2];
+    const Base b = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc) : place_fp64(P, u0, v0, w0, sc);
+    if (b.status != 1) return false;
+    int i, j;
+    if (PREC == RICK_PREC_ALL_FP32) {
+        const float s = (float)sc;
+        const float x = (float)u0 * s * P.fov_f + P.half_n_f, y = (float)v0 * s * P.fov_f + P.half_n_f;
+        i = (int)floorf(x + 0.5f);
+        j = (int)floorf(y + 0.5f);
+    } else {
+        const double x = __dadd_rn(__dmul_rn(__dmul_rn(u0, sc), P.fov), P.half_n);
+        const double y = __dadd_rn(__dmul_rn(__dmul_rn(v0, sc), P.fov), P.half_n);
+        i = (int)floor(__dadd_rn(x, 0.5));
+        j = (int)floor(__dadd_rn(y, 0.5));
+    }
+    // inside [0, N) because the whole footprint is; clamped against rounding
+    i = min(max(i, 0), P.N - 1);
+    j = min(max(j, 0), P.N - 1);
+    cell = j * P.N + i;
+    mcell = ((P.N - j) % P.N) * P.N + (P.N - i) % P.N;
+    return true;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256)
+k_density(PlaceParams P, const double* __restrict__ uvw, const double* __restrict__ chan_scale,
+          const float* __restrict__ weight, const uint8_t* __restrict__ flag, int64_t nvis,
+          double* __restrict__ D) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nvis; idx += stride) {
+        int cell, mcell;
+        float W;
+        if (!weight_cell<PREC>(P, uvw, chan_scale, weight, flag, idx, cell, mcell, W)) continue;
+        double* Dc = D + (size_t)(idx % P.C) * P.N * P.N;
+        atomicAdd(Dc + cell, (double)W);
+        atomicAdd(Dc + mcell, (double)W);
+    }
+}
+
+// mom[2c] += sum D, mom[2c+1] += sum D^2 over channel c = blockIdx.y
+__global__ void __launch_bounds__(256)
+k_density_moments(const double* __restrict__ D, int64_t cells, double* __restrict__ mom) {
+    __shared__ double s1[8], s2[8];
+    const double* Dc = D + (size_t)blockIdx.y * cells;
+    double a = 0.0, b = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cells;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double d = Dc[e];
+        a += d;
+        b += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s1[warp] = a;
+        s2[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += s1[w];
+            b += s2[w];
+        }
+        atomicAdd(mom + 2 * blockIdx.y, a);
+        atomicAdd(mom + 2 * blockIdx.y + 1, b);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(256)
+k_reweight(PlaceParams P, const double* __restrict__ uvw, const double* __restrict__ chan_scale,
+           const float* __restrict__ weight, const uint8_t* __restrict__ flag, int64_t nvis,
+           const double* __restrict__ D, const double* __restrict__ mom, int mode, double a2,
+           float* __restrict__ out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nvis; idx += stride) {
+        int cell, mcell;
+        float W;
+        if (!weight_cell<PREC>(P, uvw, chan_scale, weight, flag, idx, cell, mcell, W)) {
+            out[idx] = weight[idx];
+            continue;
+        }
+        const int c = (int)(idx % P.C);
+        const double d = D[(size_t)c * P.N * P.N + cell];
+        if (mode == RICK_WEIGHT_UNIFORM) {
+            out[idx] = (float)((double)W / d);
+        } else {
+            const double s1 = mom[2 * c], s2 = mom[2 * c + 1];
+            const double f2 = s2 > 0.0 ? a2 * s1 / s2 : 0.0;
+            out[idx] = (float)((double)W / (1.0 + f2 * d));
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_imaging_weights(const PlaceParams& P, const double* uvw, const double* chan_scale,
+                                   const float* weight, const uint8_t* flag, int64_t nvis, int mode,
+                                   double robust, double* density, double* moments, float* out,
+                                   int num_sms, cudaStream_t stream, int* launches) {
+    if (nvis <= 0) return cudaSuccess;
+    const size_t cells = (size_t)P.N * P.N;
+    cudaError_t e = cudaMemsetAsync(density, 0, sizeof(double) * cells * P.C, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(moments, 0, sizeof(double) * 2 * P.C, stream);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (nvis + 255) / 256;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    const bool f32 = P.precision == RICK_PREC_ALL_FP32;
+    if (f32)
+        k_density<RICK_PREC_ALL_FP32><<<(unsigned)blocks, 256, 0, stream>>>(P, uvw, chan_scale, weight, flag, nvis, density);
+    else
+        k_density<RICK_PREC_FP32_FP64IDX><<<(unsigned)blocks, 256, 0, stream>>>(P, uvw, chan_scale, weight, flag, nvis, density);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    double a2 = 0.0;
+    if (mode == RICK_WEIGHT_BRIGGS) {
+        int64_t mb = ((int64_t)cells + 255) / 256;
+        if (mb > num_sms * 4) mb = num_sms * 4;
+        k_density_moments<<<dim3((unsigned)mb, (unsigned)P.C), 256, 0, stream>>>(density, (int64_t)cells, moments);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+        const double a = 5.0 * std::pow(10.0, -robust);
+        a2 = a * a;
+    }
+    if (f32)
+        k_reweight<RICK_PREC_ALL_FP32><<<(unsigned)blocks, 256, 0, stream>>>(P, uvw, chan_scale, weight, flag, nvis, density, moments, mode, a2, out);
+    else
+        k_reweight<RICK_PREC_FP32_FP64IDX><<<(unsigned)blocks, 256, 0, stream>>>(P, uvw, chan_scale, weight, flag, nvis, density, moments, mode, a2, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    return cudaSuccess;
+}
 
 cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* chan_scale,
                          const float2* vis, const float* weight, const uint8_t* flag,

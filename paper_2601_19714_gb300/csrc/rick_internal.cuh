@@ -153,6 +153,13 @@ cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* 
                          VisRecord* stage, double* weight_sum, unsigned long long* counts,
                          int num_sms, cudaStream_t stream, int* launches);
 
+// Imaging weights W' (uniform / Briggs) of every visibility into out[nvis];
+// density [C][N][N] and moments [2C] are scratch (zeroed here).
+cudaError_t launch_imaging_weights(const PlaceParams& P, const double* uvw, const double* chan_scale,
+                                   const float* weight, const uint8_t* flag, int64_t nvis, int mode,
+                                   double robust, double* density, double* moments, float* out,
+                                   int num_sms, cudaStream_t stream, int* launches);
+
 cudaError_t launch_scan(const uint32_t* in, uint32_t* out, uint32_t* partials, uint64_t n,
                         cudaStream_t stream, int* launches);
 

@@ -426,10 +426,12 @@ rick_status rick_learn_create(const rick_config* cfg, int32_t lattice, const dou
     if (c.kernel_kind != RICK_KERNEL_TABLE || c.support != kLearnS || c.n_channels != 1 ||
         c.N < 64 || (c.N & (c.N - 1)) || c.n_wplanes < 1 || !(c.fov_rad > 0 && c.fov_rad < 1) ||
         (c.n_wplanes > 1 && !(c.w_max > c.w_min)) || lattice < 1 || lattice > 64 || nvis < 1 ||
-        nvis > (1ll << 30) || c.hermitian_fold != 0 || c.w_support >= 2)
+        nvis > (1ll << 30) || c.hermitian_fold != 0 || c.w_support >= 2 ||
+        c.weighting != RICK_WEIGHT_NATURAL)
         return lfail(RICK_ERR_INVALID_ARG,
                      "invalid argument: learning needs a table kernel of support 4, one channel, "
-                     "no Hermitian fold, no w-kernel, 1 <= lattice <= 64 and 1 <= nvis <= 2^30");
+                     "no Hermitian fold, no w-kernel, natural weighting, 1 <= lattice <= 64 and "
+                     "1 <= nvis <= 2^30");
     rick_learn* Lr = new rick_learn();
     Lr->cfg = c;
     Lr->L = lattice;

@@ -94,6 +94,9 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: only Gaussian and Kaiser-Bessel kernels (a table kernel needs a plan)");
+    if (c.weighting != RICK_WEIGHT_NATURAL)
+        return fail(RICK_ERR_UNSUPPORTED,
+                    "rick_grid_noalloc: uniform or Briggs weighting needs a plan (a density grid)");
     if (c.w_support >= 2)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: a w-kernel (w_support >= 2) needs a plan (Sw records per visibility)");

@@ -24,11 +24,12 @@ STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_E
 KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
 PRECISIONS = {"fp64idx": 0, "fp32": 1}
 FFT_IMPLS = {"cufft": 0, "own": 1}
+WEIGHTINGS = {"natural": 0, "uniform": 1, "briggs": 2}
 
 EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
            "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
            "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_fft_phase_correct_reduce",
-           "rick_fft_wplanes_columns", "rick_rows_phase_correct_reduce",
+           "rick_fft_wplanes_columns", "rick_rows_phase_correct_reduce", "rick_imaging_weights",
            "rick_dirty_image",
            "rick_dirty_image_host", "rick_plan_sync_status", "rick_plan_launch_count",
            "rick_plan_bins", "rick_grid_noalloc", "rick_graph_capture", "rick_graph_launch",
@@ -54,7 +55,7 @@ class rick_config(C.Structure):
                 ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
                 ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32),
                 ("w_support", C.c_int32), ("w_kernel_param", C.c_double),
-                ("fft_impl", C.c_int32)]
+                ("fft_impl", C.c_int32), ("weighting", C.c_int32), ("robust", C.c_double)]
 
 
 class rick_tune_entry(C.Structure):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "rick_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
         "rick_fft_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
         "rick_fft_wplanes_columns": [p, p, i64, p],
+        "rick_imaging_weights": [p, p, p, p, p, i64, p, p],
         "rick_rows_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
         "rick_dirty_image": [p, p, p, p, p, p, i64, p, p, p, p, p],
         "rick_dirty_image_host": [p, p, p, p, p, p, i64, p, p, p, p],
@@ -201,6 +203,8 @@ class Config:
     w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
     w_kernel_param: float = 0.0
     fft_impl: str = "cufft"     # or "own": the library's two-pass DFT (256 <= N <= 8192)
+    weighting: str = "natural"  # or "uniform", "briggs" (imaging weights)
+    robust: float = 0.0         # Briggs robustness R
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
@@ -208,7 +212,8 @@ class Config:
                            PRECISIONS[self.precision], self.tile, self.grid_threads,
                            self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes,
                            int(bool(self.hermitian_fold)), int(self.w_support),
-                           float(self.w_kernel_param), FFT_IMPLS[self.fft_impl])
+                           float(self.w_kernel_param), FFT_IMPLS[self.fft_impl],
+                           WEIGHTINGS[self.weighting], float(self.robust))
 
     @property
     def planes_total(self) -> int:
@@ -335,6 +340,13 @@ class Plan:
             _ptr(image_real, d["f32"], "image_real", 4),
             _ptr(image_complex, d["c64"], "image_complex", 8), _stream(stream)),
             "rick_fft_phase_correct_reduce")
+
+    def imaging_weights(self, uvw, chan_scale, weight, flag, nrow, weight_out, stream=None):
+        d = _dt()
+        _check(load().rick_imaging_weights(
+            self.handle, _ptr(uvw, d["f64"], "uvw", 8), _ptr(chan_scale, d["f64"], "chan_scale", 8),
+            _ptr(weight, d["f32"], "weight", 4), _ptr(flag, d["u8"], "flag"), int(nrow),
+            _ptr(weight_out, d["f32"], "weight_out", 4), _stream(stream)), "rick_imaging_weights")
 
     def fft_wplanes_columns(self, grids, n_planes, stream=None):
         d = _dt()

@@ -136,3 +136,17 @@ def test_stored_planes_with_w_kernel(lib, nw, sw, fold, expect):
                       w_max=200, kernel="gauss", kernel_param=0.94, hermitian_fold=bool(fold),
                       w_support=sw, w_kernel_param=6.0)
     assert lib.rick_stored_planes(C.byref(cfg.c())) == expect == cfg.stored_planes
+
+
+@pytest.mark.parametrize("kw", [dict(weighting="briggs", robust=float("nan"))])
+def test_weighting_configs_rejected_on_host(lib, kw):
+    from paper_2601_19714_gb300 import rick
+    cfg = rick.Config(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                      w_max=200, kernel="gauss", kernel_param=0.94, **kw).c()
+    h = C.c_void_p(123)
+    assert lib.rick_plan_create(C.byref(cfg), C.byref(h)) == 1
+    assert b"robust" in lib.rick_last_error()
+    cfg.weighting = 3
+    cfg.robust = 0.0
+    assert lib.rick_plan_create(C.byref(cfg), C.byref(h)) == 1
+    assert b"weighting" in lib.rick_last_error()
