@@ -46,7 +46,7 @@ class _Cfg(C.Structure):
                 ("w_max", C.c_double), ("mlp", C.POINTER(C.c_double)),
                 ("mlp_hidden", C.c_int32), ("mlp_lattice", C.c_int32),
                 ("w_support", C.c_int32), ("w_kernel_param", C.c_double),
-                ("weighting", C.c_int32), ("robust", C.c_double)]
+                ("weighting", C.c_int32), ("robust", C.c_double), ("Ng", C.c_int32)]
 
 
 @dataclass
@@ -68,13 +68,14 @@ class Config:
     w_kernel_param: float = 0.0
     weighting: str = "natural"  # or "uniform", "briggs" (R15)
     robust: float = 0.0         # Briggs robustness R
+    Ng: int = 0                 # padded mesh side (R16); 0 = N
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Cfg:
         cfg = _Cfg(self.N, self.Nw, self.S, _KINDS[self.kernel], self.kernel_param, self.fov,
                    self.w_min, self.w_max, None, self.mlp_hidden, self.mlp_lattice,
                    self.w_support, self.w_kernel_param, _WEIGHTINGS[self.weighting],
-                   self.robust)
+                   self.robust, self.Ng)
         if self.mlp is not None:
             arr = np.ascontiguousarray(self.mlp, dtype=np.float64)
             self._keep = [arr]
@@ -102,6 +103,7 @@ def _declare(L):
     L.oracle_kernel_value.argtypes = [C.c_int, d, C.c_int, d]
     L.oracle_gauss_legendre.argtypes = [C.c_int, p, p]
     L.oracle_taper.argtypes = [C.c_int, d, C.c_int, C.c_int, p]
+    L.oracle_taper_padded.argtypes = [C.c_int, d, C.c_int, C.c_int, C.c_int, p]
     L.oracle_ifft2.restype = C.c_int
     L.oracle_ifft2.argtypes = [C.c_int, p]
     L.oracle_gelu.restype = d
@@ -182,9 +184,11 @@ def gauss_legendre(n: int):
     return x, w
 
 
-def taper(kind: str, param: float, S: int, N: int) -> np.ndarray:
+def taper(kind: str, param: float, S: int, N: int, Ng: int = 0) -> np.ndarray:
+    """C(p) = int g(s) cos(2 pi s (p - N/2)/Ng) ds for the N image pixels
+    (Ng = N without padding, R16)."""
     out = np.zeros(N)
-    lib().oracle_taper(_KINDS[kind], float(param), int(S), int(N), _ptr(out))
+    lib().oracle_taper_padded(_KINDS[kind], float(param), int(S), int(N), int(Ng or N), _ptr(out))
     return out
 
 
@@ -296,9 +300,11 @@ def channel_stats(cfg: Config, uvw, chan_scale, weight, flag=None, channel=0):
 
 
 def grid_plane(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, plane=0):
-    """Gridded plane ``plane`` of channel ``channel`` (Eq. 3), complex128 [N, N]."""
+    """Gridded plane ``plane`` of channel ``channel`` (Eq. 3), complex128
+    [Ng, Ng] (the mesh; N x N without padding)."""
     v = _Vis(uvw, chan_scale, vis, _weights(cfg, uvw, chan_scale, weight, flag), flag)
-    out = np.zeros((cfg.N, cfg.N), np.complex128)
+    ng = cfg.Ng or cfg.N
+    out = np.zeros((ng, ng), np.complex128)
     c = cfg.c()
     n = lib().oracle_grid_plane(C.byref(c), *v.args(), channel, plane, _ptr(out))
     if n < 0:

@@ -52,6 +52,15 @@
  *                     f^2 = (5 10^-R)^2 sum(D) / sum(D^2) over the cells.  The
  *                     weights W' (stored in FP32, like the data weights)
  *                     then replace W everywhere, including the sum of weights.
+ *   R16 padding:      the paper's mesh is the image size (Sec. 2); a padded
+ *                     mesh is an extension: Ng = alpha N cells (alpha a power
+ *                     of two) of size 1/(alpha fov), x = u fov alpha + Ng/2;
+ *                     the image is the central N x N of the Ng x Ng inverse
+ *                     DFT (pixel p of the image is pixel p + (Ng - N)/2 of
+ *                     the transform, still at l = (p - N/2) fov/N), divided
+ *                     by C(p) = int g(s) cos(2 pi s (p - N/2)/Ng) ds.  The
+ *                     weighting density of R15 stays on the N x N mesh of
+ *                     cell 1/fov (x = u fov + N/2), its cells taken mod N.
  *
  * Floating point: FP64 throughout, compiled without FMA contraction so that
  * the index decisions (footprint start, plane index) are the IEEE results of
@@ -96,7 +105,12 @@ typedef struct {
     double w_kernel_param;/* beta of the w-direction Kaiser-Bessel kernel */
     int32_t weighting;    /* ORACLE_NATURAL / ORACLE_UNIFORM / ORACLE_BRIGGS (R15) */
     double robust;        /* Briggs robustness R */
+    int32_t Ng;           /* padded mesh side (R16); 0 = N (no padding) */
 } oracle_cfg;
+
+/* Mesh side and the offset of the image inside the transform (R16). */
+static int grid_n(const oracle_cfg* cfg) { return cfg->Ng > 0 ? cfg->Ng : cfg->N; }
+static int pad_off(const oracle_cfg* cfg) { return (grid_n(cfg) - cfg->N) / 2; }
 
 enum { ORACLE_NATURAL = 0, ORACLE_UNIFORM = 1, ORACLE_BRIGGS = 2 };
 
@@ -159,13 +173,13 @@ void oracle_gauss_legendre(int n, double* x, double* w)
  * p = 0..N-1 (R5): the continuous Fourier transform of the kernel at the
  * pixel's l, in cell units.  Gauss-Legendre quadrature, 32 nodes on each of
  * the S unit sub-intervals of the support. */
-void oracle_taper(int kind, double param, int S, int N, double* C)
+void oracle_taper_padded(int kind, double param, int S, int N, int Ng, double* C)
 {
     enum { NG = 32 };
     double gx[NG], gw[NG];
     oracle_gauss_legendre(NG, gx, gw);
     for (int p = 0; p < N; ++p) {
-        double nu = (double)(p - N / 2) / (double)N;
+        double nu = (double)(p - N / 2) / (double)Ng;
         double acc = 0.0;
         for (int seg = 0; seg < S; ++seg) {
             double a = -0.5 * S + seg, b = a + 1.0;
@@ -178,6 +192,12 @@ void oracle_taper(int kind, double param, int S, int N, double* C)
         }
         C[p] = acc;
     }
+}
+
+/* C(p) = int g(s) cos(2 pi s (p - N/2)/N) ds: the taper of an unpadded mesh. */
+void oracle_taper(int kind, double param, int S, int N, double* C)
+{
+    oracle_taper_padded(kind, param, S, N, N, C);
 }
 
 /* ------------------------------------------------------------------ */
@@ -444,13 +464,15 @@ static placement place(const oracle_cfg* cfg, const double* uvw, const double* s
     P.u = uvw[3 * r + 0] * scale[c];
     P.v = uvw[3 * r + 1] * scale[c];
     P.w = uvw[3 * r + 2] * scale[c];
-    double half = 0.5 * cfg->N;
-    P.x = P.u * cfg->fov + half;
-    P.y = P.v * cfg->fov + half;
+    /* R1, and R16 for a padded mesh: fov * Ng/N is exact (powers of two) */
+    int Ng = grid_n(cfg);
+    double half = 0.5 * Ng, fovg = cfg->fov * (double)Ng / (double)cfg->N;
+    P.x = P.u * fovg + half;
+    P.y = P.v * fovg + half;
     if (!isfinite(P.x) || !isfinite(P.y) || !isfinite(P.w)) { P.ok = -1; return P; }
     double sx = P.x - 0.5 * cfg->S, sy = P.y - 0.5 * cfg->S;
     double flx = floor(sx), fly = floor(sy);
-    if (flx < -1.0 || fly < -1.0 || flx + cfg->S > cfg->N - 1 + 0.0 || fly + cfg->S > cfg->N - 1 + 0.0) {
+    if (flx < -1.0 || fly < -1.0 || flx + cfg->S > Ng - 1 + 0.0 || fly + cfg->S > Ng - 1 + 0.0) {
         P.ok = -1;
         return P;
     }
@@ -577,6 +599,8 @@ static int check_cfg(const oracle_cfg* cfg)
     if (w_improved(cfg) && ((cfg->w_support & 1) || cfg->Nw < 2 || !(cfg->w_kernel_param > 0.0))) return 1;
     if (cfg->weighting < ORACLE_NATURAL || cfg->weighting > ORACLE_BRIGGS) return 1;
     if (cfg->weighting == ORACLE_BRIGGS && !isfinite(cfg->robust)) return 1;
+    if (cfg->Ng != 0 && (cfg->Ng < cfg->N || (cfg->Ng & (cfg->Ng - 1)))) return 1;
+    if (cfg->Ng != 0 && cfg->kernel == ORACLE_LEARNED) return 1;
     return 0;
 }
 
@@ -602,8 +626,9 @@ int oracle_imaging_weights(const oracle_cfg* cfg, const double* uvw, const doubl
             cell[r] = -1;
             placement P = place(cfg, uvw, scale, C, weight, flag, r, c);
             if (P.ok != 1) continue;
-            /* nearest cell; inside [0, N) because the whole footprint is */
-            long i = (long)floor(P.x + 0.5), j = (long)floor(P.y + 0.5);
+            /* nearest cell of the N x N mesh of cell 1/fov (R15, R16), mod N */
+            double xi = P.u * cfg->fov + 0.5 * N, yi = P.v * cfg->fov + 0.5 * N;
+            long i = (((long)floor(xi + 0.5)) % N + N) % N, j = (((long)floor(yi + 0.5)) % N + N) % N;
             double W = (double)weight[(size_t)r * C + c];
             D[(size_t)j * N + i] += W;
             D[(size_t)((N - j) % N) * N + (N - i) % N] += W;
@@ -635,7 +660,7 @@ int oracle_imaging_weights(const oracle_cfg* cfg, const double* uvw, const doubl
 static void cfg_taper(const oracle_cfg* cfg, double* C)
 {
     int kind = cfg->kernel == ORACLE_LEARNED ? ORACLE_KAISER_BESSEL : cfg->kernel;
-    oracle_taper(kind, cfg->kernel_param, cfg->S, cfg->N, C);
+    oracle_taper_padded(kind, cfg->kernel_param, cfg->S, cfg->N, grid_n(cfg), C);
 }
 
 /* ------------------------------------------------------------------ */
@@ -644,13 +669,14 @@ static void cfg_taper(const oracle_cfg* cfg, double* C)
 
 /* Grid channel c onto plane k: G[j][i] += W V g(i - x) g(j - y) (-1)^(i+j)
  * over the footprint of every gridded visibility of that channel whose plane
- * is k.  G is N x N complex, zeroed here.  Returns the number gridded. */
+ * is k.  G is Ng x Ng complex (the mesh, R16), zeroed here.  Returns the
+ * number gridded. */
 long oracle_grid_plane(const oracle_cfg* cfg, const double* uvw, const double* scale, int C,
                        const float* vis /* [nrow][C][2] */, const float* weight,
                        const uint8_t* flag, long nrow, int c, int k, double complex* G)
 {
     if (check_cfg(cfg)) return -1;
-    int N = cfg->N, S = cfg->S;
+    int N = grid_n(cfg), S = cfg->S;
     memset(G, 0, sizeof(double complex) * (size_t)N * N);
     double* gw = (double*)malloc(sizeof(double) * S * S);
     long n = 0;
@@ -728,9 +754,9 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
                  double complex* img, double* weight_sum_out)
 {
     if (check_cfg(cfg)) return 1;
-    int N = cfg->N;
+    int N = cfg->N, Ng = grid_n(cfg), off = pad_off(cfg);
     size_t NN = (size_t)N * N;
-    double complex* G = (double complex*)malloc(sizeof(double complex) * NN);
+    double complex* G = (double complex*)malloc(sizeof(double complex) * (size_t)Ng * Ng);
     double* Ct = (double*)malloc(sizeof(double) * N);
     if (!G || !Ct) { free(G); free(Ct); return 2; }
     cfg_taper(cfg, Ct);
@@ -741,13 +767,13 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
     for (int k = 0; k < oracle_planes_total(cfg); ++k) {
         long nk = oracle_grid_plane(cfg, uvw, scale, C, vis, weight, flag, nrow, c, k, G);
         if (nk <= 0) continue;
-        oracle_ifft2(N, G);
+        oracle_ifft2(Ng, G);
         double wk = oracle_plane_w(cfg, k);
         for (int q = 0; q < N; ++q)
             for (int p = 0; p < N; ++p) {
                 double n, d;
                 pixel_n(cfg, p, q, &n, &d);
-                img[(size_t)q * N + p] += G[(size_t)q * N + p] * turn_phasor(wk * d);
+                img[(size_t)q * N + p] += G[(size_t)(q + off) * Ng + (p + off)] * turn_phasor(wk * d);
             }
     }
     for (int q = 0; q < N; ++q)
@@ -777,7 +803,7 @@ int oracle_image_at(const oracle_cfg* cfg, const double* uvw, const double* scal
                     int plane, long npix, const int32_t* pp, const int32_t* qq, double complex* out)
 {
     if (check_cfg(cfg)) return 1;
-    int N = cfg->N, S = cfg->S;
+    int N = cfg->N, S = cfg->S, Ng = grid_n(cfg), off = pad_off(cfg);
     double* Ct = (double*)malloc(sizeof(double) * N);
     double* gw = (double*)malloc(sizeof(double) * S * S);
     double complex* ex = (double complex*)malloc(sizeof(double complex) * S * 2);
@@ -801,10 +827,11 @@ int oracle_image_at(const oracle_cfg* cfg, const double* uvw, const double* scal
             for (int a = 0; a < S; ++a) {
                 long i = P.i0 + a, j = P.j0 + a;
                 double sx = (i & 1) ? -1.0 : 1.0, sy = (j & 1) ? -1.0 : 1.0;
-                /* exp(2 pi i i p / N) with the exponent reduced exactly mod N */
-                long ip = (i * (long)p) % N, jq = (j * (long)q) % N;
-                ex[a] = sx * turn_phasor((double)ip / N);
-                ey[a] = sy * turn_phasor((double)jq / N);
+                /* exp(2 pi i i P / Ng) at the transform's pixel P = p + off,
+                 * the exponent reduced exactly mod Ng */
+                long ip = (i * (long)(p + off)) % Ng, jq = (j * (long)(q + off)) % Ng;
+                ex[a] = sx * turn_phasor((double)ip / Ng);
+                ey[a] = sy * turn_phasor((double)jq / Ng);
             }
             double complex acc = 0.0;
             for (int b = 0; b < S; ++b) {
@@ -915,23 +942,25 @@ int oracle_predict(const oracle_cfg* cfg, const double* uvw, const double* scale
 {
     if (check_cfg(cfg)) return 1;
     if (cfg->kernel == ORACLE_LEARNED) return 3;
-    int N = cfg->N, S = cfg->S;
+    int Ni = cfg->N, N = grid_n(cfg), off = pad_off(cfg), S = cfg->S;
     size_t NN = (size_t)N * N;
     double complex* F = (double complex*)malloc(sizeof(double complex) * NN);
-    double* Ct = (double*)malloc(sizeof(double) * N);
+    double* Ct = (double*)malloc(sizeof(double) * Ni);
     double* gw = (double*)malloc(sizeof(double) * S * S);
     if (!F || !Ct || !gw) { free(F); free(Ct); free(gw); return 2; }
     cfg_taper(cfg, Ct);
     for (long r = 0; r < nrow; ++r) out[r] = 0.0;
     for (int k = 0; k < oracle_planes_total(cfg); ++k) {
         double wk = oracle_plane_w(cfg, k);
-        for (int q = 0; q < N; ++q)
-            for (int p = 0; p < N; ++p) {
+        /* the model inside the central Ni x Ni of the mesh-sized plane (R16) */
+        memset(F, 0, sizeof(double complex) * NN);
+        for (int q = 0; q < Ni; ++q)
+            for (int p = 0; p < Ni; ++p) {
                 double n, d;
                 pixel_n(cfg, p, q, &n, &d);
                 double sgn = ((p + q) & 1) ? -1.0 : 1.0;
-                F[(size_t)q * N + p] = sgn * J[(size_t)q * N + p] * turn_phasor(-wk * d) /
-                                       (n * Ct[p] * Ct[q] * w_taper(cfg, d));
+                F[(size_t)(q + off) * N + (p + off)] = sgn * J[(size_t)q * Ni + p] * turn_phasor(-wk * d) /
+                                                       (n * Ct[p] * Ct[q] * w_taper(cfg, d));
             }
         fft2_forward(N, F);
         for (long r = 0; r < nrow; ++r) {
@@ -970,8 +999,8 @@ int oracle_predict_at(const oracle_cfg* cfg, const double* uvw, const double* sc
 {
     if (check_cfg(cfg)) return 1;
     if (cfg->kernel == ORACLE_LEARNED) return 3;
-    int N = cfg->N, S = cfg->S;
-    double* Ct = (double*)malloc(sizeof(double) * N);
+    int Ni = cfg->N, N = grid_n(cfg), S = cfg->S;
+    double* Ct = (double*)malloc(sizeof(double) * Ni);
     double* gw = (double*)malloc(sizeof(double) * S * S);
     if (!Ct || !gw) { free(Ct); free(gw); return 2; }
     cfg_taper(cfg, Ct);
@@ -991,7 +1020,8 @@ int oracle_predict_at(const oracle_cfg* cfg, const double* uvw, const double* sc
             for (int t2 = 0; t2 < kn; ++t2)
                 ph += plane_weight(cfg, &P, P.k + t2) * turn_phasor(-oracle_plane_w(cfg, P.k + t2) * d);
             double complex Ms = flux[s] * ph / (n * Ct[sp[s]] * Ct[sq[s]] * w_taper(cfg, d));
-            long ps = sp[s] - N / 2, qs = sq[s] - N / 2;
+            /* the transform's pixel P = p + off sits at P - Ng/2 = p - Ni/2 (R16) */
+            long ps = sp[s] - Ni / 2, qs = sq[s] - Ni / 2;
             for (int b = 0; b < S; ++b) {
                 long j = P.j0 + b - N / 2;
                 long jq = ((j * qs) % N + N) % N;
