@@ -152,6 +152,16 @@ typedef struct rick_config {
     int32_t fft_impl;
     int32_t weighting;    /* rick_weighting (0 = natural); imaging only, prediction ignores it */
     double robust;        /* Briggs robustness R (weighting = RICK_WEIGHT_BRIGGS) */
+    /* Padded mesh (0 = N, the paper's mesh = image size).  A power of two
+     * Ng = alpha N >= N: the visibilities are gridded on Ng x Ng cells of
+     * 1/(alpha fov) (x = u fov alpha + Ng/2), every plane, plane range and
+     * grid array of the API is Ng x Ng, and the image is the central N x N of
+     * the transformed planes, divided by C(p) = int g(s) cos(2 pi s (p - N/2)/Ng)
+     * ds (rick_plan_taper returns it).  Less aliasing at the field edge for
+     * alpha^2 times the grid memory and FFT work.  Needs fft_impl 0 and a
+     * Gaussian or Kaiser-Bessel kernel; not in rick_grid_noalloc.  The weighting
+     * density stays on the N x N mesh of cell 1/fov. */
+    int32_t grid_size;
 } rick_config;
 
 /* Planes a plan stores for cfg: P = Nw, or Nw + Sw with a w-kernel; ceil(P / 2)

@@ -97,10 +97,11 @@ void legendre_rule(int n, std::vector<double>& x, std::vector<double>& w) {
     }
 }
 
-// C(p) = int_{-S/2}^{S/2} g(s) cos(2 pi s (p - N/2)/N) ds: the continuous
-// Fourier transform of the kernel at pixel p, by composite Gauss-Legendre
-// quadrature (24 nodes per cell of the support).  C is even about N/2.
-void make_taper(int kind, double param, int S, int N, std::vector<double>& C) {
+// C(p) = int_{-S/2}^{S/2} g(s) cos(2 pi s (p - N/2)/Ng) ds: the continuous
+// Fourier transform of the kernel at image pixel p of a mesh of Ng cells
+// (Ng = N without padding), by composite Gauss-Legendre quadrature (24 nodes
+// per cell of the support).  C is even about N/2.
+void make_taper(int kind, double param, int S, int N, int Ng, std::vector<double>& C) {
     std::vector<double> gx, gw;
     legendre_rule(24, gx, gw);
     std::vector<double> s, wg;
@@ -116,7 +117,7 @@ void make_taper(int kind, double param, int S, int N, std::vector<double>& C) {
     std::vector<double> val(N / 2 + 1);
     for (int d = 0; d <= N / 2; ++d) {
         double acc = 0.0;
-        for (size_t i = 0; i < s.size(); ++i) acc += wg[i] * std::cos(two_pi * s[i] * d / N);
+        for (size_t i = 0; i < s.size(); ++i) acc += wg[i] * std::cos(two_pi * s[i] * d / Ng);
         val[d] = acc;
     }
     C.assign(N, 0.0);
@@ -129,6 +130,7 @@ struct rick_plan {
     rick_config cfg;
     int device = 0, num_sms = 0;
     int T = 64, NT = 0, threads = 256, grab = 8;
+    int Ng = 0;      // mesh side (grid_size, or N without padding)
     int planes = 0;  // stored planes: ceil(Nt/2) with the Hermitian fold, else Nt
                      // (Nt = Nw, or Nw + Sw with a w-kernel)
     int nrec_per_vis = 1;  // records per visibility: Sw with a w-kernel, else 1
@@ -232,6 +234,14 @@ rick_status validate(const rick_config* c) {
     const int T = c->tile ? c->tile : 32;
     RK_ARG(T == 16 || T == 32 || T == 64, "tile must be 16, 32 or 64");
     RK_ARG(T <= c->N, "tile must not exceed N");
+    const int Ng = c->grid_size ? c->grid_size : c->N;
+    RK_ARG(c->grid_size == 0 || (c->grid_size >= c->N && c->grid_size <= 65536 &&
+                                 (c->grid_size & (c->grid_size - 1)) == 0),
+           "grid_size must be 0 or a power of two in [N, 65536]");
+    if (Ng != c->N) {
+        RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE, "a padded grid needs a Gaussian or Kaiser-Bessel kernel");
+        RK_ARG(c->fft_impl == 0, "a padded grid needs fft_impl 0 (cuFFT)");
+    }
     RK_ARG(c->n_wplanes >= 1, "n_wplanes must be >= 1");
     RK_ARG(c->n_channels >= 1, "n_channels must be >= 1");
     RK_ARG(c->support >= 1 && c->support <= 16 && c->support <= T, "support must be in [1, min(16, tile)]");
@@ -284,7 +294,7 @@ rick_status validate(const rick_config* c) {
                "hermitian_fold needs a point-symmetric kernel (Gaussian or Kaiser-Bessel)");
         RK_ARG(c->w_min == -c->w_max, "hermitian_fold needs w_min == -w_max");
     }
-    const uint64_t NT = (uint64_t)(c->N / T);
+    const uint64_t NT = (uint64_t)(Ng / T);
     const uint64_t nkeys = (uint64_t)c->n_channels * stored_planes(*c) * NT * NT * 4ull;
     if (nkeys >= 0xFFFFFFFFull) {
         set_err("channels x planes x tiles exceeds the 32-bit bin space; use a larger tile or "
@@ -351,7 +361,9 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     c.grid_threads = P->threads;
     P->grab = c.tiles_per_grab ? c.tiles_per_grab : 4;
     c.tiles_per_grab = P->grab;
-    P->NT = c.N / P->T;
+    P->Ng = c.grid_size ? c.grid_size : c.N;
+    c.grid_size = P->Ng;
+    P->NT = P->Ng / P->T;
     P->planes = stored_planes(c);
     P->nkeys = (uint64_t)c.n_channels * P->planes * (uint64_t)P->NT * P->NT * 4ull;
     if (c.n_wplanes > 1) {
@@ -397,7 +409,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         P->nrec_per_vis = c.w_support;
     }
     const int taper_kind = c.kernel_kind == RICK_KERNEL_TABLE ? RICK_KERNEL_KAISER_BESSEL : c.kernel_kind;
-    make_taper(taper_kind, c.kernel_param, c.support, c.N, P->taper);
+    make_taper(taper_kind, c.kernel_param, c.support, c.N, P->Ng, P->taper);
     std::vector<float> inv(c.N);
     for (int p = 0; p < c.N; ++p) inv[p] = (float)(1.0 / P->taper[p]);
     RK_CUDA(cudaMalloc(&P->d_inv_taper, sizeof(float) * c.N));
@@ -416,7 +428,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(cudaMalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
     }
 
-    P->own_fft = c.fft_impl == 1 && fft_supported(c.N);
+    P->own_fft = c.fft_impl == 1 && fft_supported(c.N) && P->Ng == c.N;
     if (P->own_fft) {
         std::vector<float2> tw;
         fft_twiddles(c.N, tw);
@@ -424,7 +436,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
         return RICK_OK;   // no cuFFT plans
     }
-    const size_t plane_bytes = (size_t)c.N * c.N * sizeof(float2);
+    const size_t plane_bytes = (size_t)P->Ng * P->Ng * sizeof(float2);
     int B = c.fft_batch;
     if (B <= 0) {
         const size_t cap = (size_t)4 << 30;
@@ -435,8 +447,8 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     }
     P->fft_B = B;
     c.fft_batch = B;
-    RK_TRY(make_fft_plan(&P->fft_1, &P->have_1, c.N, 1));
-    if (B > 1) RK_TRY(make_fft_plan(&P->fft_b, &P->have_b, c.N, B));
+    RK_TRY(make_fft_plan(&P->fft_1, &P->have_1, P->Ng, 1));
+    if (B > 1) RK_TRY(make_fft_plan(&P->fft_b, &P->have_b, P->Ng, B));
     return RICK_OK;
 }
 
@@ -454,7 +466,7 @@ rick_status check_launch(cudaError_t e, const char* what) {
 PlaceParams place_params(const rick_plan* P, bool predict) {
     const rick_config& c = P->cfg;
     PlaceParams pp;
-    pp.N = c.N;
+    pp.N = P->Ng;
     pp.S = c.support;
     pp.Nw = c.n_wplanes;
     pp.C = c.n_channels;
@@ -467,12 +479,19 @@ PlaceParams place_params(const rick_plan* P, bool predict) {
     pp.w_support = c.w_support >= 2 ? c.w_support : 0;
     pp.Nw_total = planes_total(c);
     std::memcpy(pp.wcoef, P->w_coef, sizeof pp.wcoef);
-    pp.fov = c.fov_rad;
-    pp.half_n = 0.5 * c.N;
+    // x = u fov Ng/N + Ng/2 (exact scaling: powers of two); the weighting
+    // density's mesh is the N x N mesh of cell 1/fov
+    pp.fov = c.fov_rad * (double)P->Ng / (double)c.N;
+    pp.half_n = 0.5 * P->Ng;
+    pp.Ni = c.N;
+    pp.fov_i = c.fov_rad;
+    pp.half_i = 0.5 * c.N;
+    pp.fov_i_f = (float)c.fov_rad;
+    pp.half_i_f = (float)(0.5 * c.N);
     pp.half_s = 0.5 * c.support;
     pp.w_min = c.w_min;
     pp.w_scale = P->w_scale;
-    pp.fov_f = (float)c.fov_rad;
+    pp.fov_f = (float)pp.fov;
     pp.half_n_f = (float)pp.half_n;
     pp.half_s_f = (float)pp.half_s;
     pp.w_min_f = (float)c.w_min;
@@ -550,7 +569,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     const uint64_t items = (uint64_t)(c1 - c0) * (k1 - k0) * (uint64_t)P->NT * P->NT;
     RK_ARG(items < 0xFFFFFFFFull, "too many tiles in one call");
     GridParams G;
-    G.N = c.N;
+    G.N = P->Ng;
     G.S = c.support;
     G.T = P->T;
     G.NT = P->NT;
@@ -583,12 +602,12 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
                      int direction = CUFFT_INVERSE) {
     RK_ARG(n_planes >= 0, "n_planes must be >= 0");
     RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
-    const size_t NN = (size_t)P->cfg.N * P->cfg.N;
+    const size_t NN = (size_t)P->Ng * P->Ng;
     P->last_stream = st;
     if (P->own_fft) {
         RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
         int launches = 0;
-        rick_status s = check_launch(launch_fft2d(reinterpret_cast<float2*>(grids), n_planes, P->cfg.N,
+        rick_status s = check_launch(launch_fft2d(reinterpret_cast<float2*>(grids), n_planes, P->Ng,
                                                   direction == CUFFT_INVERSE, P->d_twid, st, &launches),
                                      "FFT kernels");
         P->launches += launches;
@@ -633,7 +652,9 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
 PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
     const rick_config& c = P->cfg;
     PhaseParams pp;
-    pp.N = c.N;
+    pp.N = P->Ng;
+    pp.Ni = c.N;
+    pp.off = (P->Ng - c.N) / 2;
     pp.nc = c1 - c0;
     pp.nk = k1 - k0;
     pp.dl = c.fov_rad / c.N;
@@ -682,7 +703,7 @@ rick_status columns_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStrea
     RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
     P->last_stream = st;
     int launches = 0;
-    rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids), n_planes, P->cfg.N,
+    rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids), n_planes, P->Ng,
                                                     true, P->d_twid, st, &launches),
                                  "FFT column kernel");
     P->launches += launches;
@@ -766,7 +787,7 @@ rick_status degrid_impl(rick_plan* P, const float* grids, int c0, int c1, int k0
     RK_ARG(items < 0xFFFFFFFFull, "too many tiles in one call");
     GridParams G;
     std::memset(&G, 0, sizeof G);
-    G.N = c.N;
+    G.N = P->Ng;
     G.S = c.support;
     G.T = P->T;
     G.NT = P->NT;
@@ -794,7 +815,7 @@ rick_status degrid_impl(rick_plan* P, const float* grids, int c0, int c1, int k0
 // the budget, else whole channels, else planes of one channel.
 void plan_groups(const rick_plan* P, int* gc, int* gk) {
     const rick_config& c = P->cfg;
-    const size_t plane = (size_t)c.N * c.N * sizeof(float2);
+    const size_t plane = (size_t)P->Ng * P->Ng * sizeof(float2);
     const size_t budget = c.grid_budget_bytes > 0 ? (size_t)c.grid_budget_bytes : (size_t)-1;
     const size_t per_chan = plane * P->planes;
     if (budget / per_chan >= (size_t)c.n_channels) {
@@ -814,7 +835,7 @@ rick_status ensure_group_grid(rick_plan* P) {
     const rick_config& c = P->cfg;
     int gc, gk;
     plan_groups(P, &gc, &gk);
-    const size_t need = (size_t)gc * gk * (size_t)c.N * c.N * sizeof(float2);
+    const size_t need = (size_t)gc * gk * (size_t)P->Ng * P->Ng * sizeof(float2);
     if (need > P->grid_cap) {
         dfree(P->d_grid);
         P->grid_cap = 0;

@@ -493,23 +493,25 @@ __device__ __forceinline__ bool weight_cell(const PlaceParams& P, const double* 
     const double u0 = uvw[3 * r], v0 = uvw[3 * r + 1], w0 = uvw[3 * r + 2];
     const Base b = PREC == RICK_PREC_ALL_FP32 ? place_fp32(P, u0, v0, w0, sc) : place_fp64(P, u0, v0, w0, sc);
     if (b.status != 1) return false;
+    // nearest cell of the Ni x Ni mesh of cell 1/fov (the image mesh, also
+    // with a padded grid), taken mod Ni
     int i, j;
     if (PREC == RICK_PREC_ALL_FP32) {
         const float s = (float)sc;
-        const float x = (float)u0 * s * P.fov_f + P.half_n_f, y = (float)v0 * s * P.fov_f + P.half_n_f;
+        const float x = (float)u0 * s * P.fov_i_f + P.half_i_f, y = (float)v0 * s * P.fov_i_f + P.half_i_f;
         i = (int)floorf(x + 0.5f);
         j = (int)floorf(y + 0.5f);
     } else {
-        const double x = __dadd_rn(__dmul_rn(__dmul_rn(u0, sc), P.fov), P.half_n);
-        const double y = __dadd_rn(__dmul_rn(__dmul_rn(v0, sc), P.fov), P.half_n);
+        const double x = __dadd_rn(__dmul_rn(__dmul_rn(u0, sc), P.fov_i), P.half_i);
+        const double y = __dadd_rn(__dmul_rn(__dmul_rn(v0, sc), P.fov_i), P.half_i);
         i = (int)floor(__dadd_rn(x, 0.5));
         j = (int)floor(__dadd_rn(y, 0.5));
     }
-    // inside [0, N) because the whole footprint is; clamped against rounding
-    i = min(max(i, 0), P.N - 1);
-    j = min(max(j, 0), P.N - 1);
-    cell = j * P.N + i;
-    mcell = ((P.N - j) % P.N) * P.N + (P.N - i) % P.N;
+    const int Ni = P.Ni;
+    i = ((i % Ni) + Ni) % Ni;
+    j = ((j % Ni) + Ni) % Ni;
+    cell = j * Ni + i;
+    mcell = ((Ni - j) % Ni) * Ni + (Ni - i) % Ni;
     return true;
 }
 
@@ -523,7 +525,7 @@ k_density(PlaceParams P, const double* __restrict__ uvw, const double* __restric
         int cell, mcell;
         float W;
         if (!weight_cell<PREC>(P, uvw, chan_scale, weight, flag, idx, cell, mcell, W)) continue;
-        double* Dc = D + (size_t)(idx % P.C) * P.N * P.N;
+        double* Dc = D + (size_t)(idx % P.C) * P.Ni * P.Ni;
         atomicAdd(Dc + cell, (double)W);
         atomicAdd(Dc + mcell, (double)W);
     }
@@ -577,7 +579,7 @@ k_reweight(PlaceParams P, const double* __restrict__ uvw, const double* __restri
             continue;
         }
         const int c = (int)(idx % P.C);
-        const double d = D[(size_t)c * P.N * P.N + cell];
+        const double d = D[(size_t)c * P.Ni * P.Ni + cell];
         if (mode == RICK_WEIGHT_UNIFORM) {
             out[idx] = (float)((double)W / d);
         } else {
@@ -595,7 +597,7 @@ cudaError_t launch_imaging_weights(const PlaceParams& P, const double* uvw, cons
                                    double robust, double* density, double* moments, float* out,
                                    int num_sms, cudaStream_t stream, int* launches) {
     if (nvis <= 0) return cudaSuccess;
-    const size_t cells = (size_t)P.N * P.N;
+    const size_t cells = (size_t)P.Ni * P.Ni;
     cudaError_t e = cudaMemsetAsync(density, 0, sizeof(double) * cells * P.C, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(moments, 0, sizeof(double) * 2 * P.C, stream);
     if (e != cudaSuccess) return e;

@@ -72,6 +72,11 @@ struct PlaceParams {
     float wcoef[kMaxWSupport][kPolyDegree + 1];
     double fov, half_n, half_s, w_min, w_scale;  // w_scale = Nw/(w_max - w_min), 0 if Nw == 1
     float fov_f, half_n_f, half_s_f, w_min_f, w_scale_f;
+    // The mesh above has N = Ng cells of 1/(fov Ng/Ni) (fov is scaled); the
+    // imaging-weight density uses the Ni x Ni mesh of cell 1/fov_i.
+    int Ni;
+    double fov_i, half_i;
+    float fov_i_f, half_i_f;
 };
 
 struct GridParams {
@@ -106,8 +111,9 @@ inline uint32_t schedule_list_cap(int64_t max_vis, int T) {
 double fit_tap_polynomials(int kind, double param, int S, GridParams& G);
 
 struct PhaseParams {
-    int N, nc, nk;
-    double dl;            // fov / N
+    int N, nc, nk;        // N: mesh side of the planes (Ng)
+    int Ni, off;          // image side and its offset in the planes (padding: (Ng - Ni)/2)
+    double dl;            // fov / Ni
     double w_first;       // w of plane plane_begin (plane centre)
     double dw;            // plane spacing (0 if Nw == 1)
     int precision;

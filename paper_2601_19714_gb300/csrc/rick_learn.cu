@@ -427,7 +427,7 @@ rick_status rick_learn_create(const rick_config* cfg, int32_t lattice, const dou
         c.N < 64 || (c.N & (c.N - 1)) || c.n_wplanes < 1 || !(c.fov_rad > 0 && c.fov_rad < 1) ||
         (c.n_wplanes > 1 && !(c.w_max > c.w_min)) || lattice < 1 || lattice > 64 || nvis < 1 ||
         nvis > (1ll << 30) || c.hermitian_fold != 0 || c.w_support >= 2 ||
-        c.weighting != RICK_WEIGHT_NATURAL)
+        c.weighting != RICK_WEIGHT_NATURAL || (c.grid_size != 0 && c.grid_size != c.N))
         return lfail(RICK_ERR_INVALID_ARG,
                      "invalid argument: learning needs a table kernel of support 4, one channel, "
                      "no Hermitian fold, no w-kernel, natural weighting, 1 <= lattice <= 64 and "

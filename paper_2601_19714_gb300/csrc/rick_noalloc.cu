@@ -94,6 +94,8 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: only Gaussian and Kaiser-Bessel kernels (a table kernel needs a plan)");
+    if (c.grid_size != 0 && c.grid_size != c.N)
+        return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: a padded grid (grid_size != N) needs a plan");
     if (c.weighting != RICK_WEIGHT_NATURAL)
         return fail(RICK_ERR_UNSUPPORTED,
                     "rick_grid_noalloc: uniform or Briggs weighting needs a plan (a density grid)");
@@ -167,6 +169,11 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     pp.predict = 0;
     pp.w_support = 0;
     pp.Nw_total = c.n_wplanes;
+    pp.Ni = c.N;
+    pp.fov_i = c.fov_rad;
+    pp.half_i = 0.5 * c.N;
+    pp.fov_i_f = (float)c.fov_rad;
+    pp.half_i_f = (float)(0.5 * c.N);
     pp.fov = c.fov_rad;
     pp.half_n = 0.5 * c.N;
     pp.half_s = 0.5 * c.support;

@@ -3,6 +3,9 @@
 //   image[c][q][p] += (-1)^(p+q) n / (sum W_c C(p) C(q))
 //                     * Re sum_k F_k[q][p] exp(+2 pi i w_k (n - 1))
 //
+// With a padded mesh (grid_size Ng > N) the planes are Ng x Ng and the image
+// is their central N x N (offset (Ng - N)/2); only that part is read.
+//
 // HBM-bound: every transformed plane is read once (8 B per pixel per plane).
 // One thread owns two adjacent pixels (one 16-byte load per plane) for all
 // channels and planes of the launch.
@@ -50,12 +53,13 @@ __global__ void __launch_bounds__(kPhaseThreads)
 k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                const float* __restrict__ inv_taper, float* __restrict__ image_real,
                float2* __restrict__ image_complex) {
-    const int N = P.N, halfN = N / 2;
+    // (p, q): image pixel; the planes are Ng x Ng with the image at offset off
+    const int N = P.N, Ni = P.Ni, halfN = Ni / 2;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (int64_t)N * halfN) return;
+    if (tid >= (int64_t)Ni * halfN) return;
     const int q = (int)(tid / halfN);
     const int p = (int)(tid - (int64_t)q * halfN) * 2;
-    const size_t NN = (size_t)N * N;
+    const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
 
     uint64_t t0[2], dt[2];
     float t0f[2], dtf[2];
@@ -84,7 +88,7 @@ k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __
         const double ws = wsum[cc];
         const float inv_ws = ws != 0.0 ? (float)(1.0 / ws) : 0.0f;
         const float4* g = reinterpret_cast<const float4*>(grids + (size_t)cc * P.nk * NN +
-                                                          (size_t)q * N + p);
+                                                          (size_t)(q + P.off) * N + p + P.off);
         float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
         if (PREC == RICK_PREC_ALL_FP32) {
             for (int k = 0; k < P.nk; ++k) {
@@ -122,13 +126,13 @@ k_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __
             }
         }
         const float s0 = scale[0] * inv_ws, s1 = scale[1] * inv_ws;
-        float2* ir = reinterpret_cast<float2*>(image_real + (size_t)cc * NN + (size_t)q * N + p);
+        float2* ir = reinterpret_cast<float2*>(image_real + (size_t)cc * NNi + (size_t)q * Ni + p);
         float2 cur = *ir;
         cur.x += s0 * acc0.x;
         cur.y += s1 * acc1.x;
         *ir = cur;
         if (COMPLEX_OUT) {
-            float4* ic = reinterpret_cast<float4*>(image_complex + (size_t)cc * NN + (size_t)q * N + p);
+            float4* ic = reinterpret_cast<float4*>(image_complex + (size_t)cc * NNi + (size_t)q * Ni + p);
             float4 v = *ic;
             v.x += s0 * acc0.x;
             v.y += s0 * acc0.y;
@@ -149,12 +153,20 @@ template <int PREC>
 __global__ void __launch_bounds__(kPhaseThreads)
 k_model_planes(PhaseParams P, const float* __restrict__ image, const float* __restrict__ inv_taper,
                float2* __restrict__ grids) {
-    const int N = P.N, halfN = N / 2;
+    // one thread per two cells of the Ng x Ng plane; (p, q) the image pixel
+    // (the cells outside the central Ni x Ni of a padded plane are zero)
+    const int N = P.N, Ni = P.Ni, halfN = Ni / 2;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (int64_t)N * halfN) return;
-    const int q = (int)(tid / halfN);
-    const int p = (int)(tid - (int64_t)q * halfN) * 2;
-    const size_t NN = (size_t)N * N;
+    if (tid >= (int64_t)N * (N / 2)) return;
+    const int qg = (int)(tid / (N / 2));
+    const int pg = (int)(tid - (int64_t)qg * (N / 2)) * 2;
+    const int q = qg - P.off, p = pg - P.off;
+    const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
+    if (q < 0 || q >= Ni || p < 0 || p >= Ni) {
+        float4* g = reinterpret_cast<float4*>(grids + (size_t)qg * N + pg);
+        for (int r = 0; r < P.nc * P.nk; ++r) __stcs(g + (size_t)r * (NN / 2), make_float4(0.f, 0.f, 0.f, 0.f));
+        return;
+    }
 
     uint64_t t0[2], dt[2];
     float t0f[2], dtf[2];
@@ -180,9 +192,9 @@ k_model_planes(PhaseParams P, const float* __restrict__ image, const float* __re
     }
 
     for (int cc = 0; cc < P.nc; ++cc) {
-        const float2 J = *reinterpret_cast<const float2*>(image + (size_t)cc * NN + (size_t)q * N + p);
+        const float2 J = *reinterpret_cast<const float2*>(image + (size_t)cc * NNi + (size_t)q * Ni + p);
         const float a0 = J.x * scale[0], a1 = J.y * scale[1];
-        float4* g = reinterpret_cast<float4*>(grids + (size_t)cc * P.nk * NN + (size_t)q * N + p);
+        float4* g = reinterpret_cast<float4*>(grids + (size_t)cc * P.nk * NN + (size_t)qg * N + pg);
         if (PREC == RICK_PREC_ALL_FP32) {
             for (int k = 0; k < P.nk; ++k) {
                 float s0, c0, s1, c1;
@@ -217,7 +229,7 @@ k_model_planes(PhaseParams P, const float* __restrict__ image, const float* __re
 
 cudaError_t launch_model_planes(const PhaseParams& P, const float* image, const float* inv_taper,
                                 float2* grids, cudaStream_t stream, int* launches) {
-    const int64_t threads = (int64_t)P.N * (P.N / 2);
+    const int64_t threads = (int64_t)P.N * (P.N / 2);   // every cell of the (padded) plane
     const int64_t blocks = (threads + kPhaseThreads - 1) / kPhaseThreads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (P.precision == RICK_PREC_ALL_FP32)
@@ -231,7 +243,7 @@ cudaError_t launch_model_planes(const PhaseParams& P, const float* image, const 
 cudaError_t launch_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                 const float* inv_taper, float* image_real, float2* image_complex,
                                 cudaStream_t stream, int* launches) {
-    const int64_t threads = (int64_t)P.N * (P.N / 2);
+    const int64_t threads = (int64_t)P.Ni * (P.Ni / 2);   // every image pixel pair
     const int64_t blocks = (threads + kPhaseThreads - 1) / kPhaseThreads;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const bool cplx = image_complex != nullptr;

@@ -55,7 +55,8 @@ class rick_config(C.Structure):
                 ("fft_batch", C.c_int32), ("tiles_per_grab", C.c_int32),
                 ("grid_budget_bytes", C.c_int64), ("hermitian_fold", C.c_int32),
                 ("w_support", C.c_int32), ("w_kernel_param", C.c_double),
-                ("fft_impl", C.c_int32), ("weighting", C.c_int32), ("robust", C.c_double)]
+                ("fft_impl", C.c_int32), ("weighting", C.c_int32), ("robust", C.c_double),
+                ("grid_size", C.c_int32)]
 
 
 class rick_tune_entry(C.Structure):
@@ -205,6 +206,7 @@ class Config:
     fft_impl: str = "cufft"     # or "own": the library's two-pass DFT (256 <= N <= 8192)
     weighting: str = "natural"  # or "uniform", "briggs" (imaging weights)
     robust: float = 0.0         # Briggs robustness R
+    grid_size: int = 0          # padded mesh side Ng (0 = N)
 
     def c(self) -> rick_config:
         return rick_config(self.N, self.n_wplanes, self.support, self.n_channels, self.fov_rad,
@@ -213,7 +215,12 @@ class Config:
                            self.fft_batch, self.tiles_per_grab, self.grid_budget_bytes,
                            int(bool(self.hermitian_fold)), int(self.w_support),
                            float(self.w_kernel_param), FFT_IMPLS[self.fft_impl],
-                           WEIGHTINGS[self.weighting], float(self.robust))
+                           WEIGHTINGS[self.weighting], float(self.robust), int(self.grid_size))
+
+    @property
+    def Ng(self) -> int:
+        """Mesh side of the planes (grid_size, or N without padding)."""
+        return self.grid_size or self.N
 
     @property
     def planes_total(self) -> int:

@@ -51,7 +51,8 @@ def run_path(plan, dev, nchan, N, Nw, complex_out=False):
     folds."""
     import torch
     Nw = plan.cfg.stored_planes if plan.cfg.n_wplanes == Nw else Nw
-    grids = torch.empty((nchan, Nw, N, N), dtype=torch.complex64, device="cuda")
+    Ng = plan.cfg.Ng if plan.cfg.N == N else N
+    grids = torch.empty((nchan, Nw, Ng, Ng), dtype=torch.complex64, device="cuda")
     wsum = torch.empty(nchan, dtype=torch.float64, device="cuda")
     counts = torch.empty(2, dtype=torch.int64, device="cuda")
     img = torch.zeros((nchan, N, N), dtype=torch.float32, device="cuda")
