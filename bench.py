@@ -927,13 +927,145 @@ def run_wkernel(args):
         "gpu_launches": rb["launches"], "clocks": rb["clocks"]}), flush=True)
 
 
+def _time_path(plan, dev, nrow, C, N, Ng, steps, warmup):
+    """Time the default step (bin, grid, FFT, phase/reduce) of a plan; returns
+    (ms per step, stage medians, gridded count, channel-0.. images on the host)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ns = plan.cfg.stored_planes
+    grids = torch.empty((C, ns, Ng, Ng), dtype=torch.complex64, device="cuda")
+    image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    wsum = torch.empty(C, dtype=torch.float64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+
+    def step(record=False):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        image.zero_()
+        if e: e[0].record(stream)
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], nrow,
+                 wsum, counts)
+        if e: e[1].record(stream)
+        plan.grid_binned(0, C, 0, ns, grids)
+        if e: e[2].record(stream)
+        plan.fft_wplanes(grids, C * ns)
+        if e: e[3].record(stream)
+        plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        if e: e[4].record(stream)
+        return e
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = []
+    a.record(stream)
+    for _ in range(steps):
+        evs.append(step(record=True))
+    b.record(stream)
+    torch.cuda.synchronize()
+    st = {k: statistics.median([e[i].elapsed_time(e[i + 1]) for e in evs])
+          for i, k in enumerate(("bin", "grid", "fft", "phase"))}
+    out = (a.elapsed_time(b) / steps, st, int(counts[0].item()), image.cpu().numpy())
+    del grids, image
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_options(args):
+    """The imaging options of the scope table's last row on the default
+    workload's observation (MeerKAT-shaped, 4096^2, 32 planes folded to 16,
+    KB S = 8), each timed as the default step:
+      weighting -- natural / uniform / Briggs R = 0 on all 16 channels (the
+        weighting passes run inside rick_bin);
+      padding -- the 4 highest channels (1498-1712 MHz) on the 4096^2 mesh and
+        on a padded 8192^2 mesh (alpha = 2), with the Kaiser-Bessel w-kernel
+        (Sw = 6, beta = 10, 32 planes) so that the w error does not mask the
+        aliasing, and the error against Eq. 1 inverted directly (the oracle's
+        O2) at the 8 brightest of the sources with a taper gain of the
+        unpadded mesh below 1e-2 (towards the field edge, where the unpadded
+        taper division amplifies aliased power most).
+    `value` = vis/s of the padded 4-channel step."""
+    import torch
+    from paper_2601_19714_gb300 import _build, rick
+    import oracle
+    _build.build()
+    img, obs = make_workload(args.seed, "cuda")
+    dev = _dev_inputs(obs)
+    C, N = obs.nchan, img.N
+    hbm, peak_kind = peaks()
+    steps, warm = max(1, args.steps), max(1, args.warmup)
+    base = dict(N=N, n_wplanes=img.Nw, support=img.S, fov_rad=img.fov, w_min=img.w_min,
+                w_max=img.w_max, kernel="kb", kernel_param=img.kernel_param,
+                hermitian_fold=not args.no_fold)
+    weighting = {}
+    for name, kw in (("natural", {}), ("uniform", dict(weighting="uniform")),
+                     ("briggs_R0", dict(weighting="briggs", robust=0.0))):
+        plan = rick.Plan(rick.Config(n_channels=C, **base, **kw))
+        plan.reserve(obs.nrow)
+        ms, st, ng, _ = _time_path(plan, dev, obs.nrow, C, N, N, steps, warm)
+        weighting[name] = {"ms_per_step": ms, "vis_per_s": ng / (ms * 1e-3), "stages_ms": st}
+        del plan
+        torch.cuda.empty_cache()
+    # padding on the 4 highest channels
+    c0 = C - 4
+    sub = dict(uvw=dev["uvw"], chan_scale=dev["chan_scale"][c0:].contiguous(),
+               vis=dev["vis"][:, c0:].contiguous(), weight=dev["weight"][:, c0:].contiguous(),
+               flag=dev["flag"][:, c0:].contiguous())
+    vis_h = sub["vis"].cpu().numpy()
+    w_h, f_h = obs.weight[:, c0:].copy(), obs.flag[:, c0:].copy()
+    sc_h = obs.chan_scale[c0:].copy()
+    dl = img.fov / N
+    src = obs.sources
+    ps = np.clip(np.rint(src[:, 0] / dl + N // 2), 0, N - 1).astype(int)
+    qs = np.clip(np.rint(src[:, 1] / dl + N // 2), 0, N - 1).astype(int)
+    padding = {}
+    probes = None
+    pbase = dict(base, n_wplanes=32, w_support=6, w_kernel_param=10.0)
+    for alpha in (1, 2):
+        plan = rick.Plan(rick.Config(n_channels=4, grid_size=alpha * N, **pbase))
+        plan.reserve(obs.nrow)
+        if probes is None:
+            taper = plan.taper()
+            gain = taper[ps] * taper[qs] / taper[N // 2] ** 2
+            order = np.nonzero(gain < 1e-2)[0]
+            order = order[np.argsort(-src[order, 2])][:8]
+            probes = (ps[order].astype(np.int32), qs[order].astype(np.int32), gain[order])
+            ocfg = oracle.Config(N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov,
+                                 img.w_min, img.w_max)
+            D = oracle.dft_at(ocfg, obs.uvw, sc_h, vis_h, w_h, f_h, channel=3,
+                              p=probes[0], q=probes[1]).real
+        ms, st, ng, im = _time_path(plan, sub, obs.nrow, 4, N, alpha * N, steps, warm)
+        got = im[3][probes[1], probes[0]]
+        padding[f"alpha_{alpha}"] = {
+            "grid": alpha * N, "ms_per_step": ms, "vis_per_s": ng / (ms * 1e-3), "stages_ms": st,
+            "error_vs_eq1_direct_edge_probes": float(np.abs(got - D).max() / np.abs(D).max())}
+        del plan
+        torch.cuda.empty_cache()
+    pb = padding["alpha_2"]
+    print(json.dumps({
+        "metric": "gridded visibilities/sec at 1 GB300 on a padded mesh (alpha 2); weighting "
+                  "and padding costs; error vs Eq. 1",
+        "value": pb["vis_per_s"], "unit": "vis/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": pb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+        "config": {"workload": "meerkat_4096sq_32w_kb8_options", "hermitian_fold": not args.no_fold,
+                   "padding_w_kernel": "Sw 6, beta 10, 32 planes",
+                   "weighting_channels": C, "padding_channels": "4 highest (1498-1712 MHz)",
+                   "probe_taper_gain_unpadded": [float(x) for x in probes[2]],
+                   "l2": "inputs larger than L2"},
+        "weighting": weighting, "padding": padding, "peak_hbm_gbs": hbm, "peak_kind": peak_kind}),
+        flush=True)
+
+
 def run_profile_small(args):
     """A small case of the default workload for ncu captures: the MeerKAT
     recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
     grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
     A step images the 2 channels and then predicts visibilities from the
-    dirty images (the degridding path).  Runs warm-up + steps steps and
+    dirty images (the degridding path); --fft own uses the library's own
+    transform (column pass + row pass fused with the reduction for imaging,
+    column + row passes for prediction) instead of cuFFT.  Runs warm-up + steps steps and
     prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
@@ -944,7 +1076,8 @@ def run_profile_small(args):
     C, N = obs.nchan, img.N
     cfg = rick.Config(N=N, n_wplanes=img.Nw, support=img.S, n_channels=C, fov_rad=img.fov,
                       w_min=img.w_min, w_max=img.w_max, kernel="kb", kernel_param=img.kernel_param,
-                      tile=32, grid_threads=128, tiles_per_grab=4, hermitian_fold=not args.no_fold)
+                      tile=32, grid_threads=128, tiles_per_grab=4, hermitian_fold=not args.no_fold,
+                      fft_impl=args.fft)
     plan = rick.Plan(cfg)
     ns = cfg.stored_planes
     grids = torch.empty((C, ns, N, N), dtype=torch.complex64, device="cuda")
@@ -958,8 +1091,12 @@ def run_profile_small(args):
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
         plan.grid_binned(0, C, 0, ns, grids)
-        plan.fft_wplanes(grids, C * ns)
-        plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        if args.fft == "own":   # column pass, then rows fused with the reduction
+            plan.fft_wplanes_columns(grids, C * ns)
+            plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        else:
+            plan.fft_wplanes(grids, C * ns)
+            plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
         # prediction from the dirty image just made (exercises the degridder)
         plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow)
         plan.model_to_wplanes(image, 0, C, 0, ns, grids)
@@ -985,7 +1122,7 @@ def run_profile_small(args):
                       "impl": "ours", "config": {"workload": "meerkat_small_4096sq_8w_2ch_kb8",
                                                  "visibilities": int(obs.nrow * C),
                                                  "gridded": n_grid, "hermitian_fold": cfg.hermitian_fold,
-                                                 "stored_planes": ns, "tile": 32,
+                                                 "stored_planes": ns, "tile": 32, "fft": args.fft,
                                                  "grid_threads": 128, "tiles_per_grab": 4}}),
           flush=True)
 
@@ -998,12 +1135,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fft", default="cufft", choices=["cufft", "own"],
+                    help="2-D DFT of the profile_small workload (the headline times both)")
     ap.add_argument("--no-fold", action="store_true",
                     help="headline without the Hermitian fold (all Nw planes stored and "
                          "transformed); the other variant is always measured beside it")
     ap.add_argument("--workload", default="meerkat",
                     choices=["meerkat", "lofar", "learned", "large", "predict", "wkernel",
-                             "profile_small"],
+                             "options", "profile_small"],
                     help="meerkat (default bench line); lofar / learned / large measure the "
                          "batched, learned-kernel and precision-stress workloads; "
                          "profile_small is the small case the ncu captures use")
@@ -1016,6 +1155,8 @@ def main():
         run_learned(args)
     elif args.workload == "large":
         run_large(args)
+    elif args.workload == "options":
+        run_options(args)
     elif args.workload == "wkernel":
         run_wkernel(args)
     elif args.workload == "predict":
