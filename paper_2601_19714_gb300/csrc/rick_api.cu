@@ -126,6 +126,9 @@ void make_taper(int kind, double param, int S, int N, int Ng, std::vector<double
 
 }  // namespace
 
+// rick_dirty_image_host transforms and downloads the channels in this many chunks
+constexpr int kHostChunks = 4;
+
 struct rick_plan {
     rick_config cfg;
     int device = 0, num_sms = 0;
@@ -168,6 +171,10 @@ struct rick_plan {
     size_t in_cap = 0;
     float* d_img = nullptr;
     size_t img_cap = 0;
+    // rick_dirty_image_host: a copy stream and events for overlapping the image
+    // download with the transform of later channels
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_done[kHostChunks] = {};
     int64_t launches = 0;
     cudaStream_t last_stream = nullptr;
     float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
@@ -215,6 +222,15 @@ void release(rick_plan* P) {
     dfree(P->d_grid);
     dfree(P->d_in);
     dfree(P->d_img);
+    for (auto& ev : P->chunk_done)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    if (P->copy_stream) {
+        cudaStreamDestroy(P->copy_stream);
+        P->copy_stream = nullptr;
+    }
     if (P->have_b) cufftDestroy(P->fft_b);
     if (P->have_1) cufftDestroy(P->fft_1);
     P->have_b = P->have_1 = false;
@@ -1120,9 +1136,38 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
     if (chan_scale)
         RK_CUDA(cudaMemcpyAsync(d_sc, chan_scale, C * sizeof(double), cudaMemcpyHostToDevice, st));
     RK_CUDA(cudaMemsetAsync(plan->d_img, 0, img_bytes, st));
-    RK_TRY(dirty_image_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, plan->d_img, nullptr, d_ws,
-                            d_cnt, st));
-    RK_CUDA(cudaMemcpyAsync(image_real, plan->d_img, img_bytes, cudaMemcpyDeviceToHost, st));
+    int gc, gk;
+    plan_groups(plan, &gc, &gk);
+    if (gc == c.n_channels && gk == plan->planes && c.n_channels > 1) {
+        // the whole grid fits: grid every channel, then transform and reduce in
+        // channel chunks, each chunk's images downloaded on the copy stream
+        // while the next chunk is transformed
+        if (!plan->copy_stream) RK_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+        for (auto& ev : plan->chunk_done)
+            if (!ev) RK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        RK_TRY(bin_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, d_ws, d_cnt, st));
+        RK_TRY(ensure_group_grid(plan));
+        float* g = reinterpret_cast<float*>(plan->d_grid);
+        RK_TRY(grid_impl(plan, 0, c.n_channels, 0, plan->planes, g, st));
+        const int nch = c.n_channels < kHostChunks ? c.n_channels : kHostChunks;
+        const size_t plane_floats = 2 * (size_t)plan->Ng * plan->Ng;
+        for (int i = 0; i < nch; ++i) {
+            const int c0 = (int)((int64_t)c.n_channels * i / nch), c1 = (int)((int64_t)c.n_channels * (i + 1) / nch);
+            float* gi = g + (size_t)c0 * plan->planes * plane_floats;
+            RK_TRY(fft_phase_impl(plan, gi, c0, c1, 0, plan->planes, d_ws, plan->d_img + (size_t)c0 * NN,
+                                  nullptr, st));
+            RK_CUDA(cudaEventRecord(plan->chunk_done[i], st));
+            RK_CUDA(cudaStreamWaitEvent(plan->copy_stream, plan->chunk_done[i], 0));
+            RK_CUDA(cudaMemcpyAsync(image_real + (size_t)c0 * NN, plan->d_img + (size_t)c0 * NN,
+                                    (size_t)(c1 - c0) * NN * sizeof(float), cudaMemcpyDeviceToHost,
+                                    plan->copy_stream));
+        }
+        RK_CUDA(cudaStreamSynchronize(plan->copy_stream));
+    } else {
+        RK_TRY(dirty_image_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, plan->d_img, nullptr, d_ws,
+                                d_cnt, st));
+        RK_CUDA(cudaMemcpyAsync(image_real, plan->d_img, img_bytes, cudaMemcpyDeviceToHost, st));
+    }
     if (weight_sum)
         RK_CUDA(cudaMemcpyAsync(weight_sum, d_ws, C * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (counts)

@@ -246,15 +246,22 @@ def test_plane_group_streaming_matches_single_pass(rk, orc):
     assert_image_close(outs[1][1], refs[0].real, taper, TOL)
 
 
-def test_host_entry_point_matches_device_path(rk, orc):
-    img, obs = meerkat(5, n_ant=8, n_steps=40, nchan=2, N=256, Nw=4, n_src=8)
-    plan = rk.Plan(plan_config(img, 2))
-    out = np.zeros((2, img.N, img.N), np.float32)
-    ws = np.zeros(2)
+@pytest.mark.parametrize("nchan,kw", [(2, {}), (5, dict(hermitian_fold=True)),
+                                     (5, dict(fft_impl="own")),
+                                     (3, dict(grid_budget_bytes=2 * 256 * 256 * 8))])
+def test_host_entry_point_matches_device_path(rk, orc, nchan, kw):
+    """rick_dirty_image_host: with the whole grid in memory the channels are
+    transformed and downloaded in chunks (uneven for 5 channels); with a
+    plane budget it streams plane groups; both equal the device path."""
+    img, obs = meerkat(5, n_ant=8, n_steps=40, nchan=nchan, N=256, Nw=4, n_src=8)
+    plan = rk.Plan(plan_config(img, nchan, **kw))
+    out = np.full((nchan, img.N, img.N), 7.0, np.float32)   # overwritten
+    ws = np.zeros(nchan)
     cnt = np.zeros(2, np.int64)
     plan.dirty_image_host(obs.uvw, obs.chan_scale, obs.vis, obs.weight, obs.flag, out, ws, cnt)
-    I_g, _, ws_g, cnt_g = run_path(plan, to_device(obs), 2, img.N, img.Nw)
-    for c in range(2):
+    ref = rk.Plan(plan_config(img, nchan, **{k: v for k, v in kw.items() if k != "grid_budget_bytes"}))
+    I_g, _, ws_g, cnt_g = run_path(ref, to_device(obs), nchan, img.N, img.Nw)
+    for c in range(nchan):
         assert_image_close(out[c], I_g[c], plan.taper(), TOL)
     np.testing.assert_allclose(ws, ws_g, rtol=1e-12)
     assert cnt.tolist() == cnt_g.tolist()
