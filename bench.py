@@ -287,9 +287,10 @@ def run_ours(args):
             plan.grid_binned(0, C, 0, ns, grids)
             if e: e[2].record(stream)
             if own:   # the own transform: column pass, then rows fused with Eq. 2's reduction
-                plan.fft_wplanes_columns(grids, C * ns)
+                # (pruned: the planes are this plan's gridder output)
+                plan.fft_wplanes_columns(grids, 0, C, 0, ns, gridded_by_plan=True)
                 if e: e[3].record(stream)
-                plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+                plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image, gridded_by_plan=True)
             else:     # cuFFT, then the reduction
                 plan.fft_wplanes(grids, C * ns)
                 if e: e[3].record(stream)
@@ -1091,9 +1092,9 @@ def run_profile_small(args):
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
         plan.grid_binned(0, C, 0, ns, grids)
-        if args.fft == "own":   # column pass, then rows fused with the reduction
-            plan.fft_wplanes_columns(grids, C * ns)
-            plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
+        if args.fft == "own":   # column pass, then rows fused with the reduction (pruned)
+            plan.fft_wplanes_columns(grids, 0, C, 0, ns, gridded_by_plan=True)
+            plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image, gridded_by_plan=True)
         else:
             plan.fft_wplanes(grids, C * ns)
             plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)

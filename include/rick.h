@@ -265,20 +265,34 @@ rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32
 rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t chan_begin,
                                           int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                           const double* weight_sum, float* image_real,
-                                          float* image_complex, void* stream);
+                                          float* image_complex, int32_t flags, void* stream);
+
+/* flags of the transform calls:
+ * RICK_GRIDDED_BY_PLAN -- grids holds the planes [plane_begin, plane_end) of
+ *   channels [chan_begin, chan_end) exactly as the preceding rick_grid_binned
+ *   of this plan's current binning wrote them.  With the library's own
+ *   transform the calls then prune: the column pass skips the tile columns
+ *   (tile-wide bands of columns) that no visibility reached, and the row pass
+ *   the planes that no visibility reached (both hold zeros and transform to
+ *   zeros).  Ignored with cuFFT. */
+#define RICK_GRIDDED_BY_PLAN 1
 
 /* The two passes of rick_fft_phase_correct_reduce with the library's own
  * transform, as separate calls (RICK_ERR_UNSUPPORTED with cuFFT):
- * rick_fft_wplanes_columns: the length-N inverse DFT down every column of
- *   n_planes planes, in place (pass 1; one launch);
+ * rick_fft_wplanes_columns: the length-N inverse DFT down every column of the
+ *   planes [plane_begin, plane_end) of channels [chan_begin, chan_end)
+ *   (grids laid out as for rick_grid_binned), in place (pass 1);
  * rick_rows_phase_correct_reduce: the row DFTs of column-transformed planes
  *   fused with the phase screen and reduction, arguments as for
- *   rick_phase_correct_reduce (pass 2; one launch; grids is only read). */
-rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
+ *   rick_phase_correct_reduce (pass 2; one launch; grids is only read).
+ * flags as for rick_fft_phase_correct_reduce (with RICK_GRIDDED_BY_PLAN each
+ * call first derives the occupancy from the bin offsets: one small launch). */
+rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int32_t chan_begin, int32_t chan_end,
+                                     int32_t plane_begin, int32_t plane_end, int32_t flags, void* stream);
 rick_status rick_rows_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
                                            int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                            const double* weight_sum, float* image_real,
-                                           float* image_complex, void* stream);
+                                           float* image_complex, int32_t flags, void* stream);
 
 /* The whole path on device buffers: bin, then for each group of channels and
  * planes that fits grid_budget_bytes grid, transform and reduce into

@@ -187,6 +187,8 @@ struct rick_plan {
     // the library's own 2-D DFT (fft_impl 1 and 256 <= N <= 8192): twiddle tables
     bool own_fft = false;
     float2* d_twid = nullptr;
+    uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
+    uint8_t* d_planeocc = nullptr;
     // w-kernel: tap polynomials and the constants of its transform C_w
     float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
     double w_c0 = 1.0, w_s_i0 = 1.0;
@@ -203,6 +205,8 @@ void dfree(T*& p) {
 void release(rick_plan* P) {
     dfree(P->d_inv_taper);
     dfree(P->d_twid);
+    dfree(P->d_colocc);
+    dfree(P->d_planeocc);
     dfree(P->d_density);
     dfree(P->d_wmom);
     dfree(P->d_wbuf);
@@ -450,6 +454,8 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         fft_twiddles(c.N, tw);
         RK_CUDA(cudaMalloc(&P->d_twid, sizeof(float2) * tw.size()));
         RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+        RK_CUDA(cudaMalloc(&P->d_colocc, (size_t)c.n_channels * P->planes * P->NT));
+        RK_CUDA(cudaMalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
         return RICK_OK;   // no cuFFT plans
     }
     const size_t plane_bytes = (size_t)P->Ng * P->Ng * sizeof(float2);
@@ -708,19 +714,43 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
     return s;
 }
 
+// Occupancy of the gridded planes [k0, k1) of channels [c0, c1) from the
+// current binning (for pruning the own transform).
+rick_status occupancy_impl(rick_plan* P, int c0, int c1, int k0, int k1, cudaStream_t st) {
+    RK_ARG(P->binned && !P->binned_for_predict,
+           "RICK_GRIDDED_BY_PLAN needs the plan's binning for gridding (rick_bin)");
+    int launches = 0;
+    rick_status s = check_launch(launch_occupancy(P->d_offsets, c0, c1 - c0, k0, k1 - k0, P->planes, P->NT,
+                                                  P->d_colocc, P->d_planeocc, st, &launches),
+                                 "occupancy kernel");
+    P->launches += launches;
+    return s;
+}
+
 // Pass 1 of the own transform (inverse DFT down every column), in place.
-rick_status columns_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t st) {
+rick_status columns_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int k1, int32_t flags,
+                         cudaStream_t st) {
+    const rick_config& c = P->cfg;
     if (!P->own_fft) {
         set_err("the column pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
         return RICK_ERR_UNSUPPORTED;
     }
-    RK_ARG(n_planes >= 0, "n_planes must be >= 0");
-    RK_ARG(n_planes == 0 || grids != nullptr, "grids is NULL");
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_ARG(grids != nullptr, "grids is NULL");
     RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
     P->last_stream = st;
+    OccMask occ;
+    if (flags & RICK_GRIDDED_BY_PLAN) {
+        RK_TRY(occupancy_impl(P, c0, c1, k0, k1, st));
+        occ.col = P->d_colocc;
+        occ.T = P->T;
+        occ.NT = P->NT;
+    }
     int launches = 0;
-    rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids), n_planes, P->Ng,
-                                                    true, P->d_twid, st, &launches),
+    rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids),
+                                                    (int64_t)(c1 - c0) * (k1 - k0), P->Ng, true,
+                                                    P->d_twid, occ, st, &launches),
                                  "FFT column kernel");
     P->launches += launches;
     return s;
@@ -729,7 +759,7 @@ rick_status columns_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStrea
 // Pass 2 fused with the phase screen and reduction, on column-transformed planes.
 rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0, int k1,
                             const double* weight_sum, float* image_real, float* image_complex,
-                            cudaStream_t st) {
+                            int32_t flags, cudaStream_t st, bool occ_ready = false) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
         set_err("the fused row pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
@@ -742,13 +772,15 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
                ((uintptr_t)image_complex & 7u) == 0,
            "grids must be 16-byte, image_real 4-byte and image_complex 8-byte aligned");
     P->last_stream = st;
+    if ((flags & RICK_GRIDDED_BY_PLAN) && !occ_ready) RK_TRY(occupancy_impl(P, c0, c1, k0, k1, st));
     int launches = 0;
     rick_status s = check_launch(launch_rows_phase_reduce(phase_params(P, c0, c1, k0, k1),
                                                           reinterpret_cast<const float2*>(grids),
                                                           weight_sum + c0, P->d_inv_taper, P->d_twid,
                                                           image_real,
-                                                          reinterpret_cast<float2*>(image_complex), st,
-                                                          &launches),
+                                                          reinterpret_cast<float2*>(image_complex),
+                                                          (flags & RICK_GRIDDED_BY_PLAN) ? P->d_planeocc : nullptr,
+                                                          st, &launches),
                                  "fused row FFT / phase kernel");
     P->launches += launches;
     return s;
@@ -758,7 +790,7 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
 // [c0, c1): with the own transform, the column pass and the fused row pass.
 rick_status fft_phase_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int k1,
                            const double* weight_sum, float* image_real, float* image_complex,
-                           cudaStream_t st) {
+                           cudaStream_t st, int32_t flags = 0) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
         RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -768,8 +800,9 @@ rick_status fft_phase_impl(rick_plan* P, float* grids, int c0, int c1, int k0, i
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
     RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
-    RK_TRY(columns_impl(P, grids, (int64_t)(c1 - c0) * (k1 - k0), st));
-    return rows_phase_impl(P, grids, c0, c1, k0, k1, weight_sum, image_real, image_complex, st);
+    RK_TRY(columns_impl(P, grids, c0, c1, k0, k1, flags, st));
+    // the occupancy computed by the column pass serves the row pass too
+    return rows_phase_impl(P, grids, c0, c1, k0, k1, weight_sum, image_real, image_complex, flags, st, true);
 }
 
 rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
@@ -880,7 +913,8 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
             const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
             RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st));
             RK_TRY(fft_phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
-                                  image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st));
+                                  image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st,
+                                  RICK_GRIDDED_BY_PLAN));
         }
     }
     return RICK_OK;
@@ -1062,24 +1096,25 @@ rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32
 rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t chan_begin,
                                           int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                           const double* weight_sum, float* image_real,
-                                          float* image_complex, void* stream) {
+                                          float* image_complex, int32_t flags, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
     return fft_phase_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, weight_sum,
-                          image_real, image_complex, as_stream(stream));
+                          image_real, image_complex, as_stream(stream), flags);
 }
 
-rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {
+rick_status rick_fft_wplanes_columns(rick_plan* plan, float* grids, int32_t chan_begin, int32_t chan_end,
+                                     int32_t plane_begin, int32_t plane_end, int32_t flags, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
-    return columns_impl(plan, grids, n_planes, as_stream(stream));
+    return columns_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, flags, as_stream(stream));
 }
 
 rick_status rick_rows_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,
                                            int32_t chan_end, int32_t plane_begin, int32_t plane_end,
                                            const double* weight_sum, float* image_real,
-                                           float* image_complex, void* stream) {
+                                           float* image_complex, int32_t flags, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
     return rows_phase_impl(plan, grids, chan_begin, chan_end, plane_begin, plane_end, weight_sum,
-                           image_real, image_complex, as_stream(stream));
+                           image_real, image_complex, flags, as_stream(stream));
 }
 
 rick_status rick_dirty_image(rick_plan* plan, const double* uvw, const double* chan_scale,
@@ -1155,7 +1190,7 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
             const int c0 = (int)((int64_t)c.n_channels * i / nch), c1 = (int)((int64_t)c.n_channels * (i + 1) / nch);
             float* gi = g + (size_t)c0 * plan->planes * plane_floats;
             RK_TRY(fft_phase_impl(plan, gi, c0, c1, 0, plan->planes, d_ws, plan->d_img + (size_t)c0 * NN,
-                                  nullptr, st));
+                                  nullptr, st, RICK_GRIDDED_BY_PLAN));
             RK_CUDA(cudaEventRecord(plan->chunk_done[i], st));
             RK_CUDA(cudaStreamWaitEvent(plan->copy_stream, plan->chunk_done[i], 0));
             RK_CUDA(cudaMemcpyAsync(image_real + (size_t)c0 * NN, plan->d_img + (size_t)c0 * NN,
@@ -1250,7 +1285,7 @@ rick_status rick_graph_capture(rick_plan* plan, const double* uvw, const double*
         if (s == RICK_OK) s = grid_impl(plan, 0, c.n_channels, 0, plan->planes, grids, st);
         if (s == RICK_OK)
             s = fft_phase_impl(plan, grids, 0, c.n_channels, 0, plan->planes, weight_sum, image_real,
-                               nullptr, st);
+                               nullptr, st, RICK_GRIDDED_BY_PLAN);
     } else if (s == RICK_OK) {
         s = dirty_image_impl(plan, uvw, chan_scale, vis, weight, flag, nrow, image_real, nullptr,
                              weight_sum, counts, st);

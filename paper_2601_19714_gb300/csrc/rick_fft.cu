@@ -26,6 +26,13 @@
 // thread per stage (16/R butterflies of the last radix-R stage).  Thread b
 // therefore ends with the outputs b + (N/16) j, j < 16, in registers.
 //
+// Pruning: planes made by the library's gridder are zero in every column tile
+// that no visibility reached and in every plane no visibility reached.  Given
+// the occupancy of the current binning (launch_occupancy: per plane and tile
+// column, from the bin offsets), the column pass skips the empty column tiles
+// (their DFT is zero, and they already hold zeros) and the fused row pass skips
+// the empty planes (they add nothing) -- the same result with less work.
+//
 // Shared arrays are indexed through skew(a) = a + a/16, which spreads the
 // stride-16 stores of the first stages over all banks.  Twiddles come from two
 // tables of e^(+2 pi i e/N) rounded from FP64 on the host, e = 64 eh + el:
@@ -237,9 +244,13 @@ __device__ __forceinline__ void load_tables(const float2* __restrict__ twid, flo
 // transformed, and written back the same way.
 template <int LOG2N, int COLS, bool INV>
 __global__ void __launch_bounds__(COLS * (1 << LOG2N) / 16)
-k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid) {
+k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, OccMask occ, int64_t plane0) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
+    // a column tile that no visibility reached is zero: skip it
+    if (occ.col != nullptr &&
+        occ.col[(plane0 + blockIdx.y) * occ.NT + (int)(blockIdx.x * COLS) / occ.T] == 0)
+        return;
     constexpr int kThreads = COLS * T;
     constexpr int kVec = COLS / 2;   // 16-byte pieces per row
     extern __shared__ __align__(16) float2 fsm[];
@@ -325,7 +336,8 @@ template <int LOG2N, int PREC, bool COMPLEX_OUT>
 __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
 k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                     const float* __restrict__ inv_taper, const float2* __restrict__ twid,
-                    float* __restrict__ image_real, float2* __restrict__ image_complex) {
+                    float* __restrict__ image_real, float2* __restrict__ image_complex,
+                    const uint8_t* __restrict__ plane_occ) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
@@ -359,25 +371,34 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 
     const size_t NN = (size_t)N * N;
     const int n_rows = P.nc * P.nk;
+    // planes no visibility reached (plane_occ == 0) are skipped
+    auto next_row = [&](int r) {
+        if (plane_occ != nullptr)
+            while (r < n_rows && plane_occ[r] == 0) ++r;
+        return r;
+    };
     float2 a[16], x[16];
-    {
-        const float2* row = grids + (size_t)q * N;
+    int r = next_row(0);
+    if (r < n_rows) {
+        const float2* row = grids + (size_t)r * NN + (size_t)q * N;
 #pragma unroll
         for (int t2 = 0; t2 < 16; ++t2) a[t2] = __ldcs(row + b + T * t2);
     }
     __syncthreads();
-    int r = 0;
     for (int cc = 0; cc < P.nc; ++cc) {
         float acc[16], acci[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = acci[j] = 0.f;
-        for (int kk = 0; kk < P.nk; ++kk, ++r) {
+        for (int kk = 0; kk < P.nk; ++kk) {
+            if (cc * P.nk + kk != r) continue;   // an empty plane
             radix16_out<LOG2N, true>(a, b, 0, buf, th, tl);
-            if (r + 1 < n_rows) {
-                const float2* row = grids + (size_t)(r + 1) * NN + (size_t)q * N;
+            const int rn = next_row(r + 1);
+            if (rn < n_rows) {
+                const float2* row = grids + (size_t)rn * NN + (size_t)q * N;
 #pragma unroll
                 for (int t2 = 0; t2 < 16; ++t2) a[t2] = __ldcs(row + b + T * t2);
             }
+            r = rn;
             __syncthreads();
             middle_stages<LOG2N, true>(buf, b, th, tl);
             last_stage<LOG2N, true>(buf, b, x);
@@ -413,8 +434,32 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 
 constexpr int kCols = 2;   // columns per CTA in pass 1
 
+// occupancy of plane p (p = cc nk + kk of the launch) and its tile columns
+// from the bin offsets: a tile column is reached if any of its tiles holds a
+// record, or a tile to its left holds a record that spills right (halo classes
+// 2 and 3; the column after the last wraps to column 0, which only the
+// Hermitian fold's mirrored footprints reach).
+__global__ void k_occupancy(const uint32_t* __restrict__ offsets, int c0, int nc, int k0, int nk,
+                            int Nw_store, int NT, uint8_t* __restrict__ col, uint8_t* __restrict__ plane) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nc * nk * NT) return;
+    const int tx = (int)(i % NT);
+    const int64_t p = i / NT;
+    const int cc = (int)(p / nk), kk = (int)(p - (int64_t)cc * nk);
+    const int txl = (tx + NT - 1) % NT;
+    const uint64_t pk = ((uint64_t)(c0 + cc) * Nw_store + (k0 + kk)) * NT;
+    uint32_t any = 0;
+    for (int ty = 0; ty < NT && !any; ++ty) {
+        const uint64_t own = ((pk + ty) * NT + tx) * 4, left = ((pk + ty) * NT + txl) * 4;
+        any |= __ldg(offsets + own + 4) - __ldg(offsets + own);     // all classes of the tile
+        any |= __ldg(offsets + left + 4) - __ldg(offsets + left + 2);  // classes 2, 3 of the left tile
+    }
+    col[i] = any ? 1 : 0;
+    if (any) plane[p] = 1;
+}
+
 template <int LOG2N, bool INV>
-cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, cudaStream_t st) {
+cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, OccMask occ, cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     auto fn = k_fft_columns<LOG2N, kCols, INV>;
     const size_t smem = (size_t)(Sh::kTw + kCols * Sh::kArray) * sizeof(float2);
@@ -422,7 +467,7 @@ cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, cud
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < n_planes; p0 += 65535) {
         const unsigned np = (unsigned)(n_planes - p0 < 65535 ? n_planes - p0 : 65535);
-        fn<<<dim3(Sh::N / kCols, np), kCols * Sh::T, smem, st>>>(grids + p0 * Sh::N * Sh::N, twid);
+        fn<<<dim3(Sh::N / kCols, np), kCols * Sh::T, smem, st>>>(grids + p0 * Sh::N * Sh::N, twid, occ, p0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -445,26 +490,28 @@ cudaError_t rows_one(float2* grids, int64_t n_planes, const float2* twid, cudaSt
 
 template <int LOG2N, int PREC, bool CPLX>
 cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                      const float2* twid, float* image_real, float2* image_complex, cudaStream_t st) {
+                      const float2* twid, float* image_real, float2* image_complex, const uint8_t* pocc,
+                      cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     auto fn = k_rows_phase_reduce<LOG2N, PREC, CPLX>;
     const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(uint2) + sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, inv_taper, twid, image_real, image_complex);
+    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc);
     return cudaGetLastError();
 }
 
 template <int LOG2N>
 cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                    const float2* twid, float* image_real, float2* image_complex, cudaStream_t st) {
+                    const float2* twid, float* image_real, float2* image_complex, const uint8_t* pocc,
+                    cudaStream_t st) {
     const bool c = image_complex != nullptr;
     if (P.precision == RICK_PREC_ALL_FP32)
-        return c ? fused_one<LOG2N, RICK_PREC_ALL_FP32, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st)
-                 : fused_one<LOG2N, RICK_PREC_ALL_FP32, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st);
-    return c ? fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st)
-             : fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st);
+        return c ? fused_one<LOG2N, RICK_PREC_ALL_FP32, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st)
+                 : fused_one<LOG2N, RICK_PREC_ALL_FP32, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st);
+    return c ? fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st)
+             : fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st);
 }
 
 int log2_exact(int N) {
@@ -500,8 +547,8 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
     cudaError_t e = cudaErrorInvalidValue;
 #define RICK_FFT_CASE(LG)                                                                   \
     case LG:                                                                                \
-        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, st)                      \
-                    : columns_one<LG, false>(grids, n_planes, twid, st);                    \
+        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, OccMask{}, st)           \
+                    : columns_one<LG, false>(grids, n_planes, twid, OccMask{}, st);         \
         if (e == cudaSuccess)                                                               \
             e = inverse ? rows_one<LG, true>(grids, n_planes, twid, st)                     \
                         : rows_one<LG, false>(grids, n_planes, twid, st);                   \
@@ -521,13 +568,13 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
 }
 
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               cudaStream_t st, int* launches) {
+                               OccMask occ, cudaStream_t st, int* launches) {
     if (n_planes <= 0) return cudaSuccess;
     cudaError_t e = cudaErrorInvalidValue;
 #define RICK_FFT_CASE(LG)                                                                   \
     case LG:                                                                                \
-        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, st)                      \
-                    : columns_one<LG, false>(grids, n_planes, twid, st);                    \
+        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, occ, st)                 \
+                    : columns_one<LG, false>(grids, n_planes, twid, occ, st);               \
         break;
     switch (log2_exact(N)) {
         RICK_FFT_CASE(8)
@@ -545,19 +592,32 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
 
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                      const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, cudaStream_t st, int* launches) {
+                                     float2* image_complex, const uint8_t* plane_occ, cudaStream_t st,
+                                     int* launches) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (log2_exact(P.N)) {
-        case 8: e = fused_n<8>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
-        case 9: e = fused_n<9>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
-        case 10: e = fused_n<10>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
-        case 11: e = fused_n<11>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
-        case 12: e = fused_n<12>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
-        case 13: e = fused_n<13>(P, grids, wsum, inv_taper, twid, image_real, image_complex, st); break;
+        case 8: e = fused_n<8>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 9: e = fused_n<9>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 10: e = fused_n<10>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 11: e = fused_n<11>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 12: e = fused_n<12>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 13: e = fused_n<13>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
         default: break;
     }
     if (e == cudaSuccess) ++*launches;
     return e;
+}
+
+cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
+                             uint8_t* col, uint8_t* plane, cudaStream_t st, int* launches) {
+    const int64_t n = (int64_t)nc * nk * NT;
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(plane, 0, (size_t)nc * nk, st);
+    if (e != cudaSuccess) return e;
+    k_occupancy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(offsets, c0, nc, k0, nk, Nw_store, NT, col, plane);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    return cudaSuccess;
 }
 
 }  // namespace rick

@@ -203,14 +203,28 @@ void fft_twiddles(int N, std::vector<float2>& out);
 // In place, unnormalised, over n_planes planes [N][N]: columns then rows.
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
                          cudaStream_t stream, int* launches);
-// Pass 1 alone (the inverse DFT down every column), in place.
+// Occupancy of gridded planes, for pruning: col[p * NT + tx] != 0 if tile
+// column tx of plane p (of the launch) may be non-zero, T its width; null col:
+// no pruning.
+struct OccMask {
+    const uint8_t* col = nullptr;
+    int T = 1, NT = 1;
+};
+// col[nc * nk * NT] and plane[nc * nk] from the bin offsets of the plan's
+// binning (channels [c0, c0 + nc), stored planes [k0, k0 + nk)).
+cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
+                             uint8_t* col, uint8_t* plane, cudaStream_t stream, int* launches);
+// Pass 1 alone (the inverse DFT down every column), in place; with occ, the
+// empty column tiles are skipped.
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               cudaStream_t stream, int* launches);
+                               OccMask occ, cudaStream_t stream, int* launches);
 // Pass 2 fused with the phase screen and reduction: grids must hold the
 // column-transformed planes [nc][nk][N][N]; image_real [nc][N][N] (+=).
+// plane_occ (nullable): planes of the launch with plane_occ == 0 are skipped.
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                      const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, cudaStream_t stream, int* launches);
+                                     float2* image_complex, const uint8_t* plane_occ, cudaStream_t stream,
+                                     int* launches);
 
 // learned kernel network (rick_mlp.cu)
 int64_t mlp_param_count(int H);

@@ -24,6 +24,7 @@ STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_E
 KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
 PRECISIONS = {"fp64idx": 0, "fp32": 1}
 FFT_IMPLS = {"cufft": 0, "own": 1}
+GRIDDED_BY_PLAN = 1             # transform flag: the planes are this plan's gridder output
 WEIGHTINGS = {"natural": 0, "uniform": 1, "briggs": 2}
 
 EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
@@ -87,10 +88,10 @@ def load(path: str = LIB_PATH):
         "rick_grid": [p, p, p, p, p, p, i64, i32, i32, p, p, p, p],
         "rick_fft_wplanes": [p, p, i64, p],
         "rick_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
-        "rick_fft_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
-        "rick_fft_wplanes_columns": [p, p, i64, p],
+        "rick_fft_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, i32, p],
+        "rick_fft_wplanes_columns": [p, p, i32, i32, i32, i32, i32, p],
         "rick_imaging_weights": [p, p, p, p, p, i64, p, p],
-        "rick_rows_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
+        "rick_rows_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, i32, p],
         "rick_dirty_image": [p, p, p, p, p, p, i64, p, p, p, p, p],
         "rick_dirty_image_host": [p, p, p, p, p, p, i64, p, p, p, p],
         "rick_plan_sync_status": [p],
@@ -339,14 +340,15 @@ class Plan:
             "rick_phase_correct_reduce")
 
     def fft_phase_correct_reduce(self, grids, chan_begin, chan_end, plane_begin, plane_end,
-                                 weight_sum, image_real, image_complex=None, stream=None):
+                                 weight_sum, image_real, image_complex=None, gridded_by_plan=False,
+                                 stream=None):
         d = _dt()
         _check(load().rick_fft_phase_correct_reduce(
             self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
             plane_end, _ptr(weight_sum, d["f64"], "weight_sum", 8),
             _ptr(image_real, d["f32"], "image_real", 4),
-            _ptr(image_complex, d["c64"], "image_complex", 8), _stream(stream)),
-            "rick_fft_phase_correct_reduce")
+            _ptr(image_complex, d["c64"], "image_complex", 8), GRIDDED_BY_PLAN if gridded_by_plan else 0,
+            _stream(stream)), "rick_fft_phase_correct_reduce")
 
     def imaging_weights(self, uvw, chan_scale, weight, flag, nrow, weight_out, stream=None):
         d = _dt()
@@ -355,21 +357,24 @@ class Plan:
             _ptr(weight, d["f32"], "weight", 4), _ptr(flag, d["u8"], "flag"), int(nrow),
             _ptr(weight_out, d["f32"], "weight_out", 4), _stream(stream)), "rick_imaging_weights")
 
-    def fft_wplanes_columns(self, grids, n_planes, stream=None):
+    def fft_wplanes_columns(self, grids, chan_begin, chan_end, plane_begin, plane_end,
+                            gridded_by_plan=False, stream=None):
         d = _dt()
-        _check(load().rick_fft_wplanes_columns(self.handle, _ptr(grids, d["c64"], "grids", 16),
-                                               int(n_planes), _stream(stream)),
-               "rick_fft_wplanes_columns")
+        _check(load().rick_fft_wplanes_columns(
+            self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
+            plane_end, GRIDDED_BY_PLAN if gridded_by_plan else 0, _stream(stream)),
+            "rick_fft_wplanes_columns")
 
     def rows_phase_correct_reduce(self, grids, chan_begin, chan_end, plane_begin, plane_end,
-                                  weight_sum, image_real, image_complex=None, stream=None):
+                                  weight_sum, image_real, image_complex=None, gridded_by_plan=False,
+                                  stream=None):
         d = _dt()
         _check(load().rick_rows_phase_correct_reduce(
             self.handle, _ptr(grids, d["c64"], "grids", 16), chan_begin, chan_end, plane_begin,
             plane_end, _ptr(weight_sum, d["f64"], "weight_sum", 8),
             _ptr(image_real, d["f32"], "image_real", 4),
-            _ptr(image_complex, d["c64"], "image_complex", 8), _stream(stream)),
-            "rick_rows_phase_correct_reduce")
+            _ptr(image_complex, d["c64"], "image_complex", 8), GRIDDED_BY_PLAN if gridded_by_plan else 0,
+            _stream(stream)), "rick_rows_phase_correct_reduce")
 
     def dirty_image(self, uvw, chan_scale, vis, weight, flag, nrow, image_real,
                     image_complex=None, weight_sum=None, counts=None, stream=None):

@@ -171,3 +171,60 @@ def test_own_and_cufft_dirty_images_match_oracle(rk, orc):
                          dev["nrow"], im)
         e = assert_image_close(im[0].cpu().numpy(), I_o.real, plan.taper(), 1e-5, full=True)
         print(impl, e)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(hermitian_fold=True),
+                                dict(hermitian_fold=True, w_support=4, w_kernel_param=8.0)])
+def test_pruned_transform_is_exactly_the_unpruned_one(rk, kw):
+    """With RICK_GRIDDED_BY_PLAN the column pass skips tile columns that no
+    visibility reached and the row pass skips empty planes: zeros transform to
+    zeros, so the image is bit-identical to the unpruned call's; a plane range
+    of a sub-block and the planes of the whole path are covered.  The data
+    leave most tile columns and some planes empty (the short baselines of a
+    small array, a wide w range)."""
+    import torch
+    img, obs = meerkat(84, n_ant=8, n_steps=30, nchan=3, N=1024, Nw=24, n_src=10)
+    x = obs.uvw[:, :2] * obs.chan_scale.max() * img.fov
+    obs.uvw[:, :2] *= 0.3 * img.N / np.abs(x).max()      # footprints in the central 60 %
+    dev = to_device(obs)
+    C, N = 3, img.N
+    cfg = plan_config(img, C, fft_impl="own", **kw)
+    plan, grids, wsum = _gridded(rk, cfg, dev, C)
+    ns = cfg.stored_planes
+    for (c0, c1, k0, k1) in ((0, C, 0, ns), (1, 3, 2, ns - 1)):
+        sub = grids[c0:c1, k0:k1].contiguous()
+        a, b = sub.clone(), sub.clone()
+        ia = torch.zeros((c1 - c0, N, N), dtype=torch.float32, device="cuda")
+        ib = torch.zeros((c1 - c0, N, N), dtype=torch.float32, device="cuda")
+        plan.fft_phase_correct_reduce(a, c0, c1, k0, k1, wsum, ia)
+        plan.fft_phase_correct_reduce(b, c0, c1, k0, k1, wsum, ib, gridded_by_plan=True)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(ia.cpu().numpy(), ib.cpu().numpy())
+        assert np.abs(ia.cpu().numpy()).max() > 0
+    # the split calls, pruned, on the whole range
+    c = grids.clone()
+    ic = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    plan.fft_wplanes_columns(c, 0, C, 0, ns, gridded_by_plan=True)
+    plan.rows_phase_correct_reduce(c, 0, C, 0, ns, wsum, ic, gridded_by_plan=True)
+    d = grids.clone()
+    idd = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    plan.fft_phase_correct_reduce(d, 0, C, 0, ns, wsum, idd)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(ic.cpu().numpy(), idd.cpu().numpy())
+
+
+def test_pruning_needs_the_plans_gridding_binning(rk):
+    import torch
+    img, obs = tiny_wstack(85, nvis=500, N=256)
+    dev = to_device(obs)
+    plan = rk.Plan(plan_config(img, 1, fft_impl="own"))
+    grids = torch.zeros((1, img.Nw, img.N, img.N), dtype=torch.complex64, device="cuda")
+    with pytest.raises(rk.RickError):   # nothing binned yet
+        plan.fft_wplanes_columns(grids, 0, 1, 0, img.Nw, gridded_by_plan=True)
+    plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], None, dev["nrow"])
+    with pytest.raises(rk.RickError):   # binned for prediction
+        plan.fft_wplanes_columns(grids, 0, 1, 0, img.Nw, gridded_by_plan=True)
+    cu = rk.Plan(plan_config(img, 1))
+    with pytest.raises(rk.RickError) as e:   # the split passes need the own transform
+        cu.fft_wplanes_columns(grids, 0, 1, 0, img.Nw)
+    assert e.value.status == 6
