@@ -1,13 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark of the w-stacking hot path on GB300.
 
-One step = the whole path over one batch: rick_bin + rick_grid_binned
+One step = the whole path over one batch: rick_bin + rick_grid_binned_sparse
 (placement, binning and gridding of every visibility of every channel onto
-its w-plane), rick_fft_wplanes (cuFFT, every plane), rick_phase_correct_reduce
-(phase screen + sum over planes into the dirty images).  The library's own
-transform (rick_fft_wplanes_columns + rick_rows_phase_correct_reduce, the row
-pass fused with the reduction) is timed beside it as "own_fft_variant".
-Inputs are resident
+its w-plane; tiles no visibility reaches are not written), then the library's
+own 2-D DFT, pruned to the reached tiles: rick_fft_wplanes_columns (column
+pass) + rick_rows_phase_correct_reduce (row pass fused with the phase screen
+and the sum over planes into the dirty images).  The cuFFT path
+(rick_grid_binned + rick_fft_wplanes + rick_phase_correct_reduce) is timed
+beside it as "fft_variant" (--fft cufft swaps the two).  Inputs are resident
 in HBM when the timed region starts; `e2e` repeats the measurement through
 rick_dirty_image_host, with the host->device copy of the inputs and the
 device->host copy of the images inside the timed region.
@@ -55,6 +56,64 @@ def peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+FFT_DESC = {
+    "own": "own 2-D DFT pruned to the reached tiles (sparse gridding, column pass, row pass "
+           "fused with the phase screen and reduction)",
+    "cufft": "cuFFT (every plane; full gridding, separate phase screen and reduction)",
+}
+
+
+def reach_counts(offsets, C, P, N, T):
+    """Tiles, tile columns and planes of the [C][P] stored planes that a
+    binned record reaches, from the bin offsets (the library's rule: a tile's
+    own bins and the spilling halo classes of its left, upper and upper-left
+    neighbours, wrapping around the mesh)."""
+    NT = N // T
+    cnt = np.diff(offsets.astype(np.int64)).reshape(C * P, NT, NT, 4)   # records per (tile, class)
+    own = cnt.sum(-1)
+    left = np.roll(cnt[..., 2] + cnt[..., 3], 1, axis=2)     # tile tx reads tx-1
+    up = np.roll(cnt[..., 1] + cnt[..., 2], 1, axis=1)       # tile ty reads ty-1
+    ul = np.roll(np.roll(cnt[..., 2], 1, axis=1), 1, axis=2)
+    reached = (own + left + up + ul) > 0                      # [C*P, NT(ty), NT(tx)]
+    return {"tiles": int(reached.sum()), "tile_columns": int(reached.any(axis=1).sum()),
+            "planes": int(reached.any(axis=(1, 2)).sum()), "tile": T,
+            "tiles_total": int(reached.size), "planes_total": C * P}
+
+
+def stage_traffic(N, C, P, nrow, n_grid, T, reach, own):
+    """Algorithmic bytes per step of each stage.  Full planes (cuFFT path):
+    the gridder writes every cell once, the FFT reads and writes every cell
+    once (the minimum of any 2-D FFT), the reduction reads every cell and the
+    images.  Pruned own transform: the gridder writes the reached tiles, the
+    column pass reads them and writes the reached tile columns in full, the
+    fused row pass reads the reached tile columns and the images."""
+    NN = N * N
+    cells = C * P * NN
+    b_bin = (24.0 * nrow + C * nrow * (8 + 4 + 1)               # inputs
+             + C * nrow * (4 + 4 + 16) * 2 + 16.0 * n_grid)     # key/rank/stage write+read, records
+    b_img = 8.0 * C * NN                                        # image read + write
+    if not own:
+        return {"bin": b_bin, "grid": 8.0 * cells + 16.0 * n_grid, "fft": 16.0 * cells,
+                "phase": 8.0 * cells + b_img}
+    tile_cells = reach["tiles"] * T * T
+    col_cells = reach["tile_columns"] * N * T
+    return {"bin": b_bin, "grid": 8.0 * tile_cells + 16.0 * n_grid,
+            "columns": 8.0 * tile_cells + 8.0 * col_cells, "rows_phase": 8.0 * col_cells + b_img}
+
+
+def dram_traffic(stage, N, C, P, reach):
+    """DRAM bytes per step of a stage, scaled from one ncu capture of the
+    small 4096^2 case: cuFFT's per cell; the pruned passes' per processed
+    unit (scaling by the units holds where traffic is proportional to them)."""
+    if N != 4096:
+        return None, None
+    per_cell = {"fft": 46.7}
+    if stage in per_cell:
+        return (per_cell[stage] * C * P * N * N,
+                f"ncu capture of the 4096^2 small case, scaled by planes ({per_cell[stage]} B/cell)")
+    return None, None
 
 
 class ClockSampler:
@@ -284,7 +343,9 @@ def run_ours(args):
             plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], nrow,
                      wsum, counts)
             if e: e[1].record(stream)
-            plan.grid_binned(0, C, 0, ns, grids)
+            # with the own transform the unreached tiles are not written: the
+            # pruned passes never read them
+            plan.grid_binned(0, C, 0, ns, grids, sparse=own)
             if e: e[2].record(stream)
             if own:   # the own transform: column pass, then rows fused with Eq. 2's reduction
                 # (pruned: the planes are this plan's gridder output)
@@ -327,48 +388,35 @@ def run_ours(args):
         st = {k: statistics.median(v) for k, v in stage_ms.items()}
         out = dict(ms=ms, st=st, launches=launches, n_grid=n_grid, n_drop=n_drop,
                    clocks=clk.summary() if clocks else None, img_ch0=image[0].cpu().numpy(),
-                   taper=plan.taper())
+                   taper=plan.taper(), reach=reach_counts(plan.bin_offsets(), C, ns, N, cfg.tile or 32))
         del grids, image, plan
         torch.cuda.empty_cache()
         return out
 
     fold = not args.no_fold
     from dataclasses import replace
-    tuned = tuned_config(fold)
-    other_cfg = tuned_config(not fold)
+    impl = args.fft
+    alt_impl = "cufft" if impl == "own" else "own"
+    tuned = replace(tuned_config(fold), fft_impl=impl)
+    other_cfg = replace(tuned_config(not fold), fft_impl=impl)
     other = measure(other_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
-    own_cfg = replace(tuned, fft_impl="own")
-    own_fft = measure(own_cfg, max(1, min(args.steps, 3)), 2, clocks=False)
+    alt = measure(replace(tuned, fft_impl=alt_impl), max(1, min(args.steps, 3)), 2, clocks=False)
     res = measure(tuned, args.steps, args.warmup, clocks=True)
     st, ms_max, launches = res["st"], res["ms"], res["launches"]
     n_grid, n_drop = res["n_grid"], res["n_drop"]
     Nst = tuned.stored_planes
 
     hbm, peak_kind = peaks()
-    NN = N * N
-    cells = C * Nst * NN
-    b_grid = 8.0 * cells + 16.0 * n_grid                  # write every cell once + read each record
-    b_fft = 2 * 8.0 * cells                               # one read + one write per plane (minimum)
-    b_phase = 8.0 * cells + 8.0 * C * NN                  # read planes + image read/write
-    b_bin = (24.0 * nrow + C * nrow * (8 + 4 + 1)         # inputs
-             + C * nrow * (4 + 4 + 16) * 2 + 16.0 * n_grid)  # key/rank/stage write+read, records
-    # the own transform: the column pass reads and writes every cell (the FFT's
-    # algorithmic 16 B/cell); the fused row pass reads every cell once (the
-    # reduction's 8 B/cell) and the image, and writes no plane
-    stage_bytes = {"bin": b_bin, "grid": b_grid, "fft": b_fft, "phase": b_phase,
-                   "columns": b_fft, "rows_phase": b_phase}
+    cells = C * Nst * N * N
+    stage_bytes = stage_traffic(N, C, Nst, nrow, n_grid, tuned.tile or 32, res["reach"],
+                                impl == "own")
     gbs = {k: stage_bytes[k] / (st[k] * 1e-3) / 1e9 for k in st}
     dominant = max(st, key=st.get)
     dom_bytes = stage_bytes[dominant]
-    # DRAM traffic of the dominant stage per step, from one ncu capture of the
-    # small 4096^2 case (dram__bytes_read.sum + dram__bytes_write.sum per
-    # launch), scaled by the planes (traffic proportional to cells)
-    per_cell = {"fft": 46.7}
-    dom_traffic, traffic_how = None, None
-    if dominant in per_cell and N == 4096:
-        dom_traffic = per_cell[dominant] * cells
-        traffic_how = (f"ncu capture of the 4096^2 small case, scaled by planes "
-                       f"({per_cell[dominant]} B/cell)")
+    # DRAM traffic of the dominant stage per step from one ncu capture of a
+    # small case of the same kernel (dram__bytes_read.sum +
+    # dram__bytes_write.sum), scaled to the step by the units it processes
+    dom_traffic, traffic_how = dram_traffic(dominant, N, C, Nst, res["reach"])
 
     # ---- end to end through the host entry point -------------------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -411,6 +459,7 @@ def run_ours(args):
                        "dropped": int(n_drop), "N": N, "w_planes": Nw,
                        "hermitian_fold": fold, "stored_planes": Nst, "support": img.S,
                        "kernel": "kaiser_bessel", "index_phase": "fp64", "fov_deg": round(math.degrees(img.fov), 4),
+                       "fft": FFT_DESC[impl],
                        "tile": tuned.tile, "grid_threads": tuned.grid_threads,
                        "tiles_per_grab": tuned.tiles_per_grab, "launch_shape": "autotuned",
                        "l2": f"inputs larger than L2 (grids {8 * cells / 1e9:.1f} GB, not flushed)",
@@ -432,17 +481,18 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": res["clocks"],
             "other_variant": {
-                "hermitian_fold": not fold, "stored_planes": other_cfg.stored_planes,
+                "hermitian_fold": not fold, "fft_impl": impl, "stored_planes": other_cfg.stored_planes,
                 "value": other["n_grid"] * world / (other["ms"] * 1e-3), "unit": UNIT,
                 "ms_per_step": other["ms"], "stages_ms": other["st"],
                 "steps": max(1, min(args.steps, 3)),
                 "tile": other_cfg.tile, "grid_threads": other_cfg.grid_threads,
                 "tiles_per_grab": other_cfg.tiles_per_grab},
-            "own_fft_variant": {
-                "fft_impl": "own (column pass + row pass fused with the reduction)",
+            "reach": res["reach"],
+            "fft_variant": {
+                "fft_impl": FFT_DESC[alt_impl],
                 "hermitian_fold": fold,
-                "value": own_fft["n_grid"] * world / (own_fft["ms"] * 1e-3), "unit": UNIT,
-                "ms_per_step": own_fft["ms"], "stages_ms": own_fft["st"],
+                "value": alt["n_grid"] * world / (alt["ms"] * 1e-3), "unit": UNIT,
+                "ms_per_step": alt["ms"], "stages_ms": alt["st"],
                 "steps": max(1, min(args.steps, 3))},
         }
         if not args.no_cpu_baseline:
@@ -1064,9 +1114,10 @@ def run_profile_small(args):
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
     grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
     A step images the 2 channels and then predicts visibilities from the
-    dirty images (the degridding path); --fft own uses the library's own
-    transform (column pass + row pass fused with the reduction for imaging,
-    column + row passes for prediction) instead of cuFFT.  Runs warm-up + steps steps and
+    dirty images (the degridding path); --fft own (default) uses sparse
+    gridding and the library's own transform (pruned column pass + row pass
+    fused with the reduction for imaging, column + row passes for prediction),
+    --fft cufft full gridding and cuFFT.  Runs warm-up + steps steps and
     prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
@@ -1091,7 +1142,7 @@ def run_profile_small(args):
     def step():
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)
-        plan.grid_binned(0, C, 0, ns, grids)
+        plan.grid_binned(0, C, 0, ns, grids, sparse=args.fft == "own")
         if args.fft == "own":   # column pass, then rows fused with the reduction (pruned)
             plan.fft_wplanes_columns(grids, 0, C, 0, ns, gridded_by_plan=True)
             plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image, gridded_by_plan=True)
@@ -1136,8 +1187,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fft", default="cufft", choices=["cufft", "own"],
-                    help="2-D DFT of the profile_small workload (the headline times both)")
+    ap.add_argument("--fft", default="own", choices=["cufft", "own"],
+                    help="2-D DFT of the headline step and of profile_small "
+                         "(the headline also times the other one)")
     ap.add_argument("--no-fold", action="store_true",
                     help="headline without the Hermitian fold (all Nw planes stored and "
                          "transformed); the other variant is always measured beside it")

@@ -220,6 +220,19 @@ rick_status rick_bin(rick_plan* plan, const double* uvw, const double* chan_scal
 rick_status rick_grid_binned(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
                              int32_t plane_begin, int32_t plane_end, float* grids, void* stream);
 
+/* rick_grid_binned without the zero fill: the tiles (tile x tile cells) that
+ * no binned visibility reaches are not written and keep whatever grids held.
+ * Such planes are complete only for the calls that take them with
+ * RICK_GRIDDED_BY_PLAN on a plan with the library's own transform, which
+ * read every unreached tile as zero without touching it; pass them to
+ * nothing else (cuFFT, rick_phase_correct_reduce and the plain transform
+ * calls read every cell).  On the sparse coverage of a real array most tiles
+ * of most planes are unreached, so this writes a fraction of the plane bytes.
+ * RICK_ERR_UNSUPPORTED without the own transform; otherwise as
+ * rick_grid_binned (Eq. 3). */
+rick_status rick_grid_binned_sparse(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
+                                    int32_t plane_begin, int32_t plane_end, float* grids, void* stream);
+
 /* The imaging weights W'[nrow][C] (device, f32) that rick_bin grids with:
  * the data weights for natural weighting, else uniform or Briggs weights of
  * the plan's configuration (see rick_weighting); visibilities that are not
@@ -270,11 +283,13 @@ rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t
 /* flags of the transform calls:
  * RICK_GRIDDED_BY_PLAN -- grids holds the planes [plane_begin, plane_end) of
  *   channels [chan_begin, chan_end) exactly as the preceding rick_grid_binned
- *   of this plan's current binning wrote them.  With the library's own
- *   transform the calls then prune: the column pass skips the tile columns
- *   (tile-wide bands of columns) that no visibility reached, and the row pass
- *   the planes that no visibility reached (both hold zeros and transform to
- *   zeros).  Ignored with cuFFT. */
+ *   or rick_grid_binned_sparse of this plan's current binning wrote them.
+ *   With the library's own transform the calls then prune: every tile that
+ *   no visibility reached is taken as zero and never read; the column pass
+ *   skips the tile columns (tile-wide bands of columns) that no visibility
+ *   reached, the row pass the planes that no visibility reached and the
+ *   unreached tile columns of the others (zeros transform to zeros).
+ *   Ignored with cuFFT. */
 #define RICK_GRIDDED_BY_PLAN 1
 
 /* The two passes of rick_fft_phase_correct_reduce with the library's own

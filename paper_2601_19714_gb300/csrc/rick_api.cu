@@ -189,6 +189,7 @@ struct rick_plan {
     float2* d_twid = nullptr;
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
     uint8_t* d_planeocc = nullptr;
+    uint32_t* d_tileocc = nullptr;   // [C][planes][NT][ceil(NT/32)] tile bits
     // w-kernel: tap polynomials and the constants of its transform C_w
     float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
     double w_c0 = 1.0, w_s_i0 = 1.0;
@@ -207,6 +208,7 @@ void release(rick_plan* P) {
     dfree(P->d_twid);
     dfree(P->d_colocc);
     dfree(P->d_planeocc);
+    dfree(P->d_tileocc);
     dfree(P->d_density);
     dfree(P->d_wmom);
     dfree(P->d_wbuf);
@@ -456,6 +458,8 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
         RK_CUDA(cudaMalloc(&P->d_colocc, (size_t)c.n_channels * P->planes * P->NT));
         RK_CUDA(cudaMalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
+        RK_CUDA(cudaMalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
+                                              ((P->NT + 31) / 32)));
         return RICK_OK;   // no cuFFT plans
     }
     const size_t plane_bytes = (size_t)P->Ng * P->Ng * sizeof(float2);
@@ -577,7 +581,10 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
     return RICK_OK;
 }
 
-rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids, cudaStream_t st) {
+// sparse: tiles no record reaches are not written (only for the pruned own
+// transform, which never reads them)
+rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids, cudaStream_t st,
+                      bool sparse = false) {
     const rick_config& c = P->cfg;
     RK_ARG(P->binned && !P->binned_for_predict, "rick_bin must precede gridding");
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -609,6 +616,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.lists = P->d_lists;
     G.list_cap = P->list_cap;
     G.w_support = 0;
+    G.skip_empty = sparse ? 1 : 0;
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, 8 * sizeof(uint32_t), st));
     int launches = 0;
@@ -721,10 +729,24 @@ rick_status occupancy_impl(rick_plan* P, int c0, int c1, int k0, int k1, cudaStr
            "RICK_GRIDDED_BY_PLAN needs the plan's binning for gridding (rick_bin)");
     int launches = 0;
     rick_status s = check_launch(launch_occupancy(P->d_offsets, c0, c1 - c0, k0, k1 - k0, P->planes, P->NT,
-                                                  P->d_colocc, P->d_planeocc, st, &launches),
+                                                  P->d_colocc, P->d_planeocc, P->d_tileocc, st, &launches),
                                  "occupancy kernel");
     P->launches += launches;
     return s;
+}
+
+// The occupancy masks of the last occupancy_impl.
+Occupancy plan_occupancy(const rick_plan* P) {
+    Occupancy o;
+    o.col = P->d_colocc;
+    o.plane = P->d_planeocc;
+    o.tile = P->d_tileocc;
+    int sh = 0;
+    while ((1 << sh) < P->T) ++sh;
+    o.tshift = sh;
+    o.NT = P->NT;
+    o.words = (P->NT + 31) / 32;
+    return o;
 }
 
 // Pass 1 of the own transform (inverse DFT down every column), in place.
@@ -740,12 +762,10 @@ rick_status columns_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int
     RK_ARG(grids != nullptr, "grids is NULL");
     RK_ARG(((uintptr_t)grids & 15u) == 0, "grids must be 16-byte aligned");
     P->last_stream = st;
-    OccMask occ;
+    Occupancy occ;
     if (flags & RICK_GRIDDED_BY_PLAN) {
         RK_TRY(occupancy_impl(P, c0, c1, k0, k1, st));
-        occ.col = P->d_colocc;
-        occ.T = P->T;
-        occ.NT = P->NT;
+        occ = plan_occupancy(P);
     }
     int launches = 0;
     rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids),
@@ -779,7 +799,7 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
                                                           weight_sum + c0, P->d_inv_taper, P->d_twid,
                                                           image_real,
                                                           reinterpret_cast<float2*>(image_complex),
-                                                          (flags & RICK_GRIDDED_BY_PLAN) ? P->d_planeocc : nullptr,
+                                                          (flags & RICK_GRIDDED_BY_PLAN) ? plan_occupancy(P) : Occupancy{},
                                                           st, &launches),
                                  "fused row FFT / phase kernel");
     P->launches += launches;
@@ -911,7 +931,7 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
         const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
         for (int k0 = 0; k0 < P->planes; k0 += gk) {
             const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
-            RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st));
+            RK_TRY(grid_impl(P, c0, c1, k0, k1, g, st, P->own_fft));
             RK_TRY(fft_phase_impl(P, g, c0, c1, k0, k1, ws, image_real + (size_t)c0 * NN,
                                   image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st,
                                   RICK_GRIDDED_BY_PLAN));
@@ -1041,6 +1061,16 @@ rick_status rick_grid_binned(rick_plan* plan, int32_t chan_begin, int32_t chan_e
                              int32_t plane_begin, int32_t plane_end, float* grids, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
     return grid_impl(plan, chan_begin, chan_end, plane_begin, plane_end, grids, as_stream(stream));
+}
+
+rick_status rick_grid_binned_sparse(rick_plan* plan, int32_t chan_begin, int32_t chan_end,
+                                    int32_t plane_begin, int32_t plane_end, float* grids, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    if (!plan->own_fft) {
+        set_err("sparse gridding is only read by the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    return grid_impl(plan, chan_begin, chan_end, plane_begin, plane_end, grids, as_stream(stream), true);
 }
 
 rick_status rick_grid(rick_plan* plan, const double* uvw, const double* chan_scale, const float* vis,
@@ -1183,7 +1213,7 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
         RK_TRY(bin_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, d_ws, d_cnt, st));
         RK_TRY(ensure_group_grid(plan));
         float* g = reinterpret_cast<float*>(plan->d_grid);
-        RK_TRY(grid_impl(plan, 0, c.n_channels, 0, plan->planes, g, st));
+        RK_TRY(grid_impl(plan, 0, c.n_channels, 0, plan->planes, g, st, plan->own_fft));
         const int nch = c.n_channels < kHostChunks ? c.n_channels : kHostChunks;
         const size_t plane_floats = 2 * (size_t)plan->Ng * plan->Ng;
         for (int i = 0; i < nch; ++i) {

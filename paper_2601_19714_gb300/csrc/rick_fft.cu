@@ -26,17 +26,25 @@
 // thread per stage (16/R butterflies of the last radix-R stage).  Thread b
 // therefore ends with the outputs b + (N/16) j, j < 16, in registers.
 //
-// Pruning: planes made by the library's gridder are zero in every column tile
-// that no visibility reached and in every plane no visibility reached.  Given
-// the occupancy of the current binning (launch_occupancy: per plane and tile
-// column, from the bin offsets), the column pass skips the empty column tiles
-// (their DFT is zero, and they already hold zeros) and the fused row pass skips
-// the empty planes (they add nothing) -- the same result with less work.
+// Pruning: planes made by the library's gridder are zero in every tile that no
+// visibility reached (or, when the gridder skipped the zero fill, unwritten
+// there).  Given the occupancy of the current binning (launch_occupancy: per
+// plane, tile column and tile, from the bin offsets), the column pass skips
+// the unreached tile columns (their DFT is zero) and reads the unreached tiles
+// of the others as zeros, and the fused row pass skips the unreached planes
+// and reads the unreached tile columns as zeros (the column pass left them
+// untouched) -- the same result as the full transform of the zero-filled
+// planes, with less work, and no read of a cell the gridder may have skipped.
 //
 // Shared arrays are indexed through skew(a) = a + a/16, which spreads the
-// stride-16 stores of the first stages over all banks.  Twiddles come from two
-// tables of e^(+2 pi i e/N) rounded from FP64 on the host, e = 64 eh + el:
-// W = T_hi[eh] T_lo[el] (conjugated for the forward transform).
+// stride-16 stores of the first stages over all banks.  Twiddles: a radix-16
+// stage with M = 16^s needs W^(e f0), f0 = 1..15, e = t1 M, for the thread's
+// butterfly t1.  A per-stage table, rounded from FP64 on the host, holds
+// W^e, W^2e, W^4e and W^8e for every t1 (e^(+2 pi i e/N); conjugated for the
+// forward transform); the other eleven powers are products of at most three
+// of them (W^7e = W^4e W^2e W^e, W^15e = W^8e W^7e).  A CTA copies the tables
+// into shared memory once: four table reads per stage and thread instead of
+// one per twiddle.
 #include <cmath>
 #include <vector>
 
@@ -148,54 +156,70 @@ struct Shape {
     static constexpr int kR16 = LOG2N / 4;            // radix-16 stages
     static constexpr int kLastR = 1 << (LOG2N % 4);   // 1: the last stage is radix 16
     static constexpr int kArray = N + N / 16;         // skewed array length
-    static constexpr int kHi = N / 64;                // twiddle tables
-    static constexpr int kTw = kHi + 64;
+    // radix-16 stages with twiddles (all but a last radix-16 stage)
+    static constexpr int kTwStages = kLastR == 1 ? kR16 - 1 : kR16;
+    // butterfly groups t1 of stage s, and the offset of its table (4 entries per t1)
+    __host__ __device__ static constexpr int stage_cnt(int s) { return (N / 16) >> (4 * s); }
+    __host__ __device__ static constexpr int stage_off(int s) {
+        int o = 0;
+        for (int i = 0; i < s; ++i) o += 4 * stage_cnt(i);
+        return o;
+    }
+    static constexpr int kTw = stage_off(kTwStages);  // twiddle table entries
     static_assert(LOG2N >= 8 && LOG2N <= 13, "256 <= N <= 8192");
 };
 
-// W_N^e (e < N) from the two tables, conjugated for the forward transform
-template <bool INV>
-__device__ __forceinline__ float2 twiddle(const float2* th, const float2* tl, int e) {
-    float2 w = cmulf(th[e >> 6], tl[e & 63]);
-    if (!INV) w.y = -w.y;
-    return w;
-}
-
-// Radix-16 stage with M = 2^log2M (not the last stage): a holds the butterfly's
-// inputs u + (N/16) t2 for u = b; the DFT, twiddles W_N^(t1 f0 M) and the
-// stores t1 16 M + g + M f0 into buf.
+// Radix-16 stage s (M = 16^s, not the last stage): a holds the butterfly's
+// inputs u + (N/16) t2 for u = b; the DFT, the twiddles W_N^(t1 f0 M) from the
+// stage's table sw (sw[j cnt + t1] = W^(2^j t1 M), j < 4) and the stores
+// t1 16 M + g + M f0 into buf.
 template <int LOG2N, bool INV>
-__device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int log2M, float2* buf,
-                                            const float2* th, const float2* tl) {
+__device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float2* buf,
+                                            const float2* tw) {
+    using Sh = Shape<LOG2N>;
     Dft<16, INV>::run(a);
+    const int log2M = 4 * s;
     const int M = 1 << log2M;
     const int t1 = b >> log2M, g = b & (M - 1);
     const int base = (t1 << (log2M + 4)) + g;
-    buf[skew(base)] = a[0];
-    if (t1 == 0) {
-#pragma unroll
-        for (int f0 = 1; f0 < 16; ++f0) buf[skew(base + M * f0)] = a[f0];
-    } else {
-        const int e1 = t1 << log2M;
-#pragma unroll
-        for (int f0 = 1; f0 < 16; ++f0)
-            buf[skew(base + M * f0)] = cmulf(a[f0], twiddle<INV>(th, tl, e1 * f0));
+    // t1 = 0: the table holds W^0 = 1 exactly, and a * 1 = a exactly
+    const int cnt = Sh::stage_cnt(s);
+    const float2* sw = tw + Sh::stage_off(s) + t1;
+    float2 w[16];
+    w[1] = sw[0];
+    w[2] = sw[cnt];
+    w[4] = sw[2 * cnt];
+    w[8] = sw[3 * cnt];
+    if (!INV) {
+        w[1].y = -w[1].y;
+        w[2].y = -w[2].y;
+        w[4].y = -w[4].y;
+        w[8].y = -w[8].y;
     }
+    w[3] = cmulf(w[2], w[1]);
+    w[5] = cmulf(w[4], w[1]);
+    w[6] = cmulf(w[4], w[2]);
+    w[7] = cmulf(w[4], w[3]);
+#pragma unroll
+    for (int f0 = 9; f0 < 16; ++f0) w[f0] = cmulf(w[8], w[f0 - 8]);
+    buf[skew(base)] = a[0];
+#pragma unroll
+    for (int f0 = 1; f0 < 16; ++f0) buf[skew(base + M * f0)] = cmulf(a[f0], w[f0]);
 }
 
 // The middle radix-16 stages (all but the first, which starts from registers,
 // and the last) on buf, in place: loads, barrier, compute and stores, barrier.
 template <int LOG2N, bool INV>
-__device__ __forceinline__ void middle_stages(float2* buf, int b, const float2* th, const float2* tl) {
+__device__ __forceinline__ void middle_stages(float2* buf, int b, const float2* tw) {
     using Sh = Shape<LOG2N>;
-    constexpr int kMiddle = Sh::kLastR == 1 ? Sh::kR16 - 2 : Sh::kR16 - 1;
+    constexpr int kMiddle = Sh::kTwStages - 1;
 #pragma unroll
     for (int s = 1; s <= kMiddle; ++s) {
         float2 a[16];
 #pragma unroll
         for (int t2 = 0; t2 < 16; ++t2) a[t2] = buf[skew(b + Sh::T * t2)];
         __syncthreads();
-        radix16_out<LOG2N, INV>(a, b, 4 * s, buf, th, tl);
+        radix16_out<LOG2N, INV>(a, b, s, buf, tw);
         __syncthreads();
     }
 }
@@ -224,17 +248,17 @@ __device__ __forceinline__ void last_stage(const float2* buf, int b, float2 (&x)
 // are in registers; on return x[j] = X[b + T j].  buf is free on entry and
 // holds the last stage's input on return (a barrier is needed before reuse).
 template <int LOG2N, bool INV>
-__device__ __forceinline__ void transform(float2 (&a)[16], float2* buf, int b, const float2* th,
-                                          const float2* tl, float2 (&x)[16]) {
-    radix16_out<LOG2N, INV>(a, b, 0, buf, th, tl);
+__device__ __forceinline__ void transform(float2 (&a)[16], float2* buf, int b, const float2* tw,
+                                          float2 (&x)[16]) {
+    radix16_out<LOG2N, INV>(a, b, 0, buf, tw);
     __syncthreads();
-    middle_stages<LOG2N, INV>(buf, b, th, tl);
+    middle_stages<LOG2N, INV>(buf, b, tw);
     last_stage<LOG2N, INV>(buf, b, x);
 }
 
 template <int LOG2N>
-__device__ __forceinline__ void load_tables(const float2* __restrict__ twid, float2* th, int tid, int nthreads) {
-    for (int i = tid; i < Shape<LOG2N>::kTw; i += nthreads) th[i] = __ldg(twid + i);
+__device__ __forceinline__ void load_tables(const float2* __restrict__ twid, float2* tw, int tid, int nthreads) {
+    for (int i = tid; i < Shape<LOG2N>::kTw; i += nthreads) tw[i] = __ldg(twid + i);
 }
 
 // ---- pass 1: columns ----------------------------------------------------------
@@ -244,28 +268,37 @@ __device__ __forceinline__ void load_tables(const float2* __restrict__ twid, flo
 // transformed, and written back the same way.
 template <int LOG2N, int COLS, bool INV>
 __global__ void __launch_bounds__(COLS * (1 << LOG2N) / 16)
-k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, OccMask occ, int64_t plane0) {
+k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, Occupancy occ, int64_t plane0) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
+    // tile rows of this column tile that a record reaches (tiles are >= 16 wide)
+    __shared__ uint8_t s_live[N / 16];
+    const int64_t pl = plane0 + blockIdx.y;
+    const int tcol = (int)(blockIdx.x * COLS) >> occ.tshift;
     // a column tile that no visibility reached is zero: skip it
-    if (occ.col != nullptr &&
-        occ.col[(plane0 + blockIdx.y) * occ.NT + (int)(blockIdx.x * COLS) / occ.T] == 0)
-        return;
+    if (occ.col != nullptr && occ.col[pl * occ.NT + tcol] == 0) return;
     constexpr int kThreads = COLS * T;
     constexpr int kVec = COLS / 2;   // 16-byte pieces per row
     extern __shared__ __align__(16) float2 fsm[];
-    float2* th = fsm;
-    float2* tl = th + Sh::kHi;
+    float2* tw = fsm;
     float2* arrays = fsm + Sh::kTw;
     const int tid = threadIdx.x;
     const int c = tid / T, b = tid - c * T;
     float2* buf = arrays + c * Sh::kArray;
     float2* plane = grids + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * COLS;
-    load_tables<LOG2N>(twid, th, tid, kThreads);
+    load_tables<LOG2N>(twid, tw, tid, kThreads);
+    if (occ.tile != nullptr) {
+        for (int ty = tid; ty < occ.NT; ty += kThreads)
+            s_live[ty] = (uint8_t)((occ.tile[(pl * occ.NT + ty) * occ.words + (tcol >> 5)] >> (tcol & 31)) & 1u);
+        __syncthreads();
+    }
 #pragma unroll 4
     for (int e = tid; e < N * kVec; e += kThreads) {
         const int row = e / kVec, piece = e - row * kVec;
-        const float4 v = __ldcs(reinterpret_cast<const float4*>(plane + (size_t)row * N) + piece);
+        // an unreached tile is zero (and possibly unwritten): not read
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (occ.tile == nullptr || s_live[row >> occ.tshift])
+            v = __ldcs(reinterpret_cast<const float4*>(plane + (size_t)row * N) + piece);
         arrays[(2 * piece) * Sh::kArray + skew(row)] = make_float2(v.x, v.y);
         arrays[(2 * piece + 1) * Sh::kArray + skew(row)] = make_float2(v.z, v.w);
     }
@@ -274,7 +307,7 @@ k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, OccMa
 #pragma unroll
     for (int t2 = 0; t2 < 16; ++t2) a[t2] = buf[skew(b + T * t2)];
     __syncthreads();
-    transform<LOG2N, INV>(a, buf, b, th, tl, x);
+    transform<LOG2N, INV>(a, buf, b, tw, x);
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < 16; ++j) buf[skew(b + T * j)] = x[j];
@@ -297,17 +330,16 @@ k_fft_rows(float2* __restrict__ grids, const float2* __restrict__ twid) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
-    float2* th = fsm;
-    float2* tl = th + Sh::kHi;
+    float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
     const int b = threadIdx.x;
     float2* row = grids + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * N;
-    load_tables<LOG2N>(twid, th, b, T);
+    load_tables<LOG2N>(twid, tw, b, T);
     float2 a[16], x[16];
 #pragma unroll
     for (int t2 = 0; t2 < 16; ++t2) a[t2] = __ldcs(row + b + T * t2);
     __syncthreads();
-    transform<LOG2N, INV>(a, buf, b, th, tl, x);
+    transform<LOG2N, INV>(a, buf, b, tw, x);
 #pragma unroll
     for (int j = 0; j < 16; ++j) __stcs(row + b + T * j, x[j]);
 }
@@ -337,18 +369,17 @@ __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
 k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                     const float* __restrict__ inv_taper, const float2* __restrict__ twid,
                     float* __restrict__ image_real, float2* __restrict__ image_complex,
-                    const uint8_t* __restrict__ plane_occ) {
+                    Occupancy occ) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
-    float2* th = fsm;
-    float2* tl = th + Sh::kHi;
+    float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
     uint2* phase = reinterpret_cast<uint2*>(buf + Sh::kArray);   // (t_0, dt) per pixel
     float* scl = reinterpret_cast<float*>(phase + N);
     const int b = threadIdx.x, q = blockIdx.x;
     const int halfN = N / 2;
-    load_tables<LOG2N>(twid, th, b, T);
+    load_tables<LOG2N>(twid, tw, b, T);
 
 #pragma unroll 1
     for (int j = 0; j < 16; ++j) {
@@ -371,19 +402,30 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 
     const size_t NN = (size_t)N * N;
     const int n_rows = P.nc * P.nk;
-    // planes no visibility reached (plane_occ == 0) are skipped
+    // planes no visibility reached are skipped
     auto next_row = [&](int r) {
-        if (plane_occ != nullptr)
-            while (r < n_rows && plane_occ[r] == 0) ++r;
+        if (occ.plane != nullptr)
+            while (r < n_rows && occ.plane[r] == 0) ++r;
         return r;
+    };
+    // row q of plane r: the inputs b + T t2 of this thread; the unreached tile
+    // columns are zero (the column pass did not touch them): not read
+    auto load_row = [&](int r, float2 (&v)[16]) {
+        const float2* row = grids + (size_t)r * NN + (size_t)q * N;
+        if (occ.col != nullptr) {
+            const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2)
+                v[t2] = __ldg(cm + ((b + T * t2) >> occ.tshift)) ? __ldcs(row + b + T * t2)
+                                                                 : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) v[t2] = __ldcs(row + b + T * t2);
+        }
     };
     float2 a[16], x[16];
     int r = next_row(0);
-    if (r < n_rows) {
-        const float2* row = grids + (size_t)r * NN + (size_t)q * N;
-#pragma unroll
-        for (int t2 = 0; t2 < 16; ++t2) a[t2] = __ldcs(row + b + T * t2);
-    }
+    if (r < n_rows) load_row(r, a);
     __syncthreads();
     for (int cc = 0; cc < P.nc; ++cc) {
         float acc[16], acci[16];
@@ -391,16 +433,12 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
         for (int j = 0; j < 16; ++j) acc[j] = acci[j] = 0.f;
         for (int kk = 0; kk < P.nk; ++kk) {
             if (cc * P.nk + kk != r) continue;   // an empty plane
-            radix16_out<LOG2N, true>(a, b, 0, buf, th, tl);
+            radix16_out<LOG2N, true>(a, b, 0, buf, tw);
             const int rn = next_row(r + 1);
-            if (rn < n_rows) {
-                const float2* row = grids + (size_t)rn * NN + (size_t)q * N;
-#pragma unroll
-                for (int t2 = 0; t2 < 16; ++t2) a[t2] = __ldcs(row + b + T * t2);
-            }
+            if (rn < n_rows) load_row(rn, a);
             r = rn;
             __syncthreads();
-            middle_stages<LOG2N, true>(buf, b, th, tl);
+            middle_stages<LOG2N, true>(buf, b, tw);
             last_stage<LOG2N, true>(buf, b, x);
             __syncthreads();   // buf is rewritten by the next row's first stage
 #pragma unroll
@@ -434,32 +472,46 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 
 constexpr int kCols = 2;   // columns per CTA in pass 1
 
-// occupancy of plane p (p = cc nk + kk of the launch) and its tile columns
-// from the bin offsets: a tile column is reached if any of its tiles holds a
-// record, or a tile to its left holds a record that spills right (halo classes
-// 2 and 3; the column after the last wraps to column 0, which only the
-// Hermitian fold's mirrored footprints reach).
+// Occupancy of the planes p = cc nk + kk of the launch from the bin offsets:
+// one thread per tile (tx fastest), reached iff tile_reach() > 0 -- the
+// gridder's own test for an empty tile.  A warp's ballot is a word of the
+// tile bits (NT >= 32) or holds whole tile rows (NT < 32); col and plane are
+// zeroed beforehand and set where a tile is reached.
 __global__ void k_occupancy(const uint32_t* __restrict__ offsets, int c0, int nc, int k0, int nk,
-                            int Nw_store, int NT, uint8_t* __restrict__ col, uint8_t* __restrict__ plane) {
+                            int Nw_store, int NT, int words, uint8_t* __restrict__ col,
+                            uint8_t* __restrict__ plane, uint32_t* __restrict__ tile) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)nc * nk * NT) return;
-    const int tx = (int)(i % NT);
-    const int64_t p = i / NT;
-    const int cc = (int)(p / nk), kk = (int)(p - (int64_t)cc * nk);
-    const int txl = (tx + NT - 1) % NT;
-    const uint64_t pk = ((uint64_t)(c0 + cc) * Nw_store + (k0 + kk)) * NT;
-    uint32_t any = 0;
-    for (int ty = 0; ty < NT && !any; ++ty) {
-        const uint64_t own = ((pk + ty) * NT + tx) * 4, left = ((pk + ty) * NT + txl) * 4;
-        any |= __ldg(offsets + own + 4) - __ldg(offsets + own);     // all classes of the tile
-        any |= __ldg(offsets + left + 4) - __ldg(offsets + left + 2);  // classes 2, 3 of the left tile
+    const int64_t n = (int64_t)nc * nk * NT * NT;
+    const int lane = threadIdx.x & 31;
+    bool reached = false;
+    int tx = 0;
+    int64_t prow = 0;   // p * NT + ty
+    if (i < n) {
+        tx = (int)(i % NT);
+        prow = i / NT;
+        const int ty = (int)(prow % NT);
+        const int64_t p = prow / NT;
+        const int cc = (int)(p / nk), kk = (int)(p - (int64_t)cc * nk);
+        const uint64_t kplane = ((uint64_t)(c0 + cc) * Nw_store + (k0 + kk)) * NT;
+        reached = tile_reach(offsets, kplane, NT, ty, tx) != 0;
+        if (reached) {
+            col[(p * NT) + tx] = 1;
+            plane[p] = 1;
+        }
     }
-    col[i] = any ? 1 : 0;
-    if (any) plane[p] = 1;
+    const unsigned m = __ballot_sync(0xffffffffu, reached);
+    if (i < n) {
+        if (NT >= 32) {
+            if (lane == 0) tile[prow * words + (tx >> 5)] = m;
+        } else if (tx == 0) {
+            tile[prow] = (m >> lane) & ((1u << NT) - 1u);
+        }
+    }
 }
 
 template <int LOG2N, bool INV>
-cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, OccMask occ, cudaStream_t st) {
+cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, const Occupancy& occ,
+                        cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     auto fn = k_fft_columns<LOG2N, kCols, INV>;
     const size_t smem = (size_t)(Sh::kTw + kCols * Sh::kArray) * sizeof(float2);
@@ -490,7 +542,7 @@ cudaError_t rows_one(float2* grids, int64_t n_planes, const float2* twid, cudaSt
 
 template <int LOG2N, int PREC, bool CPLX>
 cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                      const float2* twid, float* image_real, float2* image_complex, const uint8_t* pocc,
+                      const float2* twid, float* image_real, float2* image_complex, const Occupancy& occ,
                       cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     auto fn = k_rows_phase_reduce<LOG2N, PREC, CPLX>;
@@ -498,20 +550,20 @@ cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* w
                         (size_t)Sh::N * (sizeof(uint2) + sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc);
+    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ);
     return cudaGetLastError();
 }
 
 template <int LOG2N>
 cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                    const float2* twid, float* image_real, float2* image_complex, const uint8_t* pocc,
+                    const float2* twid, float* image_real, float2* image_complex, const Occupancy& occ,
                     cudaStream_t st) {
     const bool c = image_complex != nullptr;
     if (P.precision == RICK_PREC_ALL_FP32)
-        return c ? fused_one<LOG2N, RICK_PREC_ALL_FP32, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st)
-                 : fused_one<LOG2N, RICK_PREC_ALL_FP32, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st);
-    return c ? fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st)
-             : fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, pocc, st);
+        return c ? fused_one<LOG2N, RICK_PREC_ALL_FP32, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st)
+                 : fused_one<LOG2N, RICK_PREC_ALL_FP32, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st);
+    return c ? fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st)
+             : fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st);
 }
 
 int log2_exact(int N) {
@@ -528,16 +580,21 @@ bool fft_supported(int N) {
 }
 
 void fft_twiddles(int N, std::vector<float2>& out) {
-    const int hi = N / 64;
-    out.resize((size_t)hi + 64);
+    // per radix-16 stage s with twiddles (M = 16^s, cnt = N/16/M groups t1):
+    // entries [j cnt + t1] = e^(+2 pi i 2^j t1 M / N), j < 4, from FP64
+    const int log2n = log2_exact(N);
+    const int stages = (log2n % 4 == 0) ? log2n / 4 - 1 : log2n / 4;
+    out.clear();
     const double two_pi = 6.283185307179586476925;
-    for (int i = 0; i < hi; ++i) {
-        const double a = two_pi * (64.0 * i) / N;
-        out[i] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    for (int i = 0; i < 64; ++i) {
-        const double a = two_pi * i / N;
-        out[hi + i] = make_float2((float)std::cos(a), (float)std::sin(a));
+    for (int st = 0; st < stages; ++st) {
+        const int64_t M = (int64_t)1 << (4 * st);
+        const int cnt = (int)((N / 16) / M);
+        for (int j = 0; j < 4; ++j)
+            for (int t1 = 0; t1 < cnt; ++t1) {
+                const int64_t e = ((int64_t)t1 * M) << j;   // < N/2
+                const double a = two_pi * (double)e / N;
+                out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+            }
     }
 }
 
@@ -547,8 +604,8 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
     cudaError_t e = cudaErrorInvalidValue;
 #define RICK_FFT_CASE(LG)                                                                   \
     case LG:                                                                                \
-        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, OccMask{}, st)           \
-                    : columns_one<LG, false>(grids, n_planes, twid, OccMask{}, st);         \
+        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, Occupancy{}, st)         \
+                    : columns_one<LG, false>(grids, n_planes, twid, Occupancy{}, st);       \
         if (e == cudaSuccess)                                                               \
             e = inverse ? rows_one<LG, true>(grids, n_planes, twid, st)                     \
                         : rows_one<LG, false>(grids, n_planes, twid, st);                   \
@@ -568,7 +625,7 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
 }
 
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               OccMask occ, cudaStream_t st, int* launches) {
+                               const Occupancy& occ, cudaStream_t st, int* launches) {
     if (n_planes <= 0) return cudaSuccess;
     cudaError_t e = cudaErrorInvalidValue;
 #define RICK_FFT_CASE(LG)                                                                   \
@@ -592,16 +649,16 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
 
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                      const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, const uint8_t* plane_occ, cudaStream_t st,
+                                     float2* image_complex, const Occupancy& occ, cudaStream_t st,
                                      int* launches) {
     cudaError_t e = cudaErrorInvalidValue;
     switch (log2_exact(P.N)) {
-        case 8: e = fused_n<8>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
-        case 9: e = fused_n<9>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
-        case 10: e = fused_n<10>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
-        case 11: e = fused_n<11>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
-        case 12: e = fused_n<12>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
-        case 13: e = fused_n<13>(P, grids, wsum, inv_taper, twid, image_real, image_complex, plane_occ, st); break;
+        case 8: e = fused_n<8>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        case 9: e = fused_n<9>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        case 10: e = fused_n<10>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        case 11: e = fused_n<11>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        case 12: e = fused_n<12>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        case 13: e = fused_n<13>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
         default: break;
     }
     if (e == cudaSuccess) ++*launches;
@@ -609,12 +666,15 @@ cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, 
 }
 
 cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
-                             uint8_t* col, uint8_t* plane, cudaStream_t st, int* launches) {
-    const int64_t n = (int64_t)nc * nk * NT;
+                             uint8_t* col, uint8_t* plane, uint32_t* tile, cudaStream_t st, int* launches) {
+    const int64_t n = (int64_t)nc * nk * NT * NT;
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(plane, 0, (size_t)nc * nk, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(col, 0, (size_t)nc * nk * NT, st);
     if (e != cudaSuccess) return e;
-    k_occupancy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(offsets, c0, nc, k0, nk, Nw_store, NT, col, plane);
+    const int words = (NT + 31) / 32;
+    k_occupancy<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(offsets, c0, nc, k0, nk, Nw_store, NT, words, col,
+                                                             plane, tile);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*launches;
     return cudaSuccess;

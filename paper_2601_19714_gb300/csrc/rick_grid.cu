@@ -12,7 +12,9 @@
 //     -> global, one 8T-byte copy per row) and moves on: the threads never
 //     hold the tile's output in registers and HBM writes overlap the next
 //     tile's work;
-//   * for a tile no visibility touches, copies one shared zero row T times.
+//   * for a tile no visibility touches, copies one shared zero row T times
+//     (or, with skip_empty, writes nothing: the library's pruned transforms
+//     never read such a tile).
 // So every grid cell is written exactly once (the zero fill is fused into
 // the gridder) and no global atomics are needed: a tile is owned by one CTA,
 // and the halo of neighbouring tiles is read, not written -- the binning
@@ -510,8 +512,10 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
                                    (rng[7] - rng[6]);
             if (first + t >= n3 && total >= th3) continue;  // taken from a list earlier
             if (total == 0) {
-                for (int r = lane; r < T; r += 32) bulk_row_store(out + (size_t)r * N, zrow, row_bytes);
-                bulk_commit();
+                if (!G.skip_empty) {
+                    for (int r = lane; r < T; r += 32) bulk_row_store(out + (size_t)r * N, zrow, row_bytes);
+                    bulk_commit();
+                }
                 continue;
             }
             accumulate_range<TABLE, SS>(G, records, rng, 0u, total, G.k0 + kk, buf, P, cf, stg4, stg_ij, stg_corr);

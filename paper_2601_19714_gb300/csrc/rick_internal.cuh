@@ -95,8 +95,30 @@ struct GridParams {
     uint32_t* lists;
     uint32_t list_cap;
     int w_support;        // prediction: >= 2 accumulates the Sw partial predictions
+    // 1: tiles that no record reaches are not written (the zero fill is left
+    // out); the planes are then only valid where tile_reach() > 0
+    int skip_empty;
     float coef[kMaxSupport][kPolyDegree + 1];
 };
+
+// Records that reach tile (ty, tx) of a plane, kplane = (channel * planes +
+// plane) * NT (the plane's bin keys start at kplane * NT * 4, keys as in the
+// layout above): those of the tile's own bins (every halo class) and the
+// spilling classes of its left (2, 3), upper (1, 2) and upper-left (2)
+// neighbours, which wrap around the mesh (only the Hermitian fold's mirrored
+// footprints spill out of the last row or column).  These are the eight bin
+// bounds the gridder reads for a tile; zero means the gridder finds no
+// record for it.
+__device__ __forceinline__ uint32_t tile_reach(const uint32_t* __restrict__ offsets, uint64_t kplane,
+                                               int NT, int ty, int tx) {
+    const int txl = tx > 0 ? tx - 1 : NT - 1, tyu = ty > 0 ? ty - 1 : NT - 1;
+    const uint64_t own = ((kplane + ty) * NT + tx) * 4u, left = ((kplane + ty) * NT + txl) * 4u;
+    const uint64_t up = ((kplane + tyu) * NT + tx) * 4u, ul = ((kplane + tyu) * NT + txl) * 4u;
+    return (__ldg(offsets + own + 4) - __ldg(offsets + own)) +
+           (__ldg(offsets + left + 4) - __ldg(offsets + left + 2)) +
+           (__ldg(offsets + up + 3) - __ldg(offsets + up + 1)) +
+           (__ldg(offsets + ul + 3) - __ldg(offsets + ul + 2));
+}
 
 // Entries per longest-first list for a plan binning up to max_vis
 // visibilities with tile side T: a record is counted by at most 4 tiles (its
@@ -203,27 +225,38 @@ void fft_twiddles(int N, std::vector<float2>& out);
 // In place, unnormalised, over n_planes planes [N][N]: columns then rows.
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
                          cudaStream_t stream, int* launches);
-// Occupancy of gridded planes, for pruning: col[p * NT + tx] != 0 if tile
-// column tx of plane p (of the launch) may be non-zero, T its width; null col:
-// no pruning.
-struct OccMask {
+// Occupancy of gridded planes, for pruning (plane p of the launch, tiles of
+// side T = 1 << tshift, NT per side):
+//   col[p * NT + tx] != 0 if tile column tx of plane p is reached by a record,
+//   plane[p] != 0 if any tile of plane p is,
+//   tile[(p * NT + ty) * words + tx / 32] bit tx % 32: tile (ty, tx) is reached
+//   (words = ceil(NT / 32)).
+// A tile no record reaches is zero in the gridder's output (or, with
+// skip_empty, unwritten), so the transforms treat it as zero without reading
+// it.  Null pointers: no pruning.
+struct Occupancy {
     const uint8_t* col = nullptr;
-    int T = 1, NT = 1;
+    const uint8_t* plane = nullptr;
+    const uint32_t* tile = nullptr;
+    int tshift = 0, NT = 1, words = 1;
 };
-// col[nc * nk * NT] and plane[nc * nk] from the bin offsets of the plan's
-// binning (channels [c0, c0 + nc), stored planes [k0, k0 + nk)).
+// The three masks of the launch's planes (channels [c0, c0 + nc), stored
+// planes [k0, k0 + nk)) from the bin offsets of the plan's binning.
 cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
-                             uint8_t* col, uint8_t* plane, cudaStream_t stream, int* launches);
+                             uint8_t* col, uint8_t* plane, uint32_t* tile, cudaStream_t stream,
+                             int* launches);
 // Pass 1 alone (the inverse DFT down every column), in place; with occ, the
-// empty column tiles are skipped.
+// unreached column tiles are skipped and the unreached tiles of the others
+// read as zeros.
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               OccMask occ, cudaStream_t stream, int* launches);
+                               const Occupancy& occ, cudaStream_t stream, int* launches);
 // Pass 2 fused with the phase screen and reduction: grids must hold the
 // column-transformed planes [nc][nk][N][N]; image_real [nc][N][N] (+=).
-// plane_occ (nullable): planes of the launch with plane_occ == 0 are skipped.
+// With occ, unreached planes are skipped and unreached tile columns read as
+// zeros (the column pass left them untouched).
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
                                      const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, const uint8_t* plane_occ, cudaStream_t stream,
+                                     float2* image_complex, const Occupancy& occ, cudaStream_t stream,
                                      int* launches);
 
 // learned kernel network (rick_mlp.cu)

@@ -211,6 +211,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         G.lists = nullptr;  // natural tile order (no scheduling scratch)
         G.list_cap = 0;
         G.w_support = 0;
+        G.skip_empty = 0;
         G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 8 ? (uint32_t)c.tiles_per_grab : 4u;
         e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
                         num_sms, st, &launches);

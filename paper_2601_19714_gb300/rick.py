@@ -28,7 +28,8 @@ GRIDDED_BY_PLAN = 1             # transform flag: the planes are this plan's gri
 WEIGHTINGS = {"natural": 0, "uniform": 1, "briggs": 2}
 
 EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_plan_taper",
-           "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid",
+           "rick_set_kernel_table", "rick_bin", "rick_grid_binned", "rick_grid_binned_sparse",
+           "rick_grid",
            "rick_fft_wplanes", "rick_phase_correct_reduce", "rick_fft_phase_correct_reduce",
            "rick_fft_wplanes_columns", "rick_rows_phase_correct_reduce", "rick_imaging_weights",
            "rick_dirty_image",
@@ -85,6 +86,7 @@ def load(path: str = LIB_PATH):
         "rick_set_kernel_table": [p, p, i32, p],
         "rick_bin": [p, p, p, p, p, p, i64, p, p, p],
         "rick_grid_binned": [p, i32, i32, i32, i32, p, p],
+        "rick_grid_binned_sparse": [p, i32, i32, i32, i32, p, p],
         "rick_grid": [p, p, p, p, p, p, i64, i32, i32, p, p, p, p],
         "rick_fft_wplanes": [p, p, i64, p],
         "rick_phase_correct_reduce": [p, p, i32, i32, i32, i32, p, p, p, p],
@@ -296,6 +298,17 @@ class Plan:
                                 rec.ctypes.data), "rick_plan_bins")
         return off, rec[:nr.value]
 
+    def bin_offsets(self):
+        """The bin offsets of the current binning (host numpy u32 [n_keys + 1])."""
+        import numpy as np
+        L = load()
+        nk, nr = C.c_int64(), C.c_int64()
+        _check(L.rick_plan_bins(self.handle, C.byref(nk), C.byref(nr), None, None), "rick_plan_bins")
+        off = np.zeros(nk.value + 1, np.uint32)
+        _check(L.rick_plan_bins(self.handle, C.byref(nk), C.byref(nr), off.ctypes.data, None),
+               "rick_plan_bins")
+        return off
+
     # ---- the hot path -------------------------------------------------------
     def _vis_args(self, uvw, chan_scale, vis, weight, flag):
         d = _dt()
@@ -309,11 +322,15 @@ class Plan:
                                int(nrow), _ptr(weight_sum, d["f64"], "weight_sum", 8),
                                _ptr(counts, d["i64"], "counts", 8), _stream(stream)), "rick_bin")
 
-    def grid_binned(self, chan_begin, chan_end, plane_begin, plane_end, grids, stream=None):
+    def grid_binned(self, chan_begin, chan_end, plane_begin, plane_end, grids, stream=None,
+                    sparse=False):
+        """rick_grid_binned, or rick_grid_binned_sparse with sparse=True (the
+        unreached tiles are left unwritten: for the pruned own transform only)."""
         d = _dt()
-        _check(load().rick_grid_binned(self.handle, chan_begin, chan_end, plane_begin, plane_end,
-                                       _ptr(grids, d["c64"], "grids", 16), _stream(stream)),
-               "rick_grid_binned")
+        fn = load().rick_grid_binned_sparse if sparse else load().rick_grid_binned
+        _check(fn(self.handle, chan_begin, chan_end, plane_begin, plane_end,
+                  _ptr(grids, d["c64"], "grids", 16), _stream(stream)),
+               "rick_grid_binned_sparse" if sparse else "rick_grid_binned")
 
     def grid(self, uvw, chan_scale, vis, weight, flag, nrow, plane_begin, plane_end, grids,
              weight_sum, counts=None, stream=None):

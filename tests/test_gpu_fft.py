@@ -213,6 +213,53 @@ def test_pruned_transform_is_exactly_the_unpruned_one(rk, kw):
     np.testing.assert_array_equal(ic.cpu().numpy(), idd.cpu().numpy())
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(hermitian_fold=True), dict(tile=16), dict(tile=64),
+                                dict(hermitian_fold=True, w_support=4, w_kernel_param=8.0)])
+def test_sparse_gridding_writes_exactly_the_reached_tiles(rk, kw):
+    """rick_grid_binned_sparse into planes filled with NaN: every tile is either
+    written exactly as rick_grid_binned writes it or left NaN, and a tile left
+    NaN is all zero in the fully written planes; the pruned transform of the
+    NaN-filled sparse planes (split and fused calls) gives the image of the
+    unpruned transform of the full planes bit for bit -- no unreached cell is
+    ever read (a read would carry NaN into the image)."""
+    import torch
+    img, obs = meerkat(86, n_ant=8, n_steps=30, nchan=3, N=1024, Nw=24, n_src=10)
+    x = obs.uvw[:, :2] * obs.chan_scale.max() * img.fov
+    obs.uvw[:, :2] *= 0.3 * img.N / np.abs(x).max()      # footprints in the central 60 %
+    dev = to_device(obs)
+    C, N = 3, img.N
+    cfg = plan_config(img, C, fft_impl="own", **kw)
+    plan, full, wsum = _gridded(rk, cfg, dev, C)
+    ns = cfg.stored_planes
+    sp = torch.full_like(full, float("nan"))
+    plan.grid_binned(0, C, 0, ns, sp, sparse=True)
+    torch.cuda.synchronize()
+    T = cfg.tile or 32
+    f = full.cpu().numpy().reshape(C, ns, N // T, T, N // T, T)
+    g = sp.cpu().numpy().reshape(C, ns, N // T, T, N // T, T)
+    nan_tile = np.isnan(g.real).all(axis=(3, 5))
+    assert (np.isnan(g.real).any(axis=(3, 5)) == nan_tile).all()   # tiles are whole
+    written = ~nan_tile
+    assert (f.transpose(0, 1, 2, 4, 3, 5)[written] == g.transpose(0, 1, 2, 4, 3, 5)[written]).all()
+    assert (f.transpose(0, 1, 2, 4, 3, 5)[nan_tile] == 0).all()
+    print(kw, "unreached tiles", nan_tile.mean())
+    assert 0.3 < nan_tile.mean() < 1.0
+    for fused in (True, False):
+        a, b = full.clone(), sp.clone()
+        ia = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+        ib = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+        plan.fft_phase_correct_reduce(a, 0, C, 0, ns, wsum, ia)
+        if fused:
+            plan.fft_phase_correct_reduce(b, 0, C, 0, ns, wsum, ib, gridded_by_plan=True)
+        else:
+            plan.fft_wplanes_columns(b, 0, C, 0, ns, gridded_by_plan=True)
+            plan.rows_phase_correct_reduce(b, 0, C, 0, ns, wsum, ib, gridded_by_plan=True)
+        torch.cuda.synchronize()
+        got = ib.cpu().numpy()
+        assert np.isfinite(got).all()
+        np.testing.assert_array_equal(got, ia.cpu().numpy())
+
+
 def test_pruning_needs_the_plans_gridding_binning(rk):
     import torch
     img, obs = tiny_wstack(85, nvis=500, N=256)
@@ -227,4 +274,9 @@ def test_pruning_needs_the_plans_gridding_binning(rk):
     cu = rk.Plan(plan_config(img, 1))
     with pytest.raises(rk.RickError) as e:   # the split passes need the own transform
         cu.fft_wplanes_columns(grids, 0, 1, 0, img.Nw)
+    assert e.value.status == 6
+    cu.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], dev["nrow"],
+           torch.empty(1, dtype=torch.float64, device="cuda"))
+    with pytest.raises(rk.RickError) as e:   # and so does sparse gridding
+        cu.grid_binned(0, 1, 0, img.Nw, grids, sparse=True)
     assert e.value.status == 6
