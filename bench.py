@@ -532,7 +532,7 @@ def run_lofar(args):
     dev = _dev_inputs(obs)
     base = rick.Config(N=N, n_wplanes=Nw, support=img.S, n_channels=C, fov_rad=img.fov,
                        w_min=img.w_min, w_max=img.w_max, kernel="kb", kernel_param=img.kernel_param,
-                       hermitian_fold=not args.no_fold)
+                       hermitian_fold=not args.no_fold, fft_impl=args.fft)
     ns = base.stored_planes
     g2 = torch.empty((2, ns, N, N), dtype=torch.complex64, device="cuda")
     t0 = time.perf_counter()
@@ -572,10 +572,14 @@ def run_lofar(args):
     a.record()
     image.zero_()
     plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow, wsum)
+    own = args.fft == "own"
     for c in range(C):
-        plan.grid_binned(c, c + 1, 0, ns, g1)
-        plan.fft_wplanes(g1, ns)
-        plan.phase_correct_reduce(g1, c, c + 1, 0, ns, wsum, image[c])
+        plan.grid_binned(c, c + 1, 0, ns, g1, sparse=own)
+        if own:
+            plan.fft_phase_correct_reduce(g1, c, c + 1, 0, ns, wsum, image[c], gridded_by_plan=True)
+        else:
+            plan.fft_wplanes(g1, ns)
+            plan.phase_correct_reduce(g1, c, c + 1, 0, ns, wsum, image[c])
     b.record()
     torch.cuda.synchronize()
     ms_per_channel = a.elapsed_time(b)
@@ -590,7 +594,7 @@ def run_lofar(args):
                    "channel_flag_fractions_min_max": [float(obs.flag.mean(0).min()),
                                                       float(obs.flag.mean(0).max())],
                    "N": N, "w_planes": Nw, "hermitian_fold": cfg.hermitian_fold,
-                   "stored_planes": ns, "grid_budget_gb": 160,
+                   "stored_planes": ns, "grid_budget_gb": 160, "fft": FFT_DESC[args.fft],
                    "l2": "inputs larger than L2"},
         "graph": {"ms_per_step": ms_graph, "vis_per_s": n_grid / (ms_graph * 1e-3),
                   "kernels_per_launch": launches // max(1, args.steps)},
@@ -1112,7 +1116,8 @@ def run_profile_small(args):
     """A small case of the default workload for ncu captures: the MeerKAT
     recipe with 2 channels (856 and 1712 MHz), 500 time steps (2 M
     visibilities), 4096^2 grid, 8 w-planes (4 stored with the fold, 1 GB of
-    grids: larger than L2), Kaiser-Bessel S = 8, launch shape 32/128/4.
+    grids: larger than L2; --profile-planes sets the count), Kaiser-Bessel
+    S = 8, launch shape 32/128/4.
     A step images the 2 channels and then predicts visibilities from the
     dirty images (the degridding path); --fft own (default) uses sparse
     gridding and the library's own transform (pruned column pass + row pass
@@ -1123,7 +1128,7 @@ def run_profile_small(args):
     from paper_2601_19714_gb300 import _build, rick
     from visgen.workloads import meerkat
     _build.build()
-    img, obs = meerkat(args.seed, n_steps=500, nchan=2, N=4096, Nw=8, device="cuda")
+    img, obs = meerkat(args.seed, n_steps=500, nchan=2, N=4096, Nw=args.profile_planes, device="cuda")
     dev = _dev_inputs(obs)
     C, N = obs.nchan, img.N
     cfg = rick.Config(N=N, n_wplanes=img.Nw, support=img.S, n_channels=C, fov_rad=img.fov,
@@ -1171,7 +1176,7 @@ def run_profile_small(args):
     print(json.dumps({"metric": METRIC, "value": n_grid / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "impl": "ours", "config": {"workload": "meerkat_small_4096sq_8w_2ch_kb8",
+                      "impl": "ours", "config": {"workload": f"meerkat_small_4096sq_{img.Nw}w_2ch_kb8",
                                                  "visibilities": int(obs.nrow * C),
                                                  "gridded": n_grid, "hermitian_fold": cfg.hermitian_fold,
                                                  "stored_planes": ns, "tile": 32, "fft": args.fft,
@@ -1199,6 +1204,9 @@ def main():
                     help="meerkat (default bench line); lofar / learned / large measure the "
                          "batched, learned-kernel and precision-stress workloads; "
                          "profile_small is the small case the ncu captures use")
+    ap.add_argument("--profile-planes", type=int, default=8,
+                    help="w-planes of the profile_small workload (8: 1 GB of grids with the fold; "
+                         "32: 4.3 GB, 16 planes per channel as in the headline's row pass)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -190,12 +190,17 @@ struct rick_plan {
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
     uint8_t* d_planeocc = nullptr;
     uint32_t* d_tileocc = nullptr;   // [C][planes][NT][ceil(NT/32)] tile bits
+    uint2* d_pix_turns = nullptr;    // fused row pass: per-pixel turns and scale [N][N]
+    float* d_pix_scale = nullptr;
     // w-kernel: tap polynomials and the constants of its transform C_w
     float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
     double w_c0 = 1.0, w_s_i0 = 1.0;
 };
 
 namespace {
+
+PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1);
+
 
 template <class T>
 void dfree(T*& p) {
@@ -209,6 +214,8 @@ void release(rick_plan* P) {
     dfree(P->d_colocc);
     dfree(P->d_planeocc);
     dfree(P->d_tileocc);
+    dfree(P->d_pix_turns);
+    dfree(P->d_pix_scale);
     dfree(P->d_density);
     dfree(P->d_wmom);
     dfree(P->d_wbuf);
@@ -460,6 +467,12 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(cudaMalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
         RK_CUDA(cudaMalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
                                               ((P->NT + 31) / 32)));
+        const size_t NN = (size_t)c.N * c.N;
+        RK_CUDA(cudaMalloc(&P->d_pix_turns, sizeof(uint2) * NN));
+        RK_CUDA(cudaMalloc(&P->d_pix_scale, sizeof(float) * NN));
+        RK_CUDA(launch_pixel_phase(phase_params(P, 0, 1, 0, 1), P->d_inv_taper, P->d_pix_turns, P->d_pix_scale,
+                                   nullptr));
+        RK_CUDA(cudaDeviceSynchronize());
         return RICK_OK;   // no cuFFT plans
     }
     const size_t plane_bytes = (size_t)P->Ng * P->Ng * sizeof(float2);
@@ -691,6 +704,7 @@ PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
     pp.dw = c.n_wplanes > 1 ? P->dw : 0.0;
     const int off = c.w_support >= 2 ? c.w_support / 2 : 0;
     pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 - off + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
+    pp.k_first = k0;
     pp.precision = c.precision;
     pp.w_support = c.w_support >= 2 && c.n_wplanes > 1 ? c.w_support : 0;
     pp.w_beta = c.w_kernel_param;
@@ -796,7 +810,8 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
     int launches = 0;
     rick_status s = check_launch(launch_rows_phase_reduce(phase_params(P, c0, c1, k0, k1),
                                                           reinterpret_cast<const float2*>(grids),
-                                                          weight_sum + c0, P->d_inv_taper, P->d_twid,
+                                                          weight_sum + c0, P->d_pix_turns, P->d_pix_scale,
+                                                          P->d_twid,
                                                           image_real,
                                                           reinterpret_cast<float2*>(image_complex),
                                                           (flags & RICK_GRIDDED_BY_PLAN) ? plan_occupancy(P) : Occupancy{},

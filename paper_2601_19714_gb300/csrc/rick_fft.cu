@@ -354,55 +354,89 @@ __device__ __forceinline__ uint32_t turns_q32f(float t) {
     return (uint32_t)__float2ull_rz(f * 4294967296.0f);
 }
 
+// Per-pixel constants of the fused row pass, once per plan (they depend only
+// on the mesh, the plane spacing and the tapers): for pixel (p, q),
+//   turns[q N + p] = (t_0, dt), the phase w_0 (n - 1) of stored plane 0 and
+//     the plane step dw (n - 1) in turns, Q0.32 fixed point (FP64 -- or FP32
+//     under RICK_PREC_ALL_FP32 -- from n - 1 = -(l^2 + m^2)/(1 + n)), so that
+//     plane k's phase is t_0 + k dt, exact modulo one turn;
+//   scale[q N + p] = (-1)^(p+q) n / (C(p) C(q) C_w).
+// P describes stored plane 0 (w_first = its w).
+__global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper, uint2* __restrict__ turns,
+                              float* __restrict__ scale) {
+    const int N = P.N, halfN = N / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * N) return;
+    const int q = (int)(i / N), p = (int)(i - (int64_t)q * N);
+    const double l = (double)(p - halfN) * P.dl, m = (double)(q - halfN) * P.dl;
+    const double r2 = l * l + m * m;
+    const double n = sqrt(1.0 - r2);
+    const double delta = -r2 / (1.0 + n);
+    if (P.precision == RICK_PREC_ALL_FP32) {
+        const float lf = (float)(p - halfN) * (float)P.dl, mf = (float)(q - halfN) * (float)P.dl;
+        const float r2f = lf * lf + mf * mf;
+        const float df = -r2f / (1.0f + sqrtf(1.0f - r2f));
+        turns[i] = make_uint2(turns_q32f((float)P.w_first * df), turns_q32f((float)P.dw * df));
+    } else {
+        turns[i] = make_uint2(turns_q32(P.w_first * delta), turns_q32(P.dw * delta));
+    }
+    const float sg = ((p + q) & 1) ? -1.f : 1.f;
+    scale[i] = sg * (float)n * inv_taper[p] * inv_taper[q] * w_taper_inv(P, delta);
+}
+
 // Imaging, pass 2 fused with Eq. 2's phase screen and reduction: image row q
 // (blockIdx.x) of every channel of the launch,
 //   image[c][q][p] += (-1)^(p+q) n C_w^-1 / (sum W_c C(p) C(q))
 //                     * Re sum_k F_k[q][p] exp(+2 pi i w_k (n - 1)),
 // where F_k[q][.] is the row DFT of the column-transformed plane k.  Thread b
-// owns pixels p = b + (N/16) j; their phases t_k = w_k (n - 1) in turns are
-// Q0.32 fixed point (FP64 once per pixel for t_0 and dt, kept in shared
-// memory, then t_0 + k dt exact mod one turn), one sincospi per pixel and
-// plane.  The next row is loaded into registers while the current one is
-// transformed.  Two CTAs per SM for N <= 4096 (at most 128 registers).
-template <int LOG2N, int PREC, bool COMPLEX_OUT>
+// owns pixels p = b + (N/16) j.  With t_k = t_0 + k dt the phase of plane k
+// (turns), the sum over a block of planes k = k0..k1 is
+//   e^(2 pi i t_k1) sum_k F_k z^(k1-k),  z = e^(-2 pi i dt),
+// taken by Horner's rule: acc <- acc z + F_k, one complex multiply-add per
+// pixel and plane (z per pixel in shared memory); the exact phasor of the
+// block's last plane, from the Q0.32 turns, multiplies the result, which is
+// summed per pixel in shared memory and added to the image at the channel's
+// end (one read-modify-write of the image row per channel; the variant with
+// the complex output adds every block to the images instead).  Blocks of
+// kHornerBlock planes bound the rounding that
+// the powers of the FP32 z carry (each rotation adds about one unit of FP32
+// rounding in angle and modulus).  An unreached plane still rotates acc
+// (acc z + 0), so pruning does not change the arithmetic.
+// The per-pixel turns and scale come from the plan's table (k_pixel_phase).
+// The next row is loaded into registers while the current one is transformed.
+// Two CTAs per SM for N <= 4096 (at most 128 registers).
+constexpr int kHornerBlock = 8;   // planes per Horner block of the fused row pass
+
+template <int LOG2N, bool COMPLEX_OUT>
 __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
 k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
-                    const float* __restrict__ inv_taper, const float2* __restrict__ twid,
-                    float* __restrict__ image_real, float2* __restrict__ image_complex,
-                    Occupancy occ) {
+                    const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
+                    const float2* __restrict__ twid, float* __restrict__ image_real,
+                    float2* __restrict__ image_complex, Occupancy occ) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
-    uint2* phase = reinterpret_cast<uint2*>(buf + Sh::kArray);   // (t_0, dt) per pixel
-    float* scl = reinterpret_cast<float*>(phase + N);
+    float2* zrot = buf + Sh::kArray;                             // z = e^(-2 pi i dt) per pixel
+    // the channel's finished blocks per pixel: Re of the phased sums
+    float* part = reinterpret_cast<float*>(zrot + N);
     const int b = threadIdx.x, q = blockIdx.x;
-    const int halfN = N / 2;
+    const float* scl = pix_scale + (size_t)q * N;                // per-pixel scale (read once per channel)
+    const uint2* turns = pix_turns + (size_t)q * N;
     load_tables<LOG2N>(twid, tw, b, T);
-
-#pragma unroll 1
+#pragma unroll 4
     for (int j = 0; j < 16; ++j) {
         const int p = b + T * j;
-        const double l = (double)(p - halfN) * P.dl, m = (double)(q - halfN) * P.dl;
-        const double r2 = l * l + m * m;
-        const double n = sqrt(1.0 - r2);
-        const double delta = -r2 / (1.0 + n);
-        if (PREC == RICK_PREC_ALL_FP32) {
-            const float lf = (float)(p - halfN) * (float)P.dl, mf = (float)(q - halfN) * (float)P.dl;
-            const float r2f = lf * lf + mf * mf;
-            const float df = -r2f / (1.0f + sqrtf(1.0f - r2f));
-            phase[p] = make_uint2(turns_q32f((float)P.w_first * df), turns_q32f((float)P.dw * df));
-        } else {
-            phase[p] = make_uint2(turns_q32(P.w_first * delta), turns_q32(P.dw * delta));
-        }
-        const float sg = ((p + q) & 1) ? -1.f : 1.f;
-        scl[p] = sg * (float)n * inv_taper[p] * inv_taper[q] * w_taper_inv(P, delta);
+        float s, c;
+        sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
+        zrot[p] = make_float2(c, -s);
+        if (!COMPLEX_OUT) part[p] = 0.f;
     }
 
     const size_t NN = (size_t)N * N;
     const int n_rows = P.nc * P.nk;
-    // planes no visibility reached are skipped
+    // planes no visibility reached are not transformed
     auto next_row = [&](int r) {
         if (occ.plane != nullptr)
             while (r < n_rows && occ.plane[r] == 0) ++r;
@@ -428,49 +462,76 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     if (r < n_rows) load_row(r, a);
     __syncthreads();
     for (int cc = 0; cc < P.nc; ++cc) {
-        float acc[16], acci[16];
+        float2 acc[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = acci[j] = 0.f;
+        for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
         for (int kk = 0; kk < P.nk; ++kk) {
-            if (cc * P.nk + kk != r) continue;   // an empty plane
-            radix16_out<LOG2N, true>(a, b, 0, buf, tw);
-            const int rn = next_row(r + 1);
-            if (rn < n_rows) load_row(rn, a);
-            r = rn;
-            __syncthreads();
-            middle_stages<LOG2N, true>(buf, b, tw);
-            last_stage<LOG2N, true>(buf, b, x);
-            __syncthreads();   // buf is rewritten by the next row's first stage
+            if (cc * P.nk + kk != r) {   // an unreached plane: F_k = 0
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 z = zrot[b + T * j];
+                    acc[j] = make_float2(fmaf(acc[j].x, z.x, -acc[j].y * z.y), fmaf(acc[j].x, z.y, acc[j].y * z.x));
+                }
+            } else {
+                radix16_out<LOG2N, true>(a, b, 0, buf, tw);
+                const int rn = next_row(r + 1);
+                if (rn < n_rows) load_row(rn, a);
+                r = rn;
+                __syncthreads();
+                middle_stages<LOG2N, true>(buf, b, tw);
+                last_stage<LOG2N, true>(buf, b, x);
+                __syncthreads();   // buf is rewritten by the next row's first stage
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 z = zrot[b + T * j];
+                    acc[j] = make_float2(fmaf(acc[j].x, z.x, fmaf(-acc[j].y, z.y, x[j].x)),
+                                         fmaf(acc[j].x, z.y, fmaf(acc[j].y, z.x, x[j].y)));
+                }
+            }
+            const bool last = kk == P.nk - 1;
+            if (kk % kHornerBlock != kHornerBlock - 1 && !last) continue;
+            // end of a block: times the exact phasor of its last plane; at the
+            // channel's end, scaled into the image
+            const uint32_t k_end = (uint32_t)(P.k_first + kk);
+            float inv_ws = 0.f;
+            if (last || COMPLEX_OUT) {
+                const double ws = wsum[cc];
+                inv_ws = ws != 0.0 ? (float)(1.0 / ws) : 0.0f;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const uint2 ph = phase[b + T * j];
-                const uint32_t tk = ph.x + (uint32_t)kk * ph.y;
-                float s, c;
-                sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
-                acc[j] = fmaf(x[j].x, c, fmaf(-x[j].y, s, acc[j]));
-                if (COMPLEX_OUT) acci[j] = fmaf(x[j].x, s, fmaf(x[j].y, c, acci[j]));
-            }
-        }
-        const double ws = wsum[cc];
-        const float inv_ws = ws != 0.0 ? (float)(1.0 / ws) : 0.0f;
-        float* ir = image_real + (size_t)cc * NN + (size_t)q * N;
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int p = b + T * j;
-            const float s = scl[p] * inv_ws;
-            ir[p] += s * acc[j];
-            if (COMPLEX_OUT) {
-                float2* ic = image_complex + (size_t)cc * NN + (size_t)q * N + p;
-                float2 v = *ic;
-                v.x += s * acc[j];
-                v.y += s * acci[j];
-                *ic = v;
+                const int p = b + T * j;
+                const uint2 ph = __ldg(&turns[p]);
+                const uint32_t tk = ph.x + k_end * ph.y;
+                float sn, cs;
+                sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
+                const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
+                acc[j] = make_float2(0.f, 0.f);
+                float* ir = image_real + (size_t)cc * NN + (size_t)q * N + p;
+                if (COMPLEX_OUT) {
+                    const float s = __ldg(scl + p) * inv_ws;
+                    *ir += s * re;
+                    float2* ic = image_complex + (size_t)cc * NN + (size_t)q * N + p;
+                    float2 v = *ic;
+                    v.x += s * re;
+                    v.y += s * im;
+                    *ic = v;
+                } else if (!last) {
+                    part[p] += re;
+                } else {
+                    *ir += __ldg(scl + p) * inv_ws * (part[p] + re);
+                    part[p] = 0.f;
+                }
             }
         }
     }
 }
 
-constexpr int kCols = 2;   // columns per CTA in pass 1
+// columns per CTA in pass 1: rows of 32 bytes (a whole DRAM sector) where
+// 4 N/16 threads fit a CTA, else 16 bytes
+template <int LOG2N>
+constexpr int kCols = LOG2N <= 12 ? 4 : 2;
 
 // Occupancy of the planes p = cc nk + kk of the launch from the bin offsets:
 // one thread per tile (tx fastest), reached iff tile_reach() > 0 -- the
@@ -513,13 +574,14 @@ template <int LOG2N, bool INV>
 cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, const Occupancy& occ,
                         cudaStream_t st) {
     using Sh = Shape<LOG2N>;
-    auto fn = k_fft_columns<LOG2N, kCols, INV>;
-    const size_t smem = (size_t)(Sh::kTw + kCols * Sh::kArray) * sizeof(float2);
+    constexpr int cols = kCols<LOG2N>;
+    auto fn = k_fft_columns<LOG2N, cols, INV>;
+    const size_t smem = (size_t)(Sh::kTw + cols * Sh::kArray) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < n_planes; p0 += 65535) {
         const unsigned np = (unsigned)(n_planes - p0 < 65535 ? n_planes - p0 : 65535);
-        fn<<<dim3(Sh::N / kCols, np), kCols * Sh::T, smem, st>>>(grids + p0 * Sh::N * Sh::N, twid, occ, p0);
+        fn<<<dim3(Sh::N / cols, np), cols * Sh::T, smem, st>>>(grids + p0 * Sh::N * Sh::N, twid, occ, p0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -540,30 +602,28 @@ cudaError_t rows_one(float2* grids, int64_t n_planes, const float2* twid, cudaSt
     return cudaSuccess;
 }
 
-template <int LOG2N, int PREC, bool CPLX>
-cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                      const float2* twid, float* image_real, float2* image_complex, const Occupancy& occ,
-                      cudaStream_t st) {
+template <int LOG2N, bool CPLX>
+cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
+                      const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
+                      const Occupancy& occ, cudaStream_t st) {
     using Sh = Shape<LOG2N>;
-    auto fn = k_rows_phase_reduce<LOG2N, PREC, CPLX>;
+    auto fn = k_rows_phase_reduce<LOG2N, CPLX>;
+    // tables and the transform array, then per pixel z and (real output) the partial sum
     const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
-                        (size_t)Sh::N * (sizeof(uint2) + sizeof(float));
+                        (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ);
+    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ);
     return cudaGetLastError();
 }
 
 template <int LOG2N>
-cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const float* inv_taper,
-                    const float2* twid, float* image_real, float2* image_complex, const Occupancy& occ,
-                    cudaStream_t st) {
-    const bool c = image_complex != nullptr;
-    if (P.precision == RICK_PREC_ALL_FP32)
-        return c ? fused_one<LOG2N, RICK_PREC_ALL_FP32, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st)
-                 : fused_one<LOG2N, RICK_PREC_ALL_FP32, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st);
-    return c ? fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, true>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st)
-             : fused_one<LOG2N, RICK_PREC_FP32_FP64IDX, false>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st);
+cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
+                    const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
+                    const Occupancy& occ, cudaStream_t st) {
+    return image_complex != nullptr
+               ? fused_one<LOG2N, true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
+               : fused_one<LOG2N, false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
 }
 
 int log2_exact(int N) {
@@ -648,21 +708,33 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
 }
 
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
-                                     const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, const Occupancy& occ, cudaStream_t st,
-                                     int* launches) {
+                                     const uint2* pix_turns, const float* pix_scale, const float2* twid,
+                                     float* image_real, float2* image_complex, const Occupancy& occ,
+                                     cudaStream_t st, int* launches) {
     cudaError_t e = cudaErrorInvalidValue;
+#define RICK_FUSED_CASE(LG)                                                                              \
+    case LG:                                                                                             \
+        e = fused_n<LG>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st); \
+        break;
     switch (log2_exact(P.N)) {
-        case 8: e = fused_n<8>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
-        case 9: e = fused_n<9>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
-        case 10: e = fused_n<10>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
-        case 11: e = fused_n<11>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
-        case 12: e = fused_n<12>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
-        case 13: e = fused_n<13>(P, grids, wsum, inv_taper, twid, image_real, image_complex, occ, st); break;
+        RICK_FUSED_CASE(8)
+        RICK_FUSED_CASE(9)
+        RICK_FUSED_CASE(10)
+        RICK_FUSED_CASE(11)
+        RICK_FUSED_CASE(12)
+        RICK_FUSED_CASE(13)
         default: break;
     }
+#undef RICK_FUSED_CASE
     if (e == cudaSuccess) ++*launches;
     return e;
+}
+
+cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, uint2* turns, float* scale,
+                               cudaStream_t st) {
+    const int64_t n = (int64_t)P0.N * P0.N;
+    k_pixel_phase<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P0, inv_taper, turns, scale);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,

@@ -137,6 +137,7 @@ struct PhaseParams {
     int Ni, off;          // image side and its offset in the planes (padding: (Ng - Ni)/2)
     double dl;            // fov / Ni
     double w_first;       // w of plane plane_begin (plane centre)
+    int k_first;          // plane_begin (stored plane index)
     double dw;            // plane spacing (0 if Nw == 1)
     int precision;
     // w-kernel (w_support >= 2): every pixel is also divided by the kernel's
@@ -253,11 +254,18 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
 // Pass 2 fused with the phase screen and reduction: grids must hold the
 // column-transformed planes [nc][nk][N][N]; image_real [nc][N][N] (+=).
 // With occ, unreached planes are skipped and unreached tile columns read as
-// zeros (the column pass left them untouched).
+// zeros (the column pass left them untouched).  pix_turns / pix_scale: the
+// plan's per-pixel table (launch_pixel_phase), P.k_first the launch's first
+// stored plane.
 cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, const double* wsum,
-                                     const float* inv_taper, const float2* twid, float* image_real,
-                                     float2* image_complex, const Occupancy& occ, cudaStream_t stream,
-                                     int* launches);
+                                     const uint2* pix_turns, const float* pix_scale, const float2* twid,
+                                     float* image_real, float2* image_complex, const Occupancy& occ,
+                                     cudaStream_t stream, int* launches);
+// The per-pixel table of the fused row pass ([N][N] each): the phase of
+// stored plane 0 and the plane step in Q0.32 turns, and the pixel's scale
+// (checkerboard sign, n, tapers); P0 = the phase parameters of stored plane 0.
+cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, uint2* turns, float* scale,
+                               cudaStream_t stream);
 
 // learned kernel network (rick_mlp.cu)
 int64_t mlp_param_count(int H);
