@@ -103,16 +103,41 @@ def stage_traffic(N, C, P, nrow, n_grid, T, reach, own):
             "columns": 8.0 * tile_cells + 8.0 * col_cells, "rows_phase": 8.0 * col_cells + b_img}
 
 
+# Nominal FP32 rate of the GB300 CUDA cores: 152 SMs x 128 FP32 lanes x 2
+# flop per FMA x 2.07 GHz (the maximum SM clock, which the bench runs at).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def stage_flops(N, C, P, reach, own):
+    """Algorithmic FP32 flops per step of the transform stages: 5 n log2 n per
+    length-n complex DFT (the radix-2 count), and for the fused row pass 8 per
+    pixel and plane (the complex multiply-add of the plane sum)."""
+    lg = int(round(math.log2(N)))
+    dft = 5.0 * N * lg
+    if not own:
+        return {"fft": 2 * C * P * N * dft}
+    return {"columns": reach["tile_columns"] * reach["tile"] * dft,
+            "rows_phase": reach["planes"] * N * dft + 8.0 * reach["planes"] * N * N}
+
+
 def dram_traffic(stage, N, C, P, reach):
-    """DRAM bytes per step of a stage, scaled from one ncu capture of the
-    small 4096^2 case: cuFFT's per cell; the pruned passes' per processed
-    unit (scaling by the units holds where traffic is proportional to them)."""
+    """DRAM bytes per step of a stage from one ncu capture of a small 4096^2
+    case of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum),
+    scaled to the step by the units it processes:
+      cuFFT: 46.7 B per cell (its traffic is proportional to the planes);
+      fused row pass: 7.81 B per cell of the reached tile columns it reads
+        (8 algorithmic), plus the image read and write (8 B per pixel and
+        channel) and the per-pixel table (12 B per pixel, once per launch)."""
     if N != 4096:
         return None, None
-    per_cell = {"fft": 46.7}
-    if stage in per_cell:
-        return (per_cell[stage] * C * P * N * N,
-                f"ncu capture of the 4096^2 small case, scaled by planes ({per_cell[stage]} B/cell)")
+    cells = C * P * N * N
+    if stage == "fft":
+        return 46.7 * cells, "ncu capture of the 4096^2 small case, scaled by planes (46.7 B/cell)"
+    if stage == "rows_phase":
+        col_cells = reach["tile_columns"] * N * reach["tile"]
+        return (7.81 * col_cells + 8.0 * C * N * N + 12.0 * N * N,
+                "ncu capture of the 4096^2 small case (2 channels x 16 planes): 7.81 B per reached "
+                "column cell + 8 B per image pixel and channel + 12 B per table pixel")
     return None, None
 
 
@@ -417,6 +442,21 @@ def run_ours(args):
     # small case of the same kernel (dram__bytes_read.sum +
     # dram__bytes_write.sum), scaled to the step by the units it processes
     dom_traffic, traffic_how = dram_traffic(dominant, N, C, Nst, res["reach"])
+    flops = stage_flops(N, C, Nst, res["reach"], impl == "own")
+    if dominant in flops and impl == "own":
+        # the fused row pass issues FP32 arithmetic at ~75 % of the issue rate
+        # with DRAM ~17 % busy (ncu): its bound is the FP32 pipes, not HBM
+        ach = flops[dominant] / (st[dominant] * 1e-3) / 1e12
+        dom_roofline = {"bound": "alu", "kernel": dominant, "achieved": ach,
+                        "peak": FP32_PEAK_TFLOPS, "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz)",
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                        "hbm_achieved_gbs": gbs[dominant], "hbm_frac": gbs[dominant] / hbm,
+                        "traffic": dom_traffic, "traffic_unit": "bytes per step", "traffic_how": traffic_how}
+    else:
+        dom_roofline = {"bound": "hbm", "kernel": dominant, "achieved": gbs[dominant],
+                        "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                        "frac": gbs[dominant] / hbm,
+                        "traffic": dom_traffic, "traffic_unit": "bytes per step", "traffic_how": traffic_how}
 
     # ---- end to end through the host entry point -------------------------------
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -468,14 +508,12 @@ def run_ours(args):
             "stage_gbs": gbs,
             "gridder_vis_per_s": n_grid / (st["grid"] * 1e-3),
             "bin_plus_grid_vis_per_s": n_grid / ((st["bin"] + st["grid"]) * 1e-3),
-            "roofline": {"bound": "hbm", "kernel": dominant,
-                         "achieved": dom_bytes / (st[dominant] * 1e-3) / 1e9,
-                         "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": dom_bytes / (st[dominant] * 1e-3) / 1e9 / hbm,
-                         "traffic": dom_traffic, "traffic_unit": "bytes per step",
-                         "traffic_how": traffic_how},
+            "roofline": dom_roofline,
             "roofline_stages": {k: {"bound": "hbm", "achieved": gbs[k], "peak": hbm, "unit": "GB/s",
                                     "frac": gbs[k] / hbm} for k in st},
+            "fp32_stages": {k: {"achieved": flops[k] / (st[k] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": flops[k] / (st[k] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS}
+                            for k in flops if k in st},
             "e2e": {"value": units / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
@@ -1173,7 +1211,12 @@ def run_profile_small(args):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / args.steps
     n_grid = int(counts[0].item())
+    # the imaging binning is the last one of the step: the reached tiles and the
+    # algorithmic bytes of each imaging stage (to relate ncu's DRAM bytes to them)
+    reach = reach_counts(plan.bin_offsets(), C, ns, N, 32)
+    sbytes = stage_traffic(N, C, ns, obs.nrow, n_grid, 32, reach, args.fft == "own")
     print(json.dumps({"metric": METRIC, "value": n_grid / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+                      "reach": reach, "stage_bytes": sbytes,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                       "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                       "impl": "ours", "config": {"workload": f"meerkat_small_4096sq_{img.Nw}w_2ch_kb8",

@@ -444,14 +444,27 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     };
     // row q of plane r: the inputs b + T t2 of this thread; the unreached tile
     // columns are zero (the column pass did not touch them): not read
+    // With tiles of at least 32 columns (and N/16 >= 32) the tile column of
+    // input b + T t2 is the same for a whole warp: lanes 0..15 read the 16
+    // mask bytes and a ballot hands every lane the 16 bits.
+    const bool warp_mask = occ.tshift >= 5 && T >= 32;
     auto load_row = [&](int r, float2 (&v)[16]) {
         const float2* row = grids + (size_t)r * NN + (size_t)q * N;
         if (occ.col != nullptr) {
             const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+            uint32_t live = 0;
+            if (warp_mask) {
+                const int lane = b & 31;
+                const bool on = lane < 16 && __ldg(cm + (((b & ~31) + T * lane) >> occ.tshift)) != 0;
+                live = __ballot_sync(0xffffffffu, on);
+            } else {
+#pragma unroll
+                for (int t2 = 0; t2 < 16; ++t2)
+                    live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
+            }
 #pragma unroll
             for (int t2 = 0; t2 < 16; ++t2)
-                v[t2] = __ldg(cm + ((b + T * t2) >> occ.tshift)) ? __ldcs(row + b + T * t2)
-                                                                 : make_float2(0.f, 0.f);
+                v[t2] = (live >> t2) & 1u ? __ldcs(row + b + T * t2) : make_float2(0.f, 0.f);
         } else {
 #pragma unroll
             for (int t2 = 0; t2 < 16; ++t2) v[t2] = __ldcs(row + b + T * t2);
