@@ -336,8 +336,12 @@ def run_ours(args):
 
     def tuned_config(fold):
         # launch shape of the gridder: autotuned on two channels of this data
-        # (pattern 2), cached per problem class; untimed set-up
+        # (pattern 2), cached per problem class; untimed set-up (--launch-shape
+        # gives it instead)
         base = plan_config(img, C, fold)
+        if args.launch_shape:
+            t, k, g = (int(v) for v in args.launch_shape.split(","))
+            return replace(base, tile=t, grid_threads=k, tiles_per_grab=g)
         ns = base.stored_planes
         g2 = torch.empty((2, ns, N, N), dtype=torch.complex64, device="cuda")
         cfg, _ = autotune.tuned(
@@ -501,7 +505,8 @@ def run_ours(args):
                        "kernel": "kaiser_bessel", "index_phase": "fp64", "fov_deg": round(math.degrees(img.fov), 4),
                        "fft": FFT_DESC[impl],
                        "tile": tuned.tile, "grid_threads": tuned.grid_threads,
-                       "tiles_per_grab": tuned.tiles_per_grab, "launch_shape": "autotuned",
+                       "tiles_per_grab": tuned.tiles_per_grab,
+                       "launch_shape": "given" if args.launch_shape else "autotuned",
                        "l2": f"inputs larger than L2 (grids {8 * cells / 1e9:.1f} GB, not flushed)",
                        "parallelism": f"channel blocks x{world} (16 channels per rank, no collective on the data path)"},
             "stages_ms": st,
@@ -1247,6 +1252,8 @@ def main():
                     help="meerkat (default bench line); lofar / learned / large measure the "
                          "batched, learned-kernel and precision-stress workloads; "
                          "profile_small is the small case the ncu captures use")
+    ap.add_argument("--launch-shape", default="",
+                    help="tile,threads,grab of the gridder for the headline (default: autotuned)")
     ap.add_argument("--profile-planes", type=int, default=8,
                     help="w-planes of the profile_small workload (8: 1 GB of grids with the fold; "
                          "32: 4.3 GB, 16 planes per channel as in the headline's row pass)")

@@ -3,8 +3,9 @@
 // Eq. 2 needs, per plane, F_k[q][p] = sum_{i,j} G_k[j][i] e^{+2 pi i (i p + j q)/N}
 // (unnormalised); the prediction needs the same with e^{-...}.  The 2-D DFT is
 // a length-N DFT down every column followed by one along every row:
-//   pass 1 (k_fft_columns): one CTA transforms COLS adjacent columns of a plane
-//     in shared memory (rows of COLS x 8 bytes are read and written back);
+//   pass 1 (k_fft_columns): one CTA transforms COLS adjacent columns of a plane,
+//     each warp reading and writing rows of COLS x 8 bytes straight from and to
+//     registers;
 //   pass 2 (k_fft_rows): one CTA transforms one row, in place; or, for imaging,
 //     k_rows_phase_reduce: one CTA owns one image row q, transforms that row of
 //     every plane of every channel of the launch, applies the phase screen
@@ -263,62 +264,47 @@ __device__ __forceinline__ void load_tables(const float2* __restrict__ twid, flo
 
 // ---- pass 1: columns ----------------------------------------------------------
 
-// COLS adjacent columns of one plane per CTA (COLS * N/16 threads); rows of
-// COLS * 8 bytes are read with 16-byte loads into COLS skewed arrays,
-// transformed, and written back the same way.
+// COLS adjacent columns of one plane per CTA (COLS * N/16 threads), the
+// threads of a column interleaved: thread (b, c) = COLS b + c, so a warp holds
+// COLS columns x 32/COLS butterflies.  The first stage's inputs b + (N/16) t2
+// are read straight into registers and the last stage's outputs written
+// straight back: each warp access covers 32/COLS rows of COLS * 8 bytes (whole
+// 32-byte sectors for COLS = 4), with no staging through shared memory.  Column
+// c's skewed array is offset by 32/COLS banks from column c - 1's, so the
+// COLS arrays a half-warp touches in every stage fall on distinct banks.
 template <int LOG2N, int COLS, bool INV>
 __global__ void __launch_bounds__(COLS * (1 << LOG2N) / 16)
 k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, Occupancy occ, int64_t plane0) {
     using Sh = Shape<LOG2N>;
     constexpr int N = Sh::N, T = Sh::T;
-    // tile rows of this column tile that a record reaches (tiles are >= 16 wide)
+    constexpr int kStride = Sh::kArray + 16 / COLS;   // float2 per column array
     __shared__ uint8_t s_live[N / 16];
     const int64_t pl = plane0 + blockIdx.y;
     const int tcol = (int)(blockIdx.x * COLS) >> occ.tshift;
-    // a column tile that no visibility reached is zero: skip it
     if (occ.col != nullptr && occ.col[pl * occ.NT + tcol] == 0) return;
     constexpr int kThreads = COLS * T;
-    constexpr int kVec = COLS / 2;   // 16-byte pieces per row
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
-    float2* arrays = fsm + Sh::kTw;
     const int tid = threadIdx.x;
-    const int c = tid / T, b = tid - c * T;
-    float2* buf = arrays + c * Sh::kArray;
-    float2* plane = grids + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * COLS;
+    const int c = tid % COLS, b = tid / COLS;
+    float2* buf = fsm + Sh::kTw + c * kStride;
+    float2* col = grids + (size_t)blockIdx.y * N * N + (size_t)blockIdx.x * COLS + c;
     load_tables<LOG2N>(twid, tw, tid, kThreads);
-    if (occ.tile != nullptr) {
+    if (occ.tile != nullptr)
         for (int ty = tid; ty < occ.NT; ty += kThreads)
             s_live[ty] = (uint8_t)((occ.tile[(pl * occ.NT + ty) * occ.words + (tcol >> 5)] >> (tcol & 31)) & 1u);
-        __syncthreads();
-    }
-#pragma unroll 4
-    for (int e = tid; e < N * kVec; e += kThreads) {
-        const int row = e / kVec, piece = e - row * kVec;
-        // an unreached tile is zero (and possibly unwritten): not read
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (occ.tile == nullptr || s_live[row >> occ.tshift])
-            v = __ldcs(reinterpret_cast<const float4*>(plane + (size_t)row * N) + piece);
-        arrays[(2 * piece) * Sh::kArray + skew(row)] = make_float2(v.x, v.y);
-        arrays[(2 * piece + 1) * Sh::kArray + skew(row)] = make_float2(v.z, v.w);
-    }
     __syncthreads();
     float2 a[16], x[16];
 #pragma unroll
-    for (int t2 = 0; t2 < 16; ++t2) a[t2] = buf[skew(b + T * t2)];
-    __syncthreads();
-    transform<LOG2N, INV>(a, buf, b, tw, x);
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 16; ++j) buf[skew(b + T * j)] = x[j];
-    __syncthreads();
-#pragma unroll 4
-    for (int e = tid; e < N * kVec; e += kThreads) {
-        const int row = e / kVec, piece = e - row * kVec;
-        const float2 lo = arrays[(2 * piece) * Sh::kArray + skew(row)];
-        const float2 hi = arrays[(2 * piece + 1) * Sh::kArray + skew(row)];
-        __stcs(reinterpret_cast<float4*>(plane + (size_t)row * N) + piece, make_float4(lo.x, lo.y, hi.x, hi.y));
+    for (int t2 = 0; t2 < 16; ++t2) {
+        const int row = b + T * t2;
+        // an unreached tile is zero (and possibly unwritten): not read
+        a[t2] = (occ.tile == nullptr || s_live[row >> occ.tshift]) ? __ldcs(col + (size_t)row * N)
+                                                                  : make_float2(0.f, 0.f);
     }
+    transform<LOG2N, INV>(a, buf, b, tw, x);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) __stcs(col + (size_t)(b + T * j) * N, x[j]);
 }
 
 // ---- pass 2: rows ---------------------------------------------------------------
@@ -541,8 +527,8 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     }
 }
 
-// columns per CTA in pass 1: rows of 32 bytes (a whole DRAM sector) where
-// 4 N/16 threads fit a CTA, else 16 bytes
+// columns per CTA in pass 1: warp accesses of 32-byte row pieces (whole DRAM
+// sectors) where 4 N/16 threads fit a CTA, else 16 bytes
 template <int LOG2N>
 constexpr int kCols = LOG2N <= 12 ? 4 : 2;
 
@@ -589,7 +575,7 @@ cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, con
     using Sh = Shape<LOG2N>;
     constexpr int cols = kCols<LOG2N>;
     auto fn = k_fft_columns<LOG2N, cols, INV>;
-    const size_t smem = (size_t)(Sh::kTw + cols * Sh::kArray) * sizeof(float2);
+    const size_t smem = (size_t)(Sh::kTw + cols * (Sh::kArray + 16 / cols)) * sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < n_planes; p0 += 65535) {
