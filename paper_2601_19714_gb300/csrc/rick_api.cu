@@ -126,8 +126,10 @@ void make_taper(int kind, double param, int S, int N, int Ng, std::vector<double
 
 }  // namespace
 
-// rick_dirty_image_host transforms and downloads the channels in this many chunks
-constexpr int kHostChunks = 4;
+// rick_dirty_image_host transforms and downloads the channels in this many
+// chunks, and (natural weighting) uploads and places the rows in kInChunks
+constexpr int kHostChunks = 8;
+constexpr int kInChunks = 4;
 
 struct rick_plan {
     rick_config cfg;
@@ -175,6 +177,7 @@ struct rick_plan {
     // download with the transform of later channels
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t chunk_done[kHostChunks] = {};
+    cudaEvent_t in_done[kInChunks] = {};
     int64_t launches = 0;
     cudaStream_t last_stream = nullptr;
     float tap_coef[kMaxSupport][kPolyDegree + 1] = {};
@@ -236,6 +239,11 @@ void release(rick_plan* P) {
     dfree(P->d_in);
     dfree(P->d_img);
     for (auto& ev : P->chunk_done)
+        if (ev) {
+            cudaEventDestroy(ev);
+            ev = nullptr;
+        }
+    for (auto& ev : P->in_done)
         if (ev) {
             cudaEventDestroy(ev);
             ev = nullptr;
@@ -538,9 +546,9 @@ PlaceParams place_params(const rick_plan* P, bool predict) {
     return pp;
 }
 
-rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
-                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
-                     int64_t* counts, cudaStream_t st, bool predict = false) {
+// The first part of a binning: checks, scratch capacity, zeroed counters.
+rick_status bin_begin(rick_plan* P, int64_t nrow, double* weight_sum, bool predict, cudaStream_t st,
+                      int64_t* nrec_out) {
     const rick_config& c = P->cfg;
     RK_ARG(nrow >= 0, "nrow must be >= 0");
     RK_ARG(weight_sum != nullptr, "weight_sum is NULL");
@@ -552,17 +560,46 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
                 P->nrec_per_vis > 1 ? " * w_support" : "", (long long)nrec);
         return RICK_ERR_UNSUPPORTED;
     }
+    RK_TRY(ensure_vis_capacity(P, nrec));
+    if (!predict && c.weighting != RICK_WEIGHT_NATURAL) RK_TRY(ensure_weight_capacity(P, nvis));
+    P->last_stream = st;
+    RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
+    RK_CUDA(cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st));
+    RK_CUDA(cudaMemsetAsync(P->d_counts, 0, 2 * sizeof(unsigned long long), st));
+    *nrec_out = nrec;
+    return RICK_OK;
+}
+
+// The last part: the scan of the bin counts and the scatter into bins.
+rick_status bin_end(rick_plan* P, int64_t nrec, int64_t* counts, bool predict, cudaStream_t st) {
+    int launches = 0;
+    rick_status s = check_launch(launch_scan(P->d_hist, P->d_offsets, P->d_partials, P->nkeys, st, &launches),
+                                 "scan kernels");
+    if (s == RICK_OK)
+        s = check_launch(launch_scatter(P->d_key, P->d_rank, P->d_stage, P->d_offsets,
+                                        P->d_records, nrec, P->num_sms, st, &launches),
+                         "scatter kernel");
+    P->launches += launches;
+    RK_TRY(s);
+    if (counts)
+        RK_CUDA(cudaMemcpyAsync(counts, P->d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    P->binned = true;
+    P->binned_for_predict = predict;
+    return RICK_OK;
+}
+
+rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
+                     const float* weight, const uint8_t* flag, int64_t nrow, double* weight_sum,
+                     int64_t* counts, cudaStream_t st, bool predict = false) {
+    const rick_config& c = P->cfg;
     if (nrow > 0) {
         RK_ARG(uvw && chan_scale && (vis || predict) && weight,
                "uvw, chan_scale, vis and weight are required");
     }
-    RK_TRY(ensure_vis_capacity(P, nrec));
-    if (!predict && c.weighting != RICK_WEIGHT_NATURAL) RK_TRY(ensure_weight_capacity(P, nvis));
-    P->last_stream = st;
+    int64_t nrec = 0;
+    RK_TRY(bin_begin(P, nrow, weight_sum, predict, st, &nrec));
+    const int64_t nvis = nrow * (int64_t)c.n_channels;
     int launches = 0;
-    RK_CUDA(cudaMemsetAsync(P->d_hist, 0, sizeof(uint32_t) * P->nkeys, st));
-    RK_CUDA(cudaMemsetAsync(weight_sum, 0, sizeof(double) * c.n_channels, st));
-    RK_CUDA(cudaMemsetAsync(P->d_counts, 0, 2 * sizeof(unsigned long long), st));
     const PlaceParams pp = place_params(P, predict);
     rick_status s = RICK_OK;
     if (!predict && c.weighting != RICK_WEIGHT_NATURAL && nvis > 0) {
@@ -578,20 +615,57 @@ rick_status bin_impl(rick_plan* P, const double* uvw, const double* chan_scale, 
                      P->d_hist, P->d_key, P->d_rank, P->d_stage, weight_sum, P->d_counts,
                      P->num_sms, st, &launches),
         "placement kernel");
-    if (s == RICK_OK)
-        s = check_launch(launch_scan(P->d_hist, P->d_offsets, P->d_partials, P->nkeys, st, &launches),
-                         "scan kernels");
-    if (s == RICK_OK)
-        s = check_launch(launch_scatter(P->d_key, P->d_rank, P->d_stage, P->d_offsets,
-                                        P->d_records, nrec, P->num_sms, st, &launches),
-                         "scatter kernel");
     P->launches += launches;
     RK_TRY(s);
-    if (counts)
-        RK_CUDA(cudaMemcpyAsync(counts, P->d_counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
-    P->binned = true;
-    P->binned_for_predict = predict;
-    return RICK_OK;
+    return bin_end(P, nrec, counts, predict, st);
+}
+
+// Imaging binning from host inputs (natural weighting): the rows arrive in
+// kInChunks chunks on the copy stream, and each chunk is placed on st as soon
+// as it is in device memory, so the upload overlaps the placement.  d_* are
+// the device copies (the same layout as the host arrays).
+rick_status bin_from_host(rick_plan* P, const double* uvw, const double* chan_scale, const float* vis,
+                          const float* weight, const uint8_t* flag, int64_t nrow, double* d_uvw,
+                          double* d_sc, float* d_vis, float* d_w, uint8_t* d_f, double* weight_sum,
+                          int64_t* counts, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    const int64_t C = c.n_channels;
+    int64_t nrec = 0;
+    RK_TRY(bin_begin(P, nrow, weight_sum, false, st, &nrec));
+    if (!P->copy_stream) RK_CUDA(cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking));
+    for (auto& ev : P->in_done)
+        if (!ev) RK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    // the copies must not overtake earlier work of st on the input buffers
+    RK_CUDA(cudaEventRecord(P->in_done[0], st));
+    RK_CUDA(cudaStreamWaitEvent(P->copy_stream, P->in_done[0], 0));
+    RK_CUDA(cudaMemcpyAsync(d_sc, chan_scale, C * sizeof(double), cudaMemcpyHostToDevice, P->copy_stream));
+    const PlaceParams pp = place_params(P, false);
+    const int64_t nr = P->nrec_per_vis;
+    int launches = 0;
+    rick_status s = RICK_OK;
+    for (int i = 0; i < kInChunks && s == RICK_OK; ++i) {
+        const int64_t r0 = nrow * i / kInChunks, r1 = nrow * (i + 1) / kInChunks;
+        if (r1 == r0) continue;
+        const int64_t n = r1 - r0, v0 = r0 * C;
+        RK_CUDA(cudaMemcpyAsync(d_uvw + 3 * r0, uvw + 3 * r0, n * 3 * sizeof(double), cudaMemcpyHostToDevice,
+                                P->copy_stream));
+        RK_CUDA(cudaMemcpyAsync(d_vis + 2 * v0, vis + 2 * v0, n * C * 2 * sizeof(float), cudaMemcpyHostToDevice,
+                                P->copy_stream));
+        RK_CUDA(cudaMemcpyAsync(d_w + v0, weight + v0, n * C * sizeof(float), cudaMemcpyHostToDevice,
+                                P->copy_stream));
+        if (flag)
+            RK_CUDA(cudaMemcpyAsync(d_f + v0, flag + v0, n * C, cudaMemcpyHostToDevice, P->copy_stream));
+        RK_CUDA(cudaEventRecord(P->in_done[i], P->copy_stream));
+        RK_CUDA(cudaStreamWaitEvent(st, P->in_done[i], 0));
+        s = check_launch(launch_place(pp, d_uvw + 3 * r0, d_sc, reinterpret_cast<const float2*>(d_vis + 2 * v0),
+                                      d_w + v0, flag ? d_f + v0 : nullptr, n * C, P->d_hist, P->d_key + v0 * nr,
+                                      P->d_rank + v0 * nr, P->d_stage + v0 * nr, weight_sum, P->d_counts,
+                                      P->num_sms, st, &launches, v0),
+                         "placement kernel");
+    }
+    P->launches += launches;
+    RK_TRY(s);
+    return bin_end(P, nrec, counts, false, st);
 }
 
 // sparse: tiles no record reaches are not written (only for the pruned own
@@ -1206,26 +1280,34 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
     double* d_ws = reinterpret_cast<double*>(b + b_uvw + b_sc + b_vis + b_w + b_f);
     int64_t* d_cnt = reinterpret_cast<int64_t*>(b + b_uvw + b_sc + b_vis + b_w + b_f + b_ws);
     cudaStream_t st = as_stream(stream);
-    if (R) {
-        RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
+    int gc, gk;
+    plan_groups(plan, &gc, &gk);
+    const bool whole = gc == c.n_channels && gk == plan->planes && c.n_channels > 1;
+    // upload overlapped with placement: natural weighting (the other weightings
+    // need every visibility's density before any placement)
+    const bool overlap_in = whole && R > 0 && c.weighting == RICK_WEIGHT_NATURAL;
+    if (R) RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
+    if (R && !overlap_in) {
         RK_CUDA(cudaMemcpyAsync(d_uvw, uvw, R * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
         RK_CUDA(cudaMemcpyAsync(d_vis, vis, R * C * 2 * sizeof(float), cudaMemcpyHostToDevice, st));
         RK_CUDA(cudaMemcpyAsync(d_w, weight, R * C * sizeof(float), cudaMemcpyHostToDevice, st));
         if (flag) RK_CUDA(cudaMemcpyAsync(d_f, flag, R * C, cudaMemcpyHostToDevice, st));
     }
-    if (chan_scale)
+    if (chan_scale && !overlap_in)
         RK_CUDA(cudaMemcpyAsync(d_sc, chan_scale, C * sizeof(double), cudaMemcpyHostToDevice, st));
     RK_CUDA(cudaMemsetAsync(plan->d_img, 0, img_bytes, st));
-    int gc, gk;
-    plan_groups(plan, &gc, &gk);
-    if (gc == c.n_channels && gk == plan->planes && c.n_channels > 1) {
+    if (whole) {
         // the whole grid fits: grid every channel, then transform and reduce in
         // channel chunks, each chunk's images downloaded on the copy stream
         // while the next chunk is transformed
         if (!plan->copy_stream) RK_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
         for (auto& ev : plan->chunk_done)
             if (!ev) RK_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        RK_TRY(bin_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, d_ws, d_cnt, st));
+        if (overlap_in)
+            RK_TRY(bin_from_host(plan, uvw, chan_scale, vis, weight, flag, nrow, d_uvw, d_sc, d_vis, d_w, d_f,
+                                 d_ws, d_cnt, st));
+        else
+            RK_TRY(bin_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, d_ws, d_cnt, st));
         RK_TRY(ensure_group_grid(plan));
         float* g = reinterpret_cast<float*>(plan->d_grid);
         RK_TRY(grid_impl(plan, 0, c.n_channels, 0, plan->planes, g, st, plan->own_fft));

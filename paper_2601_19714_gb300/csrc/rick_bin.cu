@@ -249,7 +249,7 @@ k_place(PlaceParams P, const double* __restrict__ uvw, const double* __restrict_
         const uint8_t* __restrict__ flag, int64_t nvis, uint32_t* __restrict__ hist,
         uint32_t* __restrict__ key_out, uint32_t* __restrict__ rank_out,
         VisRecord* __restrict__ stage, double* __restrict__ weight_sum,
-        unsigned long long* __restrict__ counts) {
+        unsigned long long* __restrict__ counts, int64_t vis_base) {
     __shared__ double s_wsum[kPlaceThreads];
     __shared__ unsigned long long s_cnt[2];
     const int lane = threadIdx.x & 31;
@@ -298,7 +298,7 @@ k_place(PlaceParams P, const double* __restrict__ uvw, const double* __restrict_
 #pragma unroll
                     for (int q = kPolyDegree - 1; q >= 0; --q) gw = fmaf(gw, tw, P.wcoef[sw][q]);
                 }
-                finish_record(P, c, b.k + sw, b.i0, b.j0, b.fqx, b.fqy, W, V, gw, (uint32_t)idx, pl);
+                finish_record(P, c, b.k + sw, b.i0, b.j0, b.fqx, b.fqy, W, V, gw, (uint32_t)(vis_base + idx), pl);
             }
             // rank within the bin: one atomic per distinct key in the warp
             const unsigned peers = __match_any_sync(0xffffffffu, pl.key);
@@ -633,7 +633,7 @@ cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* 
                          const float2* vis, const float* weight, const uint8_t* flag,
                          int64_t nvis, uint32_t* hist, uint32_t* key, uint32_t* rank,
                          VisRecord* stage, double* weight_sum, unsigned long long* counts,
-                         int num_sms, cudaStream_t stream, int* launches) {
+                         int num_sms, cudaStream_t stream, int* launches, int64_t vis_base) {
     if (nvis <= 0) return cudaSuccess;
     // grid: a multiple of C blocks (so that the stride is a multiple of C),
     // about 8 blocks per SM, never more than the work needs
@@ -648,11 +648,11 @@ cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* 
     if (P.precision == RICK_PREC_ALL_FP32)
         k_place<RICK_PREC_ALL_FP32><<<(unsigned)blocks, kPlaceThreads, 0, stream>>>(
             P, uvw, chan_scale, vis, weight, flag, nvis, hist, key, rank, stage, weight_sum,
-            counts);
+            counts, vis_base);
     else
         k_place<RICK_PREC_FP32_FP64IDX><<<(unsigned)blocks, kPlaceThreads, 0, stream>>>(
             P, uvw, chan_scale, vis, weight, flag, nvis, hist, key, rank, stage, weight_sum,
-            counts);
+            counts, vis_base);
     ++*launches;
     return cudaGetLastError();
 }

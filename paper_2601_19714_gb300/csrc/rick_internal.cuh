@@ -176,11 +176,13 @@ __device__ __forceinline__ float w_taper_inv(const PhaseParams& P, double delta)
 
 // --- launchers (one per kernel family), all asynchronous on `stream` -------
 
+// vis_base: index of the first visibility of this call in the whole binning
+// (the pointers are offset to it; prediction records carry vis_base + index).
 cudaError_t launch_place(const PlaceParams& P, const double* uvw, const double* chan_scale,
                          const float2* vis, const float* weight, const uint8_t* flag,
                          int64_t nvis, uint32_t* hist, uint32_t* key, uint32_t* rank,
                          VisRecord* stage, double* weight_sum, unsigned long long* counts,
-                         int num_sms, cudaStream_t stream, int* launches);
+                         int num_sms, cudaStream_t stream, int* launches, int64_t vis_base = 0);
 
 // Imaging weights W' (uniform / Briggs) of every visibility into out[nvis];
 // density [C][N][N] and moments [2C] are scratch (zeroed here).

@@ -246,14 +246,19 @@ def test_plane_group_streaming_matches_single_pass(rk, orc):
     assert_image_close(outs[1][1], refs[0].real, taper, TOL)
 
 
-@pytest.mark.parametrize("nchan,kw", [(2, {}), (5, dict(hermitian_fold=True)),
-                                     (5, dict(fft_impl="own")),
-                                     (3, dict(grid_budget_bytes=2 * 256 * 256 * 8))])
-def test_host_entry_point_matches_device_path(rk, orc, nchan, kw):
-    """rick_dirty_image_host: with the whole grid in memory the channels are
-    transformed and downloaded in chunks (uneven for 5 channels); with a
-    plane budget it streams plane groups; both equal the device path."""
-    img, obs = meerkat(5, n_ant=8, n_steps=40, nchan=nchan, N=256, Nw=4, n_src=8)
+@pytest.mark.parametrize("nchan,kw,n_ant,n_steps", [(2, {}, 8, 40), (5, dict(hermitian_fold=True), 8, 40),
+                                                   (5, dict(fft_impl="own"), 8, 40),
+                                                   (3, dict(grid_budget_bytes=2 * 256 * 256 * 8), 8, 40),
+                                                   (3, dict(weighting="uniform"), 8, 40),
+                                                   (2, dict(fft_impl="own"), 7, 1)])
+def test_host_entry_point_matches_device_path(rk, orc, nchan, kw, n_ant, n_steps):
+    """rick_dirty_image_host: with the whole grid in memory the rows are
+    uploaded in chunks, each placed as it arrives (natural weighting; uniform
+    weighting uploads everything first), and the channels are transformed and
+    downloaded in chunks (uneven for 5 channels); with a plane budget it
+    streams plane groups; all equal the device path.  One time step of 7
+    antennas (21 rows) leaves row chunks of uneven size."""
+    img, obs = meerkat(5, n_ant=n_ant, n_steps=n_steps, nchan=nchan, N=256, Nw=4, n_src=8)
     plan = rk.Plan(plan_config(img, nchan, **kw))
     out = np.full((nchan, img.N, img.N), 7.0, np.float32)   # overwritten
     ws = np.zeros(nchan)
