@@ -793,16 +793,20 @@ def run_predict(args):
     stored with the fold), KB S = 8; the model is the observation's point
     sources inside the field where the taper gain is >= 1e-2, placed on their
     nearest pixels (the same model in every channel).
-    A step = rick_bin_predict + rick_model_to_wplanes + rick_fft_wplanes_forward
-    + rick_degrid_binned over all channels and planes; `value` = predicted
-    visibilities / s."""
+    A step = rick_bin_predict + rick_model_fft_wplanes (the model rows formed in
+    the own transform's row pass, pruned to the tiles the binning reaches) +
+    rick_degrid_binned over all channels and planes; with --fft cufft,
+    rick_model_to_wplanes + rick_fft_wplanes_forward (cuFFT) in place of the
+    fused call.  `value` = predicted visibilities / s."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
     _build.build()
     img, obs = make_workload(args.seed, "cuda")
     dev = _dev_inputs(obs)
     C, N = obs.nchan, img.N
-    cfg = plan_config(img, C, not args.no_fold)
+    from dataclasses import replace
+    own = args.fft == "own"
+    cfg = replace(plan_config(img, C, not args.no_fold), fft_impl=args.fft)
     ns = cfg.stored_planes
     plan = rick.Plan(cfg)
     plan.reserve(obs.nrow)
@@ -824,26 +828,31 @@ def run_predict(args):
     counts = torch.empty(2, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
+    names = ("bin", "model_fft", "degrid") if own else ("bin", "model", "fft", "degrid")
+
     def step(record=False):
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)] if record else None
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] if record else None
         if e: e[0].record(stream)
         plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow, counts)
         if e: e[1].record(stream)
-        plan.model_to_wplanes(J, 0, C, 0, ns, grids)
-        if e: e[2].record(stream)
-        plan.fft_wplanes_forward(grids, C * ns)
-        if e: e[3].record(stream)
+        if own:   # fused model rows + column pass, pruned to the binning
+            plan.model_fft_wplanes(J, 0, C, 0, ns, grids, pruned=True)
+        else:
+            plan.model_to_wplanes(J, 0, C, 0, ns, grids)
+            if e: e[2].record(stream)
+            plan.fft_wplanes_forward(grids, C * ns)
+        if e: e[len(names) - 1].record(stream)
         plan.degrid_binned(grids, 0, C, 0, ns, vis)
-        if e: e[4].record(stream)
+        if e: e[len(names)].record(stream)
         return e
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     n_pred, n_drop = counts.cpu().tolist()
-    off, _ = plan.bins()
-    own = np.diff(off.astype(np.int64)[::4])   # records per tile (own bins, all classes)
-    tiles_used = int((own > 0).sum())
+    off = plan.bin_offsets()
+    tiles_used = int((np.diff(off.astype(np.int64)[::4]) > 0).sum())   # tiles with records of their own
+    reach = reach_counts(off, C, ns, N, cfg.tile or 32)
     n0 = plan.launch_count()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     evs = []
@@ -856,14 +865,21 @@ def run_predict(args):
     ms = a.elapsed_time(b) / args.steps
     launches = plan.launch_count() - n0
     st = {k: statistics.median([e[i].elapsed_time(e[i + 1]) for e in evs])
-          for i, k in enumerate(("bin", "model", "fft", "degrid"))}
+          for i, k in enumerate(names)}
     hbm, peak_kind = peaks()
     cells = C * ns * N * N
     R = cfg.tile or 32
-    b_model = 8.0 * cells + 4.0 * C * N * N
     b_degrid = 24.0 * n_pred + 8.0 * tiles_used * (R + img.S - 1) ** 2
-    gbs = {"model": b_model / (st["model"] * 1e-3) / 1e9, "degrid": b_degrid / (st["degrid"] * 1e-3) / 1e9,
-           "fft": 16.0 * cells / (st["fft"] * 1e-3) / 1e9}
+    if own:
+        # image read once per channel; row pass writes and column pass reads the
+        # reached tile columns; the column pass writes the reached tiles
+        col_cells = reach["tile_columns"] * N * R
+        b_mf = 4.0 * C * N * N + 16.0 * col_cells + 8.0 * reach["tiles"] * R * R
+        gbs = {"model_fft": b_mf / (st["model_fft"] * 1e-3) / 1e9}
+    else:
+        b_model = 8.0 * cells + 4.0 * C * N * N
+        gbs = {"model": b_model / (st["model"] * 1e-3) / 1e9, "fft": 16.0 * cells / (st["fft"] * 1e-3) / 1e9}
+    gbs["degrid"] = b_degrid / (st["degrid"] * 1e-3) / 1e9
     # spot check against Eq. 1 summed over the sources (O2) on a few visibilities
     import oracle
     ocfg = oracle.Config(N, img.Nw, img.S, img.kernel, img.kernel_param, img.fov, img.w_min, img.w_max)
@@ -884,10 +900,10 @@ def run_predict(args):
                    "predicted": int(n_pred), "dropped": int(n_drop), "hermitian_fold": cfg.hermitian_fold,
                    "stored_planes": ns,
                    "model": f"{int(sel.sum())} of the 200 point sources (taper gain >= 1e-2) on pixels, every channel",
-                   "tiles_with_records": tiles_used},
-        "stages_ms": st, "stage_gbs": gbs,
-        "roofline_model": {"bound": "hbm", "achieved": gbs["model"], "peak": hbm, "unit": "GB/s",
-                           "frac": gbs["model"] / hbm, "peak_kind": peak_kind},
+                   "tiles_with_records": tiles_used, "fft": args.fft},
+        "stages_ms": st, "stage_gbs": gbs, "reach": reach,
+        "roofline_stages": {k: {"bound": "hbm", "achieved": v, "peak": hbm, "unit": "GB/s",
+                                "frac": v / hbm, "peak_kind": peak_kind} for k, v in gbs.items()},
         "roofline_degrid": {"bound": "hbm", "achieved": gbs["degrid"], "peak": hbm, "unit": "GB/s",
                             "frac": gbs["degrid"] / hbm, "peak_kind": peak_kind},
         "degrid_vis_per_s": n_pred / (st["degrid"] * 1e-3),
@@ -1164,8 +1180,8 @@ def run_profile_small(args):
     A step images the 2 channels and then predicts visibilities from the
     dirty images (the degridding path); --fft own (default) uses sparse
     gridding and the library's own transform (pruned column pass + row pass
-    fused with the reduction for imaging, column + row passes for prediction),
-    --fft cufft full gridding and cuFFT.  Runs warm-up + steps steps and
+    fused with the reduction for imaging; model rows fused with the row pass +
+    pruned column pass for prediction), --fft cufft full gridding and cuFFT.  Runs warm-up + steps steps and
     prints one JSON line."""
     import torch
     from paper_2601_19714_gb300 import _build, rick
@@ -1199,8 +1215,11 @@ def run_profile_small(args):
             plan.phase_correct_reduce(grids, 0, C, 0, ns, wsum, image)
         # prediction from the dirty image just made (exercises the degridder)
         plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], dev["flag"], obs.nrow)
-        plan.model_to_wplanes(image, 0, C, 0, ns, grids)
-        plan.fft_wplanes_forward(grids, C * ns)
+        if args.fft == "own":   # model rows fused with the row pass, pruned column pass
+            plan.model_fft_wplanes(image, 0, C, 0, ns, grids, pruned=True)
+        else:
+            plan.model_to_wplanes(image, 0, C, 0, ns, grids)
+            plan.fft_wplanes_forward(grids, C * ns)
         plan.degrid_binned(grids, 0, C, 0, ns, pvis)
         plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
                  wsum, counts)

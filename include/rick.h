@@ -412,6 +412,20 @@ rick_status rick_model_to_wplanes(rick_plan* plan, const float* image_real, int3
 /* In place, unnormalised 2-D forward FFT (exponent -) of n_planes planes. */
 rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
 
+/* rick_model_to_wplanes followed by rick_fft_wplanes_forward, fused, with the
+ * library's own transform (RICK_ERR_UNSUPPORTED with cuFFT): each model row
+ * M_k[q][.] is formed in registers and transformed along the row, so the
+ * model planes are never written; then the column pass.  grids receives the
+ * transformed planes, up to FP32 rounding those of the two calls.  flags:
+ * RICK_GRIDDED_BY_PLAN -- prune to the plan's current prediction binning
+ *   (rick_bin_predict): planes and tile columns that no binned visibility
+ *   reaches are skipped and only the reached tiles of grids are written (the
+ *   rest keep what they held); rick_degrid_binned of the same binning reads
+ *   nothing else.  The adjoint of rick_fft_phase_correct_reduce. */
+rick_status rick_model_fft_wplanes(rick_plan* plan, const float* image_real, int32_t chan_begin,
+                                   int32_t chan_end, int32_t plane_begin, int32_t plane_end, float* grids,
+                                   int32_t flags, void* stream);
+
 /* V for every visibility binned by rick_bin_predict whose channel and plane lie
  * in the ranges, from the transformed planes `grids` (layout as for
  * rick_grid_binned): vis_out[nrow][C] complex64 (device) receives those
@@ -423,7 +437,8 @@ rick_status rick_degrid_binned(rick_plan* plan, const float* grids, int32_t chan
 
 /* The whole prediction: rick_bin_predict, then per plane group of the
  * plan-owned grid rick_model_to_wplanes + rick_fft_wplanes_forward +
- * rick_degrid_binned.  vis_out[nrow][C] (device) is zeroed first, so skipped
+ * rick_degrid_binned (with the own transform: rick_model_fft_wplanes pruned
+ * to the binning + rick_degrid_binned).  vis_out[nrow][C] (device) is zeroed first, so skipped
  * visibilities read 0.  image_real[C][N][N] device f32. */
 rick_status rick_predict(rick_plan* plan, const double* uvw, const double* chan_scale,
                          const float* weight, const uint8_t* flag, int64_t nrow,

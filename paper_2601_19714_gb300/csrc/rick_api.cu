@@ -193,8 +193,9 @@ struct rick_plan {
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
     uint8_t* d_planeocc = nullptr;
     uint32_t* d_tileocc = nullptr;   // [C][planes][NT][ceil(NT/32)] tile bits
-    uint2* d_pix_turns = nullptr;    // fused row pass: per-pixel turns and scale [N][N]
+    uint2* d_pix_turns = nullptr;    // fused row passes: per-pixel turns and scales [N][N]
     float* d_pix_scale = nullptr;
+    float* d_pix_model_scale = nullptr;
     // w-kernel: tap polynomials and the constants of its transform C_w
     float w_coef[kMaxWSupport][kPolyDegree + 1] = {};
     double w_c0 = 1.0, w_s_i0 = 1.0;
@@ -219,6 +220,7 @@ void release(rick_plan* P) {
     dfree(P->d_tileocc);
     dfree(P->d_pix_turns);
     dfree(P->d_pix_scale);
+    dfree(P->d_pix_model_scale);
     dfree(P->d_density);
     dfree(P->d_wmom);
     dfree(P->d_wbuf);
@@ -478,8 +480,9 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         const size_t NN = (size_t)c.N * c.N;
         RK_CUDA(cudaMalloc(&P->d_pix_turns, sizeof(uint2) * NN));
         RK_CUDA(cudaMalloc(&P->d_pix_scale, sizeof(float) * NN));
+        RK_CUDA(cudaMalloc(&P->d_pix_model_scale, sizeof(float) * NN));
         RK_CUDA(launch_pixel_phase(phase_params(P, 0, 1, 0, 1), P->d_inv_taper, P->d_pix_turns, P->d_pix_scale,
-                                   nullptr));
+                                   P->d_pix_model_scale, nullptr));
         RK_CUDA(cudaDeviceSynchronize());
         return RICK_OK;   // no cuFFT plans
     }
@@ -810,11 +813,17 @@ rick_status phase_impl(rick_plan* P, const float* grids, int c0, int c1, int k0,
     return s;
 }
 
-// Occupancy of the gridded planes [k0, k1) of channels [c0, c1) from the
-// current binning (for pruning the own transform).
-rick_status occupancy_impl(rick_plan* P, int c0, int c1, int k0, int k1, cudaStream_t st) {
-    RK_ARG(P->binned && !P->binned_for_predict,
-           "RICK_GRIDDED_BY_PLAN needs the plan's binning for gridding (rick_bin)");
+// Occupancy of the planes [k0, k1) of channels [c0, c1) from the current
+// binning (for pruning the own transform): the gridding binning, or with
+// predict the prediction binning.
+rick_status occupancy_impl(rick_plan* P, int c0, int c1, int k0, int k1, cudaStream_t st,
+                           bool predict = false) {
+    if (predict)
+        RK_ARG(P->binned && P->binned_for_predict,
+               "RICK_GRIDDED_BY_PLAN on the model needs the plan's binning for prediction (rick_bin_predict)");
+    else
+        RK_ARG(P->binned && !P->binned_for_predict,
+               "RICK_GRIDDED_BY_PLAN needs the plan's binning for gridding (rick_bin)");
     int launches = 0;
     rick_status s = check_launch(launch_occupancy(P->d_offsets, c0, c1 - c0, k0, k1 - k0, P->planes, P->NT,
                                                   P->d_colocc, P->d_planeocc, P->d_tileocc, st, &launches),
@@ -928,6 +937,43 @@ rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0,
         launch_model_planes(phase_params(P, c0, c1, k0, k1), image, P->d_inv_taper,
                             reinterpret_cast<float2*>(grids), st, &launches),
         "model kernel");
+    P->launches += launches;
+    return s;
+}
+
+// Prediction's model planes and their forward 2-D DFT with the own transform:
+// the model rows are formed and transformed in one pass (never written as
+// model planes), then the column pass.  With RICK_GRIDDED_BY_PLAN (the plan's
+// prediction binning) unreached planes and tile columns are skipped and only
+// the reached tiles of the result are written.
+rick_status model_fft_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
+                           int32_t flags, cudaStream_t st) {
+    const rick_config& c = P->cfg;
+    if (!P->own_fft) {
+        set_err("the fused model pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+        return RICK_ERR_UNSUPPORTED;
+    }
+    RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
+    RK_ARG(0 <= k0 && k0 < k1 && k1 <= P->planes, "plane range");
+    RK_ARG(image && grids, "image and grids are required");
+    RK_ARG(((uintptr_t)grids & 15u) == 0 && ((uintptr_t)image & 3u) == 0,
+           "grids must be 16-byte and image 4-byte aligned");
+    P->last_stream = st;
+    Occupancy occ;
+    if (flags & RICK_GRIDDED_BY_PLAN) {
+        RK_TRY(occupancy_impl(P, c0, c1, k0, k1, st, true));
+        occ = plan_occupancy(P);
+        occ.tiles_out = true;
+    }
+    int launches = 0;
+    rick_status s = check_launch(launch_model_rows(phase_params(P, c0, c1, k0, k1), image, P->d_pix_turns,
+                                                   P->d_pix_model_scale, P->d_twid,
+                                                   reinterpret_cast<float2*>(grids), occ, st, &launches),
+                                 "fused model / row kernel");
+    if (s == RICK_OK)
+        s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids), (int64_t)(c1 - c0) * (k1 - k0),
+                                            P->Ng, false, P->d_twid, occ, st, &launches),
+                         "FFT column kernel");
     P->launches += launches;
     return s;
 }
@@ -1046,8 +1092,12 @@ rick_status predict_impl(rick_plan* P, const double* uvw, const double* chan_sca
         const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
         for (int k0 = 0; k0 < P->planes; k0 += gk) {
             const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
-            RK_TRY(model_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, st));
-            RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st, CUFFT_FORWARD));
+            if (P->own_fft) {   // fused model rows + pruned column pass
+                RK_TRY(model_fft_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, RICK_GRIDDED_BY_PLAN, st));
+            } else {
+                RK_TRY(model_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, st));
+                RK_TRY(fft_impl(P, g, (int64_t)(c1 - c0) * (k1 - k0), st, CUFFT_FORWARD));
+            }
             RK_TRY(degrid_impl(P, g, c0, c1, k0, k1, vis_out, st));
         }
     }
@@ -1566,6 +1616,14 @@ rick_status rick_model_to_wplanes(rick_plan* plan, const float* image_real, int3
     RK_ARG(plan != nullptr, "plan is NULL");
     return model_impl(plan, image_real, chan_begin, chan_end, plane_begin, plane_end, grids,
                       as_stream(stream));
+}
+
+rick_status rick_model_fft_wplanes(rick_plan* plan, const float* image_real, int32_t chan_begin,
+                                   int32_t chan_end, int32_t plane_begin, int32_t plane_end, float* grids,
+                                   int32_t flags, void* stream) {
+    RK_ARG(plan != nullptr, "plan is NULL");
+    return model_fft_impl(plan, image_real, chan_begin, chan_end, plane_begin, plane_end, grids, flags,
+                          as_stream(stream));
 }
 
 rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_planes, void* stream) {

@@ -294,17 +294,21 @@ k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, Occup
         for (int ty = tid; ty < occ.NT; ty += kThreads)
             s_live[ty] = (uint8_t)((occ.tile[(pl * occ.NT + ty) * occ.words + (tcol >> 5)] >> (tcol & 31)) & 1u);
     __syncthreads();
+    const bool in_mask = occ.tile != nullptr && !occ.tiles_out, out_mask = occ.tile != nullptr && occ.tiles_out;
     float2 a[16], x[16];
 #pragma unroll
     for (int t2 = 0; t2 < 16; ++t2) {
         const int row = b + T * t2;
         // an unreached tile is zero (and possibly unwritten): not read
-        a[t2] = (occ.tile == nullptr || s_live[row >> occ.tshift]) ? __ldcs(col + (size_t)row * N)
-                                                                  : make_float2(0.f, 0.f);
+        a[t2] = (!in_mask || s_live[row >> occ.tshift]) ? __ldcs(col + (size_t)row * N) : make_float2(0.f, 0.f);
     }
     transform<LOG2N, INV>(a, buf, b, tw, x);
+    // with tiles_out, only the reached tiles of the result are written
 #pragma unroll
-    for (int j = 0; j < 16; ++j) __stcs(col + (size_t)(b + T * j) * N, x[j]);
+    for (int j = 0; j < 16; ++j) {
+        const int row = b + T * j;
+        if (!out_mask || s_live[row >> occ.tshift]) __stcs(col + (size_t)row * N, x[j]);
+    }
 }
 
 // ---- pass 2: rows ---------------------------------------------------------------
@@ -346,10 +350,11 @@ __device__ __forceinline__ uint32_t turns_q32f(float t) {
 //     the plane step dw (n - 1) in turns, Q0.32 fixed point (FP64 -- or FP32
 //     under RICK_PREC_ALL_FP32 -- from n - 1 = -(l^2 + m^2)/(1 + n)), so that
 //     plane k's phase is t_0 + k dt, exact modulo one turn;
-//   scale[q N + p] = (-1)^(p+q) n / (C(p) C(q) C_w).
+//   scale[q N + p] = (-1)^(p+q) n / (C(p) C(q) C_w) (imaging),
+//   model_scale[q N + p] = (-1)^(p+q) / (n C(p) C(q) C_w) (prediction).
 // P describes stored plane 0 (w_first = its w).
 __global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper, uint2* __restrict__ turns,
-                              float* __restrict__ scale) {
+                              float* __restrict__ scale, float* __restrict__ model_scale) {
     const int N = P.N, halfN = N / 2;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * N) return;
@@ -367,7 +372,9 @@ __global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper
         turns[i] = make_uint2(turns_q32(P.w_first * delta), turns_q32(P.dw * delta));
     }
     const float sg = ((p + q) & 1) ? -1.f : 1.f;
-    scale[i] = sg * (float)n * inv_taper[p] * inv_taper[q] * w_taper_inv(P, delta);
+    const float c = sg * inv_taper[p] * inv_taper[q] * w_taper_inv(P, delta);
+    scale[i] = c * (float)n;
+    model_scale[i] = c / (float)n;
 }
 
 // Imaging, pass 2 fused with Eq. 2's phase screen and reduction: image row q
@@ -523,6 +530,78 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
                     part[p] = 0.f;
                 }
             }
+        }
+    }
+}
+
+// Prediction, the row pass run backwards (the adjoint of k_rows_phase_reduce):
+// for image row q (blockIdx.x) of every channel and plane of the launch, the
+// model row M_k[q][p] = J_c[q][p] (-1)^(p+q) exp(-2 pi i w_k (n - 1)) /
+// (n C(p) C(q) C_w) is formed in registers and transformed along the row
+// (exponent -), and the result is written to row q of plane k -- the first
+// pass of the forward 2-D DFT of the model plane, which is never written.
+// Thread b owns pixels p = b + (N/16) t2, the first stage's inputs.  The phase
+// of plane k is the exact phasor of the Q0.32 turns t_0 + k dt from the plan's
+// table.  With occ, unreached planes are skipped and only the reached tile
+// columns are written (the column pass reads nothing else, and the degridder
+// only the reached tiles).
+template <int LOG2N>
+__global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
+k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __restrict__ pix_turns,
+             const float* __restrict__ pix_model_scale, const float2* __restrict__ twid,
+             float2* __restrict__ grids, Occupancy occ) {
+    using Sh = Shape<LOG2N>;
+    constexpr int N = Sh::N, T = Sh::T;
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* tw = fsm;
+    float2* buf = fsm + Sh::kTw;
+    uint2* turns = reinterpret_cast<uint2*>(buf + Sh::kArray);   // (t_0, dt) per pixel
+    const int b = threadIdx.x, q = blockIdx.x;
+    load_tables<LOG2N>(twid, tw, b, T);
+    for (int j = b; j < N; j += T) turns[j] = __ldg(pix_turns + (size_t)q * N + j);
+    float ms[16];
+#pragma unroll
+    for (int t2 = 0; t2 < 16; ++t2) ms[t2] = __ldg(pix_model_scale + (size_t)q * N + b + T * t2);
+    __syncthreads();
+    const size_t NN = (size_t)N * N;
+    const bool warp_mask = occ.tshift >= 5 && T >= 32;
+    const int lane = b & 31;
+    for (int cc = 0; cc < P.nc; ++cc) {
+        float js[16];
+        const float* jr = image + (size_t)cc * NN + (size_t)q * N;
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) js[t2] = __ldg(jr + b + T * t2) * ms[t2];
+        for (int kk = 0; kk < P.nk; ++kk) {
+            const int r = cc * P.nk + kk;
+            if (occ.plane != nullptr && occ.plane[r] == 0) continue;   // no record on this plane
+            const uint32_t k = (uint32_t)(P.k_first + kk);
+            float2 a[16], x[16];
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) {
+                const uint2 ph = turns[b + T * t2];
+                float sn, cs;
+                sincospif((float)(int32_t)(ph.x + k * ph.y) * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                a[t2] = make_float2(js[t2] * cs, -js[t2] * sn);
+            }
+            transform<LOG2N, false>(a, buf, b, tw, x);
+            uint32_t live = 0xffffu;
+            if (occ.col != nullptr) {
+                const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+                if (warp_mask) {
+                    const bool on = lane < 16 && __ldg(cm + (((b & ~31) + T * lane) >> occ.tshift)) != 0;
+                    live = __ballot_sync(0xffffffffu, on);
+                } else {
+                    live = 0;
+#pragma unroll
+                    for (int t2 = 0; t2 < 16; ++t2)
+                        live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
+                }
+            }
+            float2* row = grids + (size_t)r * NN + (size_t)q * N;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if ((live >> j) & 1u) __stcs(row + b + T * j, x[j]);
+            __syncthreads();   // buf is rewritten by the next plane's first stage
         }
     }
 }
@@ -729,10 +808,40 @@ cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, 
     return e;
 }
 
+cudaError_t launch_model_rows(const PhaseParams& P, const float* image, const uint2* pix_turns,
+                              const float* pix_model_scale, const float2* twid, float2* grids,
+                              const Occupancy& occ, cudaStream_t st, int* launches) {
+    cudaError_t e = cudaErrorInvalidValue;
+#define RICK_MODEL_CASE(LG)                                                                         \
+    case LG: {                                                                                      \
+        using Sh = Shape<LG>;                                                                       \
+        auto fn = k_model_rows<LG>;                                                                 \
+        const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) + (size_t)Sh::N * sizeof(uint2); \
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
+        if (e == cudaSuccess) {                                                                     \
+            fn<<<Sh::N, Sh::T, smem, st>>>(P, image, pix_turns, pix_model_scale, twid, grids, occ); \
+            e = cudaGetLastError();                                                                 \
+        }                                                                                           \
+        break;                                                                                      \
+    }
+    switch (log2_exact(P.N)) {
+        RICK_MODEL_CASE(8)
+        RICK_MODEL_CASE(9)
+        RICK_MODEL_CASE(10)
+        RICK_MODEL_CASE(11)
+        RICK_MODEL_CASE(12)
+        RICK_MODEL_CASE(13)
+        default: break;
+    }
+#undef RICK_MODEL_CASE
+    if (e == cudaSuccess) ++*launches;
+    return e;
+}
+
 cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, uint2* turns, float* scale,
-                               cudaStream_t st) {
+                               float* model_scale, cudaStream_t st) {
     const int64_t n = (int64_t)P0.N * P0.N;
-    k_pixel_phase<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P0, inv_taper, turns, scale);
+    k_pixel_phase<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P0, inv_taper, turns, scale, model_scale);
     return cudaGetLastError();
 }
 

@@ -242,6 +242,10 @@ struct Occupancy {
     const uint8_t* plane = nullptr;
     const uint32_t* tile = nullptr;
     int tshift = 0, NT = 1, words = 1;
+    // column pass: false -- the input's unreached tiles are zero (imaging);
+    // true -- the input is dense and only the reached tiles of the output are
+    // written (prediction)
+    bool tiles_out = false;
 };
 // The three masks of the launch's planes (channels [c0, c0 + nc), stored
 // planes [k0, k0 + nk)) from the bin offsets of the plan's binning.
@@ -263,11 +267,18 @@ cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, 
                                      const uint2* pix_turns, const float* pix_scale, const float2* twid,
                                      float* image_real, float2* image_complex, const Occupancy& occ,
                                      cudaStream_t stream, int* launches);
-// The per-pixel table of the fused row pass ([N][N] each): the phase of
-// stored plane 0 and the plane step in Q0.32 turns, and the pixel's scale
-// (checkerboard sign, n, tapers); P0 = the phase parameters of stored plane 0.
+// The per-pixel table of the fused row passes ([N][N] each): the phase of
+// stored plane 0 and the plane step in Q0.32 turns, and the pixel's scale for
+// imaging (checkerboard sign, n, tapers) and for the model of a prediction
+// (sign, 1/n, tapers); P0 = the phase parameters of stored plane 0.
 cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, uint2* turns, float* scale,
-                               cudaStream_t stream);
+                               float* model_scale, cudaStream_t stream);
+// Prediction: the model rows of image[nc][N][N] for the launch's planes,
+// transformed along the rows (forward), into grids[nc][nk][N][N]; with occ,
+// unreached planes are skipped and only reached tile columns written.
+cudaError_t launch_model_rows(const PhaseParams& P, const float* image, const uint2* pix_turns,
+                              const float* pix_model_scale, const float2* twid, float2* grids,
+                              const Occupancy& occ, cudaStream_t stream, int* launches);
 
 // learned kernel network (rick_mlp.cu)
 int64_t mlp_param_count(int H);

@@ -39,7 +39,7 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_mlp_backward", "rick_adam_step", "rick_mlp_lattice_inputs", "rick_learn_create",
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
            "rick_status_string", "rick_last_error", "rick_stored_planes", "rick_bin_predict",
-           "rick_model_to_wplanes", "rick_fft_wplanes_forward", "rick_degrid_binned",
+           "rick_model_to_wplanes", "rick_fft_wplanes_forward", "rick_model_fft_wplanes", "rick_degrid_binned",
            "rick_predict"]
 
 
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH):
         "rick_bin_predict": [p, p, p, p, p, i64, p, p],
         "rick_model_to_wplanes": [p, p, i32, i32, i32, i32, p, p],
         "rick_fft_wplanes_forward": [p, p, i64, p],
+        "rick_model_fft_wplanes": [p, p, i32, i32, i32, i32, p, i32, p],
         "rick_degrid_binned": [p, p, i32, i32, i32, i32, p, p],
         "rick_predict": [p, p, p, p, p, i64, p, p, p, p],
     }
@@ -418,6 +419,16 @@ class Plan:
             self.handle, _ptr(image_real, d["f32"], "image_real", 8), chan_begin, chan_end,
             plane_begin, plane_end, _ptr(grids, d["c64"], "grids", 16), _stream(stream)),
             "rick_model_to_wplanes")
+
+    def model_fft_wplanes(self, image_real, chan_begin, chan_end, plane_begin, plane_end, grids,
+                          pruned=False, stream=None):
+        """rick_model_fft_wplanes: model planes and their forward 2-D DFT in one
+        call (own transform); pruned=True prunes to the prediction binning."""
+        d = _dt()
+        _check(load().rick_model_fft_wplanes(
+            self.handle, _ptr(image_real, d["f32"], "image_real", 4), chan_begin, chan_end,
+            plane_begin, plane_end, _ptr(grids, d["c64"], "grids", 16),
+            GRIDDED_BY_PLAN if pruned else 0, _stream(stream)), "rick_model_fft_wplanes")
 
     def fft_wplanes_forward(self, grids, n_planes, stream=None):
         d = _dt()
