@@ -233,14 +233,22 @@ __device__ __forceinline__ void accumulate_range(const GridParams& G,
         }
         __syncwarp();
         const int cnt = (int)min(32u, end - base);
-        for (int r0 = 0; r0 < cnt; r0 += RG) {
-            // 1-D taps of records r0 .. r0 + RG - 1 in one go: lane (m, q) holds
-            // tap q of record r0 + m (x taps q < S, y taps q - S)
-            float tap = 0.f;
+        // 1-D taps of records r0 .. r0 + RG - 1 in one go: lane (m, q) holds
+        // tap q of record r0 + m (x taps q < S, y taps q - S).  The taps of
+        // the next group are evaluated while the current group is
+        // accumulated, so the Horner chain's latency overlaps that work.
+        auto group_taps = [&](int r0) {
+            float t = 0.f;
             if (m < RG && r0 + m < cnt) {
                 const float4 fm = stg4[r0 + m];
-                tap = tap_poly(cf, fmaf(2.0f, q < S ? fm.x : fm.y, -1.0f));
+                t = tap_poly(cf, fmaf(2.0f, q < S ? fm.x : fm.y, -1.0f));
             }
+            return t;
+        };
+        float tap_next = group_taps(0);
+        for (int r0 = 0; r0 < cnt; r0 += RG) {
+            const float tap = tap_next;
+            if (r0 + RG < cnt) tap_next = group_taps(r0 + RG);
             const int nr = min(RG, cnt - r0);
             if constexpr (SS == 4) {
                 // two records per pass, 16 lanes each (lane = cell 4b + a, both
