@@ -541,10 +541,13 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 // (exponent -), and the result is written to row q of plane k -- the first
 // pass of the forward 2-D DFT of the model plane, which is never written.
 // Thread b owns pixels p = b + (N/16) t2, the first stage's inputs.  The phase
-// of plane k is the exact phasor of the Q0.32 turns t_0 + k dt from the plan's
-// table.  With occ, unreached planes are skipped and only the reached tile
-// columns are written (the column pass reads nothing else, and the degridder
-// only the reached tiles).
+// of plane k, ph = exp(-2 pi i t_k), is advanced from plane to plane by
+// ph <- ph z, z = exp(-2 pi i dt) (in shared memory), and formed exactly from
+// the Q0.32 turns t_0 + k dt of the plan's table at the first plane of every
+// block of 8, which bounds the FP32 rounding of the powers of z as in the
+// imaging pass.  With occ, unreached planes are skipped and only the
+// reached tile columns are written (the column pass reads nothing else, and
+// the degridder only the reached tiles).
 template <int LOG2N>
 __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
 k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __restrict__ pix_turns,
@@ -555,34 +558,68 @@ k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __rest
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
-    uint2* turns = reinterpret_cast<uint2*>(buf + Sh::kArray);   // (t_0, dt) per pixel
+    float2* zrot = buf + Sh::kArray;                            // z = e^(-2 pi i dt) per pixel
+    float* js = reinterpret_cast<float*>(zrot + N);             // J_c(p) times the pixel's scale
     const int b = threadIdx.x, q = blockIdx.x;
+    const uint2* turns = pix_turns + (size_t)q * N;
     load_tables<LOG2N>(twid, tw, b, T);
-    for (int j = b; j < N; j += T) turns[j] = __ldg(pix_turns + (size_t)q * N + j);
-    float ms[16];
-#pragma unroll
-    for (int t2 = 0; t2 < 16; ++t2) ms[t2] = __ldg(pix_model_scale + (size_t)q * N + b + T * t2);
-    __syncthreads();
+#pragma unroll 4
+    for (int t2 = 0; t2 < 16; ++t2) {
+        const int p = b + T * t2;
+        float s, c;
+        sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
+        zrot[p] = make_float2(c, -s);
+    }
     const size_t NN = (size_t)N * N;
     const bool warp_mask = occ.tshift >= 5 && T >= 32;
     const int lane = b & 31;
     for (int cc = 0; cc < P.nc; ++cc) {
-        float js[16];
         const float* jr = image + (size_t)cc * NN + (size_t)q * N;
-#pragma unroll
-        for (int t2 = 0; t2 < 16; ++t2) js[t2] = __ldg(jr + b + T * t2) * ms[t2];
+        const float* ms = pix_model_scale + (size_t)q * N;
+        __syncthreads();   // the previous channel's js reads are done
+#pragma unroll 4
+        for (int t2 = 0; t2 < 16; ++t2) {
+            const int p = b + T * t2;
+            js[p] = __ldg(jr + p) * __ldg(ms + p);
+        }
+        // ph holds the phase of plane kcur; it is formed exactly at the first
+        // plane of each block of kHornerBlock planes and advanced plane by plane
+        // -- across skipped planes too, so that pruning does not change the
+        // arithmetic
+        float2 ph[16];
+        int kcur = 0, block = -1;
         for (int kk = 0; kk < P.nk; ++kk) {
             const int r = cc * P.nk + kk;
             if (occ.plane != nullptr && occ.plane[r] == 0) continue;   // no record on this plane
-            const uint32_t k = (uint32_t)(P.k_first + kk);
+            if (kk / kHornerBlock != block) {
+                block = kk / kHornerBlock;
+                kcur = block * kHornerBlock;
+                const uint32_t k = (uint32_t)(P.k_first + kcur);
+#pragma unroll
+                for (int t2 = 0; t2 < 16; ++t2) {
+                    const uint2 t = __ldg(&turns[b + T * t2]);
+                    float sn, cs;
+                    sincospif((float)(int32_t)(t.x + k * t.y) * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                    ph[t2] = make_float2(cs, -sn);
+                }
+            }
+            for (; kcur < kk; ++kcur) {   // over skipped planes
+#pragma unroll
+                for (int t2 = 0; t2 < 16; ++t2) {
+                    const float2 z = zrot[b + T * t2];
+                    ph[t2] = make_float2(fmaf(ph[t2].x, z.x, -ph[t2].y * z.y), fmaf(ph[t2].x, z.y, ph[t2].y * z.x));
+                }
+            }
             float2 a[16], x[16];
 #pragma unroll
             for (int t2 = 0; t2 < 16; ++t2) {
-                const uint2 ph = turns[b + T * t2];
-                float sn, cs;
-                sincospif((float)(int32_t)(ph.x + k * ph.y) * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
-                a[t2] = make_float2(js[t2] * cs, -js[t2] * sn);
+                const int p = b + T * t2;
+                const float j = js[p];
+                const float2 z = zrot[p];
+                a[t2] = make_float2(j * ph[t2].x, j * ph[t2].y);
+                ph[t2] = make_float2(fmaf(ph[t2].x, z.x, -ph[t2].y * z.y), fmaf(ph[t2].x, z.y, ph[t2].y * z.x));
             }
+            kcur = kk + 1;
             transform<LOG2N, false>(a, buf, b, tw, x);
             uint32_t live = 0xffffu;
             if (occ.col != nullptr) {
@@ -816,7 +853,7 @@ cudaError_t launch_model_rows(const PhaseParams& P, const float* image, const ui
     case LG: {                                                                                      \
         using Sh = Shape<LG>;                                                                       \
         auto fn = k_model_rows<LG>;                                                                 \
-        const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) + (size_t)Sh::N * sizeof(uint2); \
+        const size_t smem = (size_t)(Sh::kTw + Sh::kArray + Sh::N) * sizeof(float2) + (size_t)Sh::N * sizeof(float); \
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
         if (e == cudaSuccess) {                                                                     \
             fn<<<Sh::N, Sh::T, smem, st>>>(P, image, pix_turns, pix_model_scale, twid, grids, occ); \
