@@ -14,7 +14,10 @@
 //     the transform).
 // Every plane is therefore read twice and written once (24 B per cell) on the
 // imaging path, against one read and one write per pass of a generic 2-D FFT
-// plus the reduction's read.
+// plus the reduction's read.  The prediction runs the same passes the other
+// way: k_model_rows forms each model row from the image (the phase screen
+// exp(-2 pi i w_k (n - 1)) and the scales) and transforms it along the row,
+// so the model planes are never written, then the column pass.
 //
 // The length-N DFT (N = 2^m, 256 <= N <= 8192) is a Stockham decimation-in-
 // frequency transform with radix-16 stages and, where m is not a multiple of
@@ -36,6 +39,9 @@
 // and reads the unreached tile columns as zeros (the column pass left them
 // untouched) -- the same result as the full transform of the zero-filled
 // planes, with less work, and no read of a cell the gridder may have skipped.
+// For the prediction the occupancy of its binning prunes the outputs instead:
+// unreached planes and tile columns are not transformed, and the column pass
+// writes only the reached tiles (the degridder reads nothing else).
 //
 // Shared arrays are indexed through skew(a) = a + a/16, which spreads the
 // stride-16 stores of the first stages over all banks.  Twiddles: a radix-16
