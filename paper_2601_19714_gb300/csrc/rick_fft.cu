@@ -46,12 +46,12 @@
 // Shared arrays are indexed through skew(a) = a + a/16, which spreads the
 // stride-16 stores of the first stages over all banks.  Twiddles: a radix-16
 // stage with M = 16^s needs W^(e f0), f0 = 1..15, e = t1 M, for the thread's
-// butterfly t1.  A per-stage table, rounded from FP64 on the host, holds
-// W^e, W^2e, W^4e and W^8e for every t1 (e^(+2 pi i e/N); conjugated for the
-// forward transform); the other eleven powers are products of at most three
-// of them (W^7e = W^4e W^2e W^e, W^15e = W^8e W^7e).  A CTA copies the tables
-// into shared memory once: four table reads per stage and thread instead of
-// one per twiddle.
+// butterfly t1.  Per-stage tables, rounded from FP64 on the host
+// (e^(+2 pi i e/N); conjugated for the forward transform), hold for stage 0,
+// whose t1 takes N/16 values, W^e, W^2e, W^4e and W^8e -- the other eleven
+// powers are products of at most three of them (W^7e = W^4e W^2e W^e, W^15e =
+// W^8e W^7e) -- and for the later stages, whose t1 takes at most N/256 values,
+// all fifteen.  A CTA copies the tables into shared memory once.
 #include <cmath>
 #include <vector>
 
@@ -165,11 +165,13 @@ struct Shape {
     static constexpr int kArray = N + N / 16;         // skewed array length
     // radix-16 stages with twiddles (all but a last radix-16 stage)
     static constexpr int kTwStages = kLastR == 1 ? kR16 - 1 : kR16;
-    // butterfly groups t1 of stage s, and the offset of its table (4 entries per t1)
+    // butterfly groups t1 of stage s, table entries per t1 (stage 0: 4 powers,
+    // the others: all 15), and the offset of the stage's table
     __host__ __device__ static constexpr int stage_cnt(int s) { return (N / 16) >> (4 * s); }
+    __host__ __device__ static constexpr int stage_per(int s) { return s == 0 ? 4 : 15; }
     __host__ __device__ static constexpr int stage_off(int s) {
         int o = 0;
-        for (int i = 0; i < s; ++i) o += 4 * stage_cnt(i);
+        for (int i = 0; i < s; ++i) o += stage_per(i) * stage_cnt(i);
         return o;
     }
     static constexpr int kTw = stage_off(kTwStages);  // twiddle table entries
@@ -178,8 +180,10 @@ struct Shape {
 
 // Radix-16 stage s (M = 16^s, not the last stage): a holds the butterfly's
 // inputs u + (N/16) t2 for u = b; the DFT, the twiddles W_N^(t1 f0 M) from the
-// stage's table sw (sw[j cnt + t1] = W^(2^j t1 M), j < 4) and the stores
-// t1 16 M + g + M f0 into buf.
+// stage's table sw (stage 0: sw[j cnt + t1] = W^(2^j t1 M), j < 4, the other
+// powers formed from them; later stages, whose t1 takes few values, hold all
+// fifteen: sw[(f0 - 1) cnt + t1] = W^(t1 f0 M)) and the stores t1 16 M + g +
+// M f0 into buf.
 template <int LOG2N, bool INV>
 __device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float2* buf,
                                             const float2* tw) {
@@ -192,6 +196,16 @@ __device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float
     // t1 = 0: the table holds W^0 = 1 exactly, and a * 1 = a exactly
     const int cnt = Sh::stage_cnt(s);
     const float2* sw = tw + Sh::stage_off(s) + t1;
+    if (Sh::stage_per(s) == 15) {
+        buf[skew(base)] = a[0];
+#pragma unroll
+        for (int f0 = 1; f0 < 16; ++f0) {
+            float2 w = sw[(f0 - 1) * cnt];
+            if (!INV) w.y = -w.y;
+            buf[skew(base + M * f0)] = cmulf(a[f0], w);
+        }
+        return;
+    }
     float2 w[16];
     w[1] = sw[0];
     w[2] = sw[cnt];
@@ -761,8 +775,9 @@ bool fft_supported(int N) {
 }
 
 void fft_twiddles(int N, std::vector<float2>& out) {
-    // per radix-16 stage s with twiddles (M = 16^s, cnt = N/16/M groups t1):
-    // entries [j cnt + t1] = e^(+2 pi i 2^j t1 M / N), j < 4, from FP64
+    // per radix-16 stage s with twiddles (M = 16^s, cnt = N/16/M groups t1),
+    // from FP64: stage 0 entries [j cnt + t1] = e^(+2 pi i 2^j t1 M / N), j < 4;
+    // later stages [(f0 - 1) cnt + t1] = e^(+2 pi i f0 t1 M / N), f0 = 1..15
     const int log2n = log2_exact(N);
     const int stages = (log2n % 4 == 0) ? log2n / 4 - 1 : log2n / 4;
     out.clear();
@@ -770,9 +785,11 @@ void fft_twiddles(int N, std::vector<float2>& out) {
     for (int st = 0; st < stages; ++st) {
         const int64_t M = (int64_t)1 << (4 * st);
         const int cnt = (int)((N / 16) / M);
-        for (int j = 0; j < 4; ++j)
+        const int per = st == 0 ? 4 : 15;
+        for (int j = 0; j < per; ++j)
             for (int t1 = 0; t1 < cnt; ++t1) {
-                const int64_t e = ((int64_t)t1 * M) << j;   // < N/2
+                const int64_t f = st == 0 ? ((int64_t)1 << j) : j + 1;
+                const int64_t e = (int64_t)t1 * M * f;   // < N
                 const double a = two_pi * (double)e / N;
                 out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
             }
