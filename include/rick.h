@@ -173,8 +173,12 @@ typedef struct rick_plan rick_plan;
 /* ---- plan ------------------------------------------------------------ */
 
 /* Validate cfg, build the kernel and taper tables (FP64 on the host) and the
- * cuFFT plans.  The current CUDA device is the plan's device.  On failure
- * *out is NULL and nothing is leaked. */
+ * cuFFT plans -- or, with the library's own transform (fft_impl 1), its
+ * twiddle tables, the per-pixel table of the fused row passes (the phase of
+ * stored plane 0 and the plane step as Q0.32 turns, and the imaging and model
+ * scales: 16 bytes per image pixel, computed once in FP64 on the device) and
+ * the occupancy masks used for pruning.  The current CUDA device is the
+ * plan's device.  On failure *out is NULL and nothing is leaked. */
 rick_status rick_plan_create(const rick_config* cfg, rick_plan** out);
 
 /* Release the plan and everything it owns.  NULL is accepted. */
