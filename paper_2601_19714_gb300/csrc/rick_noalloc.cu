@@ -9,15 +9,20 @@
 // their back breaks the accounting.  rick_grid needs a plan, and creating a
 // plan allocates tables, scratch and cuFFT work areas; this entry point takes
 // the configuration directly and keeps its scratch in one fixed array in device
-// memory that exists from the moment the library's device code is loaded.
+// memory.
 //
-// The array is kNoallocScratchBytes (32 MiB) on every GPU that loads the
-// library, held until the process exits.  A call whose binning scratch does
-// not fit (roughly 40 bytes per visibility plus 8 bytes per bin) is rejected
-// with RICK_ERR_CAPACITY before anything is launched.  All calls share the
-// array: each call clears what must start at zero, and calls whose work
-// overlaps on the GPU (different streams, or different host threads) race on
-// it -- serialise them.
+// The array is kNoallocScratchBytes (32 MiB).  CUDA loads a library's device
+// code lazily by default: the array and the kernels this call runs are loaded,
+// and take device memory, on the first call on each device (the address lookup
+// below loads the array's module; the first launch of each kernel loads that
+// kernel).  After that first call -- make it at start-up, outside any stream
+// capture, with the support and tile size that later calls use -- calls
+// allocate nothing, and the array stays until the process exits.  A call whose
+// binning scratch does not fit (roughly 40 bytes per visibility plus 8 bytes
+// per bin) is rejected with RICK_ERR_CAPACITY, and every other refusal is made
+// too, before anything is launched.  All calls share the array: each call
+// clears what must start at zero, and calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on it -- serialise them.
 #include <cmath>
 #include <cstdio>
 #include <mutex>
@@ -59,6 +64,10 @@ rick_status scratch_address(unsigned char** out) {
     if (!g_scratch_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, rick_noalloc_scratch);
+        if (e == cudaErrorMemoryAllocation)   // loading the array's module needs its 32 MiB
+            return fail(RICK_ERR_OOM,
+                        "rick_grid_noalloc: no device memory left to load the 32 MiB scratch on its first "
+                        "call on this device; make the first call at start-up");
         if (e != cudaSuccess || p == nullptr)
             return fail(RICK_ERR_CUDA, "rick_grid_noalloc: cudaGetSymbolAddress of the scratch failed");
         g_scratch_addr[dev] = p;
@@ -77,19 +86,12 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
                                          int32_t plane_begin, int32_t plane_end, float* grids,
                                          double* weight_sum, int64_t* counts, void* stream) {
     if (!cfg) return fail(RICK_ERR_INVALID_ARG, "invalid argument: cfg is NULL");
+    // the same configuration check as rick_plan_create, then what needs a plan
+    const rick_status valid = validate_config(cfg);
+    if (valid != RICK_OK) return valid;
     const rick_config& c = *cfg;
     const int T = c.tile ? c.tile : 32;
     const int threads = c.grid_threads ? c.grid_threads : 128;
-    if (c.N < 64 || c.N > 65536 || (c.N & (c.N - 1)) || !(T == 16 || T == 32 || T == 64) ||
-        (size_t)(threads / 32) * T * (T + 8) * 8 > (size_t)160 * 1024 ||
-        T > c.N || c.n_wplanes < 1 || c.n_channels < 1 || c.support < 1 || c.support > 16 ||
-        c.support > T || !(c.fov_rad > 0.0 && c.fov_rad < 1.0) ||
-        !(std::isfinite(c.w_min) && std::isfinite(c.w_max)) ||
-        (c.n_wplanes > 1 && !(c.w_max > c.w_min)) || !(c.kernel_param > 0.0) ||
-        !(threads == 128 || threads == 256 || threads == 512) ||
-        !(c.precision == RICK_PREC_FP32_FP64IDX || c.precision == RICK_PREC_ALL_FP32) ||
-        !(c.hermitian_fold == 0 || (c.hermitian_fold == 1 && c.w_min == -c.w_max)))
-        return fail(RICK_ERR_INVALID_ARG, "invalid argument: configuration");
     const int planes = rick_stored_planes(cfg);
     if (c.kernel_kind != RICK_KERNEL_GAUSS && c.kernel_kind != RICK_KERNEL_KAISER_BESSEL)
         return fail(RICK_ERR_UNSUPPORTED,
@@ -109,25 +111,32 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     if (((uintptr_t)grids & 15u) != 0)
         return fail(RICK_ERR_INVALID_ARG, "invalid argument: grids must be 16-byte aligned");
 
+    // sizes, each product tested before it is formed (validate_config bounds
+    // the bins below 2^32)
     const int NT = c.N / T;
     const uint64_t nkeys = (uint64_t)c.n_channels * planes * (uint64_t)NT * NT * 4ull;
-    const uint64_t nvis = (uint64_t)nrow * (uint64_t)c.n_channels;
+    const uint64_t limit = 0xFFFFFFFFull;
+    const bool vis_fit = (uint64_t)nrow < limit / (uint64_t)c.n_channels;
+    const uint64_t nvis = vis_fit ? (uint64_t)nrow * (uint64_t)c.n_channels : limit;
     const uint64_t items = (uint64_t)c.n_channels * (plane_end - plane_begin) * (uint64_t)NT * NT;
     // scratch layout: hist, offsets, scan partials, key, rank, stage, records, counter, counts
     const size_t b_hist = up256(nkeys * 4), b_off = up256((nkeys + 1) * 4);
     const size_t b_part = up256(scan_partials_needed(nkeys) * 4);
     const size_t b_key = up256(nvis * 4), b_rec = up256(nvis * sizeof(VisRecord));
     const size_t need = b_hist + b_off + b_part + 2 * b_key + 2 * b_rec + 256 + 256;
-    if (nkeys >= 0xFFFFFFFFull || nvis >= 0xFFFFFFFFull || items >= 0xFFFFFFFFull ||
-        need > kNoallocScratchBytes) {
+    if (!vis_fit || nkeys >= limit || items >= limit || need > kNoallocScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof msg,
-                 "rick_grid_noalloc: needs %llu bytes of scratch (%llu visibilities, %llu bins); "
+                 "rick_grid_noalloc: needs %llu bytes of scratch (%lld rows x %d channels, %llu bins); "
                  "the fixed scratch holds %llu bytes -- use rick_grid with a plan",
-                 (unsigned long long)need, (unsigned long long)nvis, (unsigned long long)nkeys,
-                 (unsigned long long)kNoallocScratchBytes);
+                 vis_fit ? (unsigned long long)need : ~0ull, (long long)nrow, c.n_channels,
+                 (unsigned long long)nkeys, (unsigned long long)kNoallocScratchBytes);
         return fail(RICK_ERR_CAPACITY, msg);
     }
+
+    GridParams G;
+    if (!(fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, G) <= 1e-6))
+        return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: kernel too narrow for its support");
 
     unsigned char* base = nullptr;
     rick_status s = scratch_address(&base);
@@ -192,7 +201,6 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     if (e == cudaSuccess)
         e = launch_scatter(key, rank, stage, offsets, records, (int64_t)nvis, num_sms, st, &launches);
     if (e == cudaSuccess) {
-        GridParams G;
         G.N = c.N;
         G.S = c.support;
         G.T = T;
@@ -204,15 +212,13 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
         G.nk = plane_end - plane_begin;
         G.n_items = (uint32_t)items;
         G.kind = c.kernel_kind;
-        if (!(fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, G) <= 1e-6))
-            return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: kernel too narrow for its support");
         G.table = nullptr;
         G.lattice = 0;
         G.lists = nullptr;  // natural tile order (no scheduling scratch)
         G.list_cap = 0;
         G.w_support = 0;
         G.skip_empty = 0;
-        G.grab = c.tiles_per_grab > 0 && c.tiles_per_grab <= 8 ? (uint32_t)c.tiles_per_grab : 4u;
+        G.grab = c.tiles_per_grab > 0 ? (uint32_t)c.tiles_per_grab : 4u;   // validated: 0..8
         e = launch_grid(G, offsets, records, reinterpret_cast<float2*>(grids), counter, threads,
                         num_sms, st, &launches);
     }
