@@ -129,6 +129,8 @@ def _declare(L):
     L.oracle_channel_stats.argtypes = [cfgp, p, p, C.c_int, p, p, i64, C.c_int, p, p, p]
     L.oracle_image.restype = C.c_int
     L.oracle_image.argtypes = vis_args + [C.c_int, p, p]
+    L.oracle_phase_accumulate.argtypes = [cfgp, C.c_int, p, p]
+    L.oracle_image_scale.argtypes = [cfgp, d, p, p]
     L.oracle_image_at.restype = C.c_int
     L.oracle_image_at.argtypes = vis_args + [C.c_int, C.c_int, i64, p, p, p]
     L.oracle_dft_at.restype = C.c_int
@@ -357,6 +359,37 @@ def image(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0):
     if rc != 0:
         raise ValueError(f"oracle_image failed ({rc})")
     return out, ws.value
+
+
+def ifft2_inplace(a: np.ndarray) -> np.ndarray:
+    """ifft2 without the copy: ``a`` (C-contiguous complex128, square, power of
+    two) is overwritten by its unnormalised inverse 2-D DFT and returned."""
+    if a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise ValueError("ifft2_inplace needs a C-contiguous complex128 array")
+    if lib().oracle_ifft2(a.shape[0], _ptr(a)) != 0:
+        raise ValueError("oracle_ifft2: N must be a power of two")
+    return a
+
+
+def phase_accumulate(cfg: Config, plane: int, F: np.ndarray, img: np.ndarray) -> None:
+    """One term of Eq. 2's sum over planes: img[q, p] += F[q, p] exp(+2 pi i
+    w_plane (n - 1)) over the N x N image (F: the transformed plane, complex128
+    [Ng, Ng]; img: complex128 [N, N], updated in place)."""
+    if F.dtype != np.complex128 or img.dtype != np.complex128 or not (F.flags.c_contiguous and
+                                                                      img.flags.c_contiguous):
+        raise ValueError("phase_accumulate needs C-contiguous complex128 arrays")
+    c = cfg.c()
+    lib().oracle_phase_accumulate(C.byref(c), int(plane), _ptr(F), _ptr(img))
+
+
+def image_scale(cfg: Config, weight_sum: float, img: np.ndarray) -> None:
+    """Eq. 2's normalisation of a summed image, in place: times (-1)^(p+q) n /
+    (sum W C(p) C(q) C_w)."""
+    if img.dtype != np.complex128 or not img.flags.c_contiguous:
+        raise ValueError("image_scale needs a C-contiguous complex128 array")
+    Ct = taper(cfg.kernel if cfg.kernel != "learned" else "kb", cfg.kernel_param, cfg.S, cfg.N, cfg.Ng)
+    c = cfg.c()
+    lib().oracle_image_scale(C.byref(c), float(weight_sum), _ptr(Ct), _ptr(img))
 
 
 def image_at(cfg: Config, uvw, chan_scale, vis, weight, flag=None, channel=0, p=(), q=(),

@@ -745,6 +745,9 @@ static double complex turn_phasor(double t)
 /* O1: the w-stacking dirty image (Eq. 2 and 3, R5, R6)                */
 /* ------------------------------------------------------------------ */
 
+void oracle_phase_accumulate(const oracle_cfg* cfg, int k, const double complex* F, double complex* img);
+void oracle_image_scale(const oracle_cfg* cfg, double ws, const double* Ct, double complex* img);
+
 /* Complex dirty image of channel c, N x N, row q (m) major, column p (l):
  *   I[q][p] = (-1)^(p+q) n / (sum W * C(p) C(q)) * sum_k F_k[q][p] exp(+2 pi i w_k (n-1))
  * where F_k is the unnormalised inverse 2-D DFT of the gridded plane k.
@@ -754,7 +757,7 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
                  double complex* img, double* weight_sum_out)
 {
     if (check_cfg(cfg)) return 1;
-    int N = cfg->N, Ng = grid_n(cfg), off = pad_off(cfg);
+    int N = cfg->N, Ng = grid_n(cfg);
     size_t NN = (size_t)N * N;
     double complex* G = (double complex*)malloc(sizeof(double complex) * (size_t)Ng * Ng);
     double* Ct = (double*)malloc(sizeof(double) * N);
@@ -768,14 +771,35 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
         long nk = oracle_grid_plane(cfg, uvw, scale, C, vis, weight, flag, nrow, c, k, G);
         if (nk <= 0) continue;
         oracle_ifft2(Ng, G);
-        double wk = oracle_plane_w(cfg, k);
-        for (int q = 0; q < N; ++q)
-            for (int p = 0; p < N; ++p) {
-                double n, d;
-                pixel_n(cfg, p, q, &n, &d);
-                img[(size_t)q * N + p] += G[(size_t)(q + off) * Ng + (p + off)] * turn_phasor(wk * d);
-            }
+        oracle_phase_accumulate(cfg, k, G, img);
     }
+    oracle_image_scale(cfg, ws, Ct, img);
+    if (weight_sum_out) *weight_sum_out = ws;
+    free(G);
+    free(Ct);
+    return 0;
+}
+
+/* Eq. 2, one term of the sum over planes: img[q][p] += F_k[q][p] exp(+2 pi i
+ * w_k (n - 1)) over the image pixels, F_k the transformed plane k (Ng x Ng;
+ * the image is its central N x N). */
+void oracle_phase_accumulate(const oracle_cfg* cfg, int k, const double complex* F, double complex* img)
+{
+    int N = cfg->N, Ng = grid_n(cfg), off = pad_off(cfg);
+    double wk = oracle_plane_w(cfg, k);
+    for (int q = 0; q < N; ++q)
+        for (int p = 0; p < N; ++p) {
+            double n, d;
+            pixel_n(cfg, p, q, &n, &d);
+            img[(size_t)q * N + p] += F[(size_t)(q + off) * Ng + (p + off)] * turn_phasor(wk * d);
+        }
+}
+
+/* The normalisation of Eq. 2 with R5, R6: img[q][p] *= (-1)^(p+q) n /
+ * (sum W C(p) C(q) C_w) (0 if sum W = 0); Ct = the taper C(p). */
+void oracle_image_scale(const oracle_cfg* cfg, double ws, const double* Ct, double complex* img)
+{
+    int N = cfg->N;
     for (int q = 0; q < N; ++q)
         for (int p = 0; p < N; ++p) {
             double n, d;
@@ -784,10 +808,6 @@ int oracle_image(const oracle_cfg* cfg, const double* uvw, const double* scale, 
             double s = ws != 0.0 ? sgn * n / (ws * Ct[p] * Ct[q] * w_taper(cfg, d)) : 0.0;
             img[(size_t)q * N + p] *= s;
         }
-    if (weight_sum_out) *weight_sum_out = ws;
-    free(G);
-    free(Ct);
-    return 0;
 }
 
 /* O1 at chosen pixels without the FFT: the same image value written as the
