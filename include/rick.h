@@ -88,6 +88,12 @@ typedef enum {
  *   Briggs:  W' = W / (1 + f^2 D(cell)),  f^2 = (5 10^-R)^2 sum D / sum D^2
  * over the cells of the channel, R = robust (R -> +inf: natural, R -> -inf:
  * proportional to uniform).  W' is stored in FP32. */
+/* The 2-D DFT of the w-planes (rick_config.fft_impl). */
+typedef enum {
+    RICK_FFT_OWN = 0,   /* the library's own transform where it applies (the default) */
+    RICK_FFT_CUFFT = 1  /* cuFFT */
+} rick_fft_impl;
+
 typedef enum {
     RICK_WEIGHT_NATURAL = 0,
     RICK_WEIGHT_UNIFORM = 1,
@@ -145,10 +151,11 @@ typedef struct rick_config {
      * trainer (RICK_ERR_INVALID_ARG / RICK_ERR_UNSUPPORTED). */
     int32_t w_support;
     double w_kernel_param;
-    /* 2-D DFT of the w-planes: 0 = cuFFT (batched, fft_batch planes per
-     * execution); 1 = the library's own two-pass transform for power-of-two
-     * 256 <= N <= 8192 (columns, then rows; the imaging path fuses the row
-     * pass with the phase screen and reduction; cuFFT for other N). */
+    /* 2-D DFT of the w-planes, rick_fft_impl: RICK_FFT_OWN (0, the default) =
+     * the library's own two-pass transform (columns, then rows; the imaging
+     * path fuses the row pass with the phase screen and reduction) on an
+     * unpadded power-of-two mesh 256 <= N <= 16384, cuFFT on any other mesh;
+     * RICK_FFT_CUFFT (1) = cuFFT, batched (fft_batch planes per execution). */
     int32_t fft_impl;
     int32_t weighting;    /* rick_weighting (0 = natural); imaging only, prediction ignores it */
     double robust;        /* Briggs robustness R (weighting = RICK_WEIGHT_BRIGGS) */
@@ -158,8 +165,8 @@ typedef struct rick_config {
      * grid array of the API is Ng x Ng, and the image is the central N x N of
      * the transformed planes, divided by C(p) = int g(s) cos(2 pi s (p - N/2)/Ng)
      * ds (rick_plan_taper returns it).  Less aliasing at the field edge for
-     * alpha^2 times the grid memory and FFT work.  Needs fft_impl 0 and a
-     * Gaussian or Kaiser-Bessel kernel; not in rick_grid_noalloc.  The weighting
+     * alpha^2 times the grid memory and FFT work.  Needs a Gaussian or
+     * Kaiser-Bessel kernel; not in rick_grid_noalloc.  The weighting
      * density stays on the N x N mesh of cell 1/fov. */
     int32_t grid_size;
 } rick_config;
@@ -520,14 +527,19 @@ rick_status rick_learn_field_grad(rick_learn* learn, const float* table, const f
  * inputs, outputs and layout as rick_grid (all channels, planes
  * [plane_begin, plane_end)), but it takes the configuration directly instead
  * of a plan, and keeps its binning scratch in one fixed 32 MiB array in device
- * memory that every GPU loading the library holds until the process exits.
- * It calls no cudaMalloc, cudaFree or allocating library routine.
- *   - Sizes whose scratch does not fit (about 40 bytes per visibility plus
- *     8 bytes per (channel, plane, tile, class) bin) return RICK_ERR_CAPACITY
- *     before anything is launched; Gaussian and Kaiser-Bessel kernels only
- *     (RICK_ERR_UNSUPPORTED for a table kernel).
- *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * memory.  It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - CUDA loads device code lazily by default, so the first call on each
+ *     device loads the 32 MiB array and the kernels the call runs, which takes
+ *     device memory (RICK_ERR_OOM if there is none left).  Make that first
+ *     call at start-up, outside any stream capture, with the support and tile
+ *     size that later calls use; later calls allocate nothing, and the array
+ *     stays until the process exits.
+ *   - The configuration is checked as by rick_plan_create.  Sizes whose scratch
+ *     does not fit (about 40 bytes per visibility plus 8 bytes per (channel,
+ *     plane, tile, class) bin) return RICK_ERR_CAPACITY; a table kernel, a
+ *     w-kernel, a padded grid, non-natural weighting or a kernel too narrow for
+ *     its support return RICK_ERR_UNSUPPORTED.  Every refusal is made before
+ *     anything is launched or written.
  *   - Every call shares the one array and clears what must start at zero;
  *     calls whose work overlaps on the GPU (other streams or threads) race on
  *     it and must be serialised by the caller.
@@ -544,6 +556,19 @@ rick_status rick_plan_sync_status(rick_plan* plan);
 
 /* Number of this library's kernels the plan has launched so far. */
 int64_t rick_plan_launch_count(const rick_plan* plan);
+
+/* The 2-D DFT the plan runs: RICK_FFT_OWN (unpadded power-of-two mesh
+ * 256 <= N <= 16384 with fft_impl = RICK_FFT_OWN) or RICK_FFT_CUFFT; -1 if
+ * plan is NULL. */
+int32_t rick_plan_fft_impl(const rick_plan* plan);
+
+/* The lengths of the gridder's three longest-first tile lists in the plan's
+ * last rick_grid_binned / rick_grid_binned_sparse / rick_grid call: the
+ * tiles reached by at least 64 T, 16 T and 4 T records (T the tile side).
+ * The first two lists are the dense tiles that the gridder splits over the
+ * warps of a CTA (the load balancing of Sec. 3.2 on one device); for tests.
+ * Synchronous (waits for the plan's last stream). */
+rick_status rick_plan_schedule_counts(rick_plan* plan, uint32_t counts[3]);
 
 /* Copy the binning result of the last rick_bin to host memory, for tests:
  * offsets[n_keys + 1] (uint32, start of every (channel, plane, tile, class)

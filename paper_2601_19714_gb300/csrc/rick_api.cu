@@ -187,7 +187,7 @@ struct rick_plan {
     double* d_wmom = nullptr;
     float* d_wbuf = nullptr;
     int64_t cap_w = 0;
-    // the library's own 2-D DFT (fft_impl 1 and 256 <= N <= 8192): twiddle tables
+    // the library's own 2-D DFT (RICK_FFT_OWN, unpadded 256 <= N <= 16384): twiddle tables
     bool own_fft = false;
     float2* d_twid = nullptr;
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
@@ -279,7 +279,6 @@ rick_status validate(const rick_config* c) {
            "grid_size must be 0 or a power of two in [N, 65536]");
     if (Ng != c->N) {
         RK_ARG(c->kernel_kind != RICK_KERNEL_TABLE, "a padded grid needs a Gaussian or Kaiser-Bessel kernel");
-        RK_ARG(c->fft_impl == 0, "a padded grid needs fft_impl 0 (cuFFT)");
     }
     RK_ARG(c->n_wplanes >= 1, "n_wplanes must be >= 1");
     RK_ARG(c->n_channels >= 1, "n_channels must be >= 1");
@@ -303,7 +302,8 @@ rick_status validate(const rick_config* c) {
     RK_ARG(c->tiles_per_grab >= 0 && c->tiles_per_grab <= 8, "tiles_per_grab must be in [0, 8]");
     RK_ARG(c->grid_budget_bytes >= 0, "grid_budget_bytes must be >= 0");
     RK_ARG(c->hermitian_fold == 0 || c->hermitian_fold == 1, "hermitian_fold must be 0 or 1");
-    RK_ARG(c->fft_impl == 0 || c->fft_impl == 1, "fft_impl must be 0 or 1");
+    RK_ARG(c->fft_impl == RICK_FFT_OWN || c->fft_impl == RICK_FFT_CUFFT,
+           "fft_impl must be 0 (own transform) or 1 (cuFFT)");
     RK_ARG(c->weighting >= RICK_WEIGHT_NATURAL && c->weighting <= RICK_WEIGHT_BRIGGS,
            "weighting must be 0 (natural), 1 (uniform) or 2 (Briggs)");
     RK_ARG(c->weighting != RICK_WEIGHT_BRIGGS || std::isfinite(c->robust), "robust must be finite");
@@ -333,9 +333,13 @@ rick_status validate(const rick_config* c) {
                "hermitian_fold needs a point-symmetric kernel (Gaussian or Kaiser-Bessel)");
         RK_ARG(c->w_min == -c->w_max, "hermitian_fold needs w_min == -w_max");
     }
+    // bins = C x stored planes x NT^2 x 4 halo classes, tested factor by factor
+    // so that the product cannot wrap
     const uint64_t NT = (uint64_t)(Ng / T);
-    const uint64_t nkeys = (uint64_t)c->n_channels * stored_planes(*c) * NT * NT * 4ull;
-    if (nkeys >= 0xFFFFFFFFull) {
+    const uint64_t per_plane = NT * NT * 4ull;   // <= 2^26
+    const uint64_t limit = 0xFFFFFFFFull;
+    const uint64_t cp = (uint64_t)c->n_channels * (uint64_t)stored_planes(*c);   // < 2^63
+    if (cp >= limit || cp * per_plane >= limit) {
         set_err("channels x planes x tiles exceeds the 32-bit bin space; use a larger tile or "
                 "fewer channels per plan");
         return RICK_ERR_UNSUPPORTED;
@@ -467,7 +471,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(cudaMalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
     }
 
-    P->own_fft = c.fft_impl == 1 && fft_supported(c.N) && P->Ng == c.N;
+    P->own_fft = c.fft_impl == RICK_FFT_OWN && fft_supported(c.N) && P->Ng == c.N;
     if (P->own_fft) {
         std::vector<float2> tw;
         fft_twiddles(c.N, tw);
@@ -851,7 +855,7 @@ rick_status columns_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int
                          cudaStream_t st) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
-        set_err("the column pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+        set_err("the column pass needs the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -879,7 +883,7 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
                             int32_t flags, cudaStream_t st, bool occ_ready = false) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
-        set_err("the fused row pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+        set_err("the fused row pass needs the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -949,8 +953,9 @@ rick_status model_impl(rick_plan* P, const float* image, int c0, int c1, int k0,
 rick_status model_fft_impl(rick_plan* P, const float* image, int c0, int c1, int k0, int k1, float* grids,
                            int32_t flags, cudaStream_t st) {
     const rick_config& c = P->cfg;
-    if (!P->own_fft) {
-        set_err("the fused model pass needs the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+    if (!P->own_fft || !fft_fused_model_supported(P->Ng)) {
+        set_err("the fused model pass needs the library's own transform on an unpadded 256 <= N <= 8192 "
+                "(RICK_FFT_OWN); use rick_model_to_wplanes + rick_fft_wplanes_forward");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -1092,7 +1097,7 @@ rick_status predict_impl(rick_plan* P, const double* uvw, const double* chan_sca
         const int c1 = c0 + gc < c.n_channels ? c0 + gc : c.n_channels;
         for (int k0 = 0; k0 < P->planes; k0 += gk) {
             const int k1 = k0 + gk < P->planes ? k0 + gk : P->planes;
-            if (P->own_fft) {   // fused model rows + pruned column pass
+            if (P->own_fft && fft_fused_model_supported(P->Ng)) {   // fused model rows + pruned column pass
                 RK_TRY(model_fft_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, RICK_GRIDDED_BY_PLAN, st));
             } else {
                 RK_TRY(model_impl(P, image + (size_t)c0 * NN, c0, c1, k0, k1, g, st));
@@ -1110,6 +1115,8 @@ namespace rick {
 // Lets other translation units of the library report a message through
 // rick_last_error().
 void set_error_message(const char* msg) { set_err("%s", msg); }
+// The configuration check of rick_plan_create, for entry points without a plan.
+rick_status validate_config(const rick_config* cfg) { return validate(cfg); }
 }  // namespace rick
 
 // ===========================================================================
@@ -1206,7 +1213,7 @@ rick_status rick_grid_binned_sparse(rick_plan* plan, int32_t chan_begin, int32_t
                                     int32_t plane_begin, int32_t plane_end, float* grids, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
     if (!plan->own_fft) {
-        set_err("sparse gridding is only read by the library's own transform (fft_impl 1, 256 <= N <= 8192)");
+        set_err("sparse gridding is only read by the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     return grid_impl(plan, chan_begin, chan_end, plane_begin, plane_end, grids, as_stream(stream), true);
@@ -1401,6 +1408,19 @@ rick_status rick_plan_sync_status(rick_plan* plan) {
 }
 
 int64_t rick_plan_launch_count(const rick_plan* plan) { return plan ? plan->launches : -1; }
+
+int32_t rick_plan_fft_impl(const rick_plan* plan) {
+    return plan ? (plan->own_fft ? RICK_FFT_OWN : RICK_FFT_CUFFT) : -1;
+}
+
+rick_status rick_plan_schedule_counts(rick_plan* plan, uint32_t counts[3]) {
+    RK_ARG(plan && counts, "plan and counts are required");
+    RK_ARG(plan->binned && !plan->binned_for_predict, "nothing gridded yet");
+    RK_CUDA(cudaStreamSynchronize(plan->last_stream));
+    // the gridder's counter words 1..3 hold the list lengths
+    RK_CUDA(cudaMemcpy(counts, plan->d_counter + 1, 3 * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    return RICK_OK;
+}
 
 rick_status rick_plan_bins(rick_plan* plan, int64_t* n_keys, int64_t* n_records, uint32_t* offsets,
                            uint32_t* records) {

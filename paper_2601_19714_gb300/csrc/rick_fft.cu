@@ -19,7 +19,7 @@
 // exp(-2 pi i w_k (n - 1)) and the scales) and transforms it along the row,
 // so the model planes are never written, then the column pass.
 //
-// The length-N DFT (N = 2^m, 256 <= N <= 8192) is a Stockham decimation-in-
+// The length-N DFT (N = 2^m, 256 <= N <= 16384) is a Stockham decimation-in-
 // frequency transform with radix-16 stages and, where m is not a multiple of
 // 4, one last stage of radix 2, 4 or 8.  With M the product of the radices of
 // the previous stages and L = N/M, a radix-R stage takes butterfly u = t1 M + g
@@ -29,6 +29,16 @@
 // natural order.  N/16 threads transform one array: one radix-16 butterfly per
 // thread per stage (16/R butterflies of the last radix-R stage).  Thread b
 // therefore ends with the outputs b + (N/16) j, j < 16, in registers.
+//
+// N = 16384: a row of 128 KB fills most of an SM's shared memory, which leaves
+// no room for the fused row pass's per-pixel state.  That pass therefore
+// splits each row DFT between two CTAs by one decimation-in-frequency step
+// (k_rows_phase_reduce_split): with H = N/2,
+//   X[2k + r] = sum_{n<H} y_r[n] W_H^(n k),  y_0[n] = x[n] + x[n+H],
+//   y_1[n] = (x[n] - x[n+H]) W_N^n,
+// so CTA r transforms y_r with the H-point transform and owns the pixels
+// 2k + r.  The column pass and the plain row pass take one 16384-point
+// transform per CTA (1024 threads).
 //
 // Pruning: planes made by the library's gridder are zero in every tile that no
 // visibility reached (or, when the gridder skipped the zero fill, unwritten
@@ -175,7 +185,7 @@ struct Shape {
         return o;
     }
     static constexpr int kTw = stage_off(kTwStages);  // twiddle table entries
-    static_assert(LOG2N >= 8 && LOG2N <= 13, "256 <= N <= 8192");
+    static_assert(LOG2N >= 8 && LOG2N <= 14, "256 <= N <= 16384");
 };
 
 // Radix-16 stage s (M = 16^s, not the last stage): a holds the butterfly's
@@ -554,6 +564,184 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     }
 }
 
+// N = 16384: k_rows_phase_reduce with every image row q split between two
+// CTAs, blockIdx.x = 2 q + r (the two halves run side by side and share the
+// row's cache lines).  CTA r forms y_r[n], n < H = N/2, from the row's two
+// halves,
+//   y_0[n] = x[n] + x[n+H],  y_1[n] = (x[n] - x[n+H]) e^(+2 pi i n/N),
+// transforms it with the H-point transform (X[2k + r] = sum_n y_r[n]
+// e^(+2 pi i n k/H)) and applies the phase screen and the plane sum of Eq. 2
+// to its pixels p = 2k + r exactly as k_rows_phase_reduce does (Horner blocks
+// of kHornerBlock planes, exact phasor at each block's end).  The twiddle of
+// y_1 is e^(2 pi i b/N) (per thread, from FP64) times e^(2 pi i t2/32) (a
+// constant, n = b + (H/16) t2).  With pruning the unreached tile columns of
+// either half are not read; a position whose two halves are both reached
+// (never on a centred uv coverage narrower than half the mesh) reads the upper
+// half when the row is consumed rather than in the prefetch, so that the
+// prefetch holds one value per position.
+template <bool COMPLEX_OUT>
+__global__ void __launch_bounds__(512, 1)
+k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
+                          const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
+                          const float2* __restrict__ twid_h, float* __restrict__ image_real,
+                          float2* __restrict__ image_complex, Occupancy occ) {
+    using Sh = Shape<13>;
+    constexpr int H = Sh::N, T = Sh::T;     // half row: 8192 points, 512 threads
+    constexpr int N = 2 * H;
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* tw = fsm;
+    float2* buf = fsm + Sh::kTw;
+    float2* zrot = buf + Sh::kArray;                             // z per owned pixel
+    float* part = reinterpret_cast<float*>(zrot + H);
+    const int b = threadIdx.x, q = blockIdx.x >> 1, par = blockIdx.x & 1;
+    const float* scl = pix_scale + (size_t)q * N;
+    const uint2* turns = pix_turns + (size_t)q * N;
+    load_tables<13>(twid_h, tw, b, T);
+#pragma unroll 4
+    for (int j = 0; j < 16; ++j) {
+        const int k = b + T * j;
+        float s, c;
+        sincospif((float)(int32_t)__ldg(&turns[2 * k + par].y) * 4.656612873077392578125e-10f /* 2^-31 */,
+                  &s, &c);
+        zrot[k] = make_float2(c, -s);
+        if (!COMPLEX_OUT) part[k] = 0.f;
+    }
+    // e^(+2 pi i b / N) for the odd half's twiddles
+    float2 wb = make_float2(1.f, 0.f);
+    if (par) {
+        double sd, cd;
+        sincospi(2.0 * (double)b / (double)N, &sd, &cd);
+        wb = make_float2((float)cd, (float)sd);
+    }
+
+    const size_t NN = (size_t)N * N;
+    const int n_rows = P.nc * P.nk;
+    auto next_row = [&](int r) {
+        if (occ.plane != nullptr)
+            while (r < n_rows && occ.plane[r] == 0) ++r;
+        return r;
+    };
+    // liveness of the inputs b + T t2 (bits 0..15) and H + b + T t2 (bits
+    // 16..31) of plane r: with tiles of at least 32 columns every warp reads
+    // one tile column per t2 and half: lanes 0..31 read the 32 mask bytes and
+    // a ballot hands every lane the bits
+    const bool warp_mask = occ.tshift >= 5;
+    auto live_bits = [&](int r) -> uint32_t {
+        if (occ.col == nullptr) return 0xffffffffu;
+        const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+        if (warp_mask) {
+            const int lane = b & 31;
+            const int pos = (b & ~31) + T * (lane & 15) + (lane >> 4) * H;
+            return __ballot_sync(0xffffffffu, __ldg(cm + (pos >> occ.tshift)) != 0);
+        }
+        uint32_t live = 0;
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+            live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
+            live |= (__ldg(cm + ((H + b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << (16 + t2);
+        }
+        return live;
+    };
+    // prefetch: one value per position (the lower half where reached, else
+    // the upper half); pf_live remembers which
+    uint32_t pf_live = 0;
+    const float2* pf_row = grids;
+    auto load_row = [&](int r, float2 (&v)[16]) {
+        pf_row = grids + (size_t)r * NN + (size_t)q * N;
+        pf_live = live_bits(r);
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+            const int n = b + T * t2;
+            v[t2] = (pf_live >> t2) & 1u          ? __ldcs(pf_row + n)
+                    : (pf_live >> (16 + t2)) & 1u ? __ldcs(pf_row + n + H)
+                                                  : make_float2(0.f, 0.f);
+        }
+    };
+    // the prefetched values to y_par
+    auto combine = [&](float2 (&v)[16]) {
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+            const bool lo = (pf_live >> t2) & 1u, hi = (pf_live >> (16 + t2)) & 1u;
+            float2 y = v[t2];
+            if (lo && hi) {
+                const float2 u = __ldcs(pf_row + b + T * t2 + H);
+                y = par ? csub(y, u) : cadd(y, u);
+            } else if (hi && par) {
+                y = make_float2(-y.x, -y.y);
+            }
+            v[t2] = par ? twiddle_const<true>(cmulf(y, wb), t2, 32) : y;
+        }
+    };
+    float2 a[16], x[16];
+    int r = next_row(0);
+    if (r < n_rows) load_row(r, a);
+    __syncthreads();
+    for (int cc = 0; cc < P.nc; ++cc) {
+        float2 acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int kk = 0; kk < P.nk; ++kk) {
+            if (cc * P.nk + kk != r) {   // an unreached plane: F_k = 0
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 z = zrot[b + T * j];
+                    acc[j] = make_float2(fmaf(acc[j].x, z.x, -acc[j].y * z.y), fmaf(acc[j].x, z.y, acc[j].y * z.x));
+                }
+            } else {
+                combine(a);
+                radix16_out<13, true>(a, b, 0, buf, tw);
+                const int rn = next_row(r + 1);
+                if (rn < n_rows) load_row(rn, a);
+                r = rn;
+                __syncthreads();
+                middle_stages<13, true>(buf, b, tw);
+                last_stage<13, true>(buf, b, x);
+                __syncthreads();   // buf is rewritten by the next row's first stage
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 z = zrot[b + T * j];
+                    acc[j] = make_float2(fmaf(acc[j].x, z.x, fmaf(-acc[j].y, z.y, x[j].x)),
+                                         fmaf(acc[j].x, z.y, fmaf(acc[j].y, z.x, x[j].y)));
+                }
+            }
+            const bool last = kk == P.nk - 1;
+            if (kk % kHornerBlock != kHornerBlock - 1 && !last) continue;
+            const uint32_t k_end = (uint32_t)(P.k_first + kk);
+            float inv_ws = 0.f;
+            if (last || COMPLEX_OUT) {
+                const double ws = wsum[cc];
+                inv_ws = ws != 0.0 ? (float)(1.0 / ws) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int k = b + T * j, p = 2 * k + par;
+                const uint2 ph = __ldg(&turns[p]);
+                const uint32_t tk = ph.x + k_end * ph.y;
+                float sn, cs;
+                sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
+                const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
+                acc[j] = make_float2(0.f, 0.f);
+                float* ir = image_real + (size_t)cc * NN + (size_t)q * N + p;
+                if (COMPLEX_OUT) {
+                    const float s = __ldg(scl + p) * inv_ws;
+                    *ir += s * re;
+                    float2* ic = image_complex + (size_t)cc * NN + (size_t)q * N + p;
+                    float2 v = *ic;
+                    v.x += s * re;
+                    v.y += s * im;
+                    *ic = v;
+                } else if (!last) {
+                    part[k] += re;
+                } else {
+                    *ir += __ldg(scl + p) * inv_ws * (part[k] + re);
+                    part[k] = 0.f;
+                }
+            }
+        }
+    }
+}
+
 // Prediction, the row pass run backwards (the adjoint of k_rows_phase_reduce):
 // for image row q (blockIdx.x) of every channel and plane of the launch, the
 // model row M_k[q][p] = J_c[q][p] (-1)^(p+q) exp(-2 pi i w_k (n - 1)) /
@@ -666,7 +854,7 @@ k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __rest
 // columns per CTA in pass 1: warp accesses of 32-byte row pieces (whole DRAM
 // sectors) where 4 N/16 threads fit a CTA, else 16 bytes
 template <int LOG2N>
-constexpr int kCols = LOG2N <= 12 ? 4 : 2;
+constexpr int kCols = LOG2N <= 12 ? 4 : LOG2N == 13 ? 2 : 1;
 
 // Occupancy of the planes p = cc nk + kk of the launch from the bin offsets:
 // one thread per tile (tx fastest), reached iff tile_reach() > 0 -- the
@@ -752,13 +940,35 @@ cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* w
     return cudaGetLastError();
 }
 
+// N = 16384: two CTAs per image row, each with the 8192-point tables (they
+// follow the 16384-point tables in twid)
+template <bool CPLX>
+cudaError_t fused_split(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
+                        const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
+                        const Occupancy& occ, cudaStream_t st) {
+    using Sh = Shape<13>;
+    auto fn = k_rows_phase_reduce_split<CPLX>;
+    const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
+                        (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    fn<<<2 * Shape<14>::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid + Shape<14>::kTw,
+                                               image_real, image_complex, occ);
+    return cudaGetLastError();
+}
+
 template <int LOG2N>
 cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
                     const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
                     const Occupancy& occ, cudaStream_t st) {
-    return image_complex != nullptr
-               ? fused_one<LOG2N, true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
-               : fused_one<LOG2N, false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
+    if constexpr (LOG2N == 14)
+        return image_complex != nullptr
+                   ? fused_split<true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
+                   : fused_split<false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
+    else
+        return image_complex != nullptr
+                   ? fused_one<LOG2N, true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
+                   : fused_one<LOG2N, false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
 }
 
 int log2_exact(int N) {
@@ -771,16 +981,22 @@ int log2_exact(int N) {
 
 bool fft_supported(int N) {
     const int m = log2_exact(N);
+    return m >= 8 && m <= 14;
+}
+
+bool fft_fused_model_supported(int N) {
+    const int m = log2_exact(N);
     return m >= 8 && m <= 13;
 }
 
-void fft_twiddles(int N, std::vector<float2>& out) {
+namespace {
+
+void append_twiddles(int N, std::vector<float2>& out) {
     // per radix-16 stage s with twiddles (M = 16^s, cnt = N/16/M groups t1),
     // from FP64: stage 0 entries [j cnt + t1] = e^(+2 pi i 2^j t1 M / N), j < 4;
     // later stages [(f0 - 1) cnt + t1] = e^(+2 pi i f0 t1 M / N), f0 = 1..15
     const int log2n = log2_exact(N);
     const int stages = (log2n % 4 == 0) ? log2n / 4 - 1 : log2n / 4;
-    out.clear();
     const double two_pi = 6.283185307179586476925;
     for (int st = 0; st < stages; ++st) {
         const int64_t M = (int64_t)1 << (4 * st);
@@ -794,6 +1010,15 @@ void fft_twiddles(int N, std::vector<float2>& out) {
                 out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
             }
     }
+}
+
+}  // namespace
+
+void fft_twiddles(int N, std::vector<float2>& out) {
+    // N = 16384: the 8192-point tables of the split fused row pass follow
+    out.clear();
+    append_twiddles(N, out);
+    if (log2_exact(N) == 14) append_twiddles(N / 2, out);
 }
 
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
@@ -815,6 +1040,7 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
         RICK_FFT_CASE(11)
         RICK_FFT_CASE(12)
         RICK_FFT_CASE(13)
+        RICK_FFT_CASE(14)
         default: break;
     }
 #undef RICK_FFT_CASE
@@ -838,6 +1064,7 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
         RICK_FFT_CASE(11)
         RICK_FFT_CASE(12)
         RICK_FFT_CASE(13)
+        RICK_FFT_CASE(14)
         default: break;
     }
 #undef RICK_FFT_CASE
@@ -861,6 +1088,7 @@ cudaError_t launch_rows_phase_reduce(const PhaseParams& P, const float2* grids, 
         RICK_FUSED_CASE(11)
         RICK_FUSED_CASE(12)
         RICK_FUSED_CASE(13)
+        RICK_FUSED_CASE(14)
         default: break;
     }
 #undef RICK_FUSED_CASE

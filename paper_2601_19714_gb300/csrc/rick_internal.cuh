@@ -174,6 +174,10 @@ __device__ __forceinline__ float w_taper_inv(const PhaseParams& P, double delta)
     return 1.0f / (P.w_s_i0 * h);
 }
 
+// The configuration check of rick_plan_create (RICK_OK, or the status and a
+// message for rick_last_error()).
+rick_status validate_config(const rick_config* cfg);
+
 // --- launchers (one per kernel family), all asynchronous on `stream` -------
 
 // vis_base: index of the first visibility of this call in the whole binning
@@ -221,9 +225,12 @@ cudaError_t launch_degrid(const GridParams& G, const uint32_t* offsets, const Vi
 
 uint64_t scan_partials_needed(uint64_t n);
 
-// The library's own 2-D DFT of the w-planes (rick_fft.cu), 256 <= N <= 8192
-// (powers of two).  twid: the table fft_twiddles(N) in device memory.
+// The library's own 2-D DFT of the w-planes (rick_fft.cu), 256 <= N <= 16384
+// (powers of two).  twid: the table fft_twiddles(N) in device memory (for
+// N = 16384 the 16384-point tables followed by the 8192-point ones).  The
+// fused model row pass of the prediction (launch_model_rows) takes N <= 8192.
 bool fft_supported(int N);
+bool fft_fused_model_supported(int N);
 void fft_twiddles(int N, std::vector<float2>& out);
 // In place, unnormalised, over n_planes planes [N][N]: columns then rows.
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,

@@ -23,7 +23,7 @@ STATUS = {0: "RICK_OK", 1: "RICK_ERR_INVALID_ARG", 2: "RICK_ERR_OOM", 3: "RICK_E
           7: "RICK_ERR_INTERNAL", 8: "RICK_ERR_CAPACITY"}
 KERNELS = {"gauss": 0, "kb": 1, "kaiser_bessel": 1, "table": 2, "learned": 2}
 PRECISIONS = {"fp64idx": 0, "fp32": 1}
-FFT_IMPLS = {"cufft": 0, "own": 1}
+FFT_IMPLS = {"own": 0, "cufft": 1}
 GRIDDED_BY_PLAN = 1             # transform flag: the planes are this plan's gridder output
 WEIGHTINGS = {"natural": 0, "uniform": 1, "briggs": 2}
 
@@ -40,7 +40,7 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
            "rick_status_string", "rick_last_error", "rick_stored_planes", "rick_bin_predict",
            "rick_model_to_wplanes", "rick_fft_wplanes_forward", "rick_model_fft_wplanes", "rick_degrid_binned",
-           "rick_predict"]
+           "rick_predict", "rick_plan_fft_impl", "rick_plan_schedule_counts"]
 
 
 class RickError(RuntimeError):
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "rick_model_fft_wplanes": [p, p, i32, i32, i32, i32, p, i32, p],
         "rick_degrid_binned": [p, p, i32, i32, i32, i32, p, p],
         "rick_predict": [p, p, p, p, p, i64, p, p, p, p],
+        "rick_plan_schedule_counts": [p, p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
     L.rick_learn_placed.restype = i64
     L.rick_plan_launch_count.argtypes = [p]
     L.rick_plan_launch_count.restype = i64
+    L.rick_plan_fft_impl.argtypes = [p]
+    L.rick_plan_fft_impl.restype = i32
     L.rick_status_string.argtypes = [st]
     L.rick_status_string.restype = C.c_char_p
     L.rick_last_error.argtypes = []
@@ -207,7 +210,7 @@ class Config:
     hermitian_fold: bool = False
     w_support: int = 0          # even Sw >= 2: Kaiser-Bessel kernel in w over Sw planes
     w_kernel_param: float = 0.0
-    fft_impl: str = "cufft"     # or "own": the library's two-pass DFT (256 <= N <= 8192)
+    fft_impl: str = "own"       # the library's two-pass DFT (unpadded 256 <= N <= 16384; cuFFT otherwise), or "cufft"
     weighting: str = "natural"  # or "uniform", "briggs" (imaging weights)
     robust: float = 0.0         # Briggs robustness R
     grid_size: int = 0          # padded mesh side Ng (0 = N)
@@ -284,6 +287,18 @@ class Plan:
 
     def launch_count(self) -> int:
         return int(load().rick_plan_launch_count(self.handle))
+
+    @property
+    def own_fft(self) -> bool:
+        """True if the plan runs the library's own 2-D DFT (else cuFFT)."""
+        return int(load().rick_plan_fft_impl(self.handle)) == FFT_IMPLS["own"]
+
+    def schedule_counts(self):
+        """Lengths of the gridder's three longest-first tile lists of the last
+        gridding call: tiles reached by >= 64T, 16T and 4T records."""
+        out = (C.c_uint32 * 3)()
+        _check(load().rick_plan_schedule_counts(self.handle, out), "rick_plan_schedule_counts")
+        return [int(v) for v in out]
 
     def sync_status(self):
         _check(load().rick_plan_sync_status(self.handle), "rick_plan_sync_status")

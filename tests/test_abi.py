@@ -154,11 +154,10 @@ def test_weighting_configs_rejected_on_host(lib, kw):
 
 @pytest.mark.parametrize("kw,word", [(dict(grid_size=384), b"grid_size"),
                                      (dict(grid_size=128), b"grid_size"),
-                                     (dict(grid_size=512, fft_impl="own"), b"fft_impl"),
                                      (dict(grid_size=512, kernel="learned", support=4,
                                            kernel_param=5.6), b"padded")])
 def test_padding_configs_rejected_on_host(lib, kw, word):
-    """A padded mesh is a power of two >= N, with cuFFT and a separable kernel."""
+    """A padded mesh is a power of two >= N, with a separable kernel."""
     from paper_2601_19714_gb300 import rick
     base = dict(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
                 w_max=200, kernel="gauss", kernel_param=0.94)
@@ -166,3 +165,18 @@ def test_padding_configs_rejected_on_host(lib, kw, word):
     h = C.c_void_p(123)
     assert lib.rick_plan_create(C.byref(rick.Config(**base).c()), C.byref(h)) == 1
     assert word in lib.rick_last_error()
+
+
+def test_fft_impl_values(lib):
+    """fft_impl 0 (the C default) is the library's own transform, 1 cuFFT;
+    other values are refused on the host."""
+    from paper_2601_19714_gb300 import rick
+    assert rick.FFT_IMPLS == {"own": 0, "cufft": 1}
+    assert rick.Config(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                       w_max=200, kernel="gauss", kernel_param=0.94).c().fft_impl == 0
+    cfg = rick.Config(N=256, n_wplanes=8, support=7, n_channels=1, fov_rad=0.03, w_min=-200,
+                      w_max=200, kernel="gauss", kernel_param=0.94).c()
+    cfg.fft_impl = 2
+    h = C.c_void_p(123)
+    assert lib.rick_plan_create(C.byref(cfg), C.byref(h)) == 1
+    assert b"fft_impl" in lib.rick_last_error()

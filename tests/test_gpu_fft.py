@@ -271,7 +271,7 @@ def test_pruning_needs_the_plans_gridding_binning(rk):
     plan.bin_predict(dev["uvw"], dev["chan_scale"], dev["weight"], None, dev["nrow"])
     with pytest.raises(rk.RickError):   # binned for prediction
         plan.fft_wplanes_columns(grids, 0, 1, 0, img.Nw, gridded_by_plan=True)
-    cu = rk.Plan(plan_config(img, 1))
+    cu = rk.Plan(plan_config(img, 1, fft_impl="cufft"))
     with pytest.raises(rk.RickError) as e:   # the split passes need the own transform
         cu.fft_wplanes_columns(grids, 0, 1, 0, img.Nw)
     assert e.value.status == 6

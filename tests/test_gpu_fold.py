@@ -158,8 +158,8 @@ def test_folded_multichannel_kaiser_bessel(rk, orc, Nw):
     the unfolded oracle and against the unfolded GPU path."""
     img, obs = meerkat(8, n_ant=12, n_steps=97, nchan=4, N=512, Nw=Nw, n_src=20)
     dev = to_device(obs)
-    plan_f = rk.Plan(plan_config(img, 4, fft_batch=3, hermitian_fold=True))
-    plan_u = rk.Plan(plan_config(img, 4, fft_batch=3))
+    plan_f = rk.Plan(plan_config(img, 4, fft_batch=3, hermitian_fold=True, fft_impl="cufft"))
+    plan_u = rk.Plan(plan_config(img, 4, fft_batch=3, fft_impl="cufft"))
     I_f, _, ws_f, cnt_f = run_path(plan_f, dev, 4, img.N, img.Nw)
     I_u, _, ws_u, cnt_u = run_path(plan_u, dev, 4, img.N, img.Nw)
     assert cnt_f.tolist() == cnt_u.tolist()

@@ -1,0 +1,185 @@
+"""The headline path at the sizes the benchmarks run it, against the oracle.
+
+rick_dirty_image with the library's own transform bins, grids only the tiles
+that visibilities reach, transforms the reached tile columns (column pass)
+and runs the row pass fused with Eq. 2's phase screen and plane sum, whose
+kernel is instantiated per mesh side: N = 4096 and 8192 one CTA per image row,
+N = 16384 two CTAs per row (the row DFT split by one decimation-in-frequency
+step).  Each case images one channel of a workload at full mesh size and full
+plane count with the Hermitian fold -- MeerKAT-shaped at 4096^2 x 32 planes
+(16 stored), LOFAR-shaped at 8192^2 x 48 planes (24 stored), the MeerKAT
+large-precision layout at 16384^2 x 32 planes (16 stored) -- on a seeded row
+subsample of the 8 h track (every plane and most tile columns still reached),
+and compares 64 pixels (corners and edge midpoints 8 pixels in, the centre,
+23 seeded anywhere and 32 seeded where the taper gain is at least 1e-2) with
+the oracle's per-visibility form of O1.  Gates: the
+taper-weighted error and the error where the taper gain A >= 1e-2 within 1e-5
+of the peak (the plain full-field error, which the unpadded taper amplifies
+up to 1/A at the corners, is printed).
+
+Also at N = 16384: the own 2-D DFT against FP64 numpy (both directions, and an
+impulse), the fused split row pass against the separate transform + phase
+kernel, and the pruned path into NaN-filled planes against the unpruned one
+(bit for bit).
+"""
+import numpy as np
+import pytest
+
+from tests.gpu_util import oracle_config, plan_config, taper_gain, to_device
+from visgen.workloads import evaluation_positions, lofar, meerkat, meerkat_large
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2601_19714_gb300 import rick
+    rick.load()
+    return rick
+
+
+def _probe_errors(got, ref, A):
+    d = np.abs(got - ref)
+    peak = np.abs(ref).max()
+    inner = A >= 1e-2
+    return dict(full=float(d.max() / peak),
+                weighted=float((d * A).max() / (np.abs(ref) * A).max()),
+                inner=float(d[inner].max() / peak), n_inner=int(inner.sum()))
+
+
+def _probes(N, A, seed=7):
+    """64 pixels: the corners, edge midpoints and centre (8 pixels in from the
+    edge), 23 seeded anywhere, and 32 seeded where the taper gain A >= 1e-2."""
+    fixed = evaluation_positions(N, 32, seed=N)
+    g = np.random.default_rng(seed)
+    inner = []
+    while len(inner) < 32:
+        pq = g.integers(0, N, 2)
+        if A[pq[1], pq[0]] >= 1e-2:
+            inner.append(pq)
+    return np.concatenate([fixed, np.array(inner)]).astype(np.int64)
+
+
+def _workload(name):
+    if name == "meerkat_4096":
+        img, obs = meerkat(11, n_ant=64, n_steps=60, nchan=1, N=4096, Nw=32,
+                           freqs=np.array([1.712e9]))
+    elif name == "lofar_8192":
+        img, obs = lofar(12, n_steps=40, nchan=1)
+    else:
+        img, obs = meerkat_large(13, channels=slice(127, 128), row_fraction=0.01)
+    return img, obs
+
+
+@pytest.mark.parametrize("name", ["meerkat_4096", "lofar_8192", "meerkat_16384"])
+def test_headline_path_matches_oracle_at_full_size(rk, orc, name):
+    import torch
+    img, obs = _workload(name)
+    if hasattr(obs.vis, "cpu"):
+        obs.vis = obs.vis.cpu().numpy()
+    dev = to_device(obs)
+    cfg = plan_config(img, 1, hermitian_fold=True)
+    plan = rk.Plan(cfg)
+    assert plan.own_fft, "the headline path runs the library's own transform"
+    N = img.N
+    image = torch.zeros((1, N, N), dtype=torch.float32, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+    plan.dirty_image(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"],
+                     obs.nrow, image, counts=counts)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    Afull = taper_gain(plan.taper())
+    pr = _probes(N, Afull)
+    p, q = pr[:, 0].astype(np.int32), pr[:, 1].astype(np.int32)
+    got = image[0][torch.from_numpy(q).long().cuda(), torch.from_numpy(p).long().cuda()].cpu().numpy()
+    ref = orc.image_at(oracle_config(orc, img), obs.uvw, obs.chan_scale, obs.vis, obs.weight, obs.flag,
+                       channel=0, p=p, q=q).real
+    A = Afull[q, p]
+    e = _probe_errors(got, ref, A)
+    print(f"{name}: N={N}, {int(counts[0].item())} gridded, stored planes {cfg.stored_planes}: {e}")
+    assert e["n_inner"] >= 32
+    assert e["weighted"] <= TOL and e["inner"] <= TOL, e
+
+
+@pytest.mark.parametrize("inverse", [True, False])
+def test_own_fft_16384_matches_fp64(rk, inverse):
+    import torch
+    N = 16384
+    g = np.random.default_rng(77 + inverse)
+    x = (g.standard_normal((1, N, N), dtype=np.float32)
+         + 1j * g.standard_normal((1, N, N), dtype=np.float32)).astype(np.complex64)
+    plan = rk.Plan(rk.Config(N=N, n_wplanes=1, support=8, n_channels=1, fov_rad=0.02, w_min=-100.0,
+                             w_max=100.0, kernel="kb", kernel_param=12.25))
+    d = torch.from_numpy(x).cuda()
+    (plan.fft_wplanes if inverse else plan.fft_wplanes_forward)(d, 1)
+    got = d.cpu().numpy()
+    del d
+    ref = (np.fft.ifft2(x[0].astype(np.complex128)) * (N * N) if inverse
+           else np.fft.fft2(x[0].astype(np.complex128)))
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    err = float(np.abs(got[0] - ref).max() / rms)
+    print(f"N={N} inverse={inverse}: own {err:.2e} of the RMS")
+    assert err <= 3e-6
+
+
+def test_impulse_16384_gives_a_plane_wave(rk):
+    import torch
+    N = 16384
+    i, j = 12345, 777
+    plan = rk.Plan(rk.Config(N=N, n_wplanes=1, support=8, n_channels=1, fov_rad=0.02, w_min=-100.0,
+                             w_max=100.0, kernel="kb", kernel_param=12.25))
+    d = torch.zeros((1, N, N), dtype=torch.complex64, device="cuda")
+    d[0, j, i] = 1.0
+    plan.fft_wplanes(d, 1)
+    rows = np.array([0, 1, 4097, 8191, 8192, 16383])
+    got = d[0, torch.from_numpy(rows).cuda()].cpu().numpy()
+    pix = np.arange(N)
+    ref = np.exp(2j * np.pi * ((i * pix[None, :] + j * rows[:, None]) % N) / N)
+    assert np.abs(got - ref).max() <= 2e-6
+
+
+@pytest.mark.parametrize("fold", [False, True])
+def test_split_row_pass_equals_separate_calls_16384(rk, fold):
+    """The fused split row pass (two CTAs per row) against the plain 16384
+    transform followed by the phase kernel, on gridded MeerKAT planes; and the
+    pruned path on sparse-gridded NaN-filled planes against the unpruned one."""
+    import torch
+    img, obs = meerkat(14, n_ant=24, n_steps=30, nchan=1, N=16384, Nw=6, n_src=20,
+                       freqs=np.array([1.712e9]))
+    dev = to_device(obs)
+    N = img.N
+    cfg = plan_config(img, 1, hermitian_fold=fold)
+    plan = rk.Plan(cfg)
+    ns = cfg.stored_planes
+    grids = torch.empty((1, ns, N, N), dtype=torch.complex64, device="cuda")
+    wsum = torch.empty(1, dtype=torch.float64, device="cuda")
+    plan.grid(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], dev["nrow"],
+              0, ns, grids, wsum)
+    sep = grids.clone()
+    i_sep = torch.zeros((1, N, N), dtype=torch.float32, device="cuda")
+    plan.fft_wplanes(sep, ns)
+    plan.phase_correct_reduce(sep, 0, 1, 0, ns, wsum, i_sep)
+    del sep
+    i_fus = torch.zeros((1, N, N), dtype=torch.float32, device="cuda")
+    plan.fft_phase_correct_reduce(grids, 0, 1, 0, ns, wsum, i_fus)
+    # pruned: sparse gridding into NaN-filled planes, then the pruned passes
+    grids.fill_(float("nan"))
+    plan.grid_binned(0, 1, 0, ns, grids, sparse=True)
+    i_pru = torch.zeros((1, N, N), dtype=torch.float32, device="cuda")
+    plan.fft_phase_correct_reduce(grids, 0, 1, 0, ns, wsum, i_pru, gridded_by_plan=True)
+    torch.cuda.synchronize()
+    a, b, c = i_fus.cpu().numpy(), i_sep.cpu().numpy(), i_pru.cpu().numpy()
+    peak = np.abs(b).max()
+    A = taper_gain(plan.taper())
+    err = float(np.abs(a - b).max() / peak)
+    werr = float((np.abs(a - b) * A).max() / (np.abs(b) * A).max())
+    print(f"fold={fold}: fused vs separate {err:.2e} full, {werr:.2e} taper-weighted")
+    assert werr <= 2e-6
+    assert np.isfinite(c).all()
+    np.testing.assert_array_equal(c, a)

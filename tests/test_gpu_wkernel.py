@@ -164,7 +164,7 @@ def test_w_kernel_multichannel_kaiser_bessel(rk, orc, fold):
     field corners of this w range; with 7 planes it would be 1.09, beyond the
     sampling limit, where C_w passes through zero)."""
     img, obs = meerkat(74, n_ant=12, n_steps=97, nchan=3, N=512, Nw=25, n_src=20)
-    plan = rk.Plan(plan_config(img, 3, fft_batch=4, hermitian_fold=fold, w_support=6,
+    plan = rk.Plan(plan_config(img, 3, fft_batch=4, fft_impl="cufft", hermitian_fold=fold, w_support=6,
                                w_kernel_param=10.0))
     I_g, _, _, cnt = run_path(plan, to_device(obs), 3, img.N, img.Nw)
     cfg = oracle_config(orc, img, w_support=6, w_kernel_param=10.0)
