@@ -1,25 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of the w-stacking hot path on GB300.
 
-One step = the whole path over one batch: rick_bin + rick_grid_binned_sparse
-(placement, binning and gridding of every visibility of every channel onto
-its w-plane; tiles no visibility reaches are not written), then the library's
-own 2-D DFT, pruned to the reached tiles: rick_fft_wplanes_columns (column
-pass) + rick_rows_phase_correct_reduce (row pass fused with the phase screen
-and the sum over planes into the dirty images).  The cuFFT path
-(rick_grid_binned + rick_fft_wplanes + rick_phase_correct_reduce) is timed
-beside it as "fft_variant" (--fft cufft swaps the two).  Inputs are resident
-in HBM when the timed region starts; `e2e` repeats the measurement through
-rick_dirty_image_host, with the host->device copy of the inputs and the
-device->host copy of the images inside the timed region.
+Workload (default): the largest single-GPU configuration -- the MeerKAT
+layout (64 antennas within 8 km, 2016 baselines), an 8 h track of 5800 steps,
+128 channels over 856-1712 MHz: 1.50 G visibilities (5 % flagged, float32
+weights, 200 point sources with power-law fluxes), 16384^2 grid, 32 w-planes
+(16 stored with the Hermitian fold, exact for the real image; see
+hermitian_fold in include/rick.h), Kaiser-Bessel S = 8, FoV 1.5 deg, FP32
+accumulation with FP64 placement and phase.  Synthetic, seeded.  The inputs
+of all 128 channels are resident in HBM (8 blocks of 16 channels) and the 128
+dirty images (137 GB) stay there.
 
-Workload (default): the MeerKAT-shaped configuration -- 64 antennas, 2016
-baselines x 1000 steps x 16 channels (856-1712 MHz) = 32.3 M visibilities,
-5 % flagged, 200 point sources, 4096^2 grid, 32 w-planes, Kaiser-Bessel S = 8,
-FoV 1.5 deg.  Synthetic, seeded.  The headline path uses the Hermitian fold
-(the 32 w-planes held as 16 stored planes, exact for the real image; see
-hermitian_fold in include/rick.h); the path without it is timed beside it
-and reported under "other_variant" (--no-fold swaps the two).
+One step = the whole path over the whole batch: per block, rick_bin
+(placement and binning of every visibility of the block's channels), then
+per group of channels that fits the grid memory left: rick_grid_binned_sparse
+(Eq. 3; tiles no visibility reaches are not written), the library's own 2-D
+DFT pruned to the reached tiles -- rick_fft_wplanes_columns (column pass) and
+rick_rows_phase_correct_reduce (row pass fused with the phase screen and the
+sum over planes of Eq. 2 into the dirty images).  `e2e` repeats the step
+through rick_dirty_image_host from pinned host buffers (one call per block,
+host->device copies of the inputs and device->host copies of all 128 images
+inside the timed region).  `cpu_baseline` is the FP64 oracle on this host's
+cores, `image_error` the same path on a 1 % row subsample against the oracle.
+
+Other workloads (--workload): meerkat (4096^2 x 32 planes, 16 channels,
+32 M visibilities), lofar, learned, large_precision, predict, wkernel,
+options, profile_small, profile_large_small.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -34,6 +40,8 @@ import statistics
 import subprocess
 import sys
 import time
+
+from dataclasses import replace
 
 import numpy as np
 
@@ -281,34 +289,71 @@ def image_error_probe(img, obs, image_ch0: np.ndarray, taper: np.ndarray, n_pix:
 # --------------------------------------------------------------------------
 
 def run_reference(args):
-    """The oracle as it stands, timed on this host: each step images a
-    bounded sample (one w-plane's visibilities of channel 0)."""
+    """The reference arm: the FP64 oracle as it stands, on this host's cores,
+    on the default workload.  Each step runs the oracle's unit of work -- one
+    w-plane of one channel at 16384^2: grid its visibilities, inverse 2-D DFT,
+    phase screen and sum -- on every core at once (one process per core, each
+    its own plane of the middle channel); the planes are those whose
+    visibility counts are closest to the channel's average per plane.  A
+    warm-up step loads the oracle in every process (the units themselves take
+    tens of seconds each).  Under torchrun only rank 0 runs."""
     from paper_2601_19714_gb300 import dist as rdist
-    ws, rank, _ = rdist.env()
+    world, rank, _ = rdist.env()
     if rank != 0:
         return
+    import multiprocessing as mp
+    n_workers = os.cpu_count() or 1
+    n_workers = max(1, min(n_workers, int((_host_mem_available() - 16e9) // 9.0e9)))
+    pool = mp.get_context("spawn").Pool(n_workers)
     import torch
-    img, obs = make_workload(args.seed, "cuda" if torch.cuda.is_available() else "cpu")
-    obs.vis = obs.vis.cpu().numpy()
+    from visgen.workloads import meerkat_large
+    nband = LARGE_CHANNELS * world
+    mid = LARGE_CHANNELS // 2
+    img, obs = meerkat_large(args.seed, nchan=nband, channels=slice(mid, mid + 1),
+                             device="cuda" if torch.cuda.is_available() else None)
+    if hasattr(obs.vis, "cpu"):
+        obs.vis = obs.vis.cpu().numpy()
+    units, avg = large_oracle_units(img, obs, n_workers)
+    kw = _oracle_cfg_kw(img)
     for _ in range(args.warmup):
-        oracle_sample(img, obs, 1)
-    rates, nv, secs = [], 0, 0.0
-    desc = ""
+        pool.map(_oracle_load, range(n_workers))
+    rates, walls, nvis, stage = [], [], 0, []
     for _ in range(args.steps):
-        r, nv, s, desc = oracle_sample(img, obs, 1)
-        rates.append(r)
-        secs += s
-    value = statistics.median(rates)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        t = time.perf_counter()
+        res = pool.starmap(_oracle_unit, [(kw,) + u for u in units])
+        wall = time.perf_counter() - t
+        nvis = sum(r[0] for r in res)
+        rates.append(nvis / wall)
+        walls.append(wall)
+        stage.append({"grid": statistics.median(r[1] for r in res), "fft": statistics.median(r[2] for r in res),
+                      "phase": statistics.median(r[3] for r in res)})
+    pool.close()
+    pool.join()
+    value = sum(nvis for _ in walls) / sum(walls)
+    desc = (f"the FP64 oracle's unit of work on this workload -- one w-plane of channel {mid} "
+            f"({obs.freqs[0] / 1e6:.1f} MHz) at {img.N}^2: grid its visibilities (Eq. 3), inverse 2-D DFT, "
+            f"phase screen and sum (Eq. 2) -- on {n_workers} planes at once, one process per core; "
+            f"planes whose visibility counts are closest to the channel's average per plane ({avg:.0f})")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "meerkat_4096sq_32w_16ch_kb8", "sample": desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": desc},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": {"workload": LARGE_WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_workers, "kind": "oracle",
+                             "nproc": os.cpu_count(), "cpu_model": _cpu_model(), "sample": desc,
+                             "seconds_per_unit": {k: statistics.median(x[k] for x in stage)
+                                                  for k in ("grid", "fft", "phase")},
+                             "warmup": "each warm-up step loads the oracle in every process"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "rates_per_step": rates}
     print(json.dumps(line), flush=True)
+
+
+def _oracle_load(_):
+    """Worker: build (if needed) and load the oracle library."""
+    import oracle
+    oracle.lib()
+    return 0
 
 
 def run_ours(args):
@@ -556,6 +601,466 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
 
+
+# --------------------------------------------------------------------------
+# the default bench line: the large MeerKAT workload (16384^2, 128 channels)
+# --------------------------------------------------------------------------
+
+LARGE_CHANNELS = 128    # channels per rank
+LARGE_BLOCK = 16        # channels binned together (one plan call each)
+LARGE_WORKLOAD = "meerkat_16384sq_32w_128ch_kb8"
+
+
+def large_blocks(world: int, rank: int):
+    """Absolute channel ranges [c0, c1) of this rank's blocks: the 856-1712 MHz
+    band split into 128 x world channels, rank r taking channels
+    [128 r, 128 r + 128) in blocks of 16 (weak scaling: every rank grids the
+    same number of channels)."""
+    base = LARGE_CHANNELS * rank
+    return [(base + b, base + b + LARGE_BLOCK) for b in range(0, LARGE_CHANNELS, LARGE_BLOCK)]
+
+
+def _oracle_unit(cfg_kw, plane, uvw, vis, weight):
+    """Worker: the oracle's work for one w-plane of one channel (O1 steps 1-5):
+    grid the plane's visibilities (Eq. 3), its inverse 2-D DFT, the phase
+    screen and sum (Eq. 2).  Returns (visibilities, grid s, FFT s, phase s)."""
+    import oracle
+    cfg = oracle.Config(**cfg_kw)
+    one = np.ones(1)
+    t0 = time.perf_counter()
+    G = oracle.grid_plane(cfg, uvw, one, vis, weight, plane=plane)
+    t1 = time.perf_counter()
+    oracle.ifft2_inplace(G)
+    t2 = time.perf_counter()
+    img = np.zeros((cfg.N, cfg.N), np.complex128)
+    oracle.phase_accumulate(cfg, plane, G, img)
+    t3 = time.perf_counter()
+    return len(uvw), t1 - t0, t2 - t1, t3 - t2
+
+
+def _oracle_probes(cfg_kw, uvw, vis, weight, flag, p, q):
+    """Worker: O1 in its per-visibility form at pixels (p, q)."""
+    import oracle
+    cfg = oracle.Config(**cfg_kw)
+    return oracle.image_at(cfg, uvw, np.ones(1), vis, weight, flag, channel=0, p=p, q=q)
+
+
+def _oracle_cfg_kw(img):
+    return dict(N=img.N, Nw=img.Nw, S=img.S, kernel=img.kernel, kernel_param=img.kernel_param,
+                fov=img.fov, w_min=img.w_min, w_max=img.w_max)
+
+
+def _host_mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def large_oracle_units(img, obs_ch, count: int):
+    """The oracle's unit of work on the large workload: one (channel, w-plane)
+    at 16384^2.  From one channel's observation, the `count` planes whose
+    visibility counts are closest to the channel's average per plane (every
+    channel grids about the same number of visibilities, so the sample's
+    visibilities per plane match the whole step's), each as (plane, uvw, vis,
+    weight) of its visibilities; and that average."""
+    import oracle
+    vis = obs_ch.vis.cpu().numpy() if hasattr(obs_ch.vis, "cpu") else obs_ch.vis
+    cfg = oracle.Config(**_oracle_cfg_kw(img))
+    uvw0 = obs_ch.uvw * obs_ch.chan_scale[0]
+    one = np.ones(1)
+    fl = None if obs_ch.flag is None else obs_ch.flag[:, :1]
+    pl = oracle.place(cfg, uvw0, one, obs_ch.weight[:, :1], fl)
+    ok = pl["status"][:, 0] == 1
+    k = pl["k"][:, 0]
+    cnt = np.bincount(k[ok], minlength=img.Nw)
+    avg_per_plane = float(ok.sum()) / img.Nw
+    order = np.argsort(np.abs(cnt - avg_per_plane), kind="stable")[:count]
+    units = []
+    for kk in order:
+        sel = ok & (k == kk)
+        units.append((int(kk), np.ascontiguousarray(uvw0[sel]), np.ascontiguousarray(vis[sel, :1]),
+                      np.ascontiguousarray(obs_ch.weight[sel, :1])))
+    return units, avg_per_plane
+
+
+def large_cpu_baseline(img, units, pool, n_workers):
+    """The FP64 oracle on this host's cores: one unit on 1 thread, then
+    n_workers units at once (one per process); per-stage seconds."""
+    kw = _oracle_cfg_kw(img)
+    one = pool.apply(_oracle_unit, (kw,) + units[0])
+    t = time.perf_counter()
+    res = pool.starmap(_oracle_unit, [(kw,) + u for u in units[:n_workers]])
+    wall = time.perf_counter() - t
+    nv = sum(r[0] for r in res)
+    med = lambda i: statistics.median(r[i] for r in res)
+    return {
+        "one_thread": {"value": one[0] / (one[1] + one[2] + one[3]), "unit": UNIT, "cores": 1,
+                       "visibilities": one[0], "plane": units[0][0],
+                       "seconds": {"grid": one[1], "fft": one[2], "phase": one[3]}},
+        "all_cores": {"value": nv / wall, "unit": UNIT, "cores": n_workers, "visibilities": nv,
+                      "wall_s": wall, "planes": [u[0] for u in units[:n_workers]],
+                      "median_seconds_per_unit": {"grid": med(1), "fft": med(2), "phase": med(3)}},
+    }
+
+
+def _large_e2e(args, rick, cfg, grid_budget, data, C, N, n_blocks):
+    """The step through rick_dirty_image_host from pinned host buffers: one call
+    per block, the inputs copied in and the block's 16 images copied back into
+    one pinned buffer (the caller consumes each block's images before the next
+    arrives).  Timed on the host clock; the median of the steps."""
+    import torch
+    from paper_2601_19714_gb300 import dist as rdist
+    h_blocks = []
+    for obs, d in data:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_blocks.append((pin(obs.uvw), pin(obs.chan_scale), d["vis"].cpu().pin_memory(), pin(obs.weight),
+                         pin(obs.flag)))
+    h_img = torch.empty((C, N, N), dtype=torch.float32).pin_memory()
+    h_ws = torch.empty((n_blocks, C), dtype=torch.float64).pin_memory()
+    h_cnt = torch.empty(2, dtype=torch.int64).pin_memory()
+    eplan = rick.Plan(replace(cfg, grid_budget_bytes=grid_budget))
+
+    def e2e_step():
+        for b, hb in enumerate(h_blocks):
+            eplan.dirty_image_host(*hb, h_img, h_ws[b], h_cnt)
+
+    e2e_step()   # warm-up (allocates the plan's staging and grid)
+    steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    rdist.barrier()
+    each = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        e2e_step()
+        each.append((time.perf_counter() - t0) * 1e3)
+    ms = rdist.max_over_ranks(statistics.median(each), device="cuda")
+    h2d = sum(x.numel() * x.element_size() for hb in h_blocks for x in hb)
+    d2h = n_blocks * (h_img.numel() * 4 + C * 8 + 16)
+    del eplan
+    torch.cuda.empty_cache()
+    return {"ms": ms, "each": each, "h2d": h2d, "d2h": d2h}
+
+
+def run_large_line(args):
+    """The default bench line (see the module docstring)."""
+    import multiprocessing as mp
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2601_19714_gb300 import _build
+    from paper_2601_19714_gb300 import autotune
+    from paper_2601_19714_gb300 import dist as rdist
+    from paper_2601_19714_gb300 import rick
+    from visgen.workloads import evaluation_positions, meerkat_large
+    _build.build()
+    world, rank, local = rdist.env()
+    want_cpu = rank == 0 and not args.no_cpu_baseline
+    # the oracle's worker processes start (spawned) before the first GPU call
+    n_workers = os.cpu_count() or 1
+    per_unit = 9.0e9   # one 16384^2 complex128 plane and one image per process
+    n_workers = max(1, min(n_workers, int((_host_mem_available() - 16e9) // per_unit)))
+    pool = mp.get_context("spawn").Pool(n_workers) if want_cpu else None
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    nband = LARGE_CHANNELS * world
+    blocks = large_blocks(world, rank)
+
+    # inputs of every block, resident in HBM (made on the device)
+    data = []
+    for c0, c1 in blocks:
+        img, obs = meerkat_large(args.seed, nchan=nband, channels=slice(c0, c1), device="cuda")
+        data.append((obs, _dev_inputs(obs)))
+    N, Nw, C = img.N, img.Nw, LARGE_BLOCK
+    nrow = data[0][0].nrow
+
+    # launch shape of the gridder: autotuned on two channels of the first
+    # block (pattern 2), cached per problem class; untimed set-up
+    base = plan_config(img, C, True)
+    ns = base.stored_planes
+    if args.launch_shape:
+        t, k, g = (int(v) for v in args.launch_shape.split(","))
+        cfg = replace(base, tile=t, grid_threads=k, tiles_per_grab=g)
+    else:
+        d0 = data[0][1]
+        g2 = torch.empty((2, ns, N, N), dtype=torch.complex64, device="cuda")
+        cfg, _ = autotune.tuned(
+            base, nrow * C, os.path.join(ROOT, "_build_cache", "autotune.json"),
+            lambda: rick.autotune(base, d0["uvw"], d0["chan_scale"], d0["vis"], d0["weight"],
+                                  d0["flag"], nrow, (0, 2), (0, ns), g2, reps=2))
+        del g2
+        torch.cuda.empty_cache()
+    T = cfg.tile or 32
+
+    plan = rick.Plan(cfg)
+    plan.reserve(nrow)
+    assert plan.own_fft
+    image = torch.empty((LARGE_CHANNELS, N, N), dtype=torch.float32, device="cuda")
+    wsum = torch.empty((len(blocks), C), dtype=torch.float64, device="cuda")
+    counts = torch.empty((len(blocks), 2), dtype=torch.int64, device="cuda")
+    plane_bytes = ns * N * N * 8
+    free = torch.cuda.mem_get_info()[0]
+    gc = max(1, min(C, int((free - 12e9) // plane_bytes)))   # channels per grid group
+    grids = torch.empty((gc, ns, N, N), dtype=torch.complex64, device="cuda")
+    groups = [(g0, min(g0 + gc, C)) for g0 in range(0, C, gc)]
+
+    # reach of every block's binning (for the algorithmic byte and flop counts)
+    reach = {"tiles": 0, "tile_columns": 0, "planes": 0, "tile": T, "tiles_total": 0, "planes_total": 0}
+    for b, (obs, d) in enumerate(data):
+        plan.bin(d["uvw"], d["chan_scale"], d["vis"], d["weight"], d["flag"], nrow, wsum[b], counts[b])
+        r = reach_counts(plan.bin_offsets(), C, ns, N, T)
+        for key in ("tiles", "tile_columns", "planes", "tiles_total", "planes_total"):
+            reach[key] += r[key]
+    names = ("bin", "grid", "columns", "rows_phase")
+
+    def step(record=False):
+        ev = []
+        image.zero_()
+        for b, (obs, d) in enumerate(data):
+            e0 = torch.cuda.Event(enable_timing=True) if record else None
+            if record: e0.record(stream)
+            plan.bin(d["uvw"], d["chan_scale"], d["vis"], d["weight"], d["flag"], nrow, wsum[b], counts[b])
+            if record:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                ev.append(("bin", e0, e1))
+            for g0, g1 in groups:
+                marks = []
+                if record:
+                    marks.append(torch.cuda.Event(enable_timing=True))
+                    marks[-1].record(stream)
+                # only the reached tiles are written; the pruned passes read nothing else
+                plan.grid_binned(g0, g1, 0, ns, grids, sparse=True)
+                if record:
+                    marks.append(torch.cuda.Event(enable_timing=True))
+                    marks[-1].record(stream)
+                plan.fft_wplanes_columns(grids, g0, g1, 0, ns, gridded_by_plan=True)
+                if record:
+                    marks.append(torch.cuda.Event(enable_timing=True))
+                    marks[-1].record(stream)
+                c0 = blocks[b][0] - blocks[0][0]
+                plan.rows_phase_correct_reduce(grids, g0, g1, 0, ns, wsum[b], image[c0 + g0:c0 + g1],
+                                               gridded_by_plan=True)
+                if record:
+                    marks.append(torch.cuda.Event(enable_timing=True))
+                    marks[-1].record(stream)
+                    ev += [("grid", marks[0], marks[1]), ("columns", marks[1], marks[2]),
+                           ("rows_phase", marks[2], marks[3])]
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cnt = counts.cpu().numpy()
+    n_grid, n_drop = int(cnt[:, 0].sum()), int(cnt[:, 1].sum())
+    launches0 = plan.launch_count()
+    rdist.barrier()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    recs = []
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        start.record(stream)
+        for _ in range(args.steps):
+            recs.append(step(record=True))
+        stop.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    rdist.barrier()
+    launches = plan.launch_count() - launches0
+    ms = rdist.max_over_ranks(start.elapsed_time(stop) / args.steps, device="cuda")
+    per_step = []
+    for ev in recs:
+        acc = {k: 0.0 for k in names}
+        for k, a, z in ev:
+            acc[k] += a.elapsed_time(z)
+        per_step.append(acc)
+    st = {k: statistics.median(s[k] for s in per_step) for k in names}
+    rows_launches = len(blocks) * len(groups)
+
+    # algorithmic bytes and flops per step, summed over the blocks' binnings
+    nrow_all = nrow * len(blocks)
+    stage_bytes = stage_traffic(N, C, ns, nrow, n_grid / len(blocks), T, reach, True)
+    stage_bytes = {k: v for k, v in stage_bytes.items()}
+    stage_bytes["bin"] = (24.0 * nrow_all + LARGE_CHANNELS * nrow * (8 + 4 + 1)
+                          + LARGE_CHANNELS * nrow * (4 + 4 + 16) * 2 + 16.0 * n_grid)
+    stage_bytes["grid"] = 8.0 * reach["tiles"] * T * T + 16.0 * n_grid
+    stage_bytes["rows_phase"] = 8.0 * reach["tile_columns"] * N * T + 8.0 * LARGE_CHANNELS * N * N
+    hbm, peak_kind = peaks()
+    gbs = {k: stage_bytes[k] / (st[k] * 1e-3) / 1e9 for k in st}
+    flops = stage_flops(N, C, ns, reach, True)
+    tfl = {k: flops[k] / (st[k] * 1e-3) / 1e12 for k in flops}
+    dom = max(st, key=st.get)
+    # the fused row pass issues FP32 arithmetic and shared-memory traffic with
+    # DRAM lightly loaded (ncu): its bound is the FP32 pipes
+    roof = {"bound": "alu", "kernel": "k_rows_phase_reduce_split (rows_phase)", "stage": dom,
+            "achieved": tfl["rows_phase"], "peak": FP32_PEAK_TFLOPS,
+            "peak_kind": "derived (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz)", "unit": "TFLOP/s",
+            "frac": tfl["rows_phase"] / FP32_PEAK_TFLOPS,
+            "per_launch": {"launches_per_step": rows_launches,
+                           "avg_ms": st["rows_phase"] / rows_launches,
+                           "flops": flops["rows_phase"] / rows_launches},
+            "hbm_achieved_gbs": gbs["rows_phase"], "hbm_frac": gbs["rows_phase"] / hbm,
+            "traffic": None,
+            "traffic_note": "ncu DRAM bytes of this kernel: profiles/rows_phase_split_meerkat_16384sq_small.md"}
+
+    # image error: the same plan's path on a 1 % row subsample of the lowest
+    # and highest channels, against the oracle's per-visibility O1 at 64 pixels
+    image_error = None
+    if rank == 0 and pool is not None:
+        del grids
+        torch.cuda.empty_cache()
+        image_error = {}
+        pr = evaluation_positions(N, 64, seed=N)
+        pp, qq = pr[:, 0].astype(np.int32), pr[:, 1].astype(np.int32)
+        A = taper_gain_of(plan.taper())[qq, pp]
+        kw = _oracle_cfg_kw(img)
+        for c in (0, nband - 1):
+            im1, ob1 = meerkat_large(args.seed, nchan=nband, channels=slice(c, c + 1), row_fraction=0.01,
+                                     device="cuda")
+            ob1.vis = ob1.vis.cpu().numpy()
+            cfg1 = replace(cfg, n_channels=1)
+            with rick.Plan(cfg1) as p1:
+                d1 = _dev_inputs(ob1)
+                out = torch.zeros((1, N, N), dtype=torch.float32, device="cuda")
+                p1.dirty_image(d1["uvw"], d1["chan_scale"], d1["vis"], d1["weight"], d1["flag"], ob1.nrow, out)
+                got = out[0][torch.from_numpy(qq).long().cuda(), torch.from_numpy(pp).long().cuda()].cpu().numpy()
+                del out
+            uvw1 = ob1.uvw * ob1.chan_scale[0]
+            chunks = np.array_split(np.arange(len(pp)), n_workers)
+            parts = pool.starmap(_oracle_probes, [(kw, uvw1, ob1.vis, ob1.weight, ob1.flag, pp[ix], qq[ix])
+                                                  for ix in chunks if len(ix)])
+            ref = np.concatenate(parts).real
+            d = np.abs(got - ref)
+            peak = np.abs(ref).max()
+            m = A >= 1e-2
+            image_error[f"channel_{c}"] = {
+                "full": float(d.max() / peak), "weighted": float((d * A).max() / (np.abs(ref) * A).max()),
+                "inner": float(d[m].max() / peak), "probe_pixels": int(len(pp)), "inner_pixels": int(m.sum()),
+                "rows": int(ob1.nrow), "freq_mhz": float(ob1.freqs[0] / 1e6)}
+        image_error["how"] = ("the headline plan's path (sparse gridding, pruned own transform, fold) on a seeded "
+                              "1 % row subsample of the channel vs the FP64 oracle O1 in its per-visibility form "
+                              "at 64 pixels (corners and edge midpoints 8 px in, the centre, seeded others); "
+                              "full = max|d|/peak, weighted = taper-weighted, inner = where the taper gain >= 1e-2")
+        grids = None
+
+    # ---- end to end through the host entry point ---------------------------
+    del image
+    if grids is not None:
+        del grids
+    torch.cuda.empty_cache()
+    units_ch = None
+    if pool is not None:
+        # the oracle's sample: planes of the middle channel of this rank's set
+        mid = LARGE_CHANNELS // 2
+        ob_mid = data[mid // LARGE_BLOCK][0]
+        from visgen import Observation
+        j = mid % LARGE_BLOCK
+        vis_mid = data[mid // LARGE_BLOCK][1]["vis"][:, j:j + 1].cpu().numpy()
+        units_ch = Observation(ob_mid.uvw, ob_mid.chan_scale[j:j + 1], vis_mid,
+                               np.ascontiguousarray(ob_mid.weight[:, j:j + 1]),
+                               np.ascontiguousarray(ob_mid.flag[:, j:j + 1]), ob_mid.sources,
+                               ob_mid.freqs[j:j + 1])
+    e2e = None
+    if not args.no_e2e:
+        e2e = _large_e2e(args, rick, cfg, gc * plane_bytes, data, C, N, len(blocks))
+    del data, plan
+    torch.cuda.empty_cache()
+
+    if rank == 0:
+        units = n_grid * world
+        line = {
+            "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": LARGE_WORKLOAD, "antennas": 64, "baselines": 2016,
+                       "time_steps": nrow // 2016, "track_h": 8, "channels": LARGE_CHANNELS,
+                       "band_mhz": [856, 1712], "visibilities": int(nrow * LARGE_CHANNELS),
+                       "gridded": int(n_grid), "dropped": int(n_drop), "N": N, "w_planes": Nw,
+                       "hermitian_fold": True, "stored_planes": ns, "support": img.S,
+                       "kernel": "kaiser_bessel", "index_phase": "fp64", "accumulate": "fp32",
+                       "fov_deg": round(math.degrees(img.fov), 4), "fft": FFT_DESC["own"],
+                       "blocks": f"{len(blocks)} x {C} channels, inputs of all blocks resident in HBM",
+                       "grid_group_channels": gc, "tile": cfg.tile, "grid_threads": cfg.grid_threads,
+                       "tiles_per_grab": cfg.tiles_per_grab,
+                       "launch_shape": "given" if args.launch_shape else "autotuned",
+                       "images": f"{LARGE_CHANNELS} x {N}^2 f32 in HBM ({LARGE_CHANNELS * N * N * 4 / 1e9:.0f} GB)",
+                       "l2": f"inputs larger than L2 (grid group {gc * plane_bytes / 1e9:.0f} GB, "
+                             f"images {LARGE_CHANNELS * N * N * 4 / 1e9:.0f} GB; not flushed)",
+                       "parallelism": f"channel sets x{world} (128 channels per rank, no collective on the data path)"},
+            "stages_ms": st,
+            "stage_gbs": gbs,
+            "gridder_vis_per_s": n_grid / (st["grid"] * 1e-3),
+            "bin_plus_grid_vis_per_s": n_grid / ((st["bin"] + st["grid"]) * 1e-3),
+            "roofline": roof,
+            "roofline_stages": {k: {"bound": "hbm", "achieved": gbs[k], "peak": hbm, "peak_kind": peak_kind,
+                                    "unit": "GB/s", "frac": gbs[k] / hbm} for k in st},
+            "fp32_stages": {k: {"achieved": tfl[k], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": tfl[k] / FP32_PEAK_TFLOPS} for k in tfl},
+            "e2e": None if e2e is None else {
+                "value": units / (e2e["ms"] * 1e-3), "unit": UNIT, "ms_per_step": e2e["ms"],
+                "ms_steps": [round(x, 3) for x in e2e["each"]], "timing": "median of the steps",
+                "entry_point": "rick_dirty_image_host, one call per block of 16 channels",
+                "h2d_bytes_per_step": int(e2e["h2d"]), "d2h_bytes_per_step": int(e2e["d2h"])},
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+            "reach": reach,
+            "image_error": image_error,
+        }
+        if pool is not None:
+            units_s, avg = large_oracle_units(img, units_ch, n_workers)
+            cb = large_cpu_baseline(img, units_s, pool, n_workers)
+            allc, one = cb["all_cores"], cb["one_thread"]
+            line["cpu_baseline"] = {
+                "value": allc["value"], "unit": UNIT, "cores": allc["cores"], "kind": "oracle",
+                "nproc": os.cpu_count(), "cpu_model": _cpu_model(),
+                "sample": (f"the FP64 oracle's unit of work on this workload -- one w-plane of channel "
+                           f"{LARGE_CHANNELS // 2} ({units_ch.freqs[0] / 1e6:.1f} MHz) at {N}^2: grid its "
+                           f"visibilities (Eq. 3), inverse 2-D DFT, phase screen and sum (Eq. 2) -- on "
+                           f"{allc['cores']} planes at once, one process per core; the planes are those "
+                           f"whose visibility counts are closest to the channel's average per plane "
+                           f"({avg:.0f}; the whole step's is {n_grid / (LARGE_CHANNELS * Nw):.0f})"),
+                "seconds_per_unit": allc["median_seconds_per_unit"], "wall_s": allc["wall_s"],
+                "visibilities": allc["visibilities"],
+                "one_thread": one,
+                "full_step_estimate_s": {
+                    "how": "composed from the per-unit stage seconds (not measured): grid scaled by "
+                           "visibilities, FFT and phase by the planes of the step (channels x Nw)",
+                    "grid": one["seconds"]["grid"] * n_grid / one["visibilities"],
+                    "fft": one["seconds"]["fft"] * LARGE_CHANNELS * Nw,
+                    "phase": one["seconds"]["phase"] * LARGE_CHANNELS * Nw}}
+        print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.close()
+        pool.join()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def taper_gain_of(taper):
+    t = np.asarray(taper, dtype=np.float64)
+    c0 = t[t.shape[0] // 2]
+    return np.outer(t, t) / (c0 * c0)
 
 # --------------------------------------------------------------------------
 # other workloads (parity/measurement cases, not the default bench line)
@@ -1258,6 +1763,60 @@ def run_profile_small(args):
           flush=True)
 
 
+def run_profile_large_small(args):
+    """A small case of the default (large) workload for ncu captures: the
+    MeerKAT large recipe at 16384^2, one channel (1712 MHz), 10 % of the
+    rows of the 8 h track (1.17 M visibilities), --profile-planes w-planes
+    (half stored with the fold; 4: 4.3 GB of grids), KB S = 8, launch shape
+    32/128/4; a step = rick_bin + sparse gridding + the pruned column pass +
+    the split row pass fused with the reduction."""
+    import torch
+    from paper_2601_19714_gb300 import _build, rick
+    from visgen.workloads import meerkat_large
+    _build.build()
+    img, obs = meerkat_large(args.seed, channels=slice(127, 128), row_fraction=0.1, Nw=args.profile_planes,
+                             device="cuda")
+    dev = _dev_inputs(obs)
+    C, N = obs.nchan, img.N
+    cfg = replace(plan_config(img, C, not args.no_fold), tile=32, grid_threads=128, tiles_per_grab=4)
+    plan = rick.Plan(cfg)
+    ns = cfg.stored_planes
+    grids = torch.empty((C, ns, N, N), dtype=torch.complex64, device="cuda")
+    image = torch.zeros((C, N, N), dtype=torch.float32, device="cuda")
+    wsum = torch.empty(C, dtype=torch.float64, device="cuda")
+    counts = torch.empty(2, dtype=torch.int64, device="cuda")
+
+    def step():
+        plan.bin(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], dev["flag"], obs.nrow,
+                 wsum, counts)
+        plan.grid_binned(0, C, 0, ns, grids, sparse=True)
+        plan.fft_wplanes_columns(grids, 0, C, 0, ns, gridded_by_plan=True)
+        plan.rows_phase_correct_reduce(grids, 0, C, 0, ns, wsum, image, gridded_by_plan=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    n_grid = int(counts[0].item())
+    reach = reach_counts(plan.bin_offsets(), C, ns, N, 32)
+    sbytes = stage_traffic(N, C, ns, obs.nrow, n_grid, 32, reach, True)
+    print(json.dumps({"metric": METRIC, "value": n_grid / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+                      "reach": reach, "stage_bytes": sbytes, "stage_flops": stage_flops(N, C, ns, reach, True),
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "impl": "ours", "config": {"workload": f"meerkat_large_small_16384sq_{img.Nw}w_1ch_kb8",
+                                                 "visibilities": int(obs.nrow * C), "gridded": n_grid,
+                                                 "hermitian_fold": cfg.hermitian_fold, "stored_planes": ns,
+                                                 "tile": 32, "grid_threads": 128, "tiles_per_grab": 4}}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1267,19 +1826,24 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true",
+                    help="leave out the CPU oracle legs (cpu_baseline, image_error)")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="leave out the end-to-end leg through the host entry point (profiling runs)")
     ap.add_argument("--fft", default="own", choices=["cufft", "own"],
                     help="2-D DFT of the headline step and of profile_small "
                          "(the headline also times the other one)")
     ap.add_argument("--no-fold", action="store_true",
                     help="headline without the Hermitian fold (all Nw planes stored and "
                          "transformed); the other variant is always measured beside it")
-    ap.add_argument("--workload", default="meerkat",
-                    choices=["meerkat", "lofar", "learned", "large", "predict", "wkernel",
-                             "options", "profile_small"],
-                    help="meerkat (default bench line); lofar / learned / large measure the "
-                         "batched, learned-kernel and precision-stress workloads; "
-                         "profile_small is the small case the ncu captures use")
+    ap.add_argument("--workload", default="large",
+                    choices=["large", "meerkat", "lofar", "learned", "large_precision", "predict",
+                             "wkernel", "options", "profile_small", "profile_large_small"],
+                    help="large (default bench line: 16384^2 x 32 planes, 128 channels, 1.5 G "
+                         "visibilities); meerkat (4096^2, 16 channels); lofar / learned / "
+                         "large_precision measure the batched, learned-kernel and precision-stress "
+                         "workloads; profile_small / profile_large_small are the small cases the ncu "
+                         "captures use")
     ap.add_argument("--launch-shape", default="",
                     help="tile,threads,grab of the gridder for the headline (default: autotuned)")
     ap.add_argument("--profile-planes", type=int, default=8,
@@ -1287,14 +1851,16 @@ def main():
                          "32: 4.3 GB, 16 planes per channel as in the headline's row pass)")
     args = ap.parse_args()
     if args.steps is None:   # the reference arm's oracle takes seconds per step
-        args.steps = 40 if args.workload == "meerkat" and args.impl == "ours" else 10
+        args.steps = {"large": 10, "meerkat": 40}.get(args.workload, 10) if args.impl == "ours" else 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "large":
+        run_large_line(args)
     elif args.workload == "lofar":
         run_lofar(args)
     elif args.workload == "learned":
         run_learned(args)
-    elif args.workload == "large":
+    elif args.workload == "large_precision":
         run_large(args)
     elif args.workload == "options":
         run_options(args)
@@ -1304,6 +1870,8 @@ def main():
         run_predict(args)
     elif args.workload == "profile_small":
         run_profile_small(args)
+    elif args.workload == "profile_large_small":
+        run_profile_large_small(args)
     else:
         run_ours(args)
 

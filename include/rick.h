@@ -502,8 +502,9 @@ rick_status rick_learn_destroy(rick_learn* learn);
 /* Number of visibilities placed on the grid (the rest are skipped/dropped). */
 int64_t rick_learn_placed(const rick_learn* learn);
 
-/* One training field: sources[ns][3] = (pixel p, pixel q, flux) on pixel
- * centres (host, 1..64), probes[np][2] pixels (host, 1..64).  Predicts the
+/* One training field: sources[ns][3] = (p, q, flux), positions in pixels
+ * anywhere in [0, N) (host, 1..64; p = N/2 is l = 0), probes[np][2] pixels
+ * (host, 1..64).  Predicts the
  * field's visibilities (Eq. 1), evaluates at the probes the w-stacking image
  * that gridding with the tap table (device [Nw][L+1][L+1][16]) would give
  * (Eq. 2, 3) and the direct Fourier inversion, and writes the loss
@@ -569,6 +570,42 @@ int32_t rick_plan_fft_impl(const rick_plan* plan);
  * warps of a CTA (the load balancing of Sec. 3.2 on one device); for tests.
  * Synchronous (waits for the plan's last stream). */
 rick_status rick_plan_schedule_counts(rick_plan* plan, uint32_t counts[3]);
+
+/* ---- failure handling (tests) ---------------------------------------
+ *
+ * The paper's pipeline has no failure handling; these hooks let a caller's
+ * (and this library's) tests drive every error path without a GPU fault. */
+
+typedef enum {
+    RICK_INJECT_NONE = 0,
+    RICK_INJECT_DEVICE_ALLOC = 1, /* a device allocation of a plan returns RICK_ERR_OOM */
+    RICK_INJECT_CUFFT_PLAN = 2,   /* a cuFFT plan creation returns RICK_ERR_CUFFT */
+    RICK_INJECT_LAUNCH = 3        /* a kernel launch is reported as failed (RICK_ERR_CUDA) */
+} rick_inject_site;
+
+/* Arm one failure: the countdown-th event of that kind from now (process
+ * wide, any thread) fails once, then the site disarms.  RICK_INJECT_NONE or
+ * countdown 0 disarms.  The call that fails returns its status and leaks
+ * nothing (a failing rick_plan_create frees what it allocated; a failing
+ * call on a plan leaves the plan's memory owned by the plan, and the plan
+ * usable).  The launched kernel of an injected launch failure has run; only
+ * its report is replaced.  The environment variable RICK_INJECT="site:n"
+ * arms the same at the library's first check, unless this call came first. */
+rick_status rick_debug_inject(int32_t site, int32_t countdown);
+
+/* 1 in a RICK_DEBUG build of the library (device-side consistency checks:
+ * a failed check records its code in the plan's status word, the guarded
+ * access is skipped, and rick_plan_sync_status returns RICK_ERR_INTERNAL
+ * and clears the word; no trap), else 0. */
+int32_t rick_debug_build(void);
+
+/* RICK_DEBUG builds only (else RICK_ERR_UNSUPPORTED): overwrite the first
+ * footprint cell (tile-relative, 0..255) of binned record `index` of the
+ * plan's current gridding binning, keeping its fractions, so that a test can
+ * make the gridder's record check fail.  A cell outside the tile is also
+ * harmless in a normal build (the gridder clips every cell to its tile).
+ * Synchronous. */
+rick_status rick_debug_poke_record(rick_plan* plan, int64_t index, int32_t cell_x, int32_t cell_y);
 
 /* Copy the binning result of the last rick_bin to host memory, for tests:
  * offsets[n_keys + 1] (uint32, start of every (channel, plane, tile, class)

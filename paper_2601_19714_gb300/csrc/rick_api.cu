@@ -10,6 +10,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -51,6 +53,49 @@ void set_err(const char* fmt, ...) {
             return RICK_ERR_INVALID_ARG;      \
         }                                     \
     } while (0)
+
+// ---- fault injection (tests of the error paths) ------------------------------
+//
+// rick_debug_inject arms one site: the countdown-th event of that kind from
+// now fails once -- a device allocation of the library returns
+// cudaErrorMemoryAllocation without allocating, a cuFFT plan creation
+// returns an error, or a kernel launch is reported as failed (the kernel has
+// been queued; the call returns RICK_ERR_CUDA as if the launch had failed).
+// The environment variable RICK_INJECT="site:countdown" arms the same at the
+// first check of a process.
+std::atomic<int> g_inject_site{0}, g_inject_left{0};
+std::once_flag g_inject_env;
+
+void inject_init() {
+    std::call_once(g_inject_env, [] {
+        const char* e = std::getenv("RICK_INJECT");
+        int a = 0, b = 0;
+        if (e && std::sscanf(e, "%d:%d", &a, &b) == 2 && a > 0 && a <= RICK_INJECT_LAUNCH && b > 0) {
+            g_inject_left.store(b);
+            g_inject_site.store(a);
+        }
+    });
+}
+
+bool inject_fire(int site) {
+    inject_init();
+    if (site == RICK_INJECT_NONE || g_inject_site.load(std::memory_order_relaxed) != site) return false;
+    if (g_inject_left.fetch_sub(1) == 1) {
+        g_inject_site.store(0);
+        return true;
+    }
+    return false;
+}
+
+// cudaMalloc for the plan's memory, with the injection point
+template <class T>
+cudaError_t dmalloc(T** p, size_t bytes) {
+    if (inject_fire(RICK_INJECT_DEVICE_ALLOC)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 // ---- FP64 host math for the tables (independent of any other code) -------
 
@@ -357,12 +402,12 @@ rick_status ensure_vis_capacity(rick_plan* P, int64_t nvis) {
     P->cap_vis = 0;
     P->list_cap = 0;
     const size_t n = (size_t)nvis;
-    RK_CUDA(cudaMalloc(&P->d_key, n * sizeof(uint32_t)));
-    RK_CUDA(cudaMalloc(&P->d_rank, n * sizeof(uint32_t)));
-    RK_CUDA(cudaMalloc(&P->d_stage, n * sizeof(VisRecord)));
-    RK_CUDA(cudaMalloc(&P->d_records, n * sizeof(VisRecord)));
+    RK_CUDA(dmalloc(&P->d_key, n * sizeof(uint32_t)));
+    RK_CUDA(dmalloc(&P->d_rank, n * sizeof(uint32_t)));
+    RK_CUDA(dmalloc(&P->d_stage, n * sizeof(VisRecord)));
+    RK_CUDA(dmalloc(&P->d_records, n * sizeof(VisRecord)));
     const uint32_t cap = schedule_list_cap(nvis, P->T);
-    RK_CUDA(cudaMalloc(&P->d_lists, 3 * (size_t)cap * sizeof(uint32_t)));
+    RK_CUDA(dmalloc(&P->d_lists, 3 * (size_t)cap * sizeof(uint32_t)));
     P->list_cap = cap;
     P->cap_vis = nvis;
     return RICK_OK;
@@ -372,12 +417,16 @@ rick_status ensure_weight_capacity(rick_plan* P, int64_t nvis) {
     if (nvis <= P->cap_w) return RICK_OK;
     dfree(P->d_wbuf);
     P->cap_w = 0;
-    RK_CUDA(cudaMalloc(&P->d_wbuf, sizeof(float) * (size_t)(nvis > 0 ? nvis : 1)));
+    RK_CUDA(dmalloc(&P->d_wbuf, sizeof(float) * (size_t)(nvis > 0 ? nvis : 1)));
     P->cap_w = nvis;
     return RICK_OK;
 }
 
 rick_status make_fft_plan(cufftHandle* h, bool* have, int N, int batch) {
+    if (inject_fire(RICK_INJECT_CUFFT_PLAN)) {
+        set_err("cuFFT plan creation failed (injected)");
+        return RICK_ERR_CUFFT;
+    }
     if (cufftCreate(h) != CUFFT_SUCCESS) {
         set_err("cufftCreate failed");
         return RICK_ERR_CUFFT;
@@ -455,36 +504,36 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
     make_taper(taper_kind, c.kernel_param, c.support, c.N, P->Ng, P->taper);
     std::vector<float> inv(c.N);
     for (int p = 0; p < c.N; ++p) inv[p] = (float)(1.0 / P->taper[p]);
-    RK_CUDA(cudaMalloc(&P->d_inv_taper, sizeof(float) * c.N));
+    RK_CUDA(dmalloc(&P->d_inv_taper, sizeof(float) * c.N));
     RK_CUDA(cudaMemcpy(P->d_inv_taper, inv.data(), sizeof(float) * c.N, cudaMemcpyHostToDevice));
 
-    RK_CUDA(cudaMalloc(&P->d_hist, sizeof(uint32_t) * P->nkeys));
-    RK_CUDA(cudaMalloc(&P->d_offsets, sizeof(uint32_t) * (P->nkeys + 1)));
-    RK_CUDA(cudaMalloc(&P->d_partials, sizeof(uint32_t) * scan_partials_needed(P->nkeys)));
-    RK_CUDA(cudaMalloc(&P->d_counter, 8 * sizeof(uint32_t)));
-    RK_CUDA(cudaMalloc(&P->d_counts, 2 * sizeof(unsigned long long)));
-    RK_CUDA(cudaMalloc(&P->d_status, sizeof(int)));
+    RK_CUDA(dmalloc(&P->d_hist, sizeof(uint32_t) * P->nkeys));
+    RK_CUDA(dmalloc(&P->d_offsets, sizeof(uint32_t) * (P->nkeys + 1)));
+    RK_CUDA(dmalloc(&P->d_partials, sizeof(uint32_t) * scan_partials_needed(P->nkeys)));
+    RK_CUDA(dmalloc(&P->d_counter, 8 * sizeof(uint32_t)));
+    RK_CUDA(dmalloc(&P->d_counts, 2 * sizeof(unsigned long long)));
+    RK_CUDA(dmalloc(&P->d_status, sizeof(int)));
     RK_CUDA(cudaMemset(P->d_status, 0, sizeof(int)));
-    RK_CUDA(cudaMalloc(&P->d_wsum, sizeof(double) * c.n_channels));
+    RK_CUDA(dmalloc(&P->d_wsum, sizeof(double) * c.n_channels));
     if (c.weighting != RICK_WEIGHT_NATURAL) {
-        RK_CUDA(cudaMalloc(&P->d_density, sizeof(double) * (size_t)c.N * c.N * c.n_channels));
-        RK_CUDA(cudaMalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
+        RK_CUDA(dmalloc(&P->d_density, sizeof(double) * (size_t)c.N * c.N * c.n_channels));
+        RK_CUDA(dmalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
     }
 
     P->own_fft = c.fft_impl == RICK_FFT_OWN && fft_supported(c.N) && P->Ng == c.N;
     if (P->own_fft) {
         std::vector<float2> tw;
         fft_twiddles(c.N, tw);
-        RK_CUDA(cudaMalloc(&P->d_twid, sizeof(float2) * tw.size()));
+        RK_CUDA(dmalloc(&P->d_twid, sizeof(float2) * tw.size()));
         RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
-        RK_CUDA(cudaMalloc(&P->d_colocc, (size_t)c.n_channels * P->planes * P->NT));
-        RK_CUDA(cudaMalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
-        RK_CUDA(cudaMalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
+        RK_CUDA(dmalloc(&P->d_colocc, (size_t)c.n_channels * P->planes * P->NT));
+        RK_CUDA(dmalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
+        RK_CUDA(dmalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
                                               ((P->NT + 31) / 32)));
         const size_t NN = (size_t)c.N * c.N;
-        RK_CUDA(cudaMalloc(&P->d_pix_turns, sizeof(uint2) * NN));
-        RK_CUDA(cudaMalloc(&P->d_pix_scale, sizeof(float) * NN));
-        RK_CUDA(cudaMalloc(&P->d_pix_model_scale, sizeof(float) * NN));
+        RK_CUDA(dmalloc(&P->d_pix_turns, sizeof(uint2) * NN));
+        RK_CUDA(dmalloc(&P->d_pix_scale, sizeof(float) * NN));
+        RK_CUDA(dmalloc(&P->d_pix_model_scale, sizeof(float) * NN));
         RK_CUDA(launch_pixel_phase(phase_params(P, 0, 1, 0, 1), P->d_inv_taper, P->d_pix_turns, P->d_pix_scale,
                                    P->d_pix_model_scale, nullptr));
         RK_CUDA(cudaDeviceSynchronize());
@@ -509,6 +558,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 rick_status check_launch(cudaError_t e, const char* what) {
+    if (e == cudaSuccess && inject_fire(RICK_INJECT_LAUNCH)) e = cudaErrorLaunchFailure;
     if (e != cudaSuccess) {
         set_err("%s: %s", what, cudaGetErrorString(e));
         return RICK_ERR_CUDA;
@@ -711,6 +761,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.list_cap = P->list_cap;
     G.w_support = 0;
     G.skip_empty = sparse ? 1 : 0;
+    G.status = P->d_status;
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, 8 * sizeof(uint32_t), st));
     int launches = 0;
@@ -1008,6 +1059,7 @@ rick_status degrid_impl(rick_plan* P, const float* grids, int c0, int c1, int k0
     G.n_items = (uint32_t)items;
     G.kind = c.kernel_kind;
     G.w_support = c.w_support >= 2 ? c.w_support : 0;
+    G.status = P->d_status;
     std::memcpy(G.coef, P->tap_coef, sizeof G.coef);
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, sizeof(uint32_t), st));
@@ -1048,7 +1100,7 @@ rick_status ensure_group_grid(rick_plan* P) {
     if (need > P->grid_cap) {
         dfree(P->d_grid);
         P->grid_cap = 0;
-        RK_CUDA(cudaMalloc(&P->d_grid, need));
+        RK_CUDA(dmalloc(&P->d_grid, need));
         P->grid_cap = need;
     }
     return RICK_OK;
@@ -1187,7 +1239,7 @@ rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t la
     if (lattice != plan->lattice) {
         dfree(plan->d_table);
         plan->lattice = 0;
-        RK_CUDA(cudaMalloc(&plan->d_table, n * sizeof(float)));
+        RK_CUDA(dmalloc(&plan->d_table, n * sizeof(float)));
         plan->lattice = lattice;
     }
     RK_CUDA(cudaMemcpyAsync(plan->d_table, taps, n * sizeof(float), cudaMemcpyDeviceToDevice,
@@ -1318,14 +1370,14 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
     if (need > plan->in_cap) {
         dfree(plan->d_in);
         plan->in_cap = 0;
-        RK_CUDA(cudaMalloc(&plan->d_in, need));
+        RK_CUDA(dmalloc(&plan->d_in, need));
         plan->in_cap = need;
     }
     const size_t NN = (size_t)c.N * c.N, img_bytes = C * NN * sizeof(float);
     if (img_bytes > plan->img_cap) {
         dfree(plan->d_img);
         plan->img_cap = 0;
-        RK_CUDA(cudaMalloc(&plan->d_img, img_bytes));
+        RK_CUDA(dmalloc(&plan->d_img, img_bytes));
         plan->img_cap = img_bytes;
     }
     unsigned char* b = plan->d_in;
@@ -1401,13 +1453,62 @@ rick_status rick_plan_sync_status(rick_plan* plan) {
     int st = 0;
     RK_CUDA(cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
-        set_err("device-side check failed (code %d)", st);
+        set_err("device-side check failed (code %d: %s)", st,
+                st == kCheckGridItem ? "a gridder work item beyond the launch's tiles"
+                : st == kCheckRecordCell ? "a record's first footprint cell outside its tile"
+                                         : "unknown");
+        RK_CUDA(cudaMemset(plan->d_status, 0, sizeof(int)));   // reported once
         return RICK_ERR_INTERNAL;
     }
     return RICK_OK;
 }
 
 int64_t rick_plan_launch_count(const rick_plan* plan) { return plan ? plan->launches : -1; }
+
+rick_status rick_debug_inject(int32_t site, int32_t countdown) {
+    RK_ARG(site >= RICK_INJECT_NONE && site <= RICK_INJECT_LAUNCH, "unknown injection site");
+    RK_ARG(countdown >= 0, "countdown must be >= 0");
+    inject_init();   // reads RICK_INJECT once, so that it cannot override this call
+    g_inject_site.store(0);
+    if (site != RICK_INJECT_NONE && countdown > 0) {
+        g_inject_left.store(countdown);
+        g_inject_site.store(site);
+    }
+    return RICK_OK;
+}
+
+int32_t rick_debug_build(void) {
+#ifdef RICK_DEBUG
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+rick_status rick_debug_poke_record(rick_plan* plan, int64_t index, int32_t cell_x, int32_t cell_y) {
+#ifdef RICK_DEBUG
+    RK_ARG(plan != nullptr, "plan is NULL");
+    RK_ARG(plan->binned && !plan->binned_for_predict, "nothing binned for gridding");
+    RK_ARG(cell_x >= 0 && cell_x < 256 && cell_y >= 0 && cell_y < 256, "cells are 8-bit fields");
+    RK_CUDA(cudaStreamSynchronize(plan->last_stream));
+    uint32_t total = 0;
+    RK_CUDA(cudaMemcpy(&total, plan->d_offsets + plan->nkeys, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+    RK_ARG(index >= 0 && index < (int64_t)total, "record index out of range");
+    VisRecord r;
+    RK_CUDA(cudaMemcpy(&r, plan->d_records + index, sizeof r, cudaMemcpyDeviceToHost));
+    r.px = (r.px & kFracMask) | ((uint32_t)cell_x << kFracBits);
+    r.py = (r.py & kFracMask) | ((uint32_t)cell_y << kFracBits);
+    RK_CUDA(cudaMemcpy(plan->d_records + index, &r, sizeof r, cudaMemcpyHostToDevice));
+    return RICK_OK;
+#else
+    (void)plan;
+    (void)index;
+    (void)cell_x;
+    (void)cell_y;
+    set_err("rick_debug_poke_record exists only in RICK_DEBUG builds");
+    return RICK_ERR_UNSUPPORTED;
+#endif
+}
 
 int32_t rick_plan_fft_impl(const rick_plan* plan) {
     return plan ? (plan->own_fft ? RICK_FFT_OWN : RICK_FFT_CUFFT) : -1;

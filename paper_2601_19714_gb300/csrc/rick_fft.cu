@@ -32,13 +32,13 @@
 //
 // N = 16384: a row of 128 KB fills most of an SM's shared memory, which leaves
 // no room for the fused row pass's per-pixel state.  That pass therefore
-// splits each row DFT between two CTAs by one decimation-in-frequency step
-// (k_rows_phase_reduce_split): with H = N/2,
-//   X[2k + r] = sum_{n<H} y_r[n] W_H^(n k),  y_0[n] = x[n] + x[n+H],
-//   y_1[n] = (x[n] - x[n+H]) W_N^n,
-// so CTA r transforms y_r with the H-point transform and owns the pixels
-// 2k + r.  The column pass and the plain row pass take one 16384-point
-// transform per CTA (1024 threads).
+// splits each row DFT between four CTAs by one radix-4 decimation-in-frequency
+// step (k_rows_phase_reduce_split): with M = N/4,
+//   X[4k + r] = sum_{n<M} y_r[n] W_M^(n k),
+//   y_r[n] = W_N^(r n) sum_{t<4} x[n + t M] W_4^(r t),
+// so CTA r transforms y_r with the 4096-point transform (two CTAs per SM) and
+// owns the pixels 4k + r.  The column pass and the plain row pass take one
+// 16384-point transform per CTA (1024 threads).
 //
 // Pruning: planes made by the library's gridder are zero in every tile that no
 // visibility reached (or, when the gridder skipped the zero fill, unwritten
@@ -63,6 +63,7 @@
 // W^8e W^7e) -- and for the later stages, whose t1 takes at most N/256 values,
 // all fifteen.  A CTA copies the tables into shared memory once.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "rick_internal.cuh"
@@ -93,6 +94,36 @@ __host__ __device__ constexpr float cos32(int k) {
 
 __host__ __device__ constexpr float sin32(int k) { return cos32(k - 8); }
 
+// cos(2 pi k / 64) for 0 <= k <= 16 (cos(pi k / 32), from the FP64 values)
+__host__ __device__ constexpr float quarter64(int k) {
+    return k == 0 ? 1.0f
+         : k == 1 ? 0.99518472667219692873f
+         : k == 2 ? 0.98078528040323043058f
+         : k == 3 ? 0.95694033573220882438f
+         : k == 4 ? 0.92387953251128673848f
+         : k == 5 ? 0.88192126434835504956f
+         : k == 6 ? 0.83146961230254523567f
+         : k == 7 ? 0.77301045336273699338f
+         : k == 8 ? 0.70710678118654757274f
+         : k == 9 ? 0.63439328416364548779f
+         : k == 10 ? 0.55557023301960228867f
+         : k == 11 ? 0.47139673682599780857f
+         : k == 12 ? 0.38268343236508983729f
+         : k == 13 ? 0.29028467725446233105f
+         : k == 14 ? 0.19509032201612833135f
+         : k == 15 ? 0.09801714032956077016f
+         : 0.0f;
+}
+
+__host__ __device__ constexpr float cos64(int k) {
+    return (k & 63) <= 16   ? quarter64(k & 63)
+         : (k & 63) <= 32 ? -quarter64(32 - (k & 63))
+         : (k & 63) <= 48 ? -quarter64((k & 63) - 32)
+                            : quarter64(64 - (k & 63));
+}
+
+__host__ __device__ constexpr float sin64(int k) { return cos64(k - 16); }
+
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -113,6 +144,18 @@ __device__ __forceinline__ float2 twiddle_const(float2 v, int e, int R) {
     if (k == 16) return make_float2(-v.x, -v.y);
     if (k == 24) return mul_si<!INV>(v);
     const float c = cos32(k), s = INV ? sin32(k) : -sin32(k);
+    return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
+}
+
+// v * e^(s 2 pi i k / 64) for compile-time k (after unrolling), s = +1 (INV) or -1
+template <bool INV>
+__device__ __forceinline__ float2 twiddle64(float2 v, int k) {
+    k &= 63;
+    if (k == 0) return v;
+    if (k == 16) return mul_si<INV>(v);
+    if (k == 32) return make_float2(-v.x, -v.y);
+    if (k == 48) return mul_si<!INV>(v);
+    const float c = cos64(k), s = INV ? sin64(k) : -sin64(k);
     return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
 }
 
@@ -165,6 +208,10 @@ struct Dft {
 };
 
 __device__ __forceinline__ int skew(int a) { return a + (a >> 4); }
+// skew(a + 16 k) = skew(a) + 17 k: an offset that is a multiple of 16 becomes
+// a constant added to the skewed base, so unrolled accesses at base + 16 k
+// need no address arithmetic of their own
+__host__ __device__ constexpr int skew16(int k16) { return k16 + k16 / 16; }
 
 template <int LOG2N>
 struct Shape {
@@ -203,16 +250,21 @@ __device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float
     const int M = 1 << log2M;
     const int t1 = b >> log2M, g = b & (M - 1);
     const int base = (t1 << (log2M + 4)) + g;
+    // output f0 goes to base + M f0: for M >= 16 (M f0 a multiple of 16) and
+    // for M = 1 (base a multiple of 16, f0 < 16) its skewed index is
+    // skew(base) plus a constant
+    float2* out = buf + skew(base);
+    auto at = [&](int f0) -> float2& { return M == 1 ? out[f0] : out[skew16(M * f0)]; };
     // t1 = 0: the table holds W^0 = 1 exactly, and a * 1 = a exactly
     const int cnt = Sh::stage_cnt(s);
     const float2* sw = tw + Sh::stage_off(s) + t1;
     if (Sh::stage_per(s) == 15) {
-        buf[skew(base)] = a[0];
+        at(0) = a[0];
 #pragma unroll
         for (int f0 = 1; f0 < 16; ++f0) {
             float2 w = sw[(f0 - 1) * cnt];
             if (!INV) w.y = -w.y;
-            buf[skew(base + M * f0)] = cmulf(a[f0], w);
+            at(f0) = cmulf(a[f0], w);
         }
         return;
     }
@@ -233,9 +285,9 @@ __device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float
     w[7] = cmulf(w[4], w[3]);
 #pragma unroll
     for (int f0 = 9; f0 < 16; ++f0) w[f0] = cmulf(w[8], w[f0 - 8]);
-    buf[skew(base)] = a[0];
+    at(0) = a[0];
 #pragma unroll
-    for (int f0 = 1; f0 < 16; ++f0) buf[skew(base + M * f0)] = cmulf(a[f0], w[f0]);
+    for (int f0 = 1; f0 < 16; ++f0) at(f0) = cmulf(a[f0], w[f0]);
 }
 
 // The middle radix-16 stages (all but the first, which starts from registers,
@@ -244,11 +296,12 @@ template <int LOG2N, bool INV>
 __device__ __forceinline__ void middle_stages(float2* buf, int b, const float2* tw) {
     using Sh = Shape<LOG2N>;
     constexpr int kMiddle = Sh::kTwStages - 1;
+    const float2* in = buf + skew(b);   // inputs b + T t2, T a multiple of 16
 #pragma unroll
     for (int s = 1; s <= kMiddle; ++s) {
         float2 a[16];
 #pragma unroll
-        for (int t2 = 0; t2 < 16; ++t2) a[t2] = buf[skew(b + Sh::T * t2)];
+        for (int t2 = 0; t2 < 16; ++t2) a[t2] = in[skew16(Sh::T * t2)];
         __syncthreads();
         radix16_out<LOG2N, INV>(a, b, s, buf, tw);
         __syncthreads();
@@ -262,12 +315,12 @@ __device__ __forceinline__ void last_stage(const float2* buf, int b, float2 (&x)
     constexpr int R = Sh::kLastR == 1 ? 16 : Sh::kLastR;
     constexpr int NB = 16 / R;          // butterflies per thread
     constexpr int M = Sh::N / R;
+    const float2* in = buf + skew(b);   // T i + M t2 is a multiple of 16
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         float2 a[R];
-        const int u = b + Sh::T * i;
 #pragma unroll
-        for (int t2 = 0; t2 < R; ++t2) a[t2] = buf[skew(u + M * t2)];
+        for (int t2 = 0; t2 < R; ++t2) a[t2] = in[skew16(Sh::T * i + M * t2)];
         Dft<R, INV>::run(a);
         // output u + M f0 = b + T (i + NB f0)
 #pragma unroll
@@ -429,6 +482,7 @@ __global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper
 // The next row is loaded into registers while the current one is transformed.
 // Two CTAs per SM for N <= 4096 (at most 128 registers).
 constexpr int kHornerBlock = 8;   // planes per Horner block of the fused row pass
+constexpr int kRowWindow = 64;    // rows (planes) whose occupancy a split row pass caches at once
 
 template <int LOG2N, bool COMPLEX_OUT>
 __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
@@ -564,113 +618,176 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     }
 }
 
-// N = 16384: k_rows_phase_reduce with every image row q split between two
-// CTAs, blockIdx.x = 2 q + r (the two halves run side by side and share the
-// row's cache lines).  CTA r forms y_r[n], n < H = N/2, from the row's two
-// halves,
-//   y_0[n] = x[n] + x[n+H],  y_1[n] = (x[n] - x[n+H]) e^(+2 pi i n/N),
-// transforms it with the H-point transform (X[2k + r] = sum_n y_r[n]
-// e^(+2 pi i n k/H)) and applies the phase screen and the plane sum of Eq. 2
-// to its pixels p = 2k + r exactly as k_rows_phase_reduce does (Horner blocks
-// of kHornerBlock planes, exact phasor at each block's end).  The twiddle of
-// y_1 is e^(2 pi i b/N) (per thread, from FP64) times e^(2 pi i t2/32) (a
-// constant, n = b + (H/16) t2).  With pruning the unreached tile columns of
-// either half are not read; a position whose two halves are both reached
-// (never on a centred uv coverage narrower than half the mesh) reads the upper
-// half when the row is consumed rather than in the prefetch, so that the
-// prefetch holds one value per position.
-template <bool COMPLEX_OUT>
-__global__ void __launch_bounds__(512, 1)
+// k_rows_phase_reduce with every image row q split between SPLIT CTAs (for
+// N = 16384: SPLIT = 4, each running the 4096-point transform, two CTAs per
+// SM), blockIdx.x = SPLIT q + r (the CTAs of a row run side by side and share
+// its cache lines).  One decimation-in-frequency step of radix SPLIT: with
+// M = N / SPLIT,
+//   X[SPLIT k + r] = sum_{n<M} y_r[n] e^(+2 pi i n k / M),
+//   y_r[n] = e^(+2 pi i r n / N) sum_{t<SPLIT} x[n + t M] e^(+2 pi i r t / SPLIT),
+// so CTA r transforms y_r with the M-point transform and owns the pixels
+// SPLIT k + r, to which it applies the phase screen and the plane sum of
+// Eq. 2 exactly as k_rows_phase_reduce does (Horner blocks of kHornerBlock
+// planes, exact phasor at each block's end).  The twiddle of y_r is
+// e^(2 pi i r b / N) (per thread, from FP64) times e^(2 pi i r t2 / (16 SPLIT))
+// (a constant of the unrolled code, n = b + (M/16) t2).  With pruning, the
+// unreached tile columns of the row are not read; the prefetch of the next
+// row holds one value per position n (its first reached part t), and the
+// other reached parts of the same position (none on a centred uv coverage
+// narrower than M) are read when the row is consumed.  Pruning also cuts the
+// arithmetic: N log2(M) butterfly work per row instead of N log2(N).
+template <int LOG2SUB, int SPLIT, bool COMPLEX_OUT>
+__global__ void __launch_bounds__((1 << LOG2SUB) / 16, LOG2SUB <= 12 ? 2 : 1)
 k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                           const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
-                          const float2* __restrict__ twid_h, float* __restrict__ image_real,
+                          const float2* __restrict__ twid_sub, float* __restrict__ image_real,
                           float2* __restrict__ image_complex, Occupancy occ) {
-    using Sh = Shape<13>;
-    constexpr int H = Sh::N, T = Sh::T;     // half row: 8192 points, 512 threads
-    constexpr int N = 2 * H;
+    static_assert(SPLIT == 2 || SPLIT == 4, "split");
+    using Sh = Shape<LOG2SUB>;
+    constexpr int M = Sh::N, T = Sh::T;     // sub-transform: points, threads
+    constexpr int N = SPLIT * M;
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
     float2* zrot = buf + Sh::kArray;                             // z per owned pixel
-    float* part = reinterpret_cast<float*>(zrot + H);
-    const int b = threadIdx.x, q = blockIdx.x >> 1, par = blockIdx.x & 1;
+    float* part = reinterpret_cast<float*>(zrot + M);
+    const int b = threadIdx.x, q = blockIdx.x / SPLIT, par = blockIdx.x % SPLIT;
     const float* scl = pix_scale + (size_t)q * N;
     const uint2* turns = pix_turns + (size_t)q * N;
-    load_tables<13>(twid_h, tw, b, T);
+    load_tables<LOG2SUB>(twid_sub, tw, b, T);
 #pragma unroll 4
     for (int j = 0; j < 16; ++j) {
         const int k = b + T * j;
         float s, c;
-        sincospif((float)(int32_t)__ldg(&turns[2 * k + par].y) * 4.656612873077392578125e-10f /* 2^-31 */,
+        sincospif((float)(int32_t)__ldg(&turns[SPLIT * k + par].y) * 4.656612873077392578125e-10f /* 2^-31 */,
                   &s, &c);
         zrot[k] = make_float2(c, -s);
         if (!COMPLEX_OUT) part[k] = 0.f;
     }
-    // e^(+2 pi i b / N) for the odd half's twiddles
+    // e^(+2 pi i r b / N) for this CTA's twiddles
     float2 wb = make_float2(1.f, 0.f);
     if (par) {
         double sd, cd;
-        sincospi(2.0 * (double)b / (double)N, &sd, &cd);
+        sincospi(2.0 * (double)(par * b) / (double)N, &sd, &cd);
         wb = make_float2((float)cd, (float)sd);
     }
 
     const size_t NN = (size_t)N * N;
     const int n_rows = P.nc * P.nk;
-    auto next_row = [&](int r) {
-        if (occ.plane != nullptr)
-            while (r < n_rows && occ.plane[r] == 0) ++r;
-        return r;
-    };
-    // liveness of the inputs b + T t2 (bits 0..15) and H + b + T t2 (bits
-    // 16..31) of plane r: with tiles of at least 32 columns every warp reads
-    // one tile column per t2 and half: lanes 0..31 read the 32 mask bytes and
-    // a ballot hands every lane the bits
-    const bool warp_mask = occ.tshift >= 5;
-    auto live_bits = [&](int r) -> uint32_t {
-        if (occ.col == nullptr) return 0xffffffffu;
+    // liveness of the inputs b + T t2 + t M of row (plane) r: bit 16 t + t2.
+    // With tiles of at least 32 columns (T >= 32) every warp reads one tile
+    // column per (t, t2): lane (t2 = lane % 16, t = lane / 16 + 2 h) reads one
+    // mask byte and ballots hand every lane the bits
+    const bool warp_mask = occ.tshift >= 5 && T >= 32;
+    const int lane = b & 31, warp = b >> 5;
+    auto live_bits_global = [&](int r) -> uint64_t {
+        if (occ.col == nullptr) return ~0ull >> (64 - 16 * SPLIT);
         const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+        uint64_t live = 0;
         if (warp_mask) {
-            const int lane = b & 31;
-            const int pos = (b & ~31) + T * (lane & 15) + (lane >> 4) * H;
-            return __ballot_sync(0xffffffffu, __ldg(cm + (pos >> occ.tshift)) != 0);
-        }
-        uint32_t live = 0;
 #pragma unroll
-        for (int t2 = 0; t2 < 16; ++t2) {
-            live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
-            live |= (__ldg(cm + ((H + b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << (16 + t2);
+            for (int h = 0; h < SPLIT / 2; ++h) {
+                const int pos = (b & ~31) + T * (lane & 15) + ((lane >> 4) + 2 * h) * M;
+                live |= (uint64_t)__ballot_sync(0xffffffffu, __ldg(cm + (pos >> occ.tshift)) != 0) << (32 * h);
+            }
+            return live;
         }
+#pragma unroll
+        for (int t = 0; t < SPLIT; ++t)
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2)
+                live |= (uint64_t)(__ldg(cm + ((b + T * t2 + t * M) >> occ.tshift)) != 0 ? 1u : 0u) << (16 * t + t2);
         return live;
     };
-    // prefetch: one value per position (the lower half where reached, else
-    // the upper half); pf_live remembers which
-    uint32_t pf_live = 0;
+    // The occupancy of the launch's rows, read a window of kRowWindow rows at
+    // a time by every warp for itself (all loads of a window in flight
+    // together): which rows are reached, and this warp's liveness bits of each
+    // (warp-uniform with warp_mask), so that stepping to the next row costs no
+    // dependent global load.  Each warp reads and writes only its own slots.
+    constexpr int kWarps = T / 32;
+    __shared__ uint64_t s_win_live[kRowWindow * (kWarps > 0 ? kWarps : 1)];
+    __shared__ uint64_t s_win_reached[kWarps > 0 ? kWarps : 1];
+    __shared__ int s_win_first[kWarps > 0 ? kWarps : 1];
+    if (lane == 0) s_win_first[warp] = -kRowWindow;
+    __syncwarp();
+    auto load_window = [&](int w0) {
+        const bool f0 = w0 + lane < n_rows && (occ.plane == nullptr || occ.plane[w0 + lane] != 0);
+        const bool f1 = w0 + 32 + lane < n_rows && (occ.plane == nullptr || occ.plane[w0 + 32 + lane] != 0);
+        const uint64_t reached = (uint64_t)__ballot_sync(0xffffffffu, f0) |
+                                 ((uint64_t)__ballot_sync(0xffffffffu, f1) << 32);
+        if (warp_mask) {
+#pragma unroll 8
+            for (int i = 0; i < kRowWindow; ++i) {
+                // every row of the launch has a mask (zero where unreached), so
+                // the loads of a window need no reached test and go out together
+                const uint64_t lb = w0 + i < n_rows ? live_bits_global(w0 + i) : 0;
+                if (lane == 0) s_win_live[i * kWarps + warp] = lb;
+            }
+        }
+        if (lane == 0) {
+            s_win_reached[warp] = reached;
+            s_win_first[warp] = w0;
+        }
+        __syncwarp();
+    };
+    auto next_row = [&](int r) {
+        for (;;) {
+            if (r >= n_rows) return n_rows;
+            if (r - s_win_first[warp] >= kRowWindow) load_window(r);
+            const int w0 = s_win_first[warp];
+            const uint64_t rest = s_win_reached[warp] >> (r - w0);
+            if (rest != 0) return r + __ffsll((long long)rest) - 1;
+            r = w0 + kRowWindow;
+        }
+    };
+    auto live_bits = [&](int r) -> uint64_t {
+        if (!warp_mask || occ.col == nullptr) return live_bits_global(r);
+        return s_win_live[(r - s_win_first[warp]) * kWarps + warp];
+    };
+    // prefetch: the first reached part of each position; pf_first (2 bits per
+    // position) says which
+    uint64_t pf_live = 0;
+    uint32_t pf_first = 0;
     const float2* pf_row = grids;
     auto load_row = [&](int r, float2 (&v)[16]) {
         pf_row = grids + (size_t)r * NN + (size_t)q * N;
         pf_live = live_bits(r);
+        pf_first = 0;
 #pragma unroll
         for (int t2 = 0; t2 < 16; ++t2) {
-            const int n = b + T * t2;
-            v[t2] = (pf_live >> t2) & 1u          ? __ldcs(pf_row + n)
-                    : (pf_live >> (16 + t2)) & 1u ? __ldcs(pf_row + n + H)
-                                                  : make_float2(0.f, 0.f);
+            int first = -1;
+#pragma unroll
+            for (int t = SPLIT - 1; t >= 0; --t)
+                if ((pf_live >> (16 * t + t2)) & 1u) first = t;
+            pf_first |= (uint32_t)(first < 0 ? 0 : first) << (2 * t2);
+            v[t2] = first >= 0 ? __ldcs(pf_row + b + T * t2 + first * M) : make_float2(0.f, 0.f);
         }
     };
-    // the prefetched values to y_par
-    auto combine = [&](float2 (&v)[16]) {
+    // y_r from the prefetched values (compile-time r)
+    auto combine_r = [&](float2 (&v)[16], auto rc) {
+        constexpr int R = decltype(rc)::value;
 #pragma unroll
         for (int t2 = 0; t2 < 16; ++t2) {
-            const bool lo = (pf_live >> t2) & 1u, hi = (pf_live >> (16 + t2)) & 1u;
+            const int first = (int)((pf_first >> (2 * t2)) & 3u);
+            // e^(2 pi i R first / SPLIT) times the prefetched part (zero if none)
+            const int k4 = (R * first * (4 / SPLIT)) & 3;   // quarter turns
             float2 y = v[t2];
-            if (lo && hi) {
-                const float2 u = __ldcs(pf_row + b + T * t2 + H);
-                y = par ? csub(y, u) : cadd(y, u);
-            } else if (hi && par) {
-                y = make_float2(-y.x, -y.y);
-            }
-            v[t2] = par ? twiddle_const<true>(cmulf(y, wb), t2, 32) : y;
+            y = k4 == 0 ? y : k4 == 1 ? mul_si<true>(y) : k4 == 2 ? make_float2(-y.x, -y.y) : mul_si<false>(y);
+#pragma unroll
+            for (int t = 1; t < SPLIT; ++t)
+                if (t != first && ((pf_live >> (16 * t + t2)) & 1u)) {
+                    const float2 u = __ldcs(pf_row + b + T * t2 + t * M);
+                    y = cadd(y, twiddle_const<true>(u, R * t, SPLIT));
+                }
+            if (0 != first && (pf_live >> t2) & 1u) y = cadd(y, __ldcs(pf_row + b + T * t2));
+            v[t2] = R == 0 ? y : twiddle64<true>(cmulf(y, wb), R * t2 * (4 / SPLIT));
         }
+    };
+    auto combine = [&](float2 (&v)[16]) {
+        if (par == 0) combine_r(v, std::integral_constant<int, 0>{});
+        else if (par == 1) combine_r(v, std::integral_constant<int, 1>{});
+        else if (SPLIT == 4 && par == 2) combine_r(v, std::integral_constant<int, 2>{});
+        else if (SPLIT == 4) combine_r(v, std::integral_constant<int, 3>{});
     };
     float2 a[16], x[16];
     int r = next_row(0);
@@ -689,13 +806,13 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                 }
             } else {
                 combine(a);
-                radix16_out<13, true>(a, b, 0, buf, tw);
+                radix16_out<LOG2SUB, true>(a, b, 0, buf, tw);
                 const int rn = next_row(r + 1);
                 if (rn < n_rows) load_row(rn, a);
                 r = rn;
                 __syncthreads();
-                middle_stages<13, true>(buf, b, tw);
-                last_stage<13, true>(buf, b, x);
+                middle_stages<LOG2SUB, true>(buf, b, tw);
+                last_stage<LOG2SUB, true>(buf, b, x);
                 __syncthreads();   // buf is rewritten by the next row's first stage
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -714,7 +831,7 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int k = b + T * j, p = 2 * k + par;
+                const int k = b + T * j, p = SPLIT * k + par;
                 const uint2 ph = __ldg(&turns[p]);
                 const uint32_t tk = ph.x + k_end * ph.y;
                 float sn, cs;
@@ -940,20 +1057,21 @@ cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* w
     return cudaGetLastError();
 }
 
-// N = 16384: two CTAs per image row, each with the 8192-point tables (they
+// N = 16384: four CTAs per image row, each with the 4096-point tables (they
 // follow the 16384-point tables in twid)
 template <bool CPLX>
 cudaError_t fused_split(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
                         const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
                         const Occupancy& occ, cudaStream_t st) {
-    using Sh = Shape<13>;
-    auto fn = k_rows_phase_reduce_split<CPLX>;
+    constexpr int kSub = 12, kSplit = 4;
+    using Sh = Shape<kSub>;
+    auto fn = k_rows_phase_reduce_split<kSub, kSplit, CPLX>;
     const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<2 * Shape<14>::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid + Shape<14>::kTw,
-                                               image_real, image_complex, occ);
+    fn<<<kSplit * Shape<14>::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid + Shape<14>::kTw,
+                                                    image_real, image_complex, occ);
     return cudaGetLastError();
 }
 
@@ -1015,10 +1133,10 @@ void append_twiddles(int N, std::vector<float2>& out) {
 }  // namespace
 
 void fft_twiddles(int N, std::vector<float2>& out) {
-    // N = 16384: the 8192-point tables of the split fused row pass follow
+    // N = 16384: the 4096-point tables of the split fused row pass follow
     out.clear();
     append_twiddles(N, out);
-    if (log2_exact(N) == 14) append_twiddles(N / 2, out);
+    if (log2_exact(N) == 14) append_twiddles(4096, out);
 }
 
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,

@@ -213,7 +213,15 @@ __device__ __forceinline__ void accumulate_range(const GridParams& G,
                 dx = -T;
                 dy = -T;
             }
-            const VisRecord rec = records[src];
+            VisRecord rec = records[src];
+            // RICK_DEBUG: the first footprint cell lies in the record's own tile
+            // (a corrupt record is dropped; the cell clipping below keeps every
+            // access inside the tile in any build)
+            if (!RICK_DCHECK((int)(rec.px >> kFracBits) < T && (int)(rec.py >> kFracBits) < T,
+                             kCheckRecordCell, G.status)) {
+                rec.wv_re = rec.wv_im = 0.f;
+                rec.px = rec.py = 0;
+            }
             const int i0 = (int)(rec.px >> kFracBits) + dx, j0 = (int)(rec.py >> kFracBits) + dy;
             stg4[lane] = make_float4((float)(rec.px & kFracMask) * kInvFrac,
                                      (float)(rec.py & kFracMask) * kInvFrac, rec.wv_re, rec.wv_im);
@@ -444,6 +452,10 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
         const uint32_t h = s_heavy;
         if (h >= nH) break;
         const uint32_t item = h < n1 ? G.lists[h] : G.lists[G.list_cap + (h - n1)];
+        if (!RICK_DCHECK(item < G.n_items, kCheckGridItem, G.status)) {   // uniform over the CTA
+            __syncthreads();   // everyone has read s_heavy before thread 0 rewrites it
+            continue;
+        }
         if (threadIdx.x < 8) s_hrng[threadIdx.x] = tile_bound(G, offsets, item, threadIdx.x);
         __syncthreads();
         uint32_t rng[8];

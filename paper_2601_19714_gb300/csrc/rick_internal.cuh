@@ -79,6 +79,20 @@ struct PlaceParams {
     float fov_i_f, half_i_f;
 };
 
+// Device-side consistency checks of the RICK_DEBUG build: a failed check
+// records its code in the plan's status word (the first failure wins), the
+// access it guards is skipped, and rick_plan_sync_status returns
+// RICK_ERR_INTERNAL.  No trap, no assert: the context stays usable.  The
+// normal build compiles the checks away.
+#ifdef RICK_DEBUG
+#define RICK_DCHECK(cond, code, status)                                      \
+    ((cond) ? true : ((status) != nullptr ? (atomicCAS((status), 0, (code)), false) : false))
+#else
+#define RICK_DCHECK(cond, code, status) true
+#endif
+constexpr int kCheckGridItem = 1;     // a gridder work item beyond the launch's tiles
+constexpr int kCheckRecordCell = 2;   // a record's first footprint cell outside its tile
+
 struct GridParams {
     int N, S, T, NT, Nw;  // Nw: stored planes (the bin keys' plane count)
     int c0, nc, k0, nk;
@@ -98,6 +112,7 @@ struct GridParams {
     // 1: tiles that no record reaches are not written (the zero fill is left
     // out); the planes are then only valid where tile_reach() > 0
     int skip_empty;
+    int* status;          // the plan's status word (RICK_DEBUG checks); may be null
     float coef[kMaxSupport][kPolyDegree + 1];
 };
 

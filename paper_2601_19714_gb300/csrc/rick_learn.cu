@@ -121,8 +121,18 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// The turns of u l for a source at pixel offset P = p - N/2 (any real p):
+// with P = Pi + Pf (Pi integer, 0 <= Pf < 1), (X + f)(Pi + Pf)/N is the exact
+// integer reduction of X Pi plus f Pi/N plus (X + f) Pf / N, each below half a
+// turn in magnitude.
+__device__ __forceinline__ float source_turns(int X, float P, float f, int N) {
+    const float Pi = floorf(P);
+    return cell_turns(X, (int)Pi, f, N) + ((float)X + f) * (P - Pi) / (float)N;
+}
+
 // V_j W_j for the field: sources src[s] = (P_s, Q_s, A_s / n_s, delta_s) with
-// P_s = p_s - N/2, Q_s = q_s - N/2 (pixel offsets from the centre).
+// P_s = p_s - N/2, Q_s = q_s - N/2 (pixel offsets from the centre; p_s, q_s
+// continuous positions in pixels).
 __global__ void k_learn_predict(const LearnVis* __restrict__ vis, LearnConst C,
                                 const float4* __restrict__ src, float2* __restrict__ wv) {
     __shared__ float4 s_src[kMaxSources];
@@ -135,8 +145,7 @@ __global__ void k_learn_predict(const LearnVis* __restrict__ vis, LearnConst C,
     float2 acc = make_float2(0.f, 0.f);
     for (int s = 0; s < C.ns; ++s) {
         const float4 q = s_src[s];
-        const float t = cell_turns(X, (int)q.x, v.fx, C.N) + cell_turns(Y, (int)q.y, v.fy, C.N) +
-                        v.w * q.w;
+        const float t = source_turns(X, q.x, v.fx, C.N) + source_turns(Y, q.y, v.fy, C.N) + v.w * q.w;
         const float2 e = turn_phasor(-t);  // Eq. 1: exp(-2 pi i (u l + v m + w (n - 1)))
         acc.x += q.z * e.x;
         acc.y += q.z * e.y;
@@ -573,8 +582,9 @@ rick_status rick_learn_field_grad(rick_learn* Lr, const float* table, const floa
     std::vector<int> pq(2 * np);
     std::vector<float2> ph((size_t)Nw * kMaxProbes, make_float2(0.f, 0.f));
     for (int s = 0; s < ns; ++s) {
-        const int p = (int)sources[3 * s], q = (int)sources[3 * s + 1];
-        if (p < 0 || p >= N || q < 0 || q >= N) return lfail(RICK_ERR_INVALID_ARG, "source outside the image");
+        const double p = sources[3 * s], q = sources[3 * s + 1];
+        if (!(p >= 0.0 && p < N && q >= 0.0 && q < N))
+            return lfail(RICK_ERR_INVALID_ARG, "source outside the image");
         const double l = (p - N / 2) * dl, m = (q - N / 2) * dl, r2 = l * l + m * m;
         const double n = std::sqrt(1.0 - r2);
         src[s] = make_float4((float)(p - N / 2), (float)(q - N / 2), (float)(sources[3 * s + 2] / n),

@@ -4,9 +4,9 @@ checkpoints.
 The network (3 -> H GELU -> H GELU -> 16 outputs) gives a correction to the
 support-4 Kaiser-Bessel taps.  It is trained on the GPU by the library's own
 kernels: ``rick_mlp_forward`` bakes the correction table on the lattice,
-``rick_learn_field_grad`` images a point-source field with Kaiser-Bessel taps
-plus that correction and measures it against the direct Fourier inversion at
-the source pixels, ``rick_mlp_backward`` carries the table gradient into the
+``rick_learn_field_grad`` images a point-source field (sources at continuous
+positions) with Kaiser-Bessel taps plus that correction and measures it
+against the direct Fourier inversion at probe pixels spread over the field, ``rick_mlp_backward`` carries the table gradient into the
 network and ``rick_adam_step`` updates it.  This module only orders those
 calls, draws the seeded fields, and saves/resumes the state (parameters, Adam
 moments, step).
@@ -42,13 +42,44 @@ def init_params(hidden: int, seed: int, zero_output: bool = True) -> np.ndarray:
 
 def training_field(seed: int, N: int, margin: int = 4, n_range=(1, 50),
                    flux=(0.01, 1.0)) -> np.ndarray:
-    """A point-source field: 1-50 sources on pixel centres anywhere in the
-    image (margin pixels from the edge), fluxes log-uniform.  [ns, 3] (p, q, A)."""
+    """A point-source field: 1-50 sources at continuous positions anywhere in
+    the image (margin pixels from the edge; positions in pixels, rounded to
+    float32, which the library takes), fluxes log-uniform.  [ns, 3] (p, q, A)."""
     g = np.random.Generator(np.random.Philox(key=[seed, 0x46494C44]))
     ns = int(g.integers(n_range[0], n_range[1] + 1))
-    pq = g.integers(margin, N - margin, size=(ns, 2))
+    pq = margin + g.random((ns, 2)) * (N - 2 * margin)
+    pq = pq.astype(np.float32).astype(np.float64)
     a = np.exp(math.log(flux[0]) + g.random(ns) * (math.log(flux[1]) - math.log(flux[0])))
-    return np.concatenate([pq.astype(np.float64), a[:, None]], axis=1)
+    return np.concatenate([pq, a[:, None]], axis=1)
+
+
+def field_probes(seed: int, N: int, src: np.ndarray, count: int = 64, margin: int = 4) -> np.ndarray:
+    """The pixels a field is judged at: the pixel nearest each of its brightest
+    sources (at most count // 4), the four corners and four edge midpoints
+    (margin pixels in), and seeded pixels anywhere in the image for the rest,
+    so that the objective sees the kernel's error over the whole field, where
+    its aliasing is largest near the edges.  [count, 2] int32 (p, q)."""
+    g = np.random.Generator(np.random.Philox(key=[seed, 0x50524F42]))
+    order = np.argsort(-src[:, 2])[: count // 4]
+    near = np.clip(np.rint(src[order, :2]), 0, N - 1).astype(np.int64)
+    e, h = margin, N // 2
+    fixed = np.array([(e, e), (N - 1 - e, e), (e, N - 1 - e), (N - 1 - e, N - 1 - e),
+                      (h, e), (h, N - 1 - e), (e, h), (N - 1 - e, h)], dtype=np.int64)
+    rest = g.integers(margin, N - margin, size=(count - len(near) - len(fixed), 2))
+    return np.concatenate([near, fixed, rest]).astype(np.int32)
+
+
+def heldout_losses(learn: rick.Learn, table, n: int, seed0: int, loss, per_field: bool = False):
+    """Loss of n held-out fields imaged with `table` (mean and median, or the
+    losses themselves)."""
+    out = []
+    for s in range(n):
+        src = training_field(seed0 + s, learn.cfg.N)
+        learn.field_grad(table, src, field_probes(seed0 + s, learn.cfg.N, src), None, loss)
+        out.append(float(loss.item()))
+    if per_field:
+        return np.array(out)
+    return float(np.mean(out)), float(np.median(out))
 
 
 @dataclass
@@ -105,8 +136,9 @@ class LearnedKernel:
             self.bake()
             total = 0.0
             for b in range(batch):
-                src = training_field(field_seed0 + self.state.step, N)
-                learn.field_grad(self.table, src, src[:, :2].astype(np.int32), self.table_grad,
+                seed = field_seed0 + self.state.step
+                src = training_field(seed, N)
+                learn.field_grad(self.table, src, field_probes(seed, N, src), self.table_grad,
                                  self.loss, accumulate=b > 0, grad_scale=1.0 / batch)
                 self.state.step += 1
                 if log_every:
@@ -121,12 +153,12 @@ class LearnedKernel:
     def heldout_loss(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000):
         """Mean and median loss over n held-out fields (seeds never trained on)."""
         self.bake()
-        out = []
-        for s in range(n):
-            src = training_field(seed0 + s, learn.cfg.N)
-            learn.field_grad(self.table, src, src[:, :2].astype(np.int32), None, self.loss)
-            out.append(float(self.loss.item()))
-        return float(np.mean(out)), float(np.median(out))
+        return heldout_losses(learn, self.table, n, seed0, self.loss)
+
+    def losses(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000) -> np.ndarray:
+        """The loss of each of n held-out fields (seeds never trained on)."""
+        self.bake()
+        return heldout_losses(learn, self.table, n, seed0, self.loss, per_field=True)
 
     # ---- checkpoint / resume ------------------------------------------------
     def save(self, path: str):

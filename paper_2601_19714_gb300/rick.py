@@ -40,7 +40,10 @@ EXPORTS = ["rick_plan_create", "rick_plan_destroy", "rick_plan_reserve", "rick_p
            "rick_learn_destroy", "rick_learn_placed", "rick_learn_field_grad",
            "rick_status_string", "rick_last_error", "rick_stored_planes", "rick_bin_predict",
            "rick_model_to_wplanes", "rick_fft_wplanes_forward", "rick_model_fft_wplanes", "rick_degrid_binned",
-           "rick_predict", "rick_plan_fft_impl", "rick_plan_schedule_counts"]
+           "rick_predict", "rick_plan_fft_impl", "rick_plan_schedule_counts", "rick_debug_inject",
+           "rick_debug_build", "rick_debug_poke_record"]
+
+INJECT_SITES = {"none": 0, "device_alloc": 1, "cufft_plan": 2, "launch": 3}
 
 
 class RickError(RuntimeError):
@@ -74,6 +77,18 @@ def load(path: str = LIB_PATH):
     global _lib
     if _lib is not None:
         return _lib
+    _lib = _open(path)
+    return _lib
+
+
+def load_debug():
+    """The RICK_DEBUG build of the library (built on first use), with the same
+    signatures; a separate library with its own state."""
+    from . import _build
+    return _open(_build.build(debug=True))
+
+
+def _open(path: str):
     if not os.path.exists(path):
         raise ImportError(f"librick.so not built ({path}); run __graft_entry__.build()")
     L = C.CDLL(path)
@@ -111,6 +126,8 @@ def load(path: str = LIB_PATH):
         "rick_degrid_binned": [p, p, i32, i32, i32, i32, p, p],
         "rick_predict": [p, p, p, p, p, i64, p, p, p, p],
         "rick_plan_schedule_counts": [p, p],
+        "rick_debug_inject": [i32, i32],
+        "rick_debug_poke_record": [p, i64, i32, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -143,8 +160,16 @@ def load(path: str = LIB_PATH):
     L.rick_last_error.restype = C.c_char_p
     L.rick_stored_planes.argtypes = [C.POINTER(rick_config)]
     L.rick_stored_planes.restype = i32
-    _lib = L
+    L.rick_debug_build.argtypes = []
+    L.rick_debug_build.restype = i32
     return L
+
+
+def inject(site: str, countdown: int = 1):
+    """Arm one injected failure (see rick_debug_inject): the countdown-th
+    event of `site` ("device_alloc", "cufft_plan", "launch") fails once;
+    inject("none") disarms."""
+    _check(load().rick_debug_inject(INJECT_SITES[site], int(countdown)), "rick_debug_inject")
 
 
 def _check(status: int, where: str):

@@ -180,3 +180,16 @@ def test_fft_impl_values(lib):
     h = C.c_void_p(123)
     assert lib.rick_plan_create(C.byref(cfg), C.byref(h)) == 1
     assert b"fft_impl" in lib.rick_last_error()
+
+
+def test_fault_injection_hook_arguments(lib):
+    """rick_debug_inject arms and disarms on the host (what a failure does is
+    checked on a GPU); the normal build is not a debug build and has no
+    record poke."""
+    assert lib.rick_debug_inject(1, 3) == 0
+    assert lib.rick_debug_inject(0, 0) == 0
+    assert lib.rick_debug_inject(9, 1) == 1
+    assert b"injection site" in lib.rick_last_error()
+    assert lib.rick_debug_inject(1, -1) == 1
+    assert lib.rick_debug_build() == 0
+    assert lib.rick_debug_poke_record(None, 0, 0, 0) == 6

@@ -52,3 +52,18 @@ def test_stage_traffic_and_flops_by_hand():
     assert f["rows_phase"] == 5 * N * 5 * N * 10 + 8 * 5 * N * N
     full = bench.stage_traffic(N, C, P, nrow=100, n_grid=150, T=T, reach=reach, own=False)
     assert full["fft"] == 16 * C * P * N * N and full["grid"] == 8 * C * P * N * N + 16 * 150
+
+
+def test_large_blocks_cover_each_ranks_channels_once():
+    """The default workload's channel blocks: rank r of N takes channels
+    [128 r, 128 r + 128) of the band split into 128 N, in 8 blocks of 16; over
+    all ranks every channel of the band is taken exactly once."""
+    for world in (1, 2, 4, 8):
+        seen = []
+        for r in range(world):
+            blk = bench.large_blocks(world, r)
+            assert len(blk) == 8 and all(c1 - c0 == 16 for c0, c1 in blk)
+            assert blk[0][0] == 128 * r
+            for c0, c1 in blk:
+                seen.extend(range(c0, c1))
+        assert seen == list(range(128 * world))

@@ -385,7 +385,7 @@ def test_invalid_arguments_are_rejected(rk):
 
 def test_launch_count_is_tracked(rk):
     img, obs = tiny_wstack(20, nvis=1000, N=128)
-    plan = rk.Plan(plan_config(img, 1))
+    plan = rk.Plan(plan_config(img, 1, fft_impl="cufft"))
     n0 = plan.launch_count()
     run_path(plan, to_device(obs), 1, img.N, img.Nw)
     # place, 3 scan kernels, scatter, tile schedule, grid, phase
