@@ -1181,7 +1181,7 @@ def run_learned(args):
     before = k.heldout_loss(learn, 64)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    k.train(learn, 10_000 // 64, lr=1e-6, batch=64)
+    k.train(learn, 10_000 // 16, lr=3e-5, batch=16)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     after = k.heldout_loss(learn, 64)
@@ -1241,8 +1241,8 @@ def run_learned(args):
         "config": {"workload": "learned_2048sq_16w_2Mvis", "N": N, "w_planes": Nw,
                    "visibilities": int(obs.nrow), "hidden": H, "lattice": L},
         "kernels": out,
-        "training": {"fields": (10_000 // 64) * 64, "seconds": train_s,
-                     "fields_per_s": (10_000 // 64) * 64 / train_s,
+        "training": {"fields": (10_000 // 16) * 16, "seconds": train_s,
+                     "fields_per_s": (10_000 // 16) * 16 / train_s,
                      "heldout_loss_kaiser_bessel_s4": before, "heldout_loss_trained": after}}),
           flush=True)
 

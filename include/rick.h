@@ -153,9 +153,10 @@ typedef struct rick_config {
     double w_kernel_param;
     /* 2-D DFT of the w-planes, rick_fft_impl: RICK_FFT_OWN (0, the default) =
      * the library's own two-pass transform (columns, then rows; the imaging
-     * path fuses the row pass with the phase screen and reduction) on an
-     * unpadded power-of-two mesh 256 <= N <= 16384, cuFFT on any other mesh;
-     * RICK_FFT_CUFFT (1) = cuFFT, batched (fft_batch planes per execution). */
+     * path fuses the row pass with the phase screen and reduction) on a
+     * power-of-two mesh 256 <= Ng <= 16384 (padded or not), cuFFT on any other
+     * mesh; RICK_FFT_CUFFT (1) = cuFFT, batched (fft_batch planes per
+     * execution). */
     int32_t fft_impl;
     int32_t weighting;    /* rick_weighting (0 = natural); imaging only, prediction ignores it */
     double robust;        /* Briggs robustness R (weighting = RICK_WEIGHT_BRIGGS) */
@@ -558,9 +559,8 @@ rick_status rick_plan_sync_status(rick_plan* plan);
 /* Number of this library's kernels the plan has launched so far. */
 int64_t rick_plan_launch_count(const rick_plan* plan);
 
-/* The 2-D DFT the plan runs: RICK_FFT_OWN (unpadded power-of-two mesh
- * 256 <= N <= 16384 with fft_impl = RICK_FFT_OWN) or RICK_FFT_CUFFT; -1 if
- * plan is NULL. */
+/* The 2-D DFT the plan runs: RICK_FFT_OWN (power-of-two mesh 256 <= Ng <=
+ * 16384 with fft_impl = RICK_FFT_OWN) or RICK_FFT_CUFFT; -1 if plan is NULL. */
 int32_t rick_plan_fft_impl(const rick_plan* plan);
 
 /* The lengths of the gridder's three longest-first tile lists in the plan's

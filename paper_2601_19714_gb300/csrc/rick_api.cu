@@ -202,6 +202,8 @@ struct rick_plan {
     uint32_t* d_counter = nullptr;   // gridder queues and list lengths (8 words)
     uint32_t* d_lists = nullptr;     // longest-first tile lists, 3 x list_cap
     uint32_t list_cap = 0;
+    uint32_t* d_light = nullptr;     // sparse gridding: the other reached tiles (one per tile of the plan)
+    uint32_t light_cap = 0;
     unsigned long long* d_counts = nullptr;
     int* d_status = nullptr;
     double* d_wsum = nullptr;
@@ -232,7 +234,7 @@ struct rick_plan {
     double* d_wmom = nullptr;
     float* d_wbuf = nullptr;
     int64_t cap_w = 0;
-    // the library's own 2-D DFT (RICK_FFT_OWN, unpadded 256 <= N <= 16384): twiddle tables
+    // the library's own 2-D DFT (RICK_FFT_OWN, mesh 256 <= Ng <= 16384): twiddle tables
     bool own_fft = false;
     float2* d_twid = nullptr;
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
@@ -279,6 +281,7 @@ void release(rick_plan* P) {
     dfree(P->d_partials);
     dfree(P->d_counter);
     dfree(P->d_lists);
+    dfree(P->d_light);
     dfree(P->d_counts);
     dfree(P->d_status);
     dfree(P->d_wsum);
@@ -520,10 +523,10 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(dmalloc(&P->d_wmom, sizeof(double) * 2 * c.n_channels));
     }
 
-    P->own_fft = c.fft_impl == RICK_FFT_OWN && fft_supported(c.N) && P->Ng == c.N;
+    P->own_fft = c.fft_impl == RICK_FFT_OWN && fft_supported(P->Ng);
     if (P->own_fft) {
         std::vector<float2> tw;
-        fft_twiddles(c.N, tw);
+        fft_twiddles(P->Ng, tw);   // the transforms run on the mesh
         RK_CUDA(dmalloc(&P->d_twid, sizeof(float2) * tw.size()));
         RK_CUDA(cudaMemcpy(P->d_twid, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
         RK_CUDA(dmalloc(&P->d_colocc, (size_t)c.n_channels * P->planes * P->NT));
@@ -531,6 +534,9 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(dmalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
                                               ((P->NT + 31) / 32)));
         const size_t NN = (size_t)c.N * c.N;
+        // the sparse gridder's list of light tiles: room for every tile of the plan
+        P->light_cap = (uint32_t)(P->nkeys / 4);
+        RK_CUDA(dmalloc(&P->d_light, sizeof(uint32_t) * (size_t)P->light_cap));
         RK_CUDA(dmalloc(&P->d_pix_turns, sizeof(uint2) * NN));
         RK_CUDA(dmalloc(&P->d_pix_scale, sizeof(float) * NN));
         RK_CUDA(dmalloc(&P->d_pix_model_scale, sizeof(float) * NN));
@@ -742,6 +748,7 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     const uint64_t items = (uint64_t)(c1 - c0) * (k1 - k0) * (uint64_t)P->NT * P->NT;
     RK_ARG(items < 0xFFFFFFFFull, "too many tiles in one call");
     GridParams G;
+    std::memset(&G, 0, sizeof G);
     G.N = P->Ng;
     G.S = c.support;
     G.T = P->T;
@@ -761,6 +768,10 @@ rick_status grid_impl(rick_plan* P, int c0, int c1, int k0, int k1, float* grids
     G.list_cap = P->list_cap;
     G.w_support = 0;
     G.skip_empty = sparse ? 1 : 0;
+    if (sparse && P->d_light) {
+        G.light = P->d_light;
+        G.light_cap = P->light_cap;
+    }
     G.status = P->d_status;
     P->last_stream = st;
     RK_CUDA(cudaMemsetAsync(P->d_counter, 0, 8 * sizeof(uint32_t), st));
@@ -906,7 +917,7 @@ rick_status columns_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int
                          cudaStream_t st) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
-        set_err("the column pass needs the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
+        set_err("the column pass needs the library's own transform (RICK_FFT_OWN, a mesh of 256 to 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -934,7 +945,7 @@ rick_status rows_phase_impl(rick_plan* P, const float* grids, int c0, int c1, in
                             int32_t flags, cudaStream_t st, bool occ_ready = false) {
     const rick_config& c = P->cfg;
     if (!P->own_fft) {
-        set_err("the fused row pass needs the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
+        set_err("the fused row pass needs the library's own transform (RICK_FFT_OWN, a mesh of 256 to 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     RK_ARG(0 <= c0 && c0 < c1 && c1 <= c.n_channels, "channel range");
@@ -1005,7 +1016,7 @@ rick_status model_fft_impl(rick_plan* P, const float* image, int c0, int c1, int
                            int32_t flags, cudaStream_t st) {
     const rick_config& c = P->cfg;
     if (!P->own_fft || !fft_fused_model_supported(P->Ng)) {
-        set_err("the fused model pass needs the library's own transform on an unpadded 256 <= N <= 8192 "
+        set_err("the fused model pass needs the library's own transform on a mesh of 256 to 8192 "
                 "(RICK_FFT_OWN); use rick_model_to_wplanes + rick_fft_wplanes_forward");
         return RICK_ERR_UNSUPPORTED;
     }
@@ -1265,7 +1276,7 @@ rick_status rick_grid_binned_sparse(rick_plan* plan, int32_t chan_begin, int32_t
                                     int32_t plane_begin, int32_t plane_end, float* grids, void* stream) {
     RK_ARG(plan != nullptr, "plan is NULL");
     if (!plan->own_fft) {
-        set_err("sparse gridding is only read by the library's own transform (RICK_FFT_OWN, unpadded 256 <= N <= 16384)");
+        set_err("sparse gridding is only read by the library's own transform (RICK_FFT_OWN, a mesh of 256 to 16384)");
         return RICK_ERR_UNSUPPORTED;
     }
     return grid_impl(plan, chan_begin, chan_end, plane_begin, plane_end, grids, as_stream(stream), true);

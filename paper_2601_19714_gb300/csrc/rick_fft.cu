@@ -438,7 +438,7 @@ __device__ __forceinline__ uint32_t turns_q32f(float t) {
 // P describes stored plane 0 (w_first = its w).
 __global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper, uint2* __restrict__ turns,
                               float* __restrict__ scale, float* __restrict__ model_scale) {
-    const int N = P.N, halfN = N / 2;
+    const int N = P.Ni, halfN = N / 2;   // image pixels (the central Ni x Ni of a padded mesh)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * N) return;
     const int q = (int)(i / N), p = (int)(i - (int64_t)q * N);
@@ -482,9 +482,8 @@ __global__ void k_pixel_phase(PhaseParams P, const float* __restrict__ inv_taper
 // The next row is loaded into registers while the current one is transformed.
 // Two CTAs per SM for N <= 4096 (at most 128 registers).
 constexpr int kHornerBlock = 8;   // planes per Horner block of the fused row pass
-constexpr int kRowWindow = 64;    // rows (planes) whose occupancy a split row pass caches at once
 
-template <int LOG2N, bool COMPLEX_OUT>
+template <int LOG2N, bool COMPLEX_OUT, bool PADDED>
 __global__ void __launch_bounds__((1 << LOG2N) / 16, LOG2N <= 12 ? 2 : 1)
 k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                     const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
@@ -498,20 +497,25 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     float2* zrot = buf + Sh::kArray;                             // z = e^(-2 pi i dt) per pixel
     // the channel's finished blocks per pixel: Re of the phased sums
     float* part = reinterpret_cast<float*>(zrot + N);
+    // image row q (blockIdx.x) is row q + off of the mesh; mesh pixel pm is
+    // image pixel pm - off (a padded mesh keeps its central Ni x Ni; without
+    // padding, off = 0 and Ni = N at compile time)
+    const int Ni = PADDED ? P.Ni : N, off = PADDED ? P.off : 0;
     const int b = threadIdx.x, q = blockIdx.x;
-    const float* scl = pix_scale + (size_t)q * N;                // per-pixel scale (read once per channel)
-    const uint2* turns = pix_turns + (size_t)q * N;
+    const float* scl = pix_scale + (size_t)q * Ni;               // per-pixel scale (read once per channel)
+    const uint2* turns = pix_turns + (size_t)q * Ni;
     load_tables<LOG2N>(twid, tw, b, T);
 #pragma unroll 4
     for (int j = 0; j < 16; ++j) {
-        const int p = b + T * j;
-        float s, c;
-        sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
-        zrot[p] = make_float2(c, -s);
-        if (!COMPLEX_OUT) part[p] = 0.f;
+        const int pm = b + T * j, p = pm - off;
+        float s = 0.f, c = 1.f;
+        if (!PADDED || (unsigned)p < (unsigned)Ni)
+            sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
+        zrot[pm] = make_float2(c, -s);
+        if (!COMPLEX_OUT) part[pm] = 0.f;
     }
 
-    const size_t NN = (size_t)N * N;
+    const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
     const int n_rows = P.nc * P.nk;
     // planes no visibility reached are not transformed
     auto next_row = [&](int r) {
@@ -526,7 +530,7 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     // mask bytes and a ballot hands every lane the 16 bits.
     const bool warp_mask = occ.tshift >= 5 && T >= 32;
     auto load_row = [&](int r, float2 (&v)[16]) {
-        const float2* row = grids + (size_t)r * NN + (size_t)q * N;
+        const float2* row = grids + (size_t)r * NN + (size_t)(q + off) * N;
         if (occ.col != nullptr) {
             const uint8_t* cm = occ.col + (size_t)r * occ.NT;
             uint32_t live = 0;
@@ -590,28 +594,36 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int p = b + T * j;
-                const uint2 ph = __ldg(&turns[p]);
+                // pixels outside the image (a padded mesh) are computed from a
+                // valid index and not stored, so that every load is unconditional
+                const int pm = b + T * j, p = pm - off;
+                const bool in_img = !PADDED || (unsigned)p < (unsigned)Ni;
+                const int pc = in_img ? p : 0;
+                const uint2 ph = __ldg(&turns[pc]);
                 const uint32_t tk = ph.x + k_end * ph.y;
                 float sn, cs;
                 sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
                 const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
                 const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
                 acc[j] = make_float2(0.f, 0.f);
-                float* ir = image_real + (size_t)cc * NN + (size_t)q * N + p;
+                float* ir = image_real + (size_t)cc * NNi + (size_t)q * Ni + pc;
                 if (COMPLEX_OUT) {
-                    const float s = __ldg(scl + p) * inv_ws;
-                    *ir += s * re;
-                    float2* ic = image_complex + (size_t)cc * NN + (size_t)q * N + p;
+                    const float s = __ldg(scl + pc) * inv_ws;
+                    float2* ic = image_complex + (size_t)cc * NNi + (size_t)q * Ni + pc;
+                    const float r0 = *ir;
                     float2 v = *ic;
                     v.x += s * re;
                     v.y += s * im;
-                    *ic = v;
+                    if (in_img) {
+                        *ir = r0 + s * re;
+                        *ic = v;
+                    }
                 } else if (!last) {
-                    part[p] += re;
+                    part[pm] += re;
                 } else {
-                    *ir += __ldg(scl + p) * inv_ws * (part[p] + re);
-                    part[p] = 0.f;
+                    const float out = *ir + __ldg(scl + pc) * inv_ws * (part[pm] + re);
+                    if (in_img) *ir = out;
+                    part[pm] = 0.f;
                 }
             }
         }
@@ -636,7 +648,7 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 // other reached parts of the same position (none on a centred uv coverage
 // narrower than M) are read when the row is consumed.  Pruning also cuts the
 // arithmetic: N log2(M) butterfly work per row instead of N log2(N).
-template <int LOG2SUB, int SPLIT, bool COMPLEX_OUT>
+template <int LOG2SUB, int SPLIT, bool COMPLEX_OUT, bool PADDED>
 __global__ void __launch_bounds__((1 << LOG2SUB) / 16, LOG2SUB <= 12 ? 2 : 1)
 k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
                           const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
@@ -651,16 +663,20 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     float2* buf = fsm + Sh::kTw;
     float2* zrot = buf + Sh::kArray;                             // z per owned pixel
     float* part = reinterpret_cast<float*>(zrot + M);
+    // image row q is mesh row q + off; mesh pixel SPLIT k + r is image pixel
+    // SPLIT k + r - off (a padded mesh keeps its central Ni x Ni; without
+    // padding, off = 0 and Ni = N at compile time)
+    const int Ni = PADDED ? P.Ni : N, off = PADDED ? P.off : 0;
     const int b = threadIdx.x, q = blockIdx.x / SPLIT, par = blockIdx.x % SPLIT;
-    const float* scl = pix_scale + (size_t)q * N;
-    const uint2* turns = pix_turns + (size_t)q * N;
+    const float* scl = pix_scale + (size_t)q * Ni;
+    const uint2* turns = pix_turns + (size_t)q * Ni;
     load_tables<LOG2SUB>(twid_sub, tw, b, T);
 #pragma unroll 4
     for (int j = 0; j < 16; ++j) {
-        const int k = b + T * j;
-        float s, c;
-        sincospif((float)(int32_t)__ldg(&turns[SPLIT * k + par].y) * 4.656612873077392578125e-10f /* 2^-31 */,
-                  &s, &c);
+        const int k = b + T * j, p = SPLIT * k + par - off;
+        float s = 0.f, c = 1.f;
+        if (!PADDED || (unsigned)p < (unsigned)Ni)
+            sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
         zrot[k] = make_float2(c, -s);
         if (!COMPLEX_OUT) part[k] = 0.f;
     }
@@ -672,15 +688,15 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
         wb = make_float2((float)cd, (float)sd);
     }
 
-    const size_t NN = (size_t)N * N;
+    const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
     const int n_rows = P.nc * P.nk;
     // liveness of the inputs b + T t2 + t M of row (plane) r: bit 16 t + t2.
     // With tiles of at least 32 columns (T >= 32) every warp reads one tile
     // column per (t, t2): lane (t2 = lane % 16, t = lane / 16 + 2 h) reads one
     // mask byte and ballots hand every lane the bits
     const bool warp_mask = occ.tshift >= 5 && T >= 32;
-    const int lane = b & 31, warp = b >> 5;
-    auto live_bits_global = [&](int r) -> uint64_t {
+    const int lane = b & 31;
+    auto live_bits = [&](int r) -> uint64_t {
         if (occ.col == nullptr) return ~0ull >> (64 - 16 * SPLIT);
         const uint8_t* cm = occ.col + (size_t)r * occ.NT;
         uint64_t live = 0;
@@ -699,50 +715,10 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                 live |= (uint64_t)(__ldg(cm + ((b + T * t2 + t * M) >> occ.tshift)) != 0 ? 1u : 0u) << (16 * t + t2);
         return live;
     };
-    // The occupancy of the launch's rows, read a window of kRowWindow rows at
-    // a time by every warp for itself (all loads of a window in flight
-    // together): which rows are reached, and this warp's liveness bits of each
-    // (warp-uniform with warp_mask), so that stepping to the next row costs no
-    // dependent global load.  Each warp reads and writes only its own slots.
-    constexpr int kWarps = T / 32;
-    __shared__ uint64_t s_win_live[kRowWindow * (kWarps > 0 ? kWarps : 1)];
-    __shared__ uint64_t s_win_reached[kWarps > 0 ? kWarps : 1];
-    __shared__ int s_win_first[kWarps > 0 ? kWarps : 1];
-    if (lane == 0) s_win_first[warp] = -kRowWindow;
-    __syncwarp();
-    auto load_window = [&](int w0) {
-        const bool f0 = w0 + lane < n_rows && (occ.plane == nullptr || occ.plane[w0 + lane] != 0);
-        const bool f1 = w0 + 32 + lane < n_rows && (occ.plane == nullptr || occ.plane[w0 + 32 + lane] != 0);
-        const uint64_t reached = (uint64_t)__ballot_sync(0xffffffffu, f0) |
-                                 ((uint64_t)__ballot_sync(0xffffffffu, f1) << 32);
-        if (warp_mask) {
-#pragma unroll 8
-            for (int i = 0; i < kRowWindow; ++i) {
-                // every row of the launch has a mask (zero where unreached), so
-                // the loads of a window need no reached test and go out together
-                const uint64_t lb = w0 + i < n_rows ? live_bits_global(w0 + i) : 0;
-                if (lane == 0) s_win_live[i * kWarps + warp] = lb;
-            }
-        }
-        if (lane == 0) {
-            s_win_reached[warp] = reached;
-            s_win_first[warp] = w0;
-        }
-        __syncwarp();
-    };
     auto next_row = [&](int r) {
-        for (;;) {
-            if (r >= n_rows) return n_rows;
-            if (r - s_win_first[warp] >= kRowWindow) load_window(r);
-            const int w0 = s_win_first[warp];
-            const uint64_t rest = s_win_reached[warp] >> (r - w0);
-            if (rest != 0) return r + __ffsll((long long)rest) - 1;
-            r = w0 + kRowWindow;
-        }
-    };
-    auto live_bits = [&](int r) -> uint64_t {
-        if (!warp_mask || occ.col == nullptr) return live_bits_global(r);
-        return s_win_live[(r - s_win_first[warp]) * kWarps + warp];
+        if (occ.plane != nullptr)
+            while (r < n_rows && occ.plane[r] == 0) ++r;
+        return r;
     };
     // prefetch: the first reached part of each position; pf_first (2 bits per
     // position) says which
@@ -750,7 +726,7 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     uint32_t pf_first = 0;
     const float2* pf_row = grids;
     auto load_row = [&](int r, float2 (&v)[16]) {
-        pf_row = grids + (size_t)r * NN + (size_t)q * N;
+        pf_row = grids + (size_t)r * NN + (size_t)(q + off) * N;
         pf_live = live_bits(r);
         pf_first = 0;
 #pragma unroll
@@ -831,27 +807,35 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
             }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int k = b + T * j, p = SPLIT * k + par;
-                const uint2 ph = __ldg(&turns[p]);
+                // pixels outside the image (a padded mesh) are computed from a
+                // valid index and not stored, so that every load is unconditional
+                const int k = b + T * j, p = SPLIT * k + par - off;
+                const bool in_img = !PADDED || (unsigned)p < (unsigned)Ni;
+                const int pc = in_img ? p : 0;
+                const uint2 ph = __ldg(&turns[pc]);
                 const uint32_t tk = ph.x + k_end * ph.y;
                 float sn, cs;
                 sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
                 const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
                 const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
                 acc[j] = make_float2(0.f, 0.f);
-                float* ir = image_real + (size_t)cc * NN + (size_t)q * N + p;
+                float* ir = image_real + (size_t)cc * NNi + (size_t)q * Ni + pc;
                 if (COMPLEX_OUT) {
-                    const float s = __ldg(scl + p) * inv_ws;
-                    *ir += s * re;
-                    float2* ic = image_complex + (size_t)cc * NN + (size_t)q * N + p;
+                    const float s = __ldg(scl + pc) * inv_ws;
+                    float2* ic = image_complex + (size_t)cc * NNi + (size_t)q * Ni + pc;
+                    const float r0 = *ir;
                     float2 v = *ic;
                     v.x += s * re;
                     v.y += s * im;
-                    *ic = v;
+                    if (in_img) {
+                        *ir = r0 + s * re;
+                        *ic = v;
+                    }
                 } else if (!last) {
                     part[k] += re;
                 } else {
-                    *ir += __ldg(scl + p) * inv_ws * (part[k] + re);
+                    const float out = *ir + __ldg(scl + pc) * inv_ws * (part[k] + re);
+                    if (in_img) *ir = out;
                     part[k] = 0.f;
                 }
             }
@@ -885,27 +869,61 @@ k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __rest
     float2* buf = fsm + Sh::kTw;
     float2* zrot = buf + Sh::kArray;                            // z = e^(-2 pi i dt) per pixel
     float* js = reinterpret_cast<float*>(zrot + N);             // J_c(p) times the pixel's scale
-    const int b = threadIdx.x, q = blockIdx.x;
-    const uint2* turns = pix_turns + (size_t)q * N;
+    // mesh row q (blockIdx.x) is image row q - off and mesh pixel pm image
+    // pixel pm - off (a padded mesh holds the image in its central Ni x Ni;
+    // the model is zero elsewhere)
+    const int Ni = P.Ni, off = P.off;
+    const int b = threadIdx.x, q = blockIdx.x, qi = q - off;
+    const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
+    const bool warp_mask = occ.tshift >= 5 && T >= 32;
+    const int lane = b & 31;
+    // the tile columns of plane r that the column pass reads
+    auto live_cols = [&](int r) -> uint32_t {
+        uint32_t live = 0xffffu;
+        if (occ.col != nullptr) {
+            const uint8_t* cm = occ.col + (size_t)r * occ.NT;
+            if (warp_mask) {
+                const bool on = lane < 16 && __ldg(cm + (((b & ~31) + T * lane) >> occ.tshift)) != 0;
+                live = __ballot_sync(0xffffffffu, on);
+            } else {
+                live = 0;
+#pragma unroll
+                for (int t2 = 0; t2 < 16; ++t2)
+                    live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
+            }
+        }
+        return live;
+    };
+    if ((unsigned)qi >= (unsigned)Ni) {
+        // a row of the padding: its transform is zero, written where it is read
+        for (int r = 0; r < P.nc * P.nk; ++r) {
+            if (occ.plane != nullptr && occ.plane[r] == 0) continue;
+            const uint32_t live = live_cols(r);
+            float2* row = grids + (size_t)r * NN + (size_t)q * N;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if ((live >> j) & 1u) __stcs(row + b + T * j, make_float2(0.f, 0.f));
+        }
+        return;
+    }
+    const uint2* turns = pix_turns + (size_t)qi * Ni;
     load_tables<LOG2N>(twid, tw, b, T);
 #pragma unroll 4
     for (int t2 = 0; t2 < 16; ++t2) {
-        const int p = b + T * t2;
-        float s, c;
-        sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
-        zrot[p] = make_float2(c, -s);
+        const int pm = b + T * t2, p = pm - off;
+        float s = 0.f, c = 1.f;
+        if ((unsigned)p < (unsigned)Ni)
+            sincospif((float)(int32_t)__ldg(&turns[p].y) * 4.656612873077392578125e-10f /* 2^-31 */, &s, &c);
+        zrot[pm] = make_float2(c, -s);
     }
-    const size_t NN = (size_t)N * N;
-    const bool warp_mask = occ.tshift >= 5 && T >= 32;
-    const int lane = b & 31;
     for (int cc = 0; cc < P.nc; ++cc) {
-        const float* jr = image + (size_t)cc * NN + (size_t)q * N;
-        const float* ms = pix_model_scale + (size_t)q * N;
+        const float* jr = image + (size_t)cc * NNi + (size_t)qi * Ni;
+        const float* ms = pix_model_scale + (size_t)qi * Ni;
         __syncthreads();   // the previous channel's js reads are done
 #pragma unroll 4
         for (int t2 = 0; t2 < 16; ++t2) {
-            const int p = b + T * t2;
-            js[p] = __ldg(jr + p) * __ldg(ms + p);
+            const int pm = b + T * t2, p = pm - off;
+            js[pm] = (unsigned)p < (unsigned)Ni ? __ldg(jr + p) * __ldg(ms + p) : 0.f;
         }
         // ph holds the phase of plane kcur; it is formed exactly at the first
         // plane of each block of kHornerBlock planes and advanced plane by plane
@@ -922,7 +940,8 @@ k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __rest
                 const uint32_t k = (uint32_t)(P.k_first + kcur);
 #pragma unroll
                 for (int t2 = 0; t2 < 16; ++t2) {
-                    const uint2 t = __ldg(&turns[b + T * t2]);
+                    const int p = b + T * t2 - off;
+                    const uint2 t = (unsigned)p < (unsigned)Ni ? __ldg(&turns[p]) : make_uint2(0u, 0u);
                     float sn, cs;
                     sincospif((float)(int32_t)(t.x + k * t.y) * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
                     ph[t2] = make_float2(cs, -sn);
@@ -946,19 +965,7 @@ k_model_rows(PhaseParams P, const float* __restrict__ image, const uint2* __rest
             }
             kcur = kk + 1;
             transform<LOG2N, false>(a, buf, b, tw, x);
-            uint32_t live = 0xffffu;
-            if (occ.col != nullptr) {
-                const uint8_t* cm = occ.col + (size_t)r * occ.NT;
-                if (warp_mask) {
-                    const bool on = lane < 16 && __ldg(cm + (((b & ~31) + T * lane) >> occ.tshift)) != 0;
-                    live = __ballot_sync(0xffffffffu, on);
-                } else {
-                    live = 0;
-#pragma unroll
-                    for (int t2 = 0; t2 < 16; ++t2)
-                        live |= (__ldg(cm + ((b + T * t2) >> occ.tshift)) != 0 ? 1u : 0u) << t2;
-                }
-            }
+            const uint32_t live = live_cols(r);
             float2* row = grids + (size_t)r * NN + (size_t)q * N;
 #pragma unroll
             for (int j = 0; j < 16; ++j)
@@ -1042,36 +1049,36 @@ cudaError_t rows_one(float2* grids, int64_t n_planes, const float2* twid, cudaSt
     return cudaSuccess;
 }
 
-template <int LOG2N, bool CPLX>
+template <int LOG2N, bool CPLX, bool PADDED>
 cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
                       const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
                       const Occupancy& occ, cudaStream_t st) {
     using Sh = Shape<LOG2N>;
-    auto fn = k_rows_phase_reduce<LOG2N, CPLX>;
+    auto fn = k_rows_phase_reduce<LOG2N, CPLX, PADDED>;
     // tables and the transform array, then per pixel z and (real output) the partial sum
     const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<Sh::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ);
+    fn<<<P.Ni, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ);
     return cudaGetLastError();
 }
 
 // N = 16384: four CTAs per image row, each with the 4096-point tables (they
 // follow the 16384-point tables in twid)
-template <bool CPLX>
+template <bool CPLX, bool PADDED>
 cudaError_t fused_split(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
                         const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
                         const Occupancy& occ, cudaStream_t st) {
     constexpr int kSub = 12, kSplit = 4;
     using Sh = Shape<kSub>;
-    auto fn = k_rows_phase_reduce_split<kSub, kSplit, CPLX>;
+    auto fn = k_rows_phase_reduce_split<kSub, kSplit, CPLX, PADDED>;
     const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    fn<<<kSplit * Shape<14>::N, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid + Shape<14>::kTw,
-                                                    image_real, image_complex, occ);
+    fn<<<kSplit * P.Ni, Sh::T, smem, st>>>(P, grids, wsum, pix_turns, pix_scale, twid + Shape<14>::kTw,
+                                            image_real, image_complex, occ);
     return cudaGetLastError();
 }
 
@@ -1079,14 +1086,18 @@ template <int LOG2N>
 cudaError_t fused_n(const PhaseParams& P, const float2* grids, const double* wsum, const uint2* pix_turns,
                     const float* pix_scale, const float2* twid, float* image_real, float2* image_complex,
                     const Occupancy& occ, cudaStream_t st) {
-    if constexpr (LOG2N == 14)
-        return image_complex != nullptr
-                   ? fused_split<true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
-                   : fused_split<false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
-    else
-        return image_complex != nullptr
-                   ? fused_one<LOG2N, true>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st)
-                   : fused_one<LOG2N, false>(P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st);
+    const bool padded = P.Ni != P.N;
+#define RICK_FUSED_ARGS P, grids, wsum, pix_turns, pix_scale, twid, image_real, image_complex, occ, st
+    if constexpr (LOG2N == 14) {
+        if (image_complex != nullptr)
+            return padded ? fused_split<true, true>(RICK_FUSED_ARGS) : fused_split<true, false>(RICK_FUSED_ARGS);
+        return padded ? fused_split<false, true>(RICK_FUSED_ARGS) : fused_split<false, false>(RICK_FUSED_ARGS);
+    } else {
+        if (image_complex != nullptr)
+            return padded ? fused_one<LOG2N, true, true>(RICK_FUSED_ARGS) : fused_one<LOG2N, true, false>(RICK_FUSED_ARGS);
+        return padded ? fused_one<LOG2N, false, true>(RICK_FUSED_ARGS) : fused_one<LOG2N, false, false>(RICK_FUSED_ARGS);
+    }
+#undef RICK_FUSED_ARGS
 }
 
 int log2_exact(int N) {
@@ -1246,7 +1257,7 @@ cudaError_t launch_model_rows(const PhaseParams& P, const float* image, const ui
 
 cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, uint2* turns, float* scale,
                                float* model_scale, cudaStream_t st) {
-    const int64_t n = (int64_t)P0.N * P0.N;
+    const int64_t n = (int64_t)P0.Ni * P0.Ni;
     k_pixel_phase<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(P0, inv_taper, turns, scale, model_scale);
     return cudaGetLastError();
 }

@@ -130,7 +130,8 @@ __device__ __forceinline__ uint32_t tile_bound(const GridParams& G, const uint32
 
 // Scheduling pass: the record count of every tile, and the tiles with at
 // least 64T, 16T, 4T records appended to the three lists (warp-aggregated
-// atomics on the list lengths counts[0..2]).
+// atomics on the list lengths counts[0..2]); with G.light, every other tile
+// with a record to the light list (length counts[4]).
 __global__ void k_schedule(GridParams G, const uint32_t* __restrict__ offsets,
                            uint32_t* __restrict__ counts) {
     const int lane = threadIdx.x & 31;
@@ -145,19 +146,25 @@ __global__ void k_schedule(GridParams G, const uint32_t* __restrict__ offsets,
 #pragma unroll
             for (int q = 0; q < 8; ++q) b[q] = tile_bound(G, offsets, item, q);
             const uint32_t R = (b[1] - b[0]) + (b[3] - b[2]) + (b[5] - b[4]) + (b[7] - b[6]);
-            level = R >= th1 ? 0 : R >= th2 ? 1 : R >= th3 ? 2 : 3;
+            level = R >= th1 ? 0 : R >= th2 ? 1 : R >= th3 ? 2 : R > 0 ? 3 : 4;
         }
 #pragma unroll
-        for (int lv = 0; lv < 3; ++lv) {
+        for (int lv = 0; lv < 4; ++lv) {
+            if (lv == 3 && G.light == nullptr) break;
             const unsigned m = __ballot_sync(kFull, level == lv);
             if (m == 0u) continue;
             const int leader = __ffs(m) - 1;
+            uint32_t* cnt = lv < 3 ? &counts[lv] : &counts[4];
             uint32_t at = 0;
-            if (lane == leader) at = atomicAdd(&counts[lv], (uint32_t)__popc(m));
+            if (lane == leader) at = atomicAdd(cnt, (uint32_t)__popc(m));
             at = __shfl_sync(kFull, at, leader);
             if (level == lv) {
                 const uint32_t pos = at + (uint32_t)__popc(m & ((1u << lane) - 1u));
-                if (pos < G.list_cap) G.lists[(size_t)lv * G.list_cap + pos] = item;
+                if (lv < 3) {
+                    if (pos < G.list_cap) G.lists[(size_t)lv * G.list_cap + pos] = item;
+                } else if (pos < G.light_cap) {
+                    G.light[pos] = item;
+                }
             }
         }
     }
@@ -435,12 +442,21 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
     // longest-first lists (if any): their lengths, capped; an overflow (which
     // the capacity bound excludes) falls back to natural order for all tiles
     uint32_t n1 = 0, n2 = 0, n3 = 0, th3 = 0xffffffffu;
+    uint32_t n_light = 0;
+    bool light = false;   // phase 2 visits the lists only (sparse mode)
     if (G.lists) {
         n1 = __ldg(work_counter + 1);
         n2 = __ldg(work_counter + 2);
         n3 = __ldg(work_counter + 3);
-        if (n1 > G.list_cap || n2 > G.list_cap || n3 > G.list_cap) n1 = n2 = n3 = 0;
-        else th3 = 4u * T;
+        if (n1 > G.list_cap || n2 > G.list_cap || n3 > G.list_cap) {
+            n1 = n2 = n3 = 0;
+        } else {
+            th3 = 4u * T;
+            if (G.light != nullptr && G.skip_empty) {
+                n_light = __ldg(work_counter + 5);
+                light = n_light <= G.light_cap;
+            }
+        }
     }
 
     // ---- phase 1: dense tiles, one per CTA --------------------------------
@@ -503,7 +519,7 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
     };
 
     // ---- phase 2: every other tile, one warp per tile ---------------------
-    const uint32_t n_pos = n3 + G.n_items;
+    const uint32_t n_pos = n3 + (light ? n_light : G.n_items);
     auto other_tiles = [&]() {
     for (;;) {
         uint32_t first = 0;
@@ -511,10 +527,13 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
         first = __shfl_sync(kFull, first, 0);
         if (first >= n_pos) break;
         const uint32_t n = min(G.grab, n_pos - first);
-        // queue positions -> tiles: the third list, then every tile in natural order
+        // queue positions -> tiles: the third list, then the light list (sparse
+        // mode) or every tile in natural order
         if (lane < (int)n) {
             const uint32_t pos = first + lane;
-            items[lane] = pos < n3 ? G.lists[2 * (size_t)G.list_cap + pos] : pos - n3;
+            items[lane] = pos < n3 ? G.lists[2 * (size_t)G.list_cap + pos]
+                          : light  ? G.light[pos - n3]
+                                   : pos - n3;
         }
         __syncwarp();
         for (uint32_t e = lane; e < 8 * n; e += 32) rng_all[e] = tile_bound(G, offsets, items[e >> 3], e & 7);
@@ -530,7 +549,7 @@ __global__ void k_grid(GridParams G, const uint32_t* __restrict__ offsets,
             for (int q = 0; q < 8; ++q) rng[q] = rng_all[8 * t + q];
             const uint32_t total = (rng[1] - rng[0]) + (rng[3] - rng[2]) + (rng[5] - rng[4]) +
                                    (rng[7] - rng[6]);
-            if (first + t >= n3 && total >= th3) continue;  // taken from a list earlier
+            if (!light && first + t >= n3 && total >= th3) continue;  // taken from a list earlier
             if (total == 0) {
                 if (!G.skip_empty) {
                     for (int r = lane; r < T; r += 32) bulk_row_store(out + (size_t)r * N, zrow, row_bytes);

@@ -108,6 +108,12 @@ struct GridParams {
     // first, then every other tile in natural order.  nullptr: natural order.
     uint32_t* lists;
     uint32_t list_cap;
+    // Sparse mode (skip_empty) only, optional: every other reached tile (fewer
+    // than 4T records, at least one), listed by the scheduling pass
+    // (work_counter[5] holds the count); the gridder then visits the lists
+    // only, never the unreached tiles.  light_cap >= the launch's tiles.
+    uint32_t* light;
+    uint32_t light_cap;
     int w_support;        // prediction: >= 2 accumulates the Sw partial predictions
     // 1: tiles that no record reaches are not written (the zero fill is left
     // out); the planes are then only valid where tile_reach() > 0

@@ -25,6 +25,7 @@
 // (different streams, or different host threads) race on it -- serialise them.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "rick_internal.cuh"
@@ -135,6 +136,7 @@ extern "C" rick_status rick_grid_noalloc(const rick_config* cfg, const double* u
     }
 
     GridParams G;
+    std::memset(&G, 0, sizeof G);
     if (!(fit_tap_polynomials(c.kernel_kind, c.kernel_param, c.support, G) <= 1e-6))
         return fail(RICK_ERR_UNSUPPORTED, "rick_grid_noalloc: kernel too narrow for its support");
 

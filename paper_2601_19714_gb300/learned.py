@@ -6,8 +6,9 @@ support-4 Kaiser-Bessel taps.  It is trained on the GPU by the library's own
 kernels: ``rick_mlp_forward`` bakes the correction table on the lattice,
 ``rick_learn_field_grad`` images a point-source field (sources at continuous
 positions) with Kaiser-Bessel taps plus that correction and measures it
-against the direct Fourier inversion at probe pixels spread over the field, ``rick_mlp_backward`` carries the table gradient into the
-network and ``rick_adam_step`` updates it.  This module only orders those
+against the direct Fourier inversion at probe pixels spread over the
+taper-gated field, ``rick_mlp_backward`` carries the table gradient into
+the network and ``rick_adam_step`` updates it.  This module only orders those
 calls, draws the seeded fields, and saves/resumes the state (parameters, Adam
 moments, step).
 
@@ -53,19 +54,25 @@ def training_field(seed: int, N: int, margin: int = 4, n_range=(1, 50),
     return np.concatenate([pq, a[:, None]], axis=1)
 
 
-def field_probes(seed: int, N: int, src: np.ndarray, count: int = 64, margin: int = 4) -> np.ndarray:
-    """The pixels a field is judged at: the pixel nearest each of its brightest
-    sources (at most count // 4), the four corners and four edge midpoints
-    (margin pixels in), and seeded pixels anywhere in the image for the rest,
-    so that the objective sees the kernel's error over the whole field, where
-    its aliasing is largest near the edges.  [count, 2] int32 (p, q)."""
+def field_probes(seed: int, N: int, src: np.ndarray, count: int = 64, inner: float = 0.4) -> np.ndarray:
+    """The pixels a field is judged at, all inside the central square of
+    half-width inner * N (for the support-4 Kaiser-Bessel taper, inner = 0.4
+    keeps the taper gain C(p) C(q) / C(N/2)^2 above about 1e-2, so that no
+    probe's error is amplified more than ~100 times by the taper division):
+    the pixel nearest each of the field's brightest sources inside it (at
+    most count // 4), the corners and edge midpoints of the square, and
+    seeded pixels in it for the rest.  [count, 2] int32 (p, q)."""
     g = np.random.Generator(np.random.Philox(key=[seed, 0x50524F42]))
-    order = np.argsort(-src[:, 2])[: count // 4]
-    near = np.clip(np.rint(src[order, :2]), 0, N - 1).astype(np.int64)
-    e, h = margin, N // 2
-    fixed = np.array([(e, e), (N - 1 - e, e), (e, N - 1 - e), (N - 1 - e, N - 1 - e),
-                      (h, e), (h, N - 1 - e), (e, h), (N - 1 - e, h)], dtype=np.int64)
-    rest = g.integers(margin, N - margin, size=(count - len(near) - len(fixed), 2))
+    h = N // 2
+    e = int(inner * N)
+    lo, hi = h - e, h + e - 1
+    inside = (np.abs(src[:, 0] - h) <= e - 1) & (np.abs(src[:, 1] - h) <= e - 1)
+    cand = np.nonzero(inside)[0]
+    order = cand[np.argsort(-src[cand, 2])][: count // 4]
+    near = np.clip(np.rint(src[order, :2]), lo, hi).astype(np.int64)
+    fixed = np.array([(lo, lo), (hi, lo), (lo, hi), (hi, hi), (h, lo), (h, hi), (lo, h), (hi, h)],
+                     dtype=np.int64)
+    rest = g.integers(lo, hi + 1, size=(count - len(near) - len(fixed), 2))
     return np.concatenate([near, fixed, rest]).astype(np.int32)
 
 

@@ -16,7 +16,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
-from tests.gpu_util import plan_config, to_device
+from tests.gpu_util import assert_image_close, plan_config, to_device
 from visgen.workloads import meerkat, tiny_wstack
 
 pytestmark = pytest.mark.gpu
@@ -36,8 +36,11 @@ def rk():
 
 
 def _free():
+    """Free device memory with torch's cached blocks returned first, so that
+    only what the library holds counts."""
     import torch
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     return torch.cuda.mem_get_info()[0]
 
 
@@ -120,8 +123,16 @@ def test_failures_inside_calls_leave_the_plan_usable(rk):
     rk.inject("none")
     assert e.value.status == OOM
     # record order within a bin follows the binning's atomics, so FP32 sums
-    # may differ in their last bits between runs
-    assert np.abs(image_with(plan) - ref).max() <= 1e-6 * np.abs(ref).max()
+    # differ in their last bits between runs, which the unpadded taper
+    # correction amplifies at the field edge: the image is compared with the
+    # parity tests' taper-aware gate
+    taper = plan.taper()
+
+    def same(got):
+        for c in range(2):
+            assert_image_close(got[c], ref[c], taper, 1e-5)
+
+    same(image_with(plan))
     grids = torch.empty((2, ns, N, N), dtype=torch.complex64, device="cuda")
     wsum = torch.empty(2, dtype=torch.float64, device="cuda")
     rk.inject("launch", 2)
@@ -132,7 +143,7 @@ def test_failures_inside_calls_leave_the_plan_usable(rk):
     assert e.value.status == CUDA
     torch.cuda.synchronize()
     plan.sync_status()
-    assert np.abs(image_with(plan) - ref).max() <= 1e-6 * np.abs(ref).max()
+    same(image_with(plan))
     plan.close()
     del grids, wsum
     torch.cuda.empty_cache()
@@ -166,7 +177,7 @@ def test_debug_build_flags_a_record_outside_its_tile(rk):
                torch.empty(1, dtype=torch.float64, device="cuda"))
         torch.cuda.synchronize()
         a, b = g_dbg.cpu().numpy(), g_ref.cpu().numpy()
-        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()   # planes: no taper involved
     # one record's first footprint cell moved outside its 32-cell tile
     assert D.rick_debug_poke_record(h, 5, 200, 3) == 0
     assert D.rick_grid_binned(h, 0, 1, 0, Nw, g_dbg.data_ptr(), stream) == 0

@@ -4,8 +4,8 @@ rick_dirty_image with the library's own transform bins, grids only the tiles
 that visibilities reach, transforms the reached tile columns (column pass)
 and runs the row pass fused with Eq. 2's phase screen and plane sum, whose
 kernel is instantiated per mesh side: N = 4096 and 8192 one CTA per image row,
-N = 16384 two CTAs per row (the row DFT split by one decimation-in-frequency
-step).  Each case images one channel of a workload at full mesh size and full
+N = 16384 four CTAs per row (the row DFT split by one radix-4
+decimation-in-frequency step).  Each case images one channel of a workload at full mesh size and full
 plane count with the Hermitian fold -- MeerKAT-shaped at 4096^2 x 32 planes
 (16 stored), LOFAR-shaped at 8192^2 x 48 planes (24 stored), the MeerKAT
 large-precision layout at 16384^2 x 32 planes (16 stored) -- on a seeded row
@@ -146,7 +146,7 @@ def test_impulse_16384_gives_a_plane_wave(rk):
 
 @pytest.mark.parametrize("fold", [False, True])
 def test_split_row_pass_equals_separate_calls_16384(rk, fold):
-    """The fused split row pass (two CTAs per row) against the plain 16384
+    """The fused split row pass (four CTAs per row) against the plain 16384
     transform followed by the phase kernel, on gridded MeerKAT planes; and the
     pruned path on sparse-gridded NaN-filled planes against the unpruned one."""
     import torch

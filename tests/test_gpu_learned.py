@@ -5,7 +5,7 @@ kernel (and, for a zero table, against plain Kaiser-Bessel gridding), the
 training objective (image and direct inversion at the probes) against the
 oracle, the training gradient against finite differences of the oracle's
 loss, what training gains over the untrained start (exactly the support-4
-Kaiser-Bessel), and checkpoint/resume."""
+Kaiser-Bessel) on held-out fields, and checkpoint/resume."""
 import numpy as np
 import pytest
 
@@ -166,23 +166,24 @@ def test_training_gradient_matches_finite_differences_of_the_oracle(rk, orc):
 
 
 def test_training_beats_the_untrained_kernel(rk):
-    """What the network gains: held-out fields imaged with the trained kernel
-    against the untrained one, which is exactly the support-4 Kaiser-Bessel
-    (the method without the learned part)."""
+    """What the network gains: 64 held-out fields (sources at continuous
+    positions, judged at 64 pixels of the taper-gated field) imaged with the
+    trained kernel against the untrained one, which is exactly the support-4
+    Kaiser-Bessel (the method without the learned part).  The network is
+    trained on 9,600 other fields (600 Adam steps of 16)."""
     from paper_2601_19714_gb300 import learned
     img, obs, learn = _field_setup(rk, seed=5, nvis=60_000, N=256, Nw=8, L=16)
     k = learned.LearnedKernel(img.Nw, 64, 16, seed=7)
-    start = k.heldout_loss(learn, 64)
-    k.train(learn, 200, lr=1e-6, batch=32)
-    after = k.heldout_loss(learn, 64)
-    gain = 1.0 - after[0] / start[0]
-    print(f"held-out loss (mean, median): Kaiser-Bessel S=4 {start}, trained {after}, "
-          f"gain {100 * gain:.1f} %")
-    # The exact Kaiser-Bessel start is already good at the source pixels (its
-    # response averaged over fractional offsets equals its taper); training
-    # may only trim what is left, and must not lose accuracy.
-    assert after[0] <= 1.02 * start[0]
-    assert float(k.bake().abs().max()) > 0.0
+    base = k.losses(learn, 64)
+    k.train(learn, 600, lr=3e-5, batch=16)
+    after = k.losses(learn, 64)
+    gain_mean = 1.0 - after.mean() / base.mean()
+    gain_median = 1.0 - np.median(after) / np.median(base)
+    better = float((after < base).mean())
+    print(f"held-out loss mean {base.mean():.3e} -> {after.mean():.3e} ({100 * gain_mean:.1f} %), "
+          f"median {np.median(base):.3e} -> {np.median(after):.3e} ({100 * gain_median:.1f} %), "
+          f"fields better {100 * better:.0f} %")
+    assert gain_mean >= 0.05 and gain_median >= 0.03 and better >= 0.55
 
 
 def test_checkpoint_resume_continues_the_same_run(rk, tmp_path):
