@@ -115,6 +115,34 @@ def stage_traffic(N, C, P, nrow, n_grid, T, reach, own):
 # flop per FMA x 2.07 GHz (the maximum SM clock, which the bench runs at).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
+# The gridder's own ceilings (its DRAM traffic is a few per cent of the HBM
+# rate): one shared-memory wavefront per cycle per SM and one warp
+# instruction per cycle per SM sub-partition (four per SM), at 2.07 GHz.
+SMEM_WAVEFRONTS_PEAK = 152 * 2.07e9
+ISSUE_PEAK = 152 * 4 * 2.07e9
+# Shared-memory wavefronts and warp instructions of k_grid per gridded
+# visibility, read from the ncu capture named (KB S = 8, tile 32, fold).
+GRID_COUNTERS = {
+    "large": {"smem_wavefronts": 22352736 / 1109055, "warp_instructions": 129622991 / 1109055,
+              "profile": "profiles/kernels_meerkat_large_small_16384sq_4w_1ch.md"},
+}
+
+
+def gridder_ceilings(n_grid, ms, key):
+    """The gridder's rate against its shared-memory and issue ceilings: the
+    per-visibility counts of an ncu capture times the visibilities gridded per
+    second, over the peak rates above."""
+    c = GRID_COUNTERS[key]
+    rate = n_grid / (ms * 1e-3)
+    out = {}
+    for name, per, peak in (("smem_wavefronts", c["smem_wavefronts"], SMEM_WAVEFRONTS_PEAK),
+                            ("issue", c["warp_instructions"], ISSUE_PEAK)):
+        out[name] = {"per_vis": per, "achieved_per_s": rate * per, "peak_per_s": peak,
+                     "frac": rate * per / peak}
+    out["binding"] = max(("smem_wavefronts", "issue"), key=lambda k: out[k]["frac"])
+    out["source"] = c["profile"]
+    return out
+
 
 def stage_flops(N, C, P, reach, own):
     """Algorithmic FP32 flops per step of the transform stages: 5 n log2 n per
@@ -921,7 +949,7 @@ def run_large_line(args):
                            "flops": flops["rows_phase"] / rows_launches},
             "hbm_achieved_gbs": gbs["rows_phase"], "hbm_frac": gbs["rows_phase"] / hbm,
             "traffic": None,
-            "traffic_note": "ncu DRAM bytes of this kernel: profiles/rows_phase_split_meerkat_16384sq_small.md"}
+            "traffic_note": "full launch not captured; the small 16384^2 case (1 channel, 2 stored planes): 6.06 GB DRAM per launch against 2.61 GB algorithmic, the excess the per-pixel phase and taper tables (profiles/kernels_meerkat_large_small_16384sq_4w_1ch.md)"}
 
     # image error: the same plan's path on a 1 % row subsample of the lowest
     # and highest channels, against the oracle's per-visibility O1 at 64 pixels
@@ -1014,7 +1042,9 @@ def run_large_line(args):
             "bin_plus_grid_vis_per_s": n_grid / ((st["bin"] + st["grid"]) * 1e-3),
             "roofline": roof,
             "roofline_stages": {k: {"bound": "hbm", "achieved": gbs[k], "peak": hbm, "peak_kind": peak_kind,
-                                    "unit": "GB/s", "frac": gbs[k] / hbm} for k in st},
+                                    "unit": "GB/s", "frac": gbs[k] / hbm,
+                                    **({"ceilings": gridder_ceilings(n_grid, st["grid"], "large")}
+                                       if k == "grid" else {})} for k in st},
             "fp32_stages": {k: {"achieved": tfl[k], "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": tfl[k] / FP32_PEAK_TFLOPS} for k in tfl},
             "e2e": None if e2e is None else {

@@ -209,7 +209,8 @@ rick_status rick_plan_taper(const rick_plan* plan, double* taper_host);
  * between lattice points and adds it to the separable support-4
  * Kaiser-Bessel taps g(a + 1 - 2 - dx) g(b + 1 - 2 - dy), so an all-zero table
  * is exactly the Kaiser-Bessel kernel.  Only for plans with kernel_kind =
- * RICK_KERNEL_TABLE; 1 <= L <= 256. */
+ * RICK_KERNEL_TABLE; 1 <= L <= 256.  The table is read by each gridding
+ * call, so a table set after rick_bin applies to the next gridding call. */
 rick_status rick_set_kernel_table(rick_plan* plan, const float* taps, int32_t lattice, void* stream);
 
 /* ---- the hot path ---------------------------------------------------- */

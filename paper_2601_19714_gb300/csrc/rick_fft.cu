@@ -124,8 +124,20 @@ __host__ __device__ constexpr float cos64(int k) {
 
 __host__ __device__ constexpr float sin64(int k) { return cos64(k - 16); }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex add and subtract as one packed two-lane FP32 instruction each
+// (add/sub.rn.f32x2, sm_100 and later): the same IEEE round-to-nearest results
+// as two scalar instructions, half the issue slots -- the butterflies are
+// mostly adds, and the transform kernels are issue-bound.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+    uint64_t ra = *reinterpret_cast<uint64_t*>(&a), rb = *reinterpret_cast<uint64_t*>(&b), rd;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2*>(&rd);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+    uint64_t ra = *reinterpret_cast<uint64_t*>(&a), rb = *reinterpret_cast<uint64_t*>(&b), rd;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+    return *reinterpret_cast<float2*>(&rd);
+}
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -641,8 +653,9 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 // SPLIT k + r, to which it applies the phase screen and the plane sum of
 // Eq. 2 exactly as k_rows_phase_reduce does (Horner blocks of kHornerBlock
 // planes, exact phasor at each block's end).  The twiddle of y_r is
-// e^(2 pi i r b / N) (per thread, from FP64) times e^(2 pi i r t2 / (16 SPLIT))
-// (a constant of the unrolled code, n = b + (M/16) t2).  With pruning, the
+// e^(2 pi i r b / N) (per thread, from a table rounded from FP64) times
+// e^(2 pi i r t2 / (16 SPLIT)) (a constant of the unrolled code,
+// n = b + (M/16) t2).  With pruning, the
 // unreached tile columns of the row are not read; the prefetch of the next
 // row holds one value per position n (its first reached part t), and the
 // other reached parts of the same position (none on a centred uv coverage
@@ -654,7 +667,8 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                           const uint2* __restrict__ pix_turns, const float* __restrict__ pix_scale,
                           const float2* __restrict__ twid_sub, float* __restrict__ image_real,
                           float2* __restrict__ image_complex, Occupancy occ) {
-    static_assert(SPLIT == 2 || SPLIT == 4, "split");
+    // the split twiddle table (fft_twiddles) is built for N = 4 x 4096
+    static_assert(SPLIT == 4 && LOG2SUB == 12, "split");
     using Sh = Shape<LOG2SUB>;
     constexpr int M = Sh::N, T = Sh::T;     // sub-transform: points, threads
     constexpr int N = SPLIT * M;
@@ -680,13 +694,9 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
         zrot[k] = make_float2(c, -s);
         if (!COMPLEX_OUT) part[k] = 0.f;
     }
-    // e^(+2 pi i r b / N) for this CTA's twiddles
-    float2 wb = make_float2(1.f, 0.f);
-    if (par) {
-        double sd, cd;
-        sincospi(2.0 * (double)(par * b) / (double)N, &sd, &cd);
-        wb = make_float2((float)cd, (float)sd);
-    }
+    // e^(+2 pi i r b / N) for this CTA's twiddles, rounded from FP64 on the
+    // host (the table after the sub-transform's stage tables)
+    const float2 wb = __ldg(twid_sub + Sh::kTw + par * T + b);
 
     const size_t NN = (size_t)N * N, NNi = (size_t)Ni * Ni;
     const int n_rows = P.nc * P.nk;
@@ -720,10 +730,13 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
             while (r < n_rows && occ.plane[r] == 0) ++r;
         return r;
     };
-    // prefetch: the first reached part of each position; pf_first (2 bits per
-    // position) says which
+    // prefetch: the lowest reached part of each position; pf_first (2 bits per
+    // position) says which, and pf_single that no position of this thread has
+    // a second reached part (the usual case: a centred uv coverage narrower
+    // than M), so that the combination needs no further load or test
     uint64_t pf_live = 0;
     uint32_t pf_first = 0;
+    bool pf_single = true;
     const float2* pf_row = grids;
     auto load_row = [&](int r, float2 (&v)[16]) {
         pf_row = grids + (size_t)r * NN + (size_t)(q + off) * N;
@@ -738,25 +751,40 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
             pf_first |= (uint32_t)(first < 0 ? 0 : first) << (2 * t2);
             v[t2] = first >= 0 ? __ldcs(pf_row + b + T * t2 + first * M) : make_float2(0.f, 0.f);
         }
+        const uint32_t l0 = (uint32_t)pf_live & 0xffffu, l1 = (uint32_t)(pf_live >> 16) & 0xffffu,
+                       l2 = (uint32_t)(pf_live >> 32) & 0xffffu, l3 = (uint32_t)(pf_live >> 48) & 0xffffu;
+        pf_single = ((l0 & (l1 | l2 | l3)) | (l1 & (l2 | l3)) | (l2 & l3)) == 0u;
+    };
+    // y * i^k for a runtime k in 0..3 (the quarter turns e^(2 pi i R t / 4))
+    auto quarter = [](float2 y, int k) {
+        const float re = (k & 1) ? y.y : y.x, im = (k & 1) ? y.x : y.y;
+        return make_float2(((k + 1) & 2) ? -re : re, (k & 2) ? -im : im);
     };
     // y_r from the prefetched values (compile-time r)
     auto combine_r = [&](float2 (&v)[16], auto rc) {
         constexpr int R = decltype(rc)::value;
+        if (pf_single) {
+            if (R == 0) return;   // y_0[n] = x[n + first M]
+#pragma unroll
+            for (int t2 = 0; t2 < 16; ++t2) {
+                const int first = (int)((pf_first >> (2 * t2)) & 3u);
+                v[t2] = twiddle64<true>(cmulf(quarter(v[t2], (R * first) & 3), wb), R * t2);
+            }
+            return;
+        }
 #pragma unroll
         for (int t2 = 0; t2 < 16; ++t2) {
             const int first = (int)((pf_first >> (2 * t2)) & 3u);
-            // e^(2 pi i R first / SPLIT) times the prefetched part (zero if none)
-            const int k4 = (R * first * (4 / SPLIT)) & 3;   // quarter turns
-            float2 y = v[t2];
-            y = k4 == 0 ? y : k4 == 1 ? mul_si<true>(y) : k4 == 2 ? make_float2(-y.x, -y.y) : mul_si<false>(y);
+            // e^(2 pi i R first / 4) times the prefetched part (zero if none),
+            // plus the other reached parts (above first)
+            float2 y = quarter(v[t2], (R * first) & 3);
 #pragma unroll
             for (int t = 1; t < SPLIT; ++t)
-                if (t != first && ((pf_live >> (16 * t + t2)) & 1u)) {
+                if (t > first && ((pf_live >> (16 * t + t2)) & 1u)) {
                     const float2 u = __ldcs(pf_row + b + T * t2 + t * M);
                     y = cadd(y, twiddle_const<true>(u, R * t, SPLIT));
                 }
-            if (0 != first && (pf_live >> t2) & 1u) y = cadd(y, __ldcs(pf_row + b + T * t2));
-            v[t2] = R == 0 ? y : twiddle64<true>(cmulf(y, wb), R * t2 * (4 / SPLIT));
+            v[t2] = R == 0 ? y : twiddle64<true>(cmulf(y, wb), R * t2);
         }
     };
     auto combine = [&](float2 (&v)[16]) {
@@ -1144,10 +1172,19 @@ void append_twiddles(int N, std::vector<float2>& out) {
 }  // namespace
 
 void fft_twiddles(int N, std::vector<float2>& out) {
-    // N = 16384: the 4096-point tables of the split fused row pass follow
+    // N = 16384: the 4096-point tables of the split fused row pass follow,
+    // then its split twiddles [r T + b] = e^(+2 pi i r b / N), r < 4, b < T = 256
     out.clear();
     append_twiddles(N, out);
-    if (log2_exact(N) == 14) append_twiddles(4096, out);
+    if (log2_exact(N) == 14) {
+        append_twiddles(4096, out);
+        const double two_pi = 6.283185307179586476925;
+        for (int r = 0; r < 4; ++r)
+            for (int b = 0; b < 256; ++b) {
+                const double a = two_pi * (double)(r * b) / N;
+                out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+            }
+    }
 }
 
 cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,

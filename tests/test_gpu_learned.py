@@ -84,6 +84,41 @@ def test_gridding_with_the_table_matches_the_oracle_learned_kernel(rk, orc):
     assert_image_close(I_g[0], I_o.real, plan.taper(), 1e-5)
 
 
+def test_table_set_after_binning_applies_to_the_next_gridding(rk):
+    """The correction taps are interpolated per record at each gridding call,
+    so a table set between rick_bin and rick_grid_binned is the one used: the
+    planes equal those of a plan that had that table from the start (to FP32
+    rounding)."""
+    import torch
+    from paper_2601_19714_gb300 import learned
+    img, obs = learned_field(23, nvis=30_000, N=256, Nw=8, n_src=5)
+    dev = to_device(obs)
+    tabs = []
+    for seed in (3, 4):
+        k = learned.LearnedKernel(img.Nw, 64, 16, seed=seed, zero_output=False)
+        with torch.no_grad():
+            k.params[-(16 * 64 + 16):] *= 0.01
+        tabs.append(k.bake().clone())
+    N, Nw = img.N, img.Nw
+    ws = torch.empty(1, dtype=torch.float64, device="cuda")
+    planes = []
+    for first, second in ((0, 1), (1, None)):
+        plan = rk.Plan(plan_config(img, 1))
+        plan.set_kernel_table(tabs[first], 16)
+        g = torch.empty((1, Nw, N, N), dtype=torch.complex64, device="cuda")
+        plan.grid(dev["uvw"], dev["chan_scale"], dev["vis"], dev["weight"], None, obs.nrow, 0, Nw, g, ws)
+        if second is not None:
+            plan.set_kernel_table(tabs[second], 16)
+            plan.grid_binned(0, 1, 0, Nw, g)
+        torch.cuda.synchronize()
+        planes.append(g.cpu().numpy())
+    # two binnings: the record order within a bin follows the atomics, so the
+    # FP32 sums agree to rounding, not bit for bit
+    peak = np.abs(planes[1]).max()
+    assert peak > 0
+    assert np.abs(planes[0] - planes[1]).max() <= 1e-6 * peak
+
+
 def test_zero_correction_is_exactly_kaiser_bessel(rk):
     """The untrained learned kernel (zero output layer) grids exactly like the
     support-4 Kaiser-Bessel kernel."""
