@@ -273,7 +273,14 @@ rick_status rick_fft_wplanes(rick_plan* plan, float* grids, int64_t n_planes, vo
  *   image[c][q][p] += (-1)^(p+q) n / (weight_sum[c] C(p) C(q))
  *                     * Re sum_k F_k[q][p] exp(+2 pi i w_k (n - 1)),
  * n = sqrt(1 - l^2 - m^2).  The phase is formed in FP64 per pixel (fixed
- * point per plane).  weight_sum is indexed by absolute channel.
+ * point per plane).  Precision of the plane sum (this call and the fused row
+ * pass alike): per block of 8 planes the sum is taken by Horner's rule with
+ * the FP32 rotation z = exp(-2 pi i dw (n - 1)), and the block's last plane
+ * gets its exact phasor (formed from the Q0.32 turns); the FP32 powers of z
+ * cost 6.6e-7 of the peak on 24 planes at N = 1024 (1.4e-6 without the
+ * blocks), within the 1e-5 gate the full-size tests apply at 4096^2 x 16,
+ * 8192^2 x 24 and 16384^2 x 16 stored planes.  weight_sum is indexed by
+ * absolute channel.
  * image_real is [chan_end-chan_begin][N][N]; image_complex (nullable) the
  * same shape complex64 and receives the value before Re. */
 rick_status rick_phase_correct_reduce(rick_plan* plan, const float* grids, int32_t chan_begin,

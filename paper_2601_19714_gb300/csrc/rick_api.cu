@@ -240,6 +240,7 @@ struct rick_plan {
     uint8_t* d_colocc = nullptr;     // occupancy for pruning: [C][planes][NT] and [C][planes]
     uint8_t* d_planeocc = nullptr;
     uint32_t* d_tileocc = nullptr;   // [C][planes][NT][ceil(NT/32)] tile bits
+    uint32_t* d_collist = nullptr;   // 2 + [C][planes][NT]: reached tile columns (Occupancy::list)
     uint2* d_pix_turns = nullptr;    // fused row passes: per-pixel turns and scales [N][N]
     float* d_pix_scale = nullptr;
     float* d_pix_model_scale = nullptr;
@@ -265,6 +266,7 @@ void release(rick_plan* P) {
     dfree(P->d_colocc);
     dfree(P->d_planeocc);
     dfree(P->d_tileocc);
+    dfree(P->d_collist);
     dfree(P->d_pix_turns);
     dfree(P->d_pix_scale);
     dfree(P->d_pix_model_scale);
@@ -533,6 +535,7 @@ rick_status plan_init(rick_plan* P, const rick_config* cfg) {
         RK_CUDA(dmalloc(&P->d_planeocc, (size_t)c.n_channels * P->planes));
         RK_CUDA(dmalloc(&P->d_tileocc, sizeof(uint32_t) * (size_t)c.n_channels * P->planes * P->NT *
                                               ((P->NT + 31) / 32)));
+        RK_CUDA(dmalloc(&P->d_collist, sizeof(uint32_t) * (2 + (size_t)c.n_channels * P->planes * P->NT)));
         const size_t NN = (size_t)c.N * c.N;
         // the sparse gridder's list of light tiles: room for every tile of the plan
         P->light_cap = (uint32_t)(P->nkeys / 4);
@@ -892,7 +895,8 @@ rick_status occupancy_impl(rick_plan* P, int c0, int c1, int k0, int k1, cudaStr
                "RICK_GRIDDED_BY_PLAN needs the plan's binning for gridding (rick_bin)");
     int launches = 0;
     rick_status s = check_launch(launch_occupancy(P->d_offsets, c0, c1 - c0, k0, k1 - k0, P->planes, P->NT,
-                                                  P->d_colocc, P->d_planeocc, P->d_tileocc, st, &launches),
+                                                  P->d_colocc, P->d_planeocc, P->d_tileocc, P->d_collist,
+                                                  st, &launches),
                                  "occupancy kernel");
     P->launches += launches;
     return s;
@@ -904,6 +908,7 @@ Occupancy plan_occupancy(const rick_plan* P) {
     o.col = P->d_colocc;
     o.plane = P->d_planeocc;
     o.tile = P->d_tileocc;
+    o.list = P->d_collist;
     int sh = 0;
     while ((1 << sh) < P->T) ++sh;
     o.tshift = sh;

@@ -302,6 +302,35 @@ __device__ __forceinline__ void radix16_out(float2 (&a)[16], int b, int s, float
     for (int f0 = 1; f0 < 16; ++f0) at(f0) = cmulf(a[f0], w[f0]);
 }
 
+// Stage 0 (M = 1) of the inverse transform whose 16 inputs of thread b all
+// carry one more factor sc (the split row pass's e^(+2 pi i r b / N)): the
+// factor is moved past the butterfly, so output f0 is multiplied by
+// sc W^(b f0) -- the products formed from sc and the stage's four table
+// powers -- instead of every input by sc (31 complex multiplies instead of 42).
+template <int LOG2N>
+__device__ __forceinline__ void radix16_first_scaled(float2 (&a)[16], int b, float2* buf, const float2* tw,
+                                                     float2 sc) {
+    using Sh = Shape<LOG2N>;
+    Dft<16, true>::run(a);
+    const int cnt = Sh::stage_cnt(0);
+    const float2* sw = tw + Sh::stage_off(0) + b;   // t1 = b
+    const float2 w1 = sw[0], w2 = sw[cnt], w4 = sw[2 * cnt], w8 = sw[3 * cnt];
+    float2 w[16];
+    w[0] = sc;
+    w[1] = cmulf(sc, w1);
+    w[2] = cmulf(sc, w2);
+    w[3] = cmulf(w[1], w2);
+    w[4] = cmulf(sc, w4);
+#pragma unroll
+    for (int f0 = 5; f0 < 8; ++f0) w[f0] = cmulf(w[f0 - 4], w4);
+    w[8] = cmulf(sc, w8);
+#pragma unroll
+    for (int f0 = 9; f0 < 16; ++f0) w[f0] = cmulf(w[f0 - 8], w8);
+    float2* out = buf + skew(16 * b);   // outputs 16 b + f0
+#pragma unroll
+    for (int f0 = 0; f0 < 16; ++f0) out[f0] = cmulf(a[f0], w[f0]);
+}
+
 // The middle radix-16 stages (all but the first, which starts from registers,
 // and the last) on buf, in place: loads, barrier, compute and stores, barrier.
 template <int LOG2N, bool INV>
@@ -403,6 +432,64 @@ k_fft_columns(float2* __restrict__ grids, const float2* __restrict__ twid, Occup
     for (int j = 0; j < 16; ++j) {
         const int row = b + T * j;
         if (!out_mask || s_live[row >> occ.tshift]) __stcs(col + (size_t)row * N, x[j]);
+    }
+}
+
+// The column pass over the reached tile columns only (occ.list): a persistent
+// CTA (one or two per SM) loads the twiddle tables once, then takes COLS
+// adjacent columns at a time from the list -- tile column entry e = p NT + tx
+// gives columns (tx << tshift) + COLS j of plane p -- with an atomic work
+// counter, and transforms them as k_fft_columns does.  The unreached tile
+// columns cost nothing: with one CTA per column most CTAs of a sparse launch
+// only looked up their mask byte and exited, and at N = 16384 (180 KB of
+// shared memory, one CTA per SM at a time) those empty CTAs took most of the
+// pass.
+template <int LOG2N, int COLS, bool INV>
+__global__ void __launch_bounds__(COLS * (1 << LOG2N) / 16)
+k_fft_columns_list(float2* __restrict__ grids, const float2* __restrict__ twid, Occupancy occ) {
+    using Sh = Shape<LOG2N>;
+    constexpr int N = Sh::N, T = Sh::T;
+    constexpr int kStride = Sh::kArray + 16 / COLS;
+    constexpr int kThreads = COLS * T;
+    __shared__ uint8_t s_live[N / 16];
+    __shared__ uint32_t s_item;
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* tw = fsm;
+    const int tid = threadIdx.x;
+    const int c = tid % COLS, b = tid / COLS;
+    float2* buf = fsm + Sh::kTw + c * kStride;
+    load_tables<LOG2N>(twid, tw, tid, kThreads);
+    const uint32_t per = (1u << occ.tshift) / COLS;          // CTA items per tile column
+    const uint64_t total = (uint64_t)__ldg(occ.list) * per;
+    const bool in_mask = !occ.tiles_out, out_mask = occ.tiles_out;
+    // thread 0 takes the next item while the current one is transformed
+    uint32_t next = tid == 0 ? atomicAdd(occ.list + 1, 1u) : 0u;
+    for (;;) {
+        if (tid == 0) s_item = next;
+        __syncthreads();   // also: the previous item's last stage has read buf
+        const uint32_t item = s_item;
+        if (item >= total) break;
+        if (tid == 0) next = atomicAdd(occ.list + 1, 1u);
+        const uint32_t e = __ldg(occ.list + 2 + item / per);
+        const int64_t pl = e / (uint32_t)occ.NT;
+        const int tcol = (int)(e - (uint32_t)pl * occ.NT);
+        const int x0 = (tcol << occ.tshift) + (int)(item % per) * COLS;
+        for (int ty = tid; ty < occ.NT; ty += kThreads)
+            s_live[ty] = (uint8_t)((occ.tile[(pl * occ.NT + ty) * occ.words + (tcol >> 5)] >> (tcol & 31)) & 1u);
+        __syncthreads();
+        float2* col = grids + (size_t)pl * N * N + x0 + c;
+        float2 a[16], x[16];
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+            const int row = b + T * t2;
+            a[t2] = (!in_mask || s_live[row >> occ.tshift]) ? __ldcs(col + (size_t)row * N) : make_float2(0.f, 0.f);
+        }
+        transform<LOG2N, INV>(a, buf, b, tw, x);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int row = b + T * j;
+            if (!out_mask || s_live[row >> occ.tshift]) __stcs(col + (size_t)row * N, x[j]);
+        }
     }
 }
 
@@ -653,9 +740,10 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 // SPLIT k + r, to which it applies the phase screen and the plane sum of
 // Eq. 2 exactly as k_rows_phase_reduce does (Horner blocks of kHornerBlock
 // planes, exact phasor at each block's end).  The twiddle of y_r is
-// e^(2 pi i r b / N) (per thread, from a table rounded from FP64) times
 // e^(2 pi i r t2 / (16 SPLIT)) (a constant of the unrolled code,
-// n = b + (M/16) t2).  With pruning, the
+// n = b + (M/16) t2) times e^(2 pi i r b / N) (per thread, from a table
+// rounded from FP64), which is the same for the thread's 16 inputs and is
+// applied with the first stage's output twiddles (radix16_first_scaled).  With pruning, the
 // unreached tile columns of the row are not read; the prefetch of the next
 // row holds one value per position n (its first reached part t), and the
 // other reached parts of the same position (none on a centred uv coverage
@@ -768,7 +856,7 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
 #pragma unroll
             for (int t2 = 0; t2 < 16; ++t2) {
                 const int first = (int)((pf_first >> (2 * t2)) & 3u);
-                v[t2] = twiddle64<true>(cmulf(quarter(v[t2], (R * first) & 3), wb), R * t2);
+                v[t2] = twiddle64<true>(quarter(v[t2], (R * first) & 3), R * t2);
             }
             return;
         }
@@ -784,7 +872,7 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                     const float2 u = __ldcs(pf_row + b + T * t2 + t * M);
                     y = cadd(y, twiddle_const<true>(u, R * t, SPLIT));
                 }
-            v[t2] = R == 0 ? y : twiddle64<true>(cmulf(y, wb), R * t2);
+            v[t2] = R == 0 ? y : twiddle64<true>(y, R * t2);
         }
     };
     auto combine = [&](float2 (&v)[16]) {
@@ -810,7 +898,12 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                 }
             } else {
                 combine(a);
-                radix16_out<LOG2SUB, true>(a, b, 0, buf, tw);
+                // e^(2 pi i r b / N), common to the thread's inputs, enters
+                // with the first stage's twiddles
+                if (par == 0)
+                    radix16_out<LOG2SUB, true>(a, b, 0, buf, tw);
+                else
+                    radix16_first_scaled<LOG2SUB>(a, b, buf, tw, wb);
                 const int rn = next_row(r + 1);
                 if (rn < n_rows) load_row(rn, a);
                 r = rn;
@@ -1045,13 +1138,44 @@ __global__ void k_occupancy(const uint32_t* __restrict__ offsets, int c0, int nc
     }
 }
 
+// The reached tile columns (col bytes set) appended to list[2 ..], their
+// count in list[0] (zeroed beforehand); warp-aggregated atomics, so the order
+// is arbitrary (each column's transform does not depend on it).
+__global__ void k_col_list(const uint8_t* __restrict__ col, int64_t n, uint32_t* __restrict__ list) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool on = i < n && col[i] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (m == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(list, (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (on) list[2 + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
 template <int LOG2N, bool INV>
 cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, const Occupancy& occ,
                         cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     constexpr int cols = kCols<LOG2N>;
-    auto fn = k_fft_columns<LOG2N, cols, INV>;
     const size_t smem = (size_t)(Sh::kTw + cols * (Sh::kArray + 16 / cols)) * sizeof(float2);
+    if (occ.list != nullptr && occ.tile != nullptr) {
+        // persistent CTAs over the listed tile columns; the work counter
+        // list[1] starts at zero for every pass
+        auto fl = k_fft_columns_list<LOG2N, cols, INV>;
+        cudaError_t e = cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, cols * Sh::T, smem)) != cudaSuccess)
+            return e;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        if ((e = cudaMemsetAsync(occ.list + 1, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
+        fl<<<(unsigned)(per_sm * sms), cols * Sh::T, smem, st>>>(grids, twid, occ);
+        return cudaGetLastError();
+    }
+    auto fn = k_fft_columns<LOG2N, cols, INV>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int64_t p0 = 0; p0 < n_planes; p0 += 65535) {
@@ -1300,7 +1424,8 @@ cudaError_t launch_pixel_phase(const PhaseParams& P0, const float* inv_taper, ui
 }
 
 cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
-                             uint8_t* col, uint8_t* plane, uint32_t* tile, cudaStream_t st, int* launches) {
+                             uint8_t* col, uint8_t* plane, uint32_t* tile, uint32_t* list, cudaStream_t st,
+                             int* launches) {
     const int64_t n = (int64_t)nc * nk * NT * NT;
     if (n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(plane, 0, (size_t)nc * nk, st);
@@ -1311,6 +1436,13 @@ cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, in
                                                              plane, tile);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*launches;
+    if (list != nullptr) {
+        const int64_t nl = (int64_t)nc * nk * NT;
+        if ((e = cudaMemsetAsync(list, 0, 2 * sizeof(uint32_t), st)) != cudaSuccess) return e;
+        k_col_list<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(col, nl, list);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        ++*launches;
+    }
     return cudaSuccess;
 }
 

@@ -270,6 +270,11 @@ struct Occupancy {
     const uint8_t* plane = nullptr;
     const uint32_t* tile = nullptr;
     int tshift = 0, NT = 1, words = 1;
+    // the reached tile columns of the launch as a list: list[0] entries
+    // col index p * NT + tx in list[2 ..], list[1] the column pass's work
+    // counter (zeroed with the list); nullptr: the column pass launches one
+    // CTA per column and skips the unreached ones
+    uint32_t* list = nullptr;
     // column pass: false -- the input's unreached tiles are zero (imaging);
     // true -- the input is dense and only the reached tiles of the output are
     // written (prediction)
@@ -278,8 +283,8 @@ struct Occupancy {
 // The three masks of the launch's planes (channels [c0, c0 + nc), stored
 // planes [k0, k0 + nk)) from the bin offsets of the plan's binning.
 cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, int nk, int Nw_store, int NT,
-                             uint8_t* col, uint8_t* plane, uint32_t* tile, cudaStream_t stream,
-                             int* launches);
+                             uint8_t* col, uint8_t* plane, uint32_t* tile, uint32_t* list,
+                             cudaStream_t stream, int* launches);
 // Pass 1 alone (the inverse DFT down every column), in place; with occ, the
 // unreached column tiles are skipped and the unreached tiles of the others
 // read as zeros.

@@ -42,13 +42,18 @@ def init_params(hidden: int, seed: int, zero_output: bool = True) -> np.ndarray:
 
 
 def training_field(seed: int, N: int, margin: int = 4, n_range=(1, 50),
-                   flux=(0.01, 1.0)) -> np.ndarray:
+                   flux=(0.01, 1.0), inner: float | None = None) -> np.ndarray:
     """A point-source field: 1-50 sources at continuous positions anywhere in
     the image (margin pixels from the edge; positions in pixels, rounded to
-    float32, which the library takes), fluxes log-uniform.  [ns, 3] (p, q, A)."""
+    float32, which the library takes), fluxes log-uniform.  With inner, the
+    sources lie in the central square of half-width inner * N instead (the
+    square the probes are taken in).  [ns, 3] (p, q, A)."""
     g = np.random.Generator(np.random.Philox(key=[seed, 0x46494C44]))
     ns = int(g.integers(n_range[0], n_range[1] + 1))
-    pq = margin + g.random((ns, 2)) * (N - 2 * margin)
+    lo, hi = margin, N - margin
+    if inner is not None:
+        lo, hi = N // 2 - int(inner * N) + margin, N // 2 + int(inner * N) - margin
+    pq = lo + g.random((ns, 2)) * (hi - lo)
     pq = pq.astype(np.float32).astype(np.float64)
     a = np.exp(math.log(flux[0]) + g.random(ns) * (math.log(flux[1]) - math.log(flux[0])))
     return np.concatenate([pq, a[:, None]], axis=1)
@@ -76,12 +81,13 @@ def field_probes(seed: int, N: int, src: np.ndarray, count: int = 64, inner: flo
     return np.concatenate([near, fixed, rest]).astype(np.int32)
 
 
-def heldout_losses(learn: rick.Learn, table, n: int, seed0: int, loss, per_field: bool = False):
+def heldout_losses(learn: rick.Learn, table, n: int, seed0: int, loss, per_field: bool = False,
+                   inner: float | None = None):
     """Loss of n held-out fields imaged with `table` (mean and median, or the
     losses themselves)."""
     out = []
     for s in range(n):
-        src = training_field(seed0 + s, learn.cfg.N)
+        src = training_field(seed0 + s, learn.cfg.N, inner=inner)
         learn.field_grad(table, src, field_probes(seed0 + s, learn.cfg.N, src), None, loss)
         out.append(float(loss.item()))
     if per_field:
@@ -131,11 +137,11 @@ class LearnedKernel:
 
     def train(self, learn: rick.Learn, updates: int, lr: float = 1e-5, batch: int = 8,
               N: int | None = None, log_every: int = 0, field_seed0: int = 1_000_000,
-              lr_final: float | None = None):
+              lr_final: float | None = None, inner: float | None = None):
         """``updates`` Adam steps, each on the mean gradient of ``batch`` fields
         (field seeds field_seed0 + 0, 1, 2, ... in order, so a resumed run
-        sees the same sequence).  The learning rate decays on a cosine from lr
-        to lr_final (default lr / 10)."""
+        sees the same sequence; ``inner`` as for training_field).  The
+        learning rate decays on a cosine from lr to lr_final (default lr / 10)."""
         N = N or learn.cfg.N
         lr_final = lr / 10 if lr_final is None else lr_final
         last = []
@@ -144,7 +150,7 @@ class LearnedKernel:
             total = 0.0
             for b in range(batch):
                 seed = field_seed0 + self.state.step
-                src = training_field(seed, N)
+                src = training_field(seed, N, inner=inner)
                 learn.field_grad(self.table, src, field_probes(seed, N, src), self.table_grad,
                                  self.loss, accumulate=b > 0, grad_scale=1.0 / batch)
                 self.state.step += 1
@@ -157,15 +163,17 @@ class LearnedKernel:
                 self.state.losses.append(("field", self.state.step, total / batch))
         return last
 
-    def heldout_loss(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000):
+    def heldout_loss(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000,
+                     inner: float | None = None):
         """Mean and median loss over n held-out fields (seeds never trained on)."""
         self.bake()
-        return heldout_losses(learn, self.table, n, seed0, self.loss)
+        return heldout_losses(learn, self.table, n, seed0, self.loss, inner=inner)
 
-    def losses(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000) -> np.ndarray:
+    def losses(self, learn: rick.Learn, n: int = 32, seed0: int = 9_000_000,
+               inner: float | None = None) -> np.ndarray:
         """The loss of each of n held-out fields (seeds never trained on)."""
         self.bake()
-        return heldout_losses(learn, self.table, n, seed0, self.loss, per_field=True)
+        return heldout_losses(learn, self.table, n, seed0, self.loss, per_field=True, inner=inner)
 
     # ---- checkpoint / resume ------------------------------------------------
     def save(self, path: str):

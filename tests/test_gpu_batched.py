@@ -69,8 +69,8 @@ def test_per_channel_launches_equal_one_batched_launch(rk, small_lofar):
 
 # kernels of this library per captured graph: place, 3 scan kernels, scatter,
 # tile schedule, grid, then the phase kernel after cuFFT's own kernels, or the
-# own transform's occupancy, column and fused row kernels
-@pytest.mark.parametrize("fft,per_graph", [("cufft", 8), ("own", 10)])
+# own transform's occupancy and tile-column list, column and fused row kernels
+@pytest.mark.parametrize("fft,per_graph", [("cufft", 8), ("own", 11)])
 def test_graph_replay_matches_eager_and_follows_new_data(rk, small_lofar, fft, per_graph):
     import torch
     img, obs = small_lofar
