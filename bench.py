@@ -130,6 +130,12 @@ GRID_COUNTERS = {
 }
 
 
+# DRAM bytes per launch of the fused split row pass on the default line: the
+# mean over the 48 launches of one step (ncu, 1 pass each; the command is in
+# the profile named in the line).
+ROWS_TRAFFIC_PER_LAUNCH = 15.092e9
+
+
 def gridder_ceilings(n_grid, ms, key):
     """The gridder's rate against its shared-memory and issue ceilings: the
     per-visibility counts of an ncu capture times the visibilities gridded per
@@ -953,8 +959,16 @@ def run_large_line(args):
                            "avg_ms": st["rows_phase"] / rows_launches,
                            "flops": flops["rows_phase"] / rows_launches},
             "hbm_achieved_gbs": gbs["rows_phase"], "hbm_frac": gbs["rows_phase"] / hbm,
-            "traffic": None,
-            "traffic_note": "full launch not captured; the small 16384^2 case (1 channel, 2 stored planes): 6.06 GB DRAM per launch against 2.61 GB algorithmic, the excess the per-pixel phase and taper tables (profiles/kernels_meerkat_large_small_16384sq_4w_1ch.md)"}
+            # ncu DRAM bytes of this kernel, averaged over the 48 launches of one
+            # step of this line (grid groups of 3 channels), 1 pass each
+            "traffic": ROWS_TRAFFIC_PER_LAUNCH if gc == 3 and len(blocks) == 8 else None,
+            "traffic_unit": "bytes per launch",
+            "traffic_algorithmic": stage_bytes["rows_phase"] / rows_launches,
+            "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of every launch of one timed "
+                            "step (12.26 GB read, 2.83 GB written per launch on average); above the "
+                            "algorithmic bytes by the per-pixel phase and taper tables (12 B per image "
+                            "pixel, read at the first plane and at each Horner block end) -- "
+                            "profiles/kernels_meerkat_large_small_16384sq_4w_1ch.md"}
 
     # image error: the same plan's path on a 1 % row subsample of the lowest
     # and highest channels, against the oracle's per-visibility O1 at 64 pixels

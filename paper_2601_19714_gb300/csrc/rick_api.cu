@@ -1122,14 +1122,15 @@ rick_status ensure_group_grid(rick_plan* P) {
     return RICK_OK;
 }
 
-rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan_scale,
-                             const float* vis, const float* weight, const uint8_t* flag,
-                             int64_t nrow, float* image_real, float* image_complex,
-                             double* weight_sum, int64_t* counts, cudaStream_t st) {
+// The plane and channel groups of the binned visibilities, gridded,
+// transformed and reduced into image_real (device).  host_out (optional):
+// each channel group's images are copied to host_out on the plan's copy
+// stream as soon as the group's last plane group is reduced, overlapped with
+// the next group's gridding and transforms; the caller synchronises the copy
+// stream.
+rick_status image_groups_impl(rick_plan* P, float* image_real, float* image_complex, double* ws,
+                              cudaStream_t st, float* host_out = nullptr) {
     const rick_config& c = P->cfg;
-    RK_ARG(image_real != nullptr, "image_real is NULL");
-    double* ws = weight_sum ? weight_sum : P->d_wsum;
-    RK_TRY(bin_impl(P, uvw, chan_scale, vis, weight, flag, nrow, ws, counts, st));
     int gc, gk;
     plan_groups(P, &gc, &gk);
     const size_t NN = (size_t)c.N * c.N;
@@ -1144,8 +1145,26 @@ rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan
                                   image_complex ? image_complex + 2 * (size_t)c0 * NN : nullptr, st,
                                   RICK_GRIDDED_BY_PLAN));
         }
+        if (host_out) {
+            // the wait takes the event's latest record, so one event serves every group
+            RK_CUDA(cudaEventRecord(P->chunk_done[0], st));
+            RK_CUDA(cudaStreamWaitEvent(P->copy_stream, P->chunk_done[0], 0));
+            RK_CUDA(cudaMemcpyAsync(host_out + (size_t)c0 * NN, image_real + (size_t)c0 * NN,
+                                    (size_t)(c1 - c0) * NN * sizeof(float), cudaMemcpyDeviceToHost,
+                                    P->copy_stream));
+        }
     }
     return RICK_OK;
+}
+
+rick_status dirty_image_impl(rick_plan* P, const double* uvw, const double* chan_scale,
+                             const float* vis, const float* weight, const uint8_t* flag,
+                             int64_t nrow, float* image_real, float* image_complex,
+                             double* weight_sum, int64_t* counts, cudaStream_t st) {
+    RK_ARG(image_real != nullptr, "image_real is NULL");
+    double* ws = weight_sum ? weight_sum : P->d_wsum;
+    RK_TRY(bin_impl(P, uvw, chan_scale, vis, weight, flag, nrow, ws, counts, st));
+    return image_groups_impl(P, image_real, image_complex, ws, st);
 }
 
 rick_status predict_impl(rick_plan* P, const double* uvw, const double* chan_scale,
@@ -1410,7 +1429,7 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
     const bool whole = gc == c.n_channels && gk == plan->planes && c.n_channels > 1;
     // upload overlapped with placement: natural weighting (the other weightings
     // need every visibility's density before any placement)
-    const bool overlap_in = whole && R > 0 && c.weighting == RICK_WEIGHT_NATURAL;
+    const bool overlap_in = R > 0 && c.weighting == RICK_WEIGHT_NATURAL;
     if (R) RK_ARG(uvw && chan_scale && vis && weight, "uvw, chan_scale, vis and weight are required");
     if (R && !overlap_in) {
         RK_CUDA(cudaMemcpyAsync(d_uvw, uvw, R * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1451,9 +1470,16 @@ rick_status rick_dirty_image_host(rick_plan* plan, const double* uvw, const doub
         }
         RK_CUDA(cudaStreamSynchronize(plan->copy_stream));
     } else {
-        RK_TRY(dirty_image_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, plan->d_img, nullptr, d_ws,
-                                d_cnt, st));
-        RK_CUDA(cudaMemcpyAsync(image_real, plan->d_img, img_bytes, cudaMemcpyDeviceToHost, st));
+        // streamed groups: each channel group's images go to the host while the
+        // next group is gridded and transformed
+        if (!plan->copy_stream) RK_CUDA(cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking));
+        if (!plan->chunk_done[0]) RK_CUDA(cudaEventCreateWithFlags(&plan->chunk_done[0], cudaEventDisableTiming));
+        rick_status s = overlap_in ? bin_from_host(plan, uvw, chan_scale, vis, weight, flag, nrow, d_uvw, d_sc,
+                                                   d_vis, d_w, d_f, d_ws, d_cnt, st)
+                                   : bin_impl(plan, d_uvw, d_sc, d_vis, d_w, d_f, nrow, d_ws, d_cnt, st);
+        if (s == RICK_OK) s = image_groups_impl(plan, plan->d_img, nullptr, d_ws, st, image_real);
+        RK_CUDA(cudaStreamSynchronize(plan->copy_stream));   // also after a failure: no copy left in flight
+        RK_TRY(s);
     }
     if (weight_sum)
         RK_CUDA(cudaMemcpyAsync(weight_sum, d_ws, C * sizeof(double), cudaMemcpyDeviceToHost, st));

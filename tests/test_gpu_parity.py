@@ -274,6 +274,7 @@ def test_plane_group_streaming_matches_single_pass(rk, orc):
 @pytest.mark.parametrize("nchan,kw,n_ant,n_steps", [(2, dict(fft_impl="cufft"), 8, 40), (5, dict(hermitian_fold=True), 8, 40),
                                                    (5, dict(fft_impl="own"), 8, 40),
                                                    (3, dict(grid_budget_bytes=2 * 256 * 256 * 8), 8, 40),
+                                                   (3, dict(grid_budget_bytes=4 * 256 * 256 * 8, fft_impl="own"), 8, 40),
                                                    (3, dict(weighting="uniform"), 8, 40),
                                                    (2, dict(fft_impl="own"), 7, 1)])
 def test_host_entry_point_matches_device_path(rk, orc, nchan, kw, n_ant, n_steps):
@@ -281,7 +282,8 @@ def test_host_entry_point_matches_device_path(rk, orc, nchan, kw, n_ant, n_steps
     uploaded in chunks, each placed as it arrives (natural weighting; uniform
     weighting uploads everything first), and the channels are transformed and
     downloaded in chunks (uneven for 5 channels); with a plane budget it
-    streams plane groups; all equal the device path.  One time step of 7
+    streams plane groups, and with a one-channel budget it downloads each
+    channel's image while the next is made; all equal the device path.  One time step of 7
     antennas (21 rows) leaves row chunks of uneven size."""
     img, obs = meerkat(5, n_ant=n_ant, n_steps=n_steps, nchan=nchan, N=256, Nw=4, n_src=8)
     plan = rk.Plan(plan_config(img, nchan, **kw))
