@@ -593,7 +593,8 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
-    float2* zrot = buf + Sh::kArray;                             // z = e^(-2 pi i dt) per pixel
+    float2* turn256 = buf + Sh::kArray;                          // e^(2 pi i j / 256)
+    float2* zrot = turn256 + 256;                                // z = e^(-2 pi i dt) per pixel
     // the channel's finished blocks per pixel: Re of the phased sums
     float* part = reinterpret_cast<float*>(zrot + N);
     // image row q (blockIdx.x) is row q + off of the mesh; mesh pixel pm is
@@ -604,6 +605,7 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
     const float* scl = pix_scale + (size_t)q * Ni;               // per-pixel scale (read once per channel)
     const uint2* turns = pix_turns + (size_t)q * Ni;
     load_tables<LOG2N>(twid, tw, b, T);
+    for (int j = b; j < 256; j += T) turn256[j] = __ldg(twid + Sh::kTw + j);
 #pragma unroll 4
     for (int j = 0; j < 16; ++j) {
         const int pm = b + T * j, p = pm - off;
@@ -698,10 +700,17 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
                 const int pm = b + T * j, p = pm - off;
                 const bool in_img = !PADDED || (unsigned)p < (unsigned)Ni;
                 const int pc = in_img ? p : 0;
+                // e^(2 pi i t) for t = tk 2^-32 turns, table-driven: the
+                // nearest 1/256 of a turn from the table, the rest
+                // (|theta| <= pi / 256) from its Taylor series to theta^3
                 const uint2 ph = __ldg(&turns[pc]);
                 const uint32_t tk = ph.x + k_end * ph.y;
-                float sn, cs;
-                sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                const uint32_t j8 = (tk + 0x800000u) >> 24;
+                const float th = (float)(int32_t)(tk - (j8 << 24)) * 1.46291807926715968e-9f;  // 2 pi 2^-32
+                const float t2 = th * th;
+                const float c = fmaf(-0.5f, t2, 1.0f), sg = th * fmaf(t2, -0.16666667f, 1.0f);
+                const float2 w = turn256[j8 & 255u];
+                const float cs = fmaf(w.x, c, -w.y * sg), sn = fmaf(w.y, c, w.x * sg);
                 const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
                 const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
                 acc[j] = make_float2(0.f, 0.f);
@@ -748,7 +757,12 @@ k_rows_phase_reduce(PhaseParams P, const float2* __restrict__ grids, const doubl
 // row holds one value per position n (its first reached part t), and the
 // other reached parts of the same position (none on a centred uv coverage
 // narrower than M) are read when the row is consumed.  Pruning also cuts the
-// arithmetic: N log2(M) butterfly work per row instead of N log2(N).
+// arithmetic: N log2(M) butterfly work per row instead of N log2(N).  Unlike
+// the unsplit pass, an unreached plane rotates acc only once its block has a
+// reached plane (before that acc is zero and stays zero), and a block with no
+// reached plane takes no phasor -- the zeros the unpruned pass computes, so
+// the pruned result is still the unpruned one.  (In the unsplit pass the same
+// change measured 9 % slower at 4096^2 and is not made.)
 template <int LOG2SUB, int SPLIT, bool COMPLEX_OUT, bool PADDED>
 __global__ void __launch_bounds__((1 << LOG2SUB) / 16, LOG2SUB <= 12 ? 2 : 1)
 k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const double* __restrict__ wsum,
@@ -763,7 +777,8 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     extern __shared__ __align__(16) float2 fsm[];
     float2* tw = fsm;
     float2* buf = fsm + Sh::kTw;
-    float2* zrot = buf + Sh::kArray;                             // z per owned pixel
+    float2* turn256 = buf + Sh::kArray;                          // e^(2 pi i j / 256)
+    float2* zrot = turn256 + 256;                                // z per owned pixel
     float* part = reinterpret_cast<float*>(zrot + M);
     // image row q is mesh row q + off; mesh pixel SPLIT k + r is image pixel
     // SPLIT k + r - off (a padded mesh keeps its central Ni x Ni; without
@@ -773,6 +788,7 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     const float* scl = pix_scale + (size_t)q * Ni;
     const uint2* turns = pix_turns + (size_t)q * Ni;
     load_tables<LOG2SUB>(twid_sub, tw, b, T);
+    for (int j = b; j < 256; j += T) turn256[j] = __ldg(twid_sub + Sh::kTw + SPLIT * T + j);
 #pragma unroll 4
     for (int j = 0; j < 16; ++j) {
         const int k = b + T * j, p = SPLIT * k + par - off;
@@ -852,11 +868,12 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     auto combine_r = [&](float2 (&v)[16], auto rc) {
         constexpr int R = decltype(rc)::value;
         if (pf_single) {
-            if (R == 0) return;   // y_0[n] = x[n + first M]
+            if constexpr (R != 0) {   // (y_0[n] = x[n + first M])
 #pragma unroll
-            for (int t2 = 0; t2 < 16; ++t2) {
-                const int first = (int)((pf_first >> (2 * t2)) & 3u);
-                v[t2] = twiddle64<true>(quarter(v[t2], (R * first) & 3), R * t2);
+                for (int t2 = 0; t2 < 16; ++t2) {
+                    const int first = (int)((pf_first >> (2 * t2)) & 3u);
+                    v[t2] = twiddle64<true>(quarter(v[t2], (R * first) & 3), R * t2);
+                }
             }
             return;
         }
@@ -889,12 +906,19 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
         float2 acc[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
+        // filled: the current block has a reached plane; any: the channel has
+        bool filled = false, any = false;
         for (int kk = 0; kk < P.nk; ++kk) {
             if (cc * P.nk + kk != r) {   // an unreached plane: F_k = 0
+                // acc z + 0; while the block has no reached plane acc is zero
+                // and stays zero, so there is nothing to rotate
+                if (filled) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float2 z = zrot[b + T * j];
-                    acc[j] = make_float2(fmaf(acc[j].x, z.x, -acc[j].y * z.y), fmaf(acc[j].x, z.y, acc[j].y * z.x));
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 z = zrot[b + T * j];
+                        acc[j] = make_float2(fmaf(acc[j].x, z.x, -acc[j].y * z.y),
+                                             fmaf(acc[j].x, z.y, acc[j].y * z.x));
+                    }
                 }
             } else {
                 combine(a);
@@ -917,9 +941,15 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                     acc[j] = make_float2(fmaf(acc[j].x, z.x, fmaf(-acc[j].y, z.y, x[j].x)),
                                          fmaf(acc[j].x, z.y, fmaf(acc[j].y, z.x, x[j].y)));
                 }
+                filled = any = true;
             }
             const bool last = kk == P.nk - 1;
             if (kk % kHornerBlock != kHornerBlock - 1 && !last) continue;
+            // a block without a reached plane adds zero: nothing to do, except
+            // at the channel's end, where the image takes the earlier blocks
+            const bool empty = !filled;
+            filled = false;
+            if (empty && (COMPLEX_OUT || !last || !any)) continue;
             const uint32_t k_end = (uint32_t)(P.k_first + kk);
             float inv_ws = 0.f;
             if (last || COMPLEX_OUT) {
@@ -933,10 +963,22 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
                 const int k = b + T * j, p = SPLIT * k + par - off;
                 const bool in_img = !PADDED || (unsigned)p < (unsigned)Ni;
                 const int pc = in_img ? p : 0;
-                const uint2 ph = __ldg(&turns[pc]);
-                const uint32_t tk = ph.x + k_end * ph.y;
-                float sn, cs;
-                sincospif((float)(int32_t)tk * 4.656612873077392578125e-10f /* 2^-31 */, &sn, &cs);
+                float sn = 0.f, cs = 1.f;   // acc is zero in an empty block
+                if (!empty) {
+                    // e^(2 pi i t) for t = tk 2^-32 turns, table-driven: the
+                    // nearest 1/256 of a turn from the table, the rest
+                    // (|theta| <= pi / 256) from its Taylor series to theta^3
+                    // (truncation below 1e-9)
+                    const uint2 ph = __ldg(&turns[pc]);
+                    const uint32_t tk = ph.x + k_end * ph.y;
+                    const uint32_t j8 = (tk + 0x800000u) >> 24;
+                    const float th = (float)(int32_t)(tk - (j8 << 24)) * 1.46291807926715968e-9f;  // 2 pi 2^-32
+                    const float t2 = th * th;
+                    const float c = fmaf(-0.5f, t2, 1.0f), s = th * fmaf(t2, -0.16666667f, 1.0f);
+                    const float2 w = turn256[j8 & 255u];
+                    cs = fmaf(w.x, c, -w.y * s);
+                    sn = fmaf(w.y, c, w.x * s);
+                }
                 const float re = fmaf(acc[j].x, cs, -acc[j].y * sn);
                 const float im = fmaf(acc[j].x, sn, acc[j].y * cs);
                 acc[j] = make_float2(0.f, 0.f);
@@ -1207,8 +1249,9 @@ cudaError_t fused_one(const PhaseParams& P, const float2* grids, const double* w
                       const Occupancy& occ, cudaStream_t st) {
     using Sh = Shape<LOG2N>;
     auto fn = k_rows_phase_reduce<LOG2N, CPLX, PADDED>;
-    // tables and the transform array, then per pixel z and (real output) the partial sum
-    const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
+    // tables, the transform array and the 256 phasors, then per pixel z and
+    // (real output) the partial sum
+    const size_t smem = (size_t)(Sh::kTw + Sh::kArray + 256) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1225,7 +1268,7 @@ cudaError_t fused_split(const PhaseParams& P, const float2* grids, const double*
     constexpr int kSub = 12, kSplit = 4;
     using Sh = Shape<kSub>;
     auto fn = k_rows_phase_reduce_split<kSub, kSplit, CPLX, PADDED>;
-    const size_t smem = (size_t)(Sh::kTw + Sh::kArray) * sizeof(float2) +
+    const size_t smem = (size_t)(Sh::kTw + Sh::kArray + 256) * sizeof(float2) +
                         (size_t)Sh::N * (sizeof(float2) + (CPLX ? 0 : 1) * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -1296,10 +1339,20 @@ void append_twiddles(int N, std::vector<float2>& out) {
 }  // namespace
 
 void fft_twiddles(int N, std::vector<float2>& out) {
+    // N < 16384: the stage tables, then e^(2 pi i j / 256), j < 256.
     // N = 16384: the 4096-point tables of the split fused row pass follow,
-    // then its split twiddles [r T + b] = e^(+2 pi i r b / N), r < 4, b < T = 256
+    // then its split twiddles [r T + b] = e^(+2 pi i r b / N), r < 4, b < T = 256,
+    // then e^(2 pi i j / 256), j < 256
     out.clear();
     append_twiddles(N, out);
+    if (log2_exact(N) < 14) {
+        // N < 16384: the 256 phasors e^(2 pi i j / 256) of the fused row pass's
+        // block-end phase screen follow the stage tables
+        for (int j = 0; j < 256; ++j) {
+            const double a = 6.283185307179586476925 * (double)j / 256.0;
+            out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+    }
     if (log2_exact(N) == 14) {
         append_twiddles(4096, out);
         const double two_pi = 6.283185307179586476925;
@@ -1308,6 +1361,11 @@ void fft_twiddles(int N, std::vector<float2>& out) {
                 const double a = two_pi * (double)(r * b) / N;
                 out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
             }
+        // and the 256 phasors e^(2 pi i j / 256) of its block-end phase screen
+        for (int j = 0; j < 256; ++j) {
+            const double a = two_pi * (double)j / 256.0;
+            out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
     }
 }
 
