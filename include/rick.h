@@ -181,7 +181,7 @@ typedef struct rick_plan rick_plan;
 /* ---- plan ------------------------------------------------------------ */
 
 /* Validate cfg, build the kernel and taper tables (FP64 on the host) and the
- * cuFFT plans -- or, with the library's own transform (fft_impl 1), its
+ * cuFFT plans -- or, with the library's own transform (RICK_FFT_OWN), its
  * twiddle tables, the per-pixel table of the fused row passes (the phase of
  * stored plane 0 and the plane step as Q0.32 turns, and the imaging and model
  * scales: 16 bytes per image pixel, computed once in FP64 on the device) and
@@ -433,7 +433,9 @@ rick_status rick_model_to_wplanes(rick_plan* plan, const float* image_real, int3
 rick_status rick_fft_wplanes_forward(rick_plan* plan, float* grids, int64_t n_planes, void* stream);
 
 /* rick_model_to_wplanes followed by rick_fft_wplanes_forward, fused, with the
- * library's own transform (RICK_ERR_UNSUPPORTED with cuFFT): each model row
+ * library's own transform on a mesh of 256 to 8192 (RICK_ERR_UNSUPPORTED with
+ * cuFFT or a 16384 mesh, where rick_predict forms the model planes and runs
+ * the plain transform instead): each model row
  * M_k[q][.] is formed in registers and transformed along the row, so the
  * model planes are never written; then the column pass.  grids receives the
  * transformed planes, up to FP32 rounding those of the two calls.  flags:
