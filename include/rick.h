@@ -316,8 +316,13 @@ rick_status rick_fft_phase_correct_reduce(rick_plan* plan, float* grids, int32_t
  * transform, as separate calls (RICK_ERR_UNSUPPORTED with cuFFT):
  * rick_fft_wplanes_columns: the length-N inverse DFT down every column of the
  *   planes [plane_begin, plane_end) of channels [chan_begin, chan_end)
- *   (grids laid out as for rick_grid_binned), in place (pass 1);
+ *   (grids laid out as for rick_grid_binned), in place (pass 1).  At N = 16384
+ *   with tiles of 32 or more it runs as two four-step passes (whole 256-byte
+ *   row segments) and leaves each plane's rows in the four-step order: the
+ *   transform's row m is stored at row 128 (m mod 128) + m / 128 (as does
+ *   rick_fft_phase_correct_reduce with grids);
  * rick_rows_phase_correct_reduce: the row DFTs of column-transformed planes
+ *   (at N = 16384 with tiles of 32 or more, rows in the four-step order above)
  *   fused with the phase screen and reduction, arguments as for
  *   rick_phase_correct_reduce (pass 2; one launch; grids is only read).
  * flags as for rick_fft_phase_correct_reduce (with RICK_GRIDDED_BY_PLAN each

@@ -838,6 +838,11 @@ rick_status fft_impl(rick_plan* P, float* grids, int64_t n_planes, cudaStream_t 
 // Phase-screen parameters of planes [k0, k1) (stored indices) of channels
 // [c0, c1): plane k is centred at w_min + (k - off + 1/2) dw, off = Sw/2 with
 // a w-kernel (its extended plane set starts below w_min), else 0.
+// At N = 16384 with tiles of at least 32, the column pass of the imaging calls
+// is the four-step pair (two passes of whole 256-byte row segments) and
+// leaves the rows in the four-step order, which the fused row pass reads.
+bool fourstep_layout(const rick_plan* P) { return P->own_fft && P->Ng == 16384 && P->T >= 32; }
+
 PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
     const rick_config& c = P->cfg;
     PhaseParams pp;
@@ -851,6 +856,7 @@ PhaseParams phase_params(const rick_plan* P, int c0, int c1, int k0, int k1) {
     const int off = c.w_support >= 2 ? c.w_support / 2 : 0;
     pp.w_first = c.n_wplanes > 1 ? c.w_min + (k0 - off + 0.5) * P->dw : 0.5 * (c.w_min + c.w_max);
     pp.k_first = k0;
+    pp.rows_four = fourstep_layout(P) ? 1 : 0;
     pp.precision = c.precision;
     pp.w_support = c.w_support >= 2 && c.n_wplanes > 1 ? c.w_support : 0;
     pp.w_beta = c.w_kernel_param;
@@ -938,7 +944,7 @@ rick_status columns_impl(rick_plan* P, float* grids, int c0, int c1, int k0, int
     int launches = 0;
     rick_status s = check_launch(launch_fft_columns(reinterpret_cast<float2*>(grids),
                                                     (int64_t)(c1 - c0) * (k1 - k0), P->Ng, true,
-                                                    P->d_twid, occ, st, &launches),
+                                                    P->d_twid, occ, st, &launches, fourstep_layout(P)),
                                  "FFT column kernel");
     P->launches += launches;
     return s;

@@ -244,7 +244,8 @@ struct Shape {
         return o;
     }
     static constexpr int kTw = stage_off(kTwStages);  // twiddle table entries
-    static_assert(LOG2N >= 8 && LOG2N <= 14, "256 <= N <= 16384");
+    // 128 (LOG2N = 7) only for the four-step column pass at N = 16384
+    static_assert(LOG2N >= 7 && LOG2N <= 14, "128 <= N <= 16384");
 };
 
 // Radix-16 stage s (M = 16^s, not the last stage): a holds the butterfly's
@@ -489,6 +490,97 @@ k_fft_columns_list(float2* __restrict__ grids, const float2* __restrict__ twid, 
         for (int j = 0; j < 16; ++j) {
             const int row = b + T * j;
             if (!out_mask || s_live[row >> occ.tshift]) __stcs(col + (size_t)row * N, x[j]);
+        }
+    }
+}
+
+// The column pass at N = 16384 (tiles of at least 32 cells) in two four-step
+// passes over groups of 32 adjacent columns, so that every global access is a
+// whole 256-byte row segment of a group (one 16384-point column per CTA
+// moves 8-byte pieces, one sector per row).  With L = 128 and rows
+// n = n1 + L n2, output k = k2 + L k1:
+//   pass A: for each n1, Y[n1 + L k2] = W_N^(n1 k2) sum_{n2} x[n1 + L n2] W_L^(n2 k2),
+//   pass B: for each k2, X[k2 + L k1] = sum_{n1} Y[n1 + L k2] W_L^(n1 k1),
+// both in place: pass A over the rows {n1 + L n2} of an n1, pass B over the
+// contiguous block {L k2 + n1} of a k2, whose result X[k2 + L k1] it stores
+// at row L k2 + k1 -- the column-transformed plane with its rows in the
+// four-step order, which the fused row pass reads as such (mesh row m at
+// row L (m mod L) + m / L).  W_N^m, m = n1 k2 < N, is the product of two
+// 128-entry tables (e^(2 pi i mh / L) and e^(2 pi i ml / N), m = L mh + ml).
+// A CTA of 256 threads holds the 32 columns' 128-point transforms (8 threads
+// each, interleaved: thread (b, c) = 32 b + c, so a warp is one row of the
+// group); persistent CTAs take (group, n1) or (group, k2) items in a fixed
+// round robin.  PRUNED: the groups of the listed reached tile columns, and in
+// pass A the unreached tiles read as zeros; else every group of n_planes
+// planes.
+constexpr int kFourL = 128;
+
+__device__ __forceinline__ float2 four_twiddle(const float2* thi, const float2* tlo, uint32_t m, bool inv) {
+    float2 w = cmulf(thi[m >> 7], tlo[m & 127u]);
+    if (!inv) w.y = -w.y;
+    return w;
+}
+
+template <bool INV, bool PRUNED, bool PASS_B>
+__global__ void __launch_bounds__(256, 4)
+k_cols_four(float2* __restrict__ grids, const float2* __restrict__ t4, Occupancy occ, uint32_t n_planes) {
+    using Sh = Shape<7>;
+    constexpr int N = 16384, L = kFourL, COLS = 32, T = Sh::T;   // T = 8 threads per transform
+    constexpr int kStride = Sh::kArray + 1;   // odd: the 32 column arrays spread over the banks
+    __shared__ uint8_t s_live[N / 32];        // tile-row liveness of the group's tile column
+    __shared__ float2 s_thi[L], s_tlo[L];
+    extern __shared__ __align__(16) float2 fsm[];
+    float2* tw = fsm;
+    const int tid = threadIdx.x, c = tid % COLS, b = tid / COLS;
+    float2* buf = fsm + Sh::kTw + c * kStride;
+    load_tables<7>(t4, tw, tid, 256);
+    for (int i = tid; i < L; i += 256) {
+        s_thi[i] = __ldg(t4 + Sh::kTw + i);
+        s_tlo[i] = __ldg(t4 + Sh::kTw + L + i);
+    }
+    // groups of 32 columns: per listed tile column 2^gs of them
+    const uint32_t gs = PRUNED ? (uint32_t)occ.tshift - 5u : 0u;
+    const uint32_t n_groups = PRUNED ? (__ldg(occ.list) << gs) : n_planes * (uint32_t)(N / COLS);
+    const uint32_t total = n_groups * L;   // below 2^32: checked at launch
+    __syncthreads();
+    for (uint32_t item = blockIdx.x; item < total; item += gridDim.x) {
+        const uint32_t g = item / L, i1 = item % L;   // i1: n1 (pass A) or k2 (pass B)
+        uint32_t pl;
+        int x0, tcol = 0;
+        if (PRUNED) {
+            const uint32_t e = __ldg(occ.list + 2 + (g >> gs));
+            pl = e / (uint32_t)occ.NT;
+            tcol = (int)(e - pl * (uint32_t)occ.NT);
+            x0 = (tcol << occ.tshift) + (int)(g & ((1u << gs) - 1u)) * COLS;
+        } else {
+            pl = g / (uint32_t)(N / COLS);
+            x0 = (int)(g % (uint32_t)(N / COLS)) * COLS;
+        }
+        __syncthreads();   // the previous item has read buf and s_live
+        if (PRUNED && !PASS_B)
+            for (int ty = tid; ty < occ.NT; ty += 256)
+                s_live[ty] = (uint8_t)((occ.tile[((size_t)pl * occ.NT + ty) * occ.words + (tcol >> 5)] >>
+                                        (tcol & 31)) & 1u);
+        __syncthreads();
+        float2* col = grids + (size_t)pl * N * N + x0 + c;
+        float2 a[16], x[16];
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+            const int j = b + T * t2;                       // n2 (pass A) or n1 (pass B)
+            const int row = PASS_B ? L * (int)i1 + j : (int)i1 + L * j;
+            a[t2] = (!PRUNED || PASS_B || s_live[row >> occ.tshift]) ? __ldcs(col + (size_t)row * N)
+                                                                     : make_float2(0.f, 0.f);
+        }
+        transform<7, INV>(a, buf, b, tw, x);                // x[j] = output b + T j
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k = b + T * j;                        // k2 (pass A) or k1 (pass B)
+            if (PASS_B) {
+                __stcs(col + (size_t)(L * (int)i1 + k) * N, x[j]);
+            } else {
+                const float2 w = four_twiddle(s_thi, s_tlo, i1 * (uint32_t)k, INV);
+                __stcs(col + (size_t)((int)i1 + L * k) * N, cmulf(x[j], w));
+            }
         }
     }
 }
@@ -843,7 +935,10 @@ k_rows_phase_reduce_split(PhaseParams P, const float2* __restrict__ grids, const
     bool pf_single = true;
     const float2* pf_row = grids;
     auto load_row = [&](int r, float2 (&v)[16]) {
-        pf_row = grids + (size_t)r * NN + (size_t)(q + off) * N;
+        // mesh row m = q + off; after the four-step column pass it is stored at
+        // row 128 (m mod 128) + m / 128
+        const int m = q + off;
+        pf_row = grids + (size_t)r * NN + (size_t)(P.rows_four ? ((m & 127) << 7) + (m >> 7) : m) * N;
         pf_live = live_bits(r);
         pf_first = 0;
 #pragma unroll
@@ -1195,11 +1290,42 @@ __global__ void k_col_list(const uint8_t* __restrict__ col, int64_t n, uint32_t*
     if (on) list[2 + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
 }
 
+// The two four-step passes at N = 16384 (k_cols_four); t4: the plan's tables
+// of the 128-point transform and of W_N^m after the split row pass's tables.
+template <bool INV, bool PRUNED>
+cudaError_t columns_four(float2* grids, int64_t n_planes, const float2* t4, const Occupancy& occ,
+                         cudaStream_t st) {
+    using Sh = Shape<7>;
+    const size_t smem = (size_t)(Sh::kTw + 32 * (Sh::kArray + 1)) * sizeof(float2);
+    auto fa = k_cols_four<INV, PRUNED, false>;
+    auto fb = k_cols_four<INV, PRUNED, true>;
+    cudaError_t e = cudaFuncSetAttribute(fa, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(fb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fa, 256, smem)) != cudaSuccess) return e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const unsigned blocks = (unsigned)(per_sm * sms);
+    fa<<<blocks, 256, smem, st>>>(grids, t4, occ, (uint32_t)n_planes);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    fb<<<blocks, 256, smem, st>>>(grids, t4, occ, (uint32_t)n_planes);
+    return cudaGetLastError();
+}
+
 template <int LOG2N, bool INV>
 cudaError_t columns_one(float2* grids, int64_t n_planes, const float2* twid, const Occupancy& occ,
-                        cudaStream_t st) {
+                        cudaStream_t st, bool fourstep = false) {
     using Sh = Shape<LOG2N>;
     constexpr int cols = kCols<LOG2N>;
+    if (LOG2N == 14 && fourstep) {
+        // every (group, n1) and (group, k2) item index below 2^32
+        if ((uint64_t)n_planes * 16384u * kFourL / 32u >= (1ull << 32)) return cudaErrorInvalidValue;
+        const float2* t4 = twid + Shape<14>::kTw + Shape<12>::kTw + 4 * 256 + 256;
+        return occ.list != nullptr && occ.tile != nullptr ? columns_four<INV, true>(grids, n_planes, t4, occ, st)
+                                                          : columns_four<INV, false>(grids, n_planes, t4, occ, st);
+    }
     const size_t smem = (size_t)(Sh::kTw + cols * (Sh::kArray + 16 / cols)) * sizeof(float2);
     if (occ.list != nullptr && occ.tile != nullptr) {
         // persistent CTAs over the listed tile columns; the work counter
@@ -1342,7 +1468,7 @@ void fft_twiddles(int N, std::vector<float2>& out) {
     // N < 16384: the stage tables, then e^(2 pi i j / 256), j < 256.
     // N = 16384: the 4096-point tables of the split fused row pass follow,
     // then its split twiddles [r T + b] = e^(+2 pi i r b / N), r < 4, b < T = 256,
-    // then e^(2 pi i j / 256), j < 256
+    // then e^(2 pi i j / 256), j < 256, then the four-step column pass's tables
     out.clear();
     append_twiddles(N, out);
     if (log2_exact(N) < 14) {
@@ -1364,6 +1490,17 @@ void fft_twiddles(int N, std::vector<float2>& out) {
         // and the 256 phasors e^(2 pi i j / 256) of its block-end phase screen
         for (int j = 0; j < 256; ++j) {
             const double a = two_pi * (double)j / 256.0;
+            out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+        // the four-step column pass: the 128-point tables, e^(2 pi i mh / 128)
+        // and e^(2 pi i ml / N), mh, ml < 128
+        append_twiddles(kFourL, out);
+        for (int j = 0; j < kFourL; ++j) {
+            const double a = two_pi * (double)j / kFourL;
+            out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
+        }
+        for (int j = 0; j < kFourL; ++j) {
+            const double a = two_pi * (double)j / N;
             out.push_back(make_float2((float)std::cos(a), (float)std::sin(a)));
         }
     }
@@ -1397,13 +1534,13 @@ cudaError_t launch_fft2d(float2* grids, int64_t n_planes, int N, bool inverse, c
 }
 
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               const Occupancy& occ, cudaStream_t st, int* launches) {
+                               const Occupancy& occ, cudaStream_t st, int* launches, bool fourstep) {
     if (n_planes <= 0) return cudaSuccess;
     cudaError_t e = cudaErrorInvalidValue;
 #define RICK_FFT_CASE(LG)                                                                   \
     case LG:                                                                                \
-        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, occ, st)                 \
-                    : columns_one<LG, false>(grids, n_planes, twid, occ, st);               \
+        e = inverse ? columns_one<LG, true>(grids, n_planes, twid, occ, st, fourstep)       \
+                    : columns_one<LG, false>(grids, n_planes, twid, occ, st, fourstep);     \
         break;
     switch (log2_exact(N)) {
         RICK_FFT_CASE(8)
@@ -1416,7 +1553,7 @@ cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inve
         default: break;
     }
 #undef RICK_FFT_CASE
-    if (e == cudaSuccess) *launches += (int)((n_planes + 65534) / 65535);
+    if (e == cudaSuccess) *launches += fourstep && N == 16384 ? 2 : (int)((n_planes + 65534) / 65535);
     return e;
 }
 

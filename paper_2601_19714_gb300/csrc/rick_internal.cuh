@@ -159,6 +159,7 @@ struct PhaseParams {
     double dl;            // fov / Ni
     double w_first;       // w of plane plane_begin (plane centre)
     int k_first;          // plane_begin (stored plane index)
+    int rows_four;        // N = 16384: the planes' rows are in the four-step order
     double dw;            // plane spacing (0 if Nw == 1)
     int precision;
     // w-kernel (w_support >= 2): every pixel is also divided by the kernel's
@@ -288,8 +289,12 @@ cudaError_t launch_occupancy(const uint32_t* offsets, int c0, int nc, int k0, in
 // Pass 1 alone (the inverse DFT down every column), in place; with occ, the
 // unreached column tiles are skipped and the unreached tiles of the others
 // read as zeros.
+// fourstep (N = 16384 only): the two four-step passes, which leave the rows
+// of every plane in the four-step order (mesh row m at row 128 (m mod 128) +
+// m / 128), the order the fused row pass reads with PhaseParams::rows_four.
 cudaError_t launch_fft_columns(float2* grids, int64_t n_planes, int N, bool inverse, const float2* twid,
-                               const Occupancy& occ, cudaStream_t stream, int* launches);
+                               const Occupancy& occ, cudaStream_t stream, int* launches,
+                               bool fourstep = false);
 // Pass 2 fused with the phase screen and reduction: grids must hold the
 // column-transformed planes [nc][nk][N][N]; image_real [nc][N][N] (+=).
 // With occ, unreached planes are skipped and unreached tile columns read as
