@@ -133,7 +133,7 @@ GRID_COUNTERS = {
 # DRAM bytes per launch of the fused split row pass on the default line: the
 # mean over the 48 launches of one step (ncu, 1 pass each; the command is in
 # the profile named in the line).
-ROWS_TRAFFIC_PER_LAUNCH = 15.187e9
+ROWS_TRAFFIC_PER_LAUNCH = 15.289e9
 
 
 def gridder_ceilings(n_grid, ms, key):
@@ -965,7 +965,7 @@ def run_large_line(args):
             "traffic_unit": "bytes per launch",
             "traffic_algorithmic": stage_bytes["rows_phase"] / rows_launches,
             "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of every launch of one timed "
-                            "step (12.36 GB read, 2.83 GB written per launch on average); above the "
+                            "step (12.46 GB read, 2.83 GB written per launch on average); above the "
                             "algorithmic bytes by the per-pixel phase and taper tables (12 B per image "
                             "pixel, read at the first plane and at each Horner block end) -- "
                             "profiles/kernels_meerkat_large_small_16384sq_4w_1ch.md"}
