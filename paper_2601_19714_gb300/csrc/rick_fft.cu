@@ -37,8 +37,11 @@
 //   X[4k + r] = sum_{n<M} y_r[n] W_M^(n k),
 //   y_r[n] = W_N^(r n) sum_{t<4} x[n + t M] W_4^(r t),
 // so CTA r transforms y_r with the 4096-point transform (two CTAs per SM) and
-// owns the pixels 4k + r.  The column pass and the plain row pass take one
-// 16384-point transform per CTA (1024 threads).
+// owns the pixels 4k + r.  The plain column and row passes take one
+// 16384-point transform per CTA (1024 threads); the imaging column pass (tiles
+// of at least 32) is instead two four-step passes of 128-point transforms over
+// groups of 32 columns (k_cols_four), which leave the rows in the four-step
+// order that the split row pass reads.
 //
 // Pruning: planes made by the library's gridder are zero in every tile that no
 // visibility reached (or, when the gridder skipped the zero fill, unwritten
