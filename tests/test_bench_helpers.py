@@ -67,3 +67,17 @@ def test_large_blocks_cover_each_ranks_channels_once():
             for c0, c1 in blk:
                 seen.extend(range(c0, c1))
         assert seen == list(range(128 * world))
+
+
+def test_gridder_ceilings_are_counts_times_rate_over_peaks():
+    """The gridder's ceiling fractions: per-visibility counts of the ncu
+    capture times the visibilities gridded per second, over one shared-memory
+    wavefront per cycle per SM and four warp instructions per cycle per SM at
+    2.07 GHz (152 SMs); the binding ceiling is the larger fraction."""
+    c = bench.GRID_COUNTERS["large"]
+    out = bench.gridder_ceilings(2.0e9, 1000.0, "large")   # 2 G visibilities in one second
+    assert out["smem_wavefronts"]["achieved_per_s"] == 2.0e9 * c["smem_wavefronts"]
+    assert abs(out["smem_wavefronts"]["frac"] - 2.0e9 * c["smem_wavefronts"] / (152 * 2.07e9)) < 1e-12
+    assert abs(out["issue"]["frac"] - 2.0e9 * c["warp_instructions"] / (152 * 4 * 2.07e9)) < 1e-12
+    assert out["binding"] == max(("smem_wavefronts", "issue"), key=lambda k: out[k]["frac"])
+    assert out["source"].startswith("profiles/") and out["source"].endswith(".md")
